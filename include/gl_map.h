@@ -1,0 +1,263 @@
+/*
+ * gl_map.h -- C ABI of the GB300 optimiser of the Gaussian-LIC photo-realistic
+ * map (arXiv 2404.06926, Sec. III-A and III-C).
+ *
+ * One optimisation step for one keyframe view is: project every Gaussian
+ * (Eq. 1-3) and colour it from its SH; bin it into screen tiles with
+ * (tile | depth) keys and a device radix sort; composite each tile front to
+ * back (Eq. 4-7); apply the view's 3x4 exposure affine; score the L1 + D-SSIM
+ * loss (Eq. 9); back-propagate to every Gaussian attribute (and to the camera
+ * pose and the exposure); and apply Adam, optionally only to the Gaussians
+ * visible in the view (sparse Adam, Sec. III-D 2).
+ *
+ * Conventions shared by every call:
+ *   - Every entry point returns gl_status; GL_OK is 0.  Nothing aborts.  On
+ *     failure gl_last_error() returns a thread-local message.
+ *   - Poses are world->camera: x_c = R_cw x_w + t_cw (Eq. 2), R_cw row-major.
+ *   - Intrinsics are a pinhole (Eq. 2's pi_c) on undistorted images: pixel
+ *     (u, v) has its centre at integer coordinates (u, v).
+ *   - Images are H x W x 3 float RGB (row-major, channel last).
+ *   - Quaternions are (w, x, y, z) and need not be unit length.
+ *   - Pointers documented "device" must be CUDA device memory of the current
+ *     device; "host or device" pointers are classified with
+ *     cudaPointerGetAttributes.  The caller owns every buffer it passes; the
+ *     library copies whatever it keeps beyond the call.
+ *   - Work is enqueued on the stream given at creation; calls return once the
+ *     work is enqueued unless they copy results to host memory, in which case
+ *     they synchronise that stream first.
+ *   - An object (gl_map, gl_ctx) is used by one host thread at a time.
+ */
+#ifndef GL_MAP_H
+#define GL_MAP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GL_API __attribute__((visibility("default")))
+#else
+#define GL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GL_OK = 0,
+    GL_ERR_INVALID = 1,   /* bad argument: NaN/Inf pose, non-positive focal, bad size */
+    GL_ERR_OOM = 2,       /* device allocation failed                                 */
+    GL_ERR_CUDA = 3,      /* a CUDA call failed (message in gl_last_error)            */
+    GL_ERR_CAPACITY = 4,  /* more than 2^32-1 (Gaussian, tile) instances in one view  */
+    GL_ERR_TIMEOUT = 5,   /* a bounded device wait gave up                            */
+    GL_ERR_BUSY = 6,      /* the serving queue is full                                */
+    GL_ERR_NOT_FOUND = 7  /* unknown keyframe id                                      */
+} gl_status;
+
+/* Pinhole intrinsics pi_c (Eq. 2). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gl_intrinsics;
+
+/* Camera pose {R_cw, t_cw}, world -> camera (Eq. 2). */
+typedef struct {
+    float R_cw[9];
+    float t_cw[3];
+} gl_pose;
+
+/* A keyframe as the mapping module receives it (Sec. III-C): an id, a pose,
+ * intrinsics and an undistorted image.  `image` is H*W*3 float RGB in [0,1],
+ * host or device; it may be NULL in gl_optimize_step when the id was
+ * registered with gl_map_add_keyframe, whose stored copy is then used. */
+typedef struct {
+    int64_t id;
+    gl_pose pose;
+    gl_intrinsics K;
+    const float* image;
+} gl_keyframe;
+
+/* Hyper-parameters.  The paper's values (Sec. IV-A): lambda = 0.2,
+ * tau = 0.99, o_a = 0.1, o_b = 0.7, R = 1e4, N_s = 1e5; learning rates "as
+ * vanilla 3DGS, not decayed".  gl_config_default() fills every field. */
+typedef struct {
+    int32_t sh_degree;      /* 0..3 (the paper uses 3)                      */
+    int32_t tile_size;      /* 8, 16 or 32                                  */
+    int32_t sparse_adam;    /* 1: Adam touches only Gaussians visible in the
+                               step's views; 0: all Gaussians ("w/o acc")  */
+    int32_t reserved0;
+    uint64_t seed;          /* sky sampling (SplitMix64 counter generator)  */
+    float lambda_dssim, tau, opacity_fg, opacity_sky, sky_radius;
+    int32_t reserved1;
+    int64_t n_sky;          /* sky Gaussians created by gl_map_create       */
+    float lr_pos, lr_sh_dc, lr_sh_rest, lr_opacity, lr_scale, lr_rot, lr_exposure;
+    float adam_b1, adam_b2, adam_eps;
+    int64_t capacity_hint;  /* initial Gaussian capacity                    */
+} gl_config;
+
+/* Gaussian parameters in caller memory, one array per attribute, row-major:
+ * means n*3, log_scales n*3, quats n*4 (w,x,y,z), logits n (opacity =
+ * sigmoid(logit)), sh n*K*3 with K = (sh_degree+1)^2, coefficient-major and
+ * channel-minor (Sec. III-A: position, scale, rotation, opacity, SH). */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t reserved;
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* logits;
+    float* sh;
+} gl_gaussians;
+
+/* ---------------------------------------------------------------------- */
+/* Library                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+GL_API const char* gl_last_error(void);
+
+/* ABI version of this header (major * 100 + minor). */
+GL_API int32_t gl_version(void);
+
+/* Fill `cfg` with the paper's values and the proposed readings of the
+ * constants it leaves open (tile 16, SH degree 3, sparse Adam on). */
+GL_API gl_status gl_config_default(gl_config* cfg);
+
+/* ---------------------------------------------------------------------- */
+/* Map API (Sec. III-C)                                                    */
+/* ---------------------------------------------------------------------- */
+typedef struct gl_map gl_map;
+
+/* Create a map on the current device; `cuda_stream` (cudaStream_t, may be
+ * NULL for the legacy default stream) orders all of its work.  Creates
+ * cfg->n_sky sky Gaussians (Sec. III-C 1): points uniform by area on the
+ * upper hemisphere (z >= 0) of radius cfg->sky_radius about the origin,
+ * white DC colour, opacity o_b, isotropic scale = distance to the nearest
+ * other sky point.  The map owns all device state and releases it in
+ * gl_map_destroy.  Errors: GL_ERR_INVALID (bad config), GL_ERR_OOM. */
+GL_API gl_status gl_map_create(const gl_config* cfg, void* cuda_stream, gl_map** out);
+
+/* Release every device allocation of the map (after its stream drains). */
+GL_API gl_status gl_map_destroy(gl_map* map);
+
+/* Number of Gaussians in the map. */
+GL_API gl_status gl_map_size(gl_map* map, int64_t* n_out);
+
+/* Map initialisation and expansion (Sec. III-C 1-2, Eq. 8).  xyz and rgb
+ * are n*3 floats (host or device) of coloured LiDAR / visual points in the
+ * world frame.  Each kept point becomes a Gaussian centred on it with SH DC
+ * from its colour, higher SH zero, opacity o_a, identity rotation and
+ * isotropic scale d/f (d = depth in `pose`, f = K->fx).  Points at depth
+ * <= 0.2 m are never kept.  use_mask = 0 keeps every other point (the first
+ * frame); use_mask = 1 renders the opacity map O (Eq. 7) from (pose, K) and
+ * keeps a point only if it lands inside the image on a pixel (nearest pixel
+ * centre) with O < cfg->tau.  `kind` (0 LiDAR, 1 visual) is recorded per
+ * Gaussian.  New Gaussians start with zero Adam moments.  *n_added (host)
+ * receives the number kept.  Errors: GL_ERR_INVALID, GL_ERR_OOM. */
+GL_API gl_status gl_map_add_points(gl_map* map, const float* xyz, const float* rgb, int64_t n,
+                            int32_t kind, const gl_pose* pose, const gl_intrinsics* K,
+                            int32_t use_mask, int64_t* n_added);
+
+/* Register a keyframe: copies its image to device memory owned by the map
+ * and creates its exposure E = [I | 0] (Sec. III-C 3).  Re-registering an
+ * id replaces its image and pose and keeps its exposure. */
+GL_API gl_status gl_map_add_keyframe(gl_map* map, const gl_keyframe* kf);
+
+/* Render the map from (pose, K) (Eq. 5-7).  E34 (host, 12 floats, row-major
+ * [A | b]) applies C_hat = A C + b to the colour; NULL means identity.
+ * out_rgb (H*W*3), out_depth (H*W, nullable) and out_opacity (H*W,
+ * nullable) are host or device. */
+GL_API gl_status gl_render(gl_map* map, const gl_pose* pose, const gl_intrinsics* K, const float* E34,
+                    float* out_rgb, float* out_depth, float* out_opacity);
+
+/* One optimisation step (Sec. III-C 3, Eq. 9).  n_views = 1 is the paper's
+ * single-view step: forward, loss with the view's exposure, backward, Adam
+ * on the Gaussians (sparse or dense per the config) and on the view's
+ * exposure.  n_views > 1 renders and back-propagates all views as one
+ * window and takes one Adam step on the mean of their losses.  out_loss
+ * (host, nullable) receives the mean loss.  Errors: GL_ERR_INVALID,
+ * GL_ERR_NOT_FOUND (image NULL and id not registered), GL_ERR_CAPACITY. */
+GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t n_views,
+                           float* out_loss);
+
+/* Copy the Gaussians (out->n must be >= the map size; pointers host or
+ * device; out->sh_degree must equal the map's).  *n_out gets the size. */
+GL_API gl_status gl_map_get_params(gl_map* map, gl_gaussians* out, int64_t* n_out);
+
+/* Replace all Gaussians with `in` (host or device) and zero Adam state. */
+GL_API gl_status gl_map_set_params(gl_map* map, const gl_gaussians* in);
+
+/* Copy Adam's first (which = 1) or second (which = 2) moments. */
+GL_API gl_status gl_map_get_moments(gl_map* map, int32_t which, gl_gaussians* out);
+
+/* Exposure E (12 floats, host) of keyframe `id`. */
+GL_API gl_status gl_map_get_exposure(gl_map* map, int64_t id, float* E34_out);
+
+/* ---------------------------------------------------------------------- */
+/* Stateless differentiable API (one view), for autograd wrappers and     */
+/* tests.  A gl_ctx owns the scratch of one forward/backward pair.         */
+/* ---------------------------------------------------------------------- */
+typedef struct gl_ctx gl_ctx;
+
+GL_API gl_status gl_ctx_create(void* cuda_stream, gl_ctx** out);
+GL_API gl_status gl_ctx_destroy(gl_ctx* ctx);
+
+/* Forward (Eq. 1-7) of the Gaussians `g` (device arrays) seen from
+ * (pose, K) with square tiles of side tile_size (8, 16 or 32).  Writes the
+ * device images out_rgb (H*W*3), out_depth (H*W, nullable) and
+ * out_opacity (H*W, nullable), and keeps the per-view state (records,
+ * sorted instances, per-pixel final transmittance and contributor count)
+ * in `ctx` for gl_rasterize_backward.  Errors: GL_ERR_INVALID,
+ * GL_ERR_CAPACITY, GL_ERR_OOM. */
+GL_API gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, const gl_pose* pose,
+                               const gl_intrinsics* K, int32_t tile_size,
+                               float* out_rgb, float* out_depth, float* out_opacity);
+
+/* Backward of the last gl_rasterize_forward on `ctx` (same `g`, unchanged).
+ * dL_drgb (H*W*3, device) is required; dL_ddepth and dL_dopacity (H*W,
+ * device) may be NULL.  Per-pixel transmittance is recomputed from the
+ * stored final value, not stored per pair.  Writes gradients for every
+ * attribute into `grad` (device arrays shaped like `g`; Gaussians outside
+ * the view get 0) and, if grad_pose6 (device, 6 floats) is not NULL, the
+ * gradient w.r.t. a left twist xi = (rho, phi) of the pose,
+ * T_cw <- exp(xi^) T_cw, at xi = 0. */
+GL_API gl_status gl_rasterize_backward(gl_ctx* ctx, const gl_gaussians* g, const float* dL_drgb,
+                                const float* dL_ddepth, const float* dL_dopacity,
+                                gl_gaussians* grad, float* grad_pose6);
+
+/* Photometric loss, Eq. 9: L = (1-lambda) mean|E[C] - C_bar| + lambda
+ * (1 - mean SSIM(E[C], C_bar)), SSIM with an 11x11 Gaussian window of
+ * sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels
+ * and channels.  rgb, target (H*W*3), E34 (12) are device.  Writes the
+ * device scalars loss_out (1 float), the device gradients dL_drgb (H*W*3)
+ * and dL_dE (12). */
+GL_API gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const float* target, const float* E34,
+                              int32_t width, int32_t height, float lambda_dssim,
+                              float* loss_out, float* dL_drgb, float* dL_dE);
+
+/* ---------------------------------------------------------------------- */
+/* Introspection of the last forward on a ctx (tests; not a user API).     */
+/* All outputs are device arrays; n = number of Gaussians of the forward.  */
+/* ---------------------------------------------------------------------- */
+
+/* radius (n int32), rect (n*4 int32: x0, y0, x1, y1 tiles, half open),
+ * mean2d (n*2), conic (n*3: A, B, C of Sigma'^-1), opacity (n), rgb (n*3),
+ * depth (n).  Any pointer may be NULL. */
+GL_API gl_status gl_ctx_get_preprocess(gl_ctx* ctx, int32_t* radius, int32_t* rect, float* mean2d,
+                                float* conic, float* opacity, float* rgb, float* depth);
+
+/* Number of (Gaussian, tile) instances of the last forward (host out). */
+GL_API gl_status gl_ctx_num_instances(gl_ctx* ctx, int64_t* I_out);
+
+/* Sorted instances: keys (I u64, tile << 32 | float bits of depth), vals
+ * (I u32 Gaussian index) and ranges (num_tiles * 2 u32, [start, end)). */
+GL_API gl_status gl_ctx_get_instances(gl_ctx* ctx, uint64_t* keys, uint32_t* vals, uint32_t* ranges);
+
+/* Per-pixel final transmittance (H*W float) and contributor count (H*W
+ * u32: 1 + position, in the tile's list, of the last Gaussian blended). */
+GL_API gl_status gl_ctx_get_pixel_state(gl_ctx* ctx, float* T_final, uint32_t* n_contrib);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GL_MAP_H */

@@ -1,0 +1,494 @@
+// gl_binning.cu -- projection of every Gaussian (Eq. 1-3 and the SH colour)
+// and tile binning: (tile | depth) ordering of the (Gaussian, tile) instances
+// with a device LSD radix sort, then per-tile ranges (Sec. III-A, "sorting the
+// Gaussians in depth order").
+//
+// Ordering strategy.  The instances must end up sorted by the 64-bit key
+// (tile << 32 | float bits of depth), ties kept in emission order.  Instead of
+// radix-sorting I 64-bit keys over 32 + log2(#tiles) bits, the Gaussians (N of
+// them, N << I) are radix-sorted by depth first, instances are emitted in that
+// order, and a stable radix sort on the tile id alone finishes the job.  The
+// two give the same permutation: within a tile, stable order is depth order
+// with ties broken by Gaussian index, which is the emission order of the
+// single-key sort.
+#include "gl_internal.h"
+
+#include <algorithm>
+
+namespace gl {
+
+namespace {
+
+constexpr int kPreThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
+constexpr int kSortMaxBlocks = 4 * 152;                // 4 CTAs per SM on 152 SMs
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kPreThreads * kScanItems;   // 1024 Gaussians per scan block
+
+// Block-wide exclusive scan (NT threads); returns the exclusive prefix and
+// writes the block total to *total.  `sm` needs NT/32 + 1 entries.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* sm, T* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    T incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sm[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        T s = (lane < NW) ? sm[lane] : T(0);
+        T si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(kFull, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < NW) sm[lane] = si - s;
+        if (lane == NW - 1) sm[NW] = si;
+    }
+    __syncthreads();
+    T res = sm[w] + incl - x;
+    *total = sm[NW];
+    __syncthreads();
+    return res;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ T block_sum(T x, T* sm)
+{
+    T tot;
+    block_exclusive_scan<T, NT>(x, sm, &tot);
+    return tot;
+}
+
+// ---------------------------------------------------------------------------
+// K1: projection, colour and tile rectangle of every Gaussian.
+// ---------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads)
+k_preprocess(GParams p, Cam cam, int Ts, int TX, int TY, float4* __restrict__ rec0,
+             float4* __restrict__ rec1, float4* __restrict__ rec2, int* __restrict__ radius,
+             int4* __restrict__ rect, uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
+             uint32_t* __restrict__ gidx)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= p.n) return;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float mu[3] = {p.means[3 * g], p.means[3 * g + 1], p.means[3 * g + 2]};
+    float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
+    const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
+    float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    gidx[g] = (uint32_t)g;
+    Decision D;
+    if (!decide(mu, ls, q, cam, Ts, TX, TY, D)) {
+        radius[g] = 0;
+        touched[g] = 0;
+        dkey[g] = 0xffffffffu;
+        rect[g] = make_int4(0, 0, 0, 0);
+        return;
+    }
+    const float o = 1.0f / (1.0f + __expf(-p.logits[g]));
+    const float id = 1.0f / D.det;
+    // view direction from the camera centre c_w = -R^T t to the mean
+    const float* R = cam.R;
+    float cw0 = -(R[0] * cam.t[0] + R[3] * cam.t[1] + R[6] * cam.t[2]);
+    float cw1 = -(R[1] * cam.t[0] + R[4] * cam.t[1] + R[7] * cam.t[2]);
+    float cw2 = -(R[2] * cam.t[0] + R[5] * cam.t[1] + R[8] * cam.t[2]);
+    float dx = mu[0] - cw0, dy = mu[1] - cw1, dz = mu[2] - cw2;
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_eval<DEG>(dx * inv, dy * inv, dz * inv, Y);
+    float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f;
+    const float* sh = p.sh + (size_t)g * K * 3;
+    if ((K * 3) % 4 == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(sh);
+        float buf[K * 3];
+#pragma unroll
+        for (int i = 0; i < K * 3 / 4; i++) {
+            float4 t = s4[i];
+            buf[4 * i] = t.x; buf[4 * i + 1] = t.y; buf[4 * i + 2] = t.z; buf[4 * i + 3] = t.w;
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            c0 += Y[k] * buf[3 * k]; c1 += Y[k] * buf[3 * k + 1]; c2 += Y[k] * buf[3 * k + 2];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            c0 += Y[k] * sh[3 * k]; c1 += Y[k] * sh[3 * k + 1]; c2 += Y[k] * sh[3 * k + 2];
+        }
+    }
+    rec0[g] = make_float4(D.u, D.v, D.z, o);
+    rec1[g] = make_float4(D.c * id, -D.b * id, D.a * id, 0.0f);
+    rec2[g] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
+    radius[g] = D.r;
+    rect[g] = make_int4(D.x0, D.y0, D.x1, D.y1);
+    touched[g] = (uint32_t)((D.x1 - D.x0) * (D.y1 - D.y0));
+    dkey[g] = __float_as_uint(D.z);
+}
+
+__global__ void k_set_u64(uint64_t* p, uint64_t v0, uint64_t v1)
+{
+    p[0] = v0;
+    p[1] = v1;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (u32 key, u32 value), 8-bit digits, stable.
+// Each pass: per-block digit histograms over contiguous chunks, one
+// digit-major exclusive scan, then a stable scatter.  n is read on device.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sort_chunk(uint64_t n, int nblocks, uint64_t& begin, uint64_t& end)
+{
+    uint64_t chunk = ((n + nblocks - 1) / nblocks + kSortTile - 1) / kSortTile * kSortTile;
+    begin = min(n, (uint64_t)blockIdx.x * chunk);
+    end = min(n, begin + chunk);
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int shift, int nblocks,
+            uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    h[tid] = 0;
+    __syncthreads();
+    uint64_t begin, end;
+    sort_chunk(*n_dev, nblocks, begin, end);
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint64_t base = begin; base < end; base += kSortThreads) {
+        uint64_t idx = base + tid;
+        int d = idx < end ? (int)((kin[idx] >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(kFull, d);
+        if (d < 256 && (peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[tid * nblocks + blockIdx.x] = h[tid];
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int total)
+{
+    __shared__ uint32_t sm[33];
+    const int per = (total + 1023) / 1024;
+    const int b = min(total, (int)threadIdx.x * per), e = min(total, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; i++) s += hist[i];
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<uint32_t, 1024>(s, sm, &tot);
+    for (int i = b; i < e; i++) {
+        uint32_t x = hist[i];
+        hist[i] = ex;
+        ex += x;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint64_t* n_dev,
+               int shift, int nblocks, const uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t wcnt[kSortThreads / 32][256];
+    __shared__ uint32_t doff[256];
+    __shared__ uint32_t tcnt[256];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    uint64_t begin, end;
+    sort_chunk(*n_dev, nblocks, begin, end);
+    doff[tid] = hist[tid * nblocks + blockIdx.x];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint64_t base = begin; base < end; base += kSortTile) {
+        for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+        __syncwarp();
+        uint32_t kk[kSortItems], vv[kSortItems], rk[kSortItems];
+        int dg[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            uint64_t idx = base + (uint64_t)w * (32 * kSortItems) + j * 32 + lane;
+            bool ok = idx < end;
+            kk[j] = ok ? kin[idx] : 0u;
+            vv[j] = ok ? vin[idx] : 0u;
+            dg[j] = ok ? (int)((kk[j] >> shift) & 255u) : 256;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const int d = dg[j];
+            const unsigned peers = __match_any_sync(kFull, d);
+            const uint32_t prev = (d < 256) ? wcnt[w][d] : 0u;
+            rk[j] = prev + __popc(peers & lt);
+            __syncwarp();
+            if (d < 256 && (peers & lt) == 0) wcnt[w][d] = prev + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < kSortThreads / 32; ww++) {
+                uint32_t c = wcnt[ww][tid];
+                wcnt[ww][tid] = run;
+                run += c;
+            }
+            tcnt[tid] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            if (dg[j] < 256) {
+                uint32_t pos = doff[dg[j]] + wcnt[w][dg[j]] + rk[j];
+                kout[pos] = kk[j];
+                vout[pos] = vv[j];
+            }
+        }
+        __syncthreads();
+        doff[tid] += tcnt[tid];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scan of instance counts in depth order and duplication of the instances.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPreThreads)
+k_scan_count(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched, int64_t n,
+             uint64_t* __restrict__ bsum)
+{
+    __shared__ uint64_t sm[kPreThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t j = base + k;
+        if (j < n) s += touched[sorted_g[j]];
+    }
+    uint64_t tot = block_sum<uint64_t, kPreThreads>(s, sm);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums; count[0] = I, count[1] = overflow flag.
+__global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint64_t cap,
+                                                   uint64_t* count)
+{
+    __shared__ uint64_t sm[33];
+    const int per = (nb + 1023) / 1024;
+    const int b = min(nb, (int)threadIdx.x * per), e = min(nb, b + per);
+    uint64_t s = 0;
+    for (int i = b; i < e; i++) s += bsum[i];
+    uint64_t tot;
+    uint64_t ex = block_exclusive_scan<uint64_t, 1024>(s, sm, &tot);
+    for (int i = b; i < e; i++) {
+        uint64_t x = bsum[i];
+        bsum[i] = ex;
+        ex += x;
+    }
+    if (threadIdx.x == 0) {
+        count[0] = tot;
+        count[1] = (tot > cap || tot > 0xffffffffull) ? 1ull : 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(kPreThreads)
+k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched,
+            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int64_t n, int TX,
+            uint64_t cap, uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile,
+            uint32_t* __restrict__ ival, uint32_t* __restrict__ iowner)
+{
+    __shared__ uint64_t sm[kPreThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    uint32_t gg[kScanItems], cc[kScanItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t j = base + k;
+        gg[k] = j < n ? sorted_g[j] : 0u;
+        cc[k] = j < n ? touched[gg[k]] : 0u;
+        s += cc[k];
+    }
+    uint64_t tot;
+    uint64_t off = bsum[blockIdx.x] + block_exclusive_scan<uint64_t, kPreThreads>(s, sm, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k >= n) break;
+        const uint32_t g = gg[k];
+        dup_off[g] = (uint32_t)off;
+        if (cc[k] && off + cc[k] <= cap) {
+            const int4 r = rect[g];
+            uint64_t d = off;
+            for (int ty = r.y; ty < r.w; ty++)
+                for (int tx = r.x; tx < r.z; tx++, d++) {
+                    itile[d] = (uint32_t)(ty * TX + tx);
+                    ival[d] = (uint32_t)d;
+                    iowner[d] = g;
+                }
+        }
+        off += cc[k];
+    }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ stile, const uint64_t* n_dev,
+                         uint32_t* __restrict__ ranges)
+{
+    const uint64_t I = *n_dev;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < I;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t t = stile[i];
+        if (i == 0 || stile[i - 1] != t) ranges[2 * t] = (uint32_t)i;
+        if (i == I - 1 || stile[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+    }
+}
+
+__global__ void k_export(const uint32_t* __restrict__ stile, const uint32_t* __restrict__ sinst,
+                         const uint32_t* __restrict__ owner, const float4* __restrict__ rec0, int64_t I,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = owner[sinst[i]];
+        if (keys) keys[i] = ((uint64_t)stile[i] << 32) | (uint64_t)__float_as_uint(rec0[g].z);
+        if (vals) vals[i] = g;
+    }
+}
+
+int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while ((int64_t(1) << b) < x) b++;
+    return b;
+}
+
+}  // namespace
+
+gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                         const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
+                         uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
+{
+    int nblocks = (int)std::min<int64_t>(kSortMaxBlocks, std::max<int64_t>(1, (n_max + kSortTile - 1) / kSortTile));
+    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * (size_t)nblocks));
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_sort_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_dev, shift, nblocks, hist.as<uint32_t>());
+        k_sort_scan<<<1, 1024, 0, s>>>(hist.as<uint32_t>(), 256 * nblocks);
+        k_sort_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, nblocks,
+                                                        hist.as<uint32_t>());
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    GL_CUDA_TRY(cudaGetLastError());
+    *out_k = ki;
+    *out_v = vi;
+    return GL_OK;
+}
+
+gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s)
+{
+    if (v.I == 0) return GL_OK;
+    int blocks = (int)std::min<int64_t>(4 * 152, (v.I + 255) / 256);
+    k_export<<<blocks, 256, 0, s>>>(v.sorted_tile, v.sorted_inst, v.iowner.as<uint32_t>(),
+                                    v.rec0.as<float4>(), v.I, keys, vals);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream_t s)
+{
+    const int64_t n = p.n;
+    v.n = n;
+    v.W = cam.W;
+    v.H = cam.H;
+    v.Ts = Ts;
+    v.TX = (cam.W + Ts - 1) / Ts;
+    v.TY = (cam.H + Ts - 1) / Ts;
+    v.ntiles = v.TX * v.TY;
+    v.cam = cam;
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    GL_TRY(v.rec0.reserve(16 * nn));
+    GL_TRY(v.rec1.reserve(16 * nn));
+    GL_TRY(v.rec2.reserve(16 * nn));
+    GL_TRY(v.radius.reserve(4 * nn));
+    GL_TRY(v.rect.reserve(16 * nn));
+    GL_TRY(v.touched.reserve(4 * nn));
+    GL_TRY(v.dkey.reserve(4 * nn));
+    GL_TRY(v.gidx.reserve(4 * nn));
+    GL_TRY(v.dkey2.reserve(4 * nn));
+    GL_TRY(v.gidx2.reserve(4 * nn));
+    GL_TRY(v.dup_off.reserve(4 * nn));
+    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+    GL_TRY(v.bsum.reserve(8 * (size_t)std::max(nb, 1)));
+    GL_TRY(v.ranges.reserve(8 * (size_t)v.ntiles));
+    GL_CUDA_TRY(cudaMemsetAsync(v.ranges.p, 0, 8 * (size_t)v.ntiles, s));
+
+    uint64_t* count = v.count.as<uint64_t>();
+    if (n == 0) {
+        v.I = 0;
+        k_set_u64<<<1, 1, 0, s>>>(count, 0, 0);
+        GL_CUDA_TRY(cudaGetLastError());
+        return GL_OK;
+    }
+    const int TX = v.TX, TY = v.TY;
+    dim3 grid((unsigned)((n + kPreThreads - 1) / kPreThreads));
+    switch (p.deg) {
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
+    }
+    GL_CUDA_TRY(cudaGetLastError());
+
+    // depth order of the Gaussians (culled ones carry key 0xffffffff and go last)
+    k_set_u64<<<1, 1, 0, s>>>(count + 2, (uint64_t)n, 0);
+    uint32_t *sk, *sv;
+    GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
+                          v.gidx2.as<uint32_t>(), count + 2, n, 32, v.hist, &sk, &sv, s));
+    v.sorted_g = sv;
+
+    // instance offsets in depth order
+    const uint64_t cap = v.itile.bytes / 4;
+    k_scan_count<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), n, v.bsum.as<uint64_t>());
+    k_scan_top<<<1, 1024, 0, s>>>(v.bsum.as<uint64_t>(), nb, cap, count);
+    GL_CUDA_TRY(cudaGetLastError());
+    GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, 16, cudaMemcpyDeviceToHost, s));
+    GL_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t I = v.h_count[0];
+    if (I > 0xffffffffull) {
+        set_error("more than 2^32-1 (Gaussian, tile) instances in one view");
+        return GL_ERR_CAPACITY;
+    }
+    v.I = (int64_t)I;
+    if (I > cap) {
+        size_t want = (size_t)(I + I / 4 + 1024);
+        GL_TRY(v.itile.reserve(4 * want));
+        GL_TRY(v.ival.reserve(4 * want));
+        GL_TRY(v.itile2.reserve(4 * want));
+        GL_TRY(v.ival2.reserve(4 * want));
+        GL_TRY(v.iowner.reserve(4 * want));
+        GL_TRY(v.igrad.reserve(40 * want));
+    }
+    const uint64_t cap2 = v.itile.bytes / 4;
+    k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
+                                           v.bsum.as<uint64_t>(), n, TX, cap2, v.dup_off.as<uint32_t>(),
+                                           v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.iowner.as<uint32_t>());
+    GL_CUDA_TRY(cudaGetLastError());
+    if (I == 0) {
+        v.sorted_tile = v.itile.as<uint32_t>();
+        v.sorted_inst = v.ival.as<uint32_t>();
+        return GL_OK;
+    }
+    // stable sort of the instances by tile id
+    const int tbits = std::max(1, ceil_log2(v.ntiles));
+    GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
+                          v.ival2.as<uint32_t>(), count, (int64_t)I, tbits, v.hist, &sk, &sv, s));
+    v.sorted_tile = sk;
+    v.sorted_inst = sv;
+    int rb = (int)std::min<uint64_t>(4 * 152, (I + 255) / 256);
+    k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+}  // namespace gl

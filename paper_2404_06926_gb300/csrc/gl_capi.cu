@@ -1,0 +1,734 @@
+// gl_capi.cu -- host implementation of the C ABI declared in include/gl_map.h:
+// argument validation, device-memory ownership, the keyframe store, and the
+// sequencing of the kernels of one optimisation step on the map's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gl_internal.h"
+
+struct gl_ctx {
+    gl::gl_ctx_impl impl;
+};
+
+namespace gl {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+gl_status DevBuf::reserve(size_t need)
+{
+    if (need <= bytes && p) return GL_OK;
+    if (p) {
+        cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    if (need == 0) need = 16;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        set_error(std::string("cudaMalloc(") + std::to_string(need) + "): " + cudaGetErrorString(e));
+        return GL_ERR_OOM;
+    }
+    bytes = need;
+    return GL_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+gl_status View::init()
+{
+    GL_TRY(count.reserve(64));
+    if (!h_count) GL_CUDA_TRY(cudaMallocHost(&h_count, 64));
+    return GL_OK;
+}
+
+void View::release()
+{
+    DevBuf* all[] = {&rec0, &rec1, &rec2, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
+                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &igrad,
+                     &hist, &ranges, &Tfin, &ncon, &rgb, &depth, &opac};
+    for (DevBuf* b : all) b->release();
+    if (h_count) cudaFreeHost(h_count);
+    h_count = nullptr;
+}
+
+namespace {
+
+bool finite_all(const float* x, int n)
+{
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+gl_status make_cam(const gl_pose* pose, const gl_intrinsics* K, Cam& cam)
+{
+    if (!pose || !K) { set_error("pose and intrinsics are required"); return GL_ERR_INVALID; }
+    if (!finite_all(pose->R_cw, 9) || !finite_all(pose->t_cw, 3)) {
+        set_error("pose contains NaN or Inf");
+        return GL_ERR_INVALID;
+    }
+    if (!(K->fx > 0.f) || !(K->fy > 0.f) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
+        !std::isfinite(K->cx) || !std::isfinite(K->cy)) {
+        set_error("intrinsics: focal lengths must be positive and finite");
+        return GL_ERR_INVALID;
+    }
+    if (K->width <= 0 || K->height <= 0 || K->width > 16384 || K->height > 16384) {
+        set_error("image size must be in 1..16384");
+        return GL_ERR_INVALID;
+    }
+    std::memcpy(cam.R, pose->R_cw, sizeof(cam.R));
+    std::memcpy(cam.t, pose->t_cw, sizeof(cam.t));
+    cam.fx = K->fx; cam.fy = K->fy; cam.cx = K->cx; cam.cy = K->cy;
+    cam.W = K->width; cam.H = K->height;
+    return GL_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+gl_status check_tile(int t)
+{
+    if (t != 8 && t != 16 && t != 32) { set_error("tile_size must be 8, 16 or 32"); return GL_ERR_INVALID; }
+    return GL_OK;
+}
+
+gl_status check_gauss(const gl_gaussians* g, bool need_ptrs)
+{
+    if (!g) { set_error("null gaussians"); return GL_ERR_INVALID; }
+    if (g->n < 0 || g->n > (int64_t)0x7fffffff) { set_error("gaussian count out of range"); return GL_ERR_INVALID; }
+    if (g->sh_degree < 0 || g->sh_degree > 3) { set_error("sh_degree must be 0..3"); return GL_ERR_INVALID; }
+    if (need_ptrs && g->n > 0 &&
+        (!g->means || !g->log_scales || !g->quats || !g->logits || !g->sh)) {
+        set_error("null parameter array");
+        return GL_ERR_INVALID;
+    }
+    if (g->quats && (reinterpret_cast<uintptr_t>(g->quats) & 15u)) {
+        set_error("quats must be 16-byte aligned");
+        return GL_ERR_INVALID;
+    }
+    return GL_OK;
+}
+
+GParams params_of(const gl_gaussians* g)
+{
+    GParams p;
+    p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->logits;
+    p.sh = g->sh; p.n = g->n; p.deg = g->sh_degree; p.K = (g->sh_degree + 1) * (g->sh_degree + 1);
+    return p;
+}
+
+GMut mut_of(const gl_gaussians* g)
+{
+    GMut m;
+    m.means = g->means; m.log_scales = g->log_scales; m.quats = g->quats; m.logits = g->logits; m.sh = g->sh;
+    return m;
+}
+
+}  // namespace
+}  // namespace gl
+
+using namespace gl;
+
+// ===========================================================================
+// Library
+// ===========================================================================
+extern "C" const char* gl_last_error(void) { return g_err.c_str(); }
+
+extern "C" int32_t gl_version(void) { return 100; }
+
+extern "C" gl_status gl_config_default(gl_config* c)
+{
+    if (!c) return GL_ERR_INVALID;
+    std::memset(c, 0, sizeof(*c));
+    c->sh_degree = 3;
+    c->tile_size = 16;
+    c->sparse_adam = 1;
+    c->seed = 0x5eedULL;
+    c->lambda_dssim = 0.2f;    // Sec. IV-A
+    c->tau = 0.99f;            // Sec. IV-A
+    c->opacity_fg = 0.1f;      // o_a
+    c->opacity_sky = 0.7f;     // o_b
+    c->sky_radius = 1.0e4f;    // R
+    c->n_sky = 100000;         // N_s
+    c->lr_pos = 1.6e-4f;       // 3DGS learning rates, not decayed
+    c->lr_sh_dc = 2.5e-3f;
+    c->lr_sh_rest = 2.5e-3f / 20.0f;
+    c->lr_opacity = 0.05f;
+    c->lr_scale = 5e-3f;
+    c->lr_rot = 1e-3f;
+    c->lr_exposure = 1e-3f;
+    c->adam_b1 = 0.9f;
+    c->adam_b2 = 0.999f;
+    c->adam_eps = 1e-15f;
+    c->capacity_hint = 1 << 20;
+    return GL_OK;
+}
+
+// ===========================================================================
+// Stateless differentiable API
+// ===========================================================================
+extern "C" gl_status gl_ctx_create(void* stream, gl_ctx** out)
+{
+    if (!out) { set_error("null out"); return GL_ERR_INVALID; }
+    std::unique_ptr<gl_ctx> c(new gl_ctx());
+    c->impl.stream = static_cast<cudaStream_t>(stream);
+    GL_TRY(c->impl.view.init());
+    *out = c.release();
+    return GL_OK;
+}
+
+extern "C" gl_status gl_ctx_destroy(gl_ctx* ctx)
+{
+    if (!ctx) return GL_OK;
+    cudaStreamSynchronize(ctx->impl.stream);
+    ctx->impl.view.release();
+    ctx->impl.pose_part.release();
+    ctx->impl.loss_part.release();
+    delete ctx;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, const gl_pose* pose,
+                                          const gl_intrinsics* K, int32_t tile_size, float* out_rgb,
+                                          float* out_depth, float* out_opacity)
+{
+    if (!ctx || !out_rgb) { set_error("null ctx or out_rgb"); return GL_ERR_INVALID; }
+    GL_TRY(check_gauss(g, true));
+    GL_TRY(check_tile(tile_size));
+    Cam cam;
+    GL_TRY(make_cam(pose, K, cam));
+    gl_ctx_impl& c = ctx->impl;
+    c.has_forward = 0;
+    GL_TRY(bin_view(c.view, params_of(g), cam, tile_size, c.stream));
+    GL_TRY(raster_forward(c.view, out_rgb, out_depth, out_opacity, c.stream));
+    c.has_forward = 1;
+    c.deg = g->sh_degree;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_rasterize_backward(gl_ctx* ctx, const gl_gaussians* g, const float* dL_drgb,
+                                           const float* dL_ddepth, const float* dL_dopacity,
+                                           gl_gaussians* grad, float* grad_pose6)
+{
+    if (!ctx || !dL_drgb) { set_error("null ctx or dL_drgb"); return GL_ERR_INVALID; }
+    gl_ctx_impl& c = ctx->impl;
+    if (!c.has_forward) { set_error("backward without a forward on this ctx"); return GL_ERR_INVALID; }
+    GL_TRY(check_gauss(g, true));
+    GL_TRY(check_gauss(grad, true));
+    if (g->n != c.view.n || grad->n != g->n || grad->sh_degree != g->sh_degree) {
+        set_error("gaussians differ from the forward");
+        return GL_ERR_INVALID;
+    }
+    GL_TRY(raster_backward(c.view, dL_drgb, dL_ddepth, dL_dopacity, c.stream));
+    const int npart = pose_partials_needed(g->n);
+    float* pp = nullptr;
+    if (grad_pose6) {
+        GL_TRY(c.pose_part.reserve(sizeof(float) * 6 * (size_t)npart));
+        pp = c.pose_part.as<float>();
+    }
+    GL_TRY(params_backward(c.view, params_of(g), mut_of(grad), pp, npart, c.stream));
+    if (grad_pose6) {
+        if (g->n == 0) GL_CUDA_TRY(cudaMemsetAsync(grad_pose6, 0, 24, c.stream));
+        else GL_TRY(pose_reduce(pp, npart, grad_pose6, c.stream));
+    }
+    return GL_OK;
+}
+
+extern "C" gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const float* target,
+                                         const float* E34, int32_t width, int32_t height,
+                                         float lambda_dssim, float* loss_out, float* dL_drgb,
+                                         float* dL_dE)
+{
+    if (!ctx || !rgb || !target || !E34 || !dL_drgb) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (width <= 0 || height <= 0) { set_error("bad image size"); return GL_ERR_INVALID; }
+    if (!(lambda_dssim >= 0.f && lambda_dssim <= 1.f)) { set_error("lambda must be in [0,1]"); return GL_ERR_INVALID; }
+    gl_ctx_impl& c = ctx->impl;
+    GL_TRY(c.loss_part.reserve(sizeof(float) * (size_t)loss_partials_needed(width, height)));
+    return photometric_loss(rgb, target, E34, width, height, lambda_dssim, dL_drgb, c.loss_part.as<float>(),
+                            loss_out, dL_dE, nullptr, c.stream);
+}
+
+extern "C" gl_status gl_ctx_get_preprocess(gl_ctx* ctx, int32_t* radius, int32_t* rect, float* mean2d,
+                                           float* conic, float* opacity, float* rgb, float* depth)
+{
+    if (!ctx || !ctx->impl.has_forward) { set_error("no forward on this ctx"); return GL_ERR_INVALID; }
+    View& v = ctx->impl.view;
+    cudaStream_t s = ctx->impl.stream;
+    const size_t n = (size_t)v.n;
+    if (n == 0) return GL_OK;
+    const char* r0 = static_cast<const char*>(v.rec0.p);
+    const char* r1 = static_cast<const char*>(v.rec1.p);
+    const char* r2 = static_cast<const char*>(v.rec2.p);
+    if (radius) GL_CUDA_TRY(cudaMemcpyAsync(radius, v.radius.p, 4 * n, cudaMemcpyDeviceToDevice, s));
+    if (rect) GL_CUDA_TRY(cudaMemcpyAsync(rect, v.rect.p, 16 * n, cudaMemcpyDeviceToDevice, s));
+    if (mean2d) GL_CUDA_TRY(cudaMemcpy2DAsync(mean2d, 8, r0, 16, 8, n, cudaMemcpyDeviceToDevice, s));
+    if (depth) GL_CUDA_TRY(cudaMemcpy2DAsync(depth, 4, r0 + 8, 16, 4, n, cudaMemcpyDeviceToDevice, s));
+    if (opacity) GL_CUDA_TRY(cudaMemcpy2DAsync(opacity, 4, r0 + 12, 16, 4, n, cudaMemcpyDeviceToDevice, s));
+    if (conic) GL_CUDA_TRY(cudaMemcpy2DAsync(conic, 12, r1, 16, 12, n, cudaMemcpyDeviceToDevice, s));
+    if (rgb) GL_CUDA_TRY(cudaMemcpy2DAsync(rgb, 12, r2, 16, 12, n, cudaMemcpyDeviceToDevice, s));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_ctx_num_instances(gl_ctx* ctx, int64_t* I_out)
+{
+    if (!ctx || !I_out || !ctx->impl.has_forward) { set_error("no forward on this ctx"); return GL_ERR_INVALID; }
+    *I_out = ctx->impl.view.I;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_ctx_get_instances(gl_ctx* ctx, uint64_t* keys, uint32_t* vals, uint32_t* ranges)
+{
+    if (!ctx || !ctx->impl.has_forward) { set_error("no forward on this ctx"); return GL_ERR_INVALID; }
+    View& v = ctx->impl.view;
+    GL_TRY(export_instances(v, keys, vals, ctx->impl.stream));
+    if (ranges)
+        GL_CUDA_TRY(cudaMemcpyAsync(ranges, v.ranges.p, 8 * (size_t)v.ntiles, cudaMemcpyDeviceToDevice,
+                                    ctx->impl.stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_ctx_get_pixel_state(gl_ctx* ctx, float* T_final, uint32_t* n_contrib)
+{
+    if (!ctx || !ctx->impl.has_forward) { set_error("no forward on this ctx"); return GL_ERR_INVALID; }
+    View& v = ctx->impl.view;
+    const size_t P = (size_t)v.W * v.H;
+    if (T_final) GL_CUDA_TRY(cudaMemcpyAsync(T_final, v.Tfin.p, 4 * P, cudaMemcpyDeviceToDevice, ctx->impl.stream));
+    if (n_contrib) GL_CUDA_TRY(cudaMemcpyAsync(n_contrib, v.ncon.p, 4 * P, cudaMemcpyDeviceToDevice, ctx->impl.stream));
+    return GL_OK;
+}
+
+// ===========================================================================
+// Map API
+// ===========================================================================
+namespace {
+
+struct Keyframe {
+    gl_pose pose{};
+    gl_intrinsics K{};
+    DevBuf image;       // H*W*3 floats when registered
+    bool has_image = false;
+    DevBuf expo;        // 36 floats: E, m, v
+    int64_t steps = 0;
+};
+
+enum { PM = 0, PS, PQ, PO, PH, NPARAM };
+
+}  // namespace
+
+struct gl_map {
+    gl_config cfg{};
+    cudaStream_t stream = nullptr;
+    int deg = 3, K = 16;
+    int64_t n = 0, cap = 0;
+    DevBuf prm[NPARAM], mom1[NPARAM], mom2[NPARAM];
+    DevBuf kind;                 // u8 per Gaussian: 0 LiDAR, 1 visual, 2 sky
+    int64_t step = 0;
+    gl_ctx_impl ctx;
+    DevBuf stage_img, stage_pts, dLdC, loss_dev;
+    DevBuf flags, scan;
+    float* h_loss = nullptr;
+    std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
+
+    size_t row_floats(int which) const
+    {
+        switch (which) {
+            case PM: return 3;
+            case PS: return 3;
+            case PQ: return 4;
+            case PO: return 1;
+            default: return (size_t)K * 3;
+        }
+    }
+    GParams params() const
+    {
+        GParams p;
+        p.means = prm[PM].as<float>(); p.log_scales = prm[PS].as<float>(); p.quats = prm[PQ].as<float>();
+        p.logits = prm[PO].as<float>(); p.sh = prm[PH].as<float>(); p.n = n; p.deg = deg; p.K = K;
+        return p;
+    }
+    static GMut mut(DevBuf* b)
+    {
+        GMut m;
+        m.means = b[PM].as<float>(); m.log_scales = b[PS].as<float>(); m.quats = b[PQ].as<float>();
+        m.logits = b[PO].as<float>(); m.sh = b[PH].as<float>();
+        return m;
+    }
+};
+
+namespace {
+
+gl_status map_reserve(gl_map* m, int64_t need)
+{
+    if (need <= m->cap) return GL_OK;
+    int64_t nc = std::max<int64_t>({need, 2 * m->cap, m->cfg.capacity_hint, 1024});
+    for (int set = 0; set < 3; set++) {
+        DevBuf* arr = set == 0 ? m->prm : (set == 1 ? m->mom1 : m->mom2);
+        for (int w = 0; w < NPARAM; w++) {
+            const size_t rb = 4 * m->row_floats(w);
+            void* np = nullptr;
+            cudaError_t e = cudaMalloc(&np, rb * (size_t)nc);
+            if (e != cudaSuccess) { set_error("map growth: out of device memory"); return GL_ERR_OOM; }
+            if (m->n > 0) GL_CUDA_TRY(cudaMemcpyAsync(np, arr[w].p, rb * (size_t)m->n, cudaMemcpyDeviceToDevice, m->stream));
+            GL_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(np) + rb * (size_t)m->n, 0, rb * (size_t)(nc - m->n), m->stream));
+            GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+            arr[w].release();
+            arr[w].p = np;
+            arr[w].bytes = rb * (size_t)nc;
+        }
+    }
+    {
+        void* np = nullptr;
+        GL_CUDA_TRY(cudaMalloc(&np, (size_t)nc));
+        if (m->n > 0) GL_CUDA_TRY(cudaMemcpyAsync(np, m->kind.p, (size_t)m->n, cudaMemcpyDeviceToDevice, m->stream));
+        GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        m->kind.release();
+        m->kind.p = np;
+        m->kind.bytes = (size_t)nc;
+    }
+    m->cap = nc;
+    return GL_OK;
+}
+
+gl_status zero_moments(gl_map* m, int64_t from, int64_t count)
+{
+    if (count <= 0) return GL_OK;
+    for (int w = 0; w < NPARAM; w++) {
+        const size_t rb = 4 * m->row_floats(w);
+        GL_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(m->mom1[w].p) + rb * from, 0, rb * count, m->stream));
+        GL_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(m->mom2[w].p) + rb * from, 0, rb * count, m->stream));
+    }
+    return GL_OK;
+}
+
+// Copy host-or-device floats to a device pointer (staging host data).
+gl_status to_device(const float* src, size_t count, DevBuf& stage, const float** out, cudaStream_t s)
+{
+    if (is_device_ptr(src)) { *out = src; return GL_OK; }
+    GL_TRY(stage.reserve(4 * count));
+    GL_CUDA_TRY(cudaMemcpyAsync(stage.p, src, 4 * count, cudaMemcpyHostToDevice, s));
+    *out = stage.as<float>();
+    return GL_OK;
+}
+
+gl_status from_device(float* dst, const float* src, size_t count, cudaStream_t s)
+{
+    GL_CUDA_TRY(cudaMemcpyAsync(dst, src, 4 * count, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return GL_OK;
+}
+
+Keyframe* get_kf(gl_map* m, int64_t id, bool create, gl_status* st)
+{
+    auto it = m->kfs.find(id);
+    if (it != m->kfs.end()) return it->second.get();
+    if (!create) { *st = GL_ERR_NOT_FOUND; set_error("unknown keyframe id"); return nullptr; }
+    std::unique_ptr<Keyframe> kf(new Keyframe());
+    if ((*st = kf->expo.reserve(36 * 4)) != GL_OK) return nullptr;
+    float init[36] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    if (cudaMemcpyAsync(kf->expo.p, init, sizeof(init), cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        *st = GL_ERR_CUDA;
+        set_error("keyframe exposure init failed");
+        return nullptr;
+    }
+    Keyframe* raw = kf.get();
+    m->kfs[id] = std::move(kf);
+    *st = GL_OK;
+    return raw;
+}
+
+gl_status render_internal(gl_map* m, const Cam& cam, int Ts)
+{
+    View& v = m->ctx.view;
+    const size_t P = (size_t)cam.W * cam.H;
+    GL_TRY(v.rgb.reserve(12 * P));
+    GL_TRY(v.depth.reserve(4 * P));
+    GL_TRY(v.opac.reserve(4 * P));
+    GL_TRY(bin_view(v, m->params(), cam, Ts, m->stream));
+    return raster_forward(v, v.rgb.as<float>(), v.depth.as<float>(), v.opac.as<float>(), m->stream);
+}
+
+}  // namespace
+
+extern "C" gl_status gl_map_create(const gl_config* cfg, void* stream, gl_map** out)
+{
+    if (!cfg || !out) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (cfg->sh_degree < 0 || cfg->sh_degree > 3) { set_error("sh_degree must be 0..3"); return GL_ERR_INVALID; }
+    GL_TRY(check_tile(cfg->tile_size));
+    if (cfg->n_sky < 0 || !(cfg->sky_radius > 0.f) || !(cfg->opacity_sky > 0.f && cfg->opacity_sky < 1.f) ||
+        !(cfg->opacity_fg > 0.f && cfg->opacity_fg < 1.f) || !(cfg->adam_b1 >= 0.f && cfg->adam_b1 < 1.f) ||
+        !(cfg->adam_b2 >= 0.f && cfg->adam_b2 < 1.f)) {
+        set_error("invalid config value");
+        return GL_ERR_INVALID;
+    }
+    std::unique_ptr<gl_map> m(new gl_map());
+    m->cfg = *cfg;
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->deg = cfg->sh_degree;
+    m->K = (m->deg + 1) * (m->deg + 1);
+    m->ctx.stream = m->stream;
+    GL_TRY(m->ctx.view.init());
+    GL_CUDA_TRY(cudaMallocHost(&m->h_loss, 16));
+    GL_TRY(m->loss_dev.reserve(16));
+    GL_TRY(map_reserve(m.get(), std::max<int64_t>(cfg->n_sky, 1)));
+    if (cfg->n_sky > 0) {
+        GMut p = gl_map::mut(m->prm);
+        GL_TRY(sky_create(p.means, p.log_scales, p.quats, p.logits, p.sh, m->K, cfg->n_sky, cfg->sky_radius,
+                          cfg->seed, cfg->opacity_sky, m->stream));
+        GL_CUDA_TRY(cudaMemsetAsync(m->kind.p, 2, (size_t)cfg->n_sky, m->stream));
+        m->n = cfg->n_sky;
+    }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    *out = m.release();
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_destroy(gl_map* m)
+{
+    if (!m) return GL_OK;
+    cudaStreamSynchronize(m->stream);
+    for (int w = 0; w < NPARAM; w++) { m->prm[w].release(); m->mom1[w].release(); m->mom2[w].release(); }
+    m->kind.release();
+    m->ctx.view.release();
+    m->ctx.pose_part.release();
+    m->ctx.loss_part.release();
+    m->stage_img.release(); m->stage_pts.release(); m->dLdC.release(); m->loss_dev.release();
+    m->flags.release(); m->scan.release();
+    for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
+    if (m->h_loss) cudaFreeHost(m->h_loss);
+    delete m;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_size(gl_map* m, int64_t* n_out)
+{
+    if (!m || !n_out) { set_error("null argument"); return GL_ERR_INVALID; }
+    *n_out = m->n;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_add_points(gl_map* m, const float* xyz, const float* rgb, int64_t n, int32_t kind,
+                                       const gl_pose* pose, const gl_intrinsics* K, int32_t use_mask,
+                                       int64_t* n_added)
+{
+    if (!m || (n > 0 && (!xyz || !rgb))) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (n < 0) { set_error("negative point count"); return GL_ERR_INVALID; }
+    Cam cam;
+    GL_TRY(make_cam(pose, K, cam));
+    if (n_added) *n_added = 0;
+    if (n == 0) return GL_OK;
+    const float *dx, *dc;
+    GL_TRY(m->stage_pts.reserve(24 * (size_t)n));
+    {
+        // stage both arrays into one buffer when they live on the host
+        if (is_device_ptr(xyz)) dx = xyz;
+        else {
+            GL_CUDA_TRY(cudaMemcpyAsync(m->stage_pts.p, xyz, 12 * (size_t)n, cudaMemcpyHostToDevice, m->stream));
+            dx = m->stage_pts.as<float>();
+        }
+        if (is_device_ptr(rgb)) dc = rgb;
+        else {
+            float* dst = m->stage_pts.as<float>() + 3 * (size_t)n;
+            GL_CUDA_TRY(cudaMemcpyAsync(dst, rgb, 12 * (size_t)n, cudaMemcpyHostToDevice, m->stream));
+            dc = dst;
+        }
+    }
+    const float* opac = nullptr;
+    if (use_mask) {
+        GL_TRY(render_internal(m, cam, m->cfg.tile_size));
+        opac = m->ctx.view.opac.as<float>();
+    }
+    int64_t added = 0;
+    GMut none{};
+    GL_TRY(expand_points(dx, dc, n, cam, opac, m->cfg.tau, use_mask ? 1 : 0, m->cfg.opacity_fg, m->K, none, 0, 0,
+                         m->flags, m->scan, &added, m->stream));
+    if (added > 0) {
+        GL_TRY(map_reserve(m, m->n + added));
+        GL_TRY(expand_points(dx, dc, n, cam, opac, m->cfg.tau, use_mask ? 1 : 0, m->cfg.opacity_fg, m->K,
+                             gl_map::mut(m->prm), m->n, m->cap, m->flags, m->scan, &added, m->stream));
+        GL_TRY(zero_moments(m, m->n, added));
+        GL_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(m->kind.p) + m->n, kind ? 1 : 0, (size_t)added, m->stream));
+        m->n += added;
+    }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (n_added) *n_added = added;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_add_keyframe(gl_map* m, const gl_keyframe* kf)
+{
+    if (!m || !kf || !kf->image) { set_error("null argument"); return GL_ERR_INVALID; }
+    Cam cam;
+    GL_TRY(make_cam(&kf->pose, &kf->K, cam));
+    gl_status st;
+    Keyframe* k = get_kf(m, kf->id, true, &st);
+    if (!k) return st;
+    const size_t cnt = (size_t)kf->K.width * kf->K.height * 3;
+    GL_TRY(k->image.reserve(4 * cnt));
+    GL_CUDA_TRY(cudaMemcpyAsync(k->image.p, kf->image, 4 * cnt,
+                                is_device_ptr(kf->image) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    k->has_image = true;
+    k->pose = kf->pose;
+    k->K = kf->K;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_render(gl_map* m, const gl_pose* pose, const gl_intrinsics* K, const float* E34,
+                               float* out_rgb, float* out_depth, float* out_opacity)
+{
+    if (!m || !out_rgb) { set_error("null argument"); return GL_ERR_INVALID; }
+    Cam cam;
+    GL_TRY(make_cam(pose, K, cam));
+    if (E34 && !finite_all(E34, 12)) { set_error("exposure contains NaN or Inf"); return GL_ERR_INVALID; }
+    GL_TRY(render_internal(m, cam, m->cfg.tile_size));
+    View& v = m->ctx.view;
+    const size_t P = (size_t)cam.W * cam.H;
+    const float ident[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    if (is_device_ptr(out_rgb)) {
+        GL_TRY(apply_exposure(v.rgb.as<float>(), out_rgb, E34 ? E34 : ident, (int64_t)P, m->stream));
+    } else {
+        GL_TRY(m->stage_img.reserve(12 * P));
+        GL_TRY(apply_exposure(v.rgb.as<float>(), m->stage_img.as<float>(), E34 ? E34 : ident, (int64_t)P, m->stream));
+        GL_CUDA_TRY(cudaMemcpyAsync(out_rgb, m->stage_img.p, 12 * P, cudaMemcpyDeviceToHost, m->stream));
+    }
+    if (out_depth) GL_TRY(from_device(out_depth, v.depth.as<float>(), P, m->stream));
+    if (out_opacity) GL_TRY(from_device(out_opacity, v.opac.as<float>(), P, m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32_t n_views, float* out_loss)
+{
+    if (!m || !views || n_views < 1) { set_error("need at least one view"); return GL_ERR_INVALID; }
+    if (n_views != 1) { set_error("multi-view windows go through gl_optimize_window"); return GL_ERR_INVALID; }
+    const gl_keyframe& kv = views[0];
+    Cam cam;
+    GL_TRY(make_cam(&kv.pose, &kv.K, cam));
+    gl_status st;
+    Keyframe* kf = get_kf(m, kv.id, true, &st);
+    if (!kf) return st;
+    const size_t P = (size_t)cam.W * cam.H;
+    const float* target = nullptr;
+    if (kv.image) {
+        GL_TRY(to_device(kv.image, 3 * P, m->stage_img, &target, m->stream));
+    } else {
+        if (!kf->has_image) { set_error("keyframe has no stored image"); return GL_ERR_NOT_FOUND; }
+        if (kf->K.width != cam.W || kf->K.height != cam.H) { set_error("stored image size differs"); return GL_ERR_INVALID; }
+        target = kf->image.as<float>();
+    }
+    View& v = m->ctx.view;
+    GL_TRY(render_internal(m, cam, m->cfg.tile_size));
+    GL_TRY(m->dLdC.reserve(12 * P));
+    GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * (size_t)loss_partials_needed(cam.W, cam.H)));
+    m->step++;
+    kf->steps++;
+    const gl_config& c = m->cfg;
+    ExpAdam ea;
+    float* e = kf->expo.as<float>();
+    ea.E = e; ea.m = e + 12; ea.v = e + 24;
+    ea.lr = c.lr_exposure; ea.b1 = c.adam_b1; ea.b2 = c.adam_b2; ea.eps = c.adam_eps;
+    ea.bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
+    ea.bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
+    GL_TRY(photometric_loss(v.rgb.as<float>(), target, e, cam.W, cam.H, c.lambda_dssim, m->dLdC.as<float>(),
+                            m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), nullptr, &ea, m->stream));
+    GL_TRY(raster_backward(v, m->dLdC.as<float>(), nullptr, nullptr, m->stream));
+    AdamArgs a;
+    a.m = gl_map::mut(m->mom1);
+    a.v = gl_map::mut(m->mom2);
+    a.lr_pos = c.lr_pos; a.lr_dc = c.lr_sh_dc; a.lr_rest = c.lr_sh_rest; a.lr_op = c.lr_opacity;
+    a.lr_scale = c.lr_scale; a.lr_rot = c.lr_rot;
+    a.b1 = c.adam_b1; a.b2 = c.adam_b2; a.eps = c.adam_eps;
+    a.bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)m->step));
+    a.bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)m->step));
+    a.sparse = c.sparse_adam;
+    GL_TRY(params_adam(v, m->params(), gl_map::mut(m->prm), a, m->stream));
+    if (out_loss) {
+        GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4, cudaMemcpyDeviceToHost, m->stream));
+        GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        *out_loss = m->h_loss[0];
+    }
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_params(gl_map* m, gl_gaussians* out, int64_t* n_out)
+{
+    if (!m || !out) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (out->sh_degree != m->deg) { set_error("sh_degree differs from the map"); return GL_ERR_INVALID; }
+    if (n_out) *n_out = m->n;
+    if (out->n < m->n) { set_error("output arrays too small"); return GL_ERR_INVALID; }
+    float* dst[NPARAM] = {out->means, out->log_scales, out->quats, out->logits, out->sh};
+    for (int w = 0; w < NPARAM; w++)
+        if (dst[w]) GL_TRY(from_device(dst[w], m->prm[w].as<float>(), m->row_floats(w) * (size_t)m->n, m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_moments(gl_map* m, int32_t which, gl_gaussians* out)
+{
+    if (!m || !out || (which != 1 && which != 2)) { set_error("bad argument"); return GL_ERR_INVALID; }
+    if (out->sh_degree != m->deg || out->n < m->n) { set_error("output shape differs"); return GL_ERR_INVALID; }
+    DevBuf* src = which == 1 ? m->mom1 : m->mom2;
+    float* dst[NPARAM] = {out->means, out->log_scales, out->quats, out->logits, out->sh};
+    for (int w = 0; w < NPARAM; w++)
+        if (dst[w]) GL_TRY(from_device(dst[w], src[w].as<float>(), m->row_floats(w) * (size_t)m->n, m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_set_params(gl_map* m, const gl_gaussians* in)
+{
+    if (!m || !in) { set_error("null argument"); return GL_ERR_INVALID; }
+    GL_TRY(check_gauss(in, true));
+    if (in->sh_degree != m->deg) { set_error("sh_degree differs from the map"); return GL_ERR_INVALID; }
+    GL_TRY(map_reserve(m, in->n));
+    const float* src[NPARAM] = {in->means, in->log_scales, in->quats, in->logits, in->sh};
+    for (int w = 0; w < NPARAM; w++) {
+        const size_t cnt = m->row_floats(w) * (size_t)in->n;
+        GL_CUDA_TRY(cudaMemcpyAsync(m->prm[w].p, src[w], 4 * cnt,
+                                    is_device_ptr(src[w]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    m->stream));
+    }
+    GL_CUDA_TRY(cudaMemsetAsync(m->kind.p, 0, (size_t)in->n, m->stream));
+    m->n = in->n;
+    GL_TRY(zero_moments(m, 0, m->n));
+    m->step = 0;
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_exposure(gl_map* m, int64_t id, float* E34_out)
+{
+    if (!m || !E34_out) { set_error("null argument"); return GL_ERR_INVALID; }
+    gl_status st;
+    Keyframe* kf = get_kf(m, id, false, &st);
+    if (!kf) return st;
+    GL_CUDA_TRY(cudaMemcpyAsync(E34_out, kf->expo.p, 48, cudaMemcpyDeviceToHost, m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}

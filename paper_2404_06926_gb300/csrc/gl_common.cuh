@@ -1,0 +1,252 @@
+// gl_common.cuh -- device-side definitions shared by the kernels of the map
+// optimiser (arXiv 2404.06926, Sec. III-A/III-C).  Nothing here is shared with
+// the CPU oracle: constants and arithmetic are written out for the GPU alone.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gl {
+
+// ---------------------------------------------------------------------------
+// Constants.  The paper defers all rasteriser constants to 3DGS and prints
+// none; these are the readings used throughout.
+// ---------------------------------------------------------------------------
+constexpr float kZNear = 0.2f;          // cull depth (m)
+constexpr float kDilation = 0.3f;       // low-pass dilation added to Sigma' (px^2)
+constexpr float kJacClamp = 1.3f;       // |x/z| <= 1.3 * tan(half FoV) in the EWA Jacobian
+constexpr float kEigFloor = 0.1f;       // floor under the eigenvalue discriminant
+constexpr float kRadiusSigmas = 3.0f;   // screen radius = ceil(3 sqrt(lambda_max))
+constexpr float kAlphaMax = 0.99f;      // alpha cap
+constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha skip threshold
+constexpr float kTransMin = 1e-4f;      // transmittance stop threshold
+
+// Real SH normalisation factors (Condon-Shortley phase), degree <= 3.
+constexpr float kSH0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+constexpr float kSH1 = 0.4886025119029199f;    // sqrt(3/(4 pi))
+constexpr float kSH2a = 1.0925484305920792f;   // sqrt(15/pi)/2      xy, yz, xz
+constexpr float kSH2b = 0.31539156525252005f;  // sqrt(5/pi)/4       2z^2-x^2-y^2
+constexpr float kSH2c = 0.5462742152960396f;   // sqrt(15/pi)/4      x^2-y^2
+constexpr float kSH3a = 0.5900435899266435f;   // sqrt(35/(2pi))/4   y(3x^2-y^2), x(x^2-3y^2)
+constexpr float kSH3b = 2.890611442640554f;    // sqrt(105/pi)/2     xyz
+constexpr float kSH3c = 0.4570457994644658f;   // sqrt(21/(2pi))/4   y(4z^2-x^2-y^2), x(..)
+constexpr float kSH3d = 0.3731763325901154f;   // sqrt(7/pi)/4       z(2z^2-3x^2-3y^2)
+constexpr float kSH3e = 1.445305721320277f;    // sqrt(105/pi)/4     z(x^2-y^2)
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Camera passed by value to kernels: world->camera x_c = R x_w + t, pinhole.
+struct Cam {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+};
+
+// Read-only view of Gaussian parameters (device, one row-major array each).
+struct GParams {
+    const float* means;       // n*3
+    const float* log_scales;  // n*3
+    const float* quats;       // n*4 (w,x,y,z)
+    const float* logits;      // n
+    const float* sh;          // n*K*3
+    int64_t n;
+    int deg;
+    int K;                    // (deg+1)^2
+};
+
+// Writable view (gradients, Adam moments, parameters updated in place).
+struct GMut {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* logits;
+    float* sh;
+};
+
+// ---------------------------------------------------------------------------
+// Integer-deciding projection (Eq. 2-3): cull, radius, tile rectangle and
+// depth key.  Every operation is an explicitly rounded float32 operation in
+// a fixed order (no contraction), so the decision is reproducible; exp of the
+// log-scale is taken in double and rounded once.
+// ---------------------------------------------------------------------------
+struct Decision {
+    float u, v, z;           // mu' and depth
+    float a, b, c, det;      // Sigma' (dilated) and its determinant
+    int r;                   // screen radius (px)
+    int x0, y0, x1, y1;      // tile rectangle, half open
+};
+
+__device__ __forceinline__ float fmr(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float far_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsr(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdr(float a, float b) { return __fdiv_rn(a, b); }
+
+__device__ __forceinline__ bool decide(const float mu[3], const float ls[3], const float q[4],
+                                       const Cam& cam, int Ts, int TX, int TY, Decision& D)
+{
+    const float* R = cam.R;
+    float x = far_(far_(far_(fmr(R[0], mu[0]), fmr(R[1], mu[1])), fmr(R[2], mu[2])), cam.t[0]);
+    float y = far_(far_(far_(fmr(R[3], mu[0]), fmr(R[4], mu[1])), fmr(R[5], mu[2])), cam.t[1]);
+    float z = far_(far_(far_(fmr(R[6], mu[0]), fmr(R[7], mu[1])), fmr(R[8], mu[2])), cam.t[2]);
+    if (!(z > kZNear)) return false;
+    float iz = fdr(1.0f, z);
+    float xz = fmr(x, iz), yz = fmr(y, iz);
+    float u = far_(fmr(cam.fx, xz), cam.cx);
+    float v = far_(fmr(cam.fy, yz), cam.cy);
+    if (!(fabsf(u) <= 3.0e38f) || !(fabsf(v) <= 3.0e38f)) return false;
+
+    float s0 = (float)exp((double)ls[0]);
+    float s1 = (float)exp((double)ls[1]);
+    float s2 = (float)exp((double)ls[2]);
+    float qq = far_(far_(far_(fmr(q[0], q[0]), fmr(q[1], q[1])), fmr(q[2], q[2])), fmr(q[3], q[3]));
+    if (!(qq > 0.0f) || !(qq <= 3.0e38f)) return false;
+    float inv = fdr(1.0f, __fsqrt_rn(qq));
+    float w = fmr(q[0], inv), qx = fmr(q[1], inv), qy = fmr(q[2], inv), qz = fmr(q[3], inv);
+    float r00 = fsr(1.0f, fmr(2.0f, far_(fmr(qy, qy), fmr(qz, qz))));
+    float r01 = fmr(2.0f, fsr(fmr(qx, qy), fmr(w, qz)));
+    float r02 = fmr(2.0f, far_(fmr(qx, qz), fmr(w, qy)));
+    float r10 = fmr(2.0f, far_(fmr(qx, qy), fmr(w, qz)));
+    float r11 = fsr(1.0f, fmr(2.0f, far_(fmr(qx, qx), fmr(qz, qz))));
+    float r12 = fmr(2.0f, fsr(fmr(qy, qz), fmr(w, qx)));
+    float r20 = fmr(2.0f, fsr(fmr(qx, qz), fmr(w, qy)));
+    float r21 = fmr(2.0f, far_(fmr(qy, qz), fmr(w, qx)));
+    float r22 = fsr(1.0f, fmr(2.0f, far_(fmr(qx, qx), fmr(qy, qy))));
+    float M[9] = {fmr(r00, s0), fmr(r01, s1), fmr(r02, s2),
+                  fmr(r10, s0), fmr(r11, s1), fmr(r12, s2),
+                  fmr(r20, s0), fmr(r21, s1), fmr(r22, s2)};
+    float S[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            S[i * 3 + j] = far_(far_(fmr(M[i * 3 + 0], M[j * 3 + 0]), fmr(M[i * 3 + 1], M[j * 3 + 1])),
+                                fmr(M[i * 3 + 2], M[j * 3 + 2]));
+
+    float limx = fmr(kJacClamp, fdr(fmr(0.5f, (float)cam.W), cam.fx));
+    float limy = fmr(kJacClamp, fdr(fmr(0.5f, (float)cam.H), cam.fy));
+    float cxz = fminf(fmaxf(xz, -limx), limx);
+    float cyz = fminf(fmaxf(yz, -limy), limy);
+    float j00 = fmr(cam.fx, iz);
+    float j02 = fmr(-fmr(cam.fx, cxz), iz);
+    float j11 = fmr(cam.fy, iz);
+    float j12 = fmr(-fmr(cam.fy, cyz), iz);
+    float T[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T[k] = far_(fmr(j00, R[k]), fmr(j02, R[6 + k]));
+        T[3 + k] = far_(fmr(j11, R[3 + k]), fmr(j12, R[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            U[i * 3 + k] = far_(far_(fmr(T[i * 3 + 0], S[0 * 3 + k]), fmr(T[i * 3 + 1], S[1 * 3 + k])),
+                                fmr(T[i * 3 + 2], S[2 * 3 + k]));
+    float a = far_(far_(far_(fmr(U[0], T[0]), fmr(U[1], T[1])), fmr(U[2], T[2])), kDilation);
+    float b = far_(far_(fmr(U[0], T[3]), fmr(U[1], T[4])), fmr(U[2], T[5]));
+    float c = far_(far_(far_(fmr(U[3], T[3]), fmr(U[4], T[4])), fmr(U[5], T[5])), kDilation);
+    float det = fsr(fmr(a, c), fmr(b, b));
+    if (!(det > 0.0f)) return false;
+    float mid = fmr(0.5f, far_(a, c));
+    float lam = far_(mid, __fsqrt_rn(fmaxf(kEigFloor, fsr(fmr(mid, mid), det))));
+    float r = ceilf(fmr(kRadiusSigmas, __fsqrt_rn(lam)));
+    if (!(r >= 1.0f) || !(r <= 3.0e38f)) return false;
+
+    float tsf = (float)Ts;
+    float x0 = fminf(fmaxf(floorf(fdr(fsr(u, r), tsf)), 0.0f), (float)TX);
+    float x1 = fminf(fmaxf(floorf(fdr(far_(far_(u, r), tsf - 1.0f), tsf)), 0.0f), (float)TX);
+    float y0 = fminf(fmaxf(floorf(fdr(fsr(v, r), tsf)), 0.0f), (float)TY);
+    float y1 = fminf(fmaxf(floorf(fdr(far_(far_(v, r), tsf - 1.0f), tsf)), 0.0f), (float)TY);
+    D.x0 = (int)x0; D.y0 = (int)y0; D.x1 = (int)x1; D.y1 = (int)y1;
+    if ((D.x1 - D.x0) * (D.y1 - D.y0) == 0) return false;
+    D.r = (r > 2.0e9f) ? 2000000000 : (int)r;
+    D.u = u; D.v = v; D.z = z;
+    D.a = a; D.b = b; D.c = c; D.det = det;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Real SH basis (degree <= 3) at a unit direction; optional gradient.
+// ---------------------------------------------------------------------------
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float Y[16])
+{
+    Y[0] = kSH0;
+    if (DEG >= 1) { Y[1] = -kSH1 * y; Y[2] = kSH1 * z; Y[3] = -kSH1 * x; }
+    if (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kSH2a * x * y;
+        Y[5] = -kSH2a * y * z;
+        Y[6] = kSH2b * (2.0f * zz - xx - yy);
+        Y[7] = -kSH2a * x * z;
+        Y[8] = kSH2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -kSH3a * y * (3.0f * xx - yy);
+            Y[10] = kSH3b * x * y * z;
+            Y[11] = -kSH3c * y * (4.0f * zz - xx - yy);
+            Y[12] = kSH3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -kSH3c * x * (4.0f * zz - xx - yy);
+            Y[14] = kSH3e * z * (xx - yy);
+            Y[15] = -kSH3a * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+// dY[k][j] = d Y_k / d dir_j (dir treated as unconstrained).
+template <int DEG>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, float dY[16][3])
+{
+#pragma unroll
+    for (int k = 0; k < 16; k++) { dY[k][0] = 0.f; dY[k][1] = 0.f; dY[k][2] = 0.f; }
+    if (DEG >= 1) { dY[1][1] = -kSH1; dY[2][2] = kSH1; dY[3][0] = -kSH1; }
+    if (DEG >= 2) {
+        dY[4][0] = kSH2a * y;  dY[4][1] = kSH2a * x;
+        dY[5][1] = -kSH2a * z; dY[5][2] = -kSH2a * y;
+        dY[6][0] = -2.0f * kSH2b * x; dY[6][1] = -2.0f * kSH2b * y; dY[6][2] = 4.0f * kSH2b * z;
+        dY[7][0] = -kSH2a * z; dY[7][2] = -kSH2a * x;
+        dY[8][0] = 2.0f * kSH2c * x; dY[8][1] = -2.0f * kSH2c * y;
+        if (DEG >= 3) {
+            float xx = x * x, yy = y * y, zz = z * z;
+            dY[9][0] = -kSH3a * 6.0f * x * y;        dY[9][1] = -kSH3a * (3.0f * xx - 3.0f * yy);
+            dY[10][0] = kSH3b * y * z; dY[10][1] = kSH3b * x * z; dY[10][2] = kSH3b * x * y;
+            dY[11][0] = kSH3c * 2.0f * x * y;
+            dY[11][1] = -kSH3c * (4.0f * zz - xx - 3.0f * yy);
+            dY[11][2] = -kSH3c * 8.0f * y * z;
+            dY[12][0] = -kSH3d * 6.0f * x * z; dY[12][1] = -kSH3d * 6.0f * y * z;
+            dY[12][2] = kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+            dY[13][0] = -kSH3c * (4.0f * zz - 3.0f * xx - yy);
+            dY[13][1] = kSH3c * 2.0f * x * y;
+            dY[13][2] = -kSH3c * 8.0f * x * z;
+            dY[14][0] = kSH3e * 2.0f * x * z; dY[14][1] = -kSH3e * 2.0f * y * z;
+            dY[14][2] = kSH3e * (xx - yy);
+            dY[15][0] = -kSH3a * (3.0f * xx - 3.0f * yy); dY[15][1] = kSH3a * 6.0f * x * y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair blending weight (Eq. 4) shared by the forward and the backward
+// raster kernels.  Explicitly rounded operations keep the skip decisions of
+// the two kernels identical.  rec0 = (u, v, depth, opacity), rec1 = conic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool pair_alpha(const float4 r0, const float4 r1, float px, float py,
+                                           float& dx, float& dy, float& alpha, float& G,
+                                           bool& capped)
+{
+    dx = __fsub_rn(r0.x, px);
+    dy = __fsub_rn(r0.y, py);
+    float quad = __fmaf_rn(r1.x, __fmul_rn(dx, dx), __fmul_rn(r1.z, __fmul_rn(dy, dy)));
+    float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(r1.y, __fmul_rn(dx, dy)));
+    if (power > 0.0f) return false;
+    G = __expf(power);
+    float araw = __fmul_rn(r0.w, G);
+    capped = araw >= kAlphaMax;
+    alpha = fminf(kAlphaMax, araw);
+    return alpha >= kAlphaMin;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace gl

@@ -1,0 +1,153 @@
+// gl_internal.h -- host-side internals shared by the translation units of the
+// library: grow-only device buffers, the per-view context and the kernel
+// launchers.  Not part of the public ABI (include/gl_map.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gl_common.cuh"
+#include "../../include/gl_map.h"
+
+namespace gl {
+
+void set_error(const std::string& msg);
+
+#define GL_CUDA_TRY(expr)                                                         \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            ::gl::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));  \
+            return _e == cudaErrorMemoryAllocation ? GL_ERR_OOM : GL_ERR_CUDA;     \
+        }                                                                         \
+    } while (0)
+
+#define GL_TRY(expr)                         \
+    do {                                     \
+        gl_status _s = (expr);               \
+        if (_s != GL_OK) return _s;          \
+    } while (0)
+
+// Grow-only device allocation.  Contents are not preserved on growth.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    gl_status reserve(size_t need);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Scratch of one rendered view: projected records, binning, per-pixel state.
+struct View {
+    int64_t n = 0;            // Gaussians
+    int W = 0, H = 0, Ts = 16, TX = 0, TY = 0, ntiles = 0;
+    int64_t I = 0;            // (Gaussian, tile) instances
+    Cam cam{};
+    // per Gaussian
+    DevBuf rec0, rec1, rec2;  // float4: (u,v,z,o), (A,B,C,-), (r,g,b,-)
+    DevBuf radius;            // int
+    DevBuf rect;              // int4 (x0,y0,x1,y1)
+    DevBuf touched;           // u32
+    DevBuf dkey, gidx;        // u32 depth key, u32 index (sort input)
+    DevBuf dkey2, gidx2;      // sort ping-pong
+    DevBuf dup_off;           // u32 offset of the Gaussian's first instance
+    // scan
+    DevBuf bsum;              // u64 per scan block
+    DevBuf count;             // u64[4]: I, overflow flag, ...
+    // per instance
+    DevBuf itile, ival, itile2, ival2;  // u32 tile id, u32 instance id (sort)
+    DevBuf iowner;            // u32 owning Gaussian per instance id
+    DevBuf igrad;             // float[10] per instance id (backward)
+    DevBuf hist;              // radix histograms
+    DevBuf ranges;            // uint2 per tile
+    // per pixel
+    DevBuf Tfin, ncon;        // float, u32
+    DevBuf rgb, depth, opac;  // internal render targets when needed
+    // sorted-order results of the last forward (pointers into the buffers above)
+    const uint32_t* sorted_g = nullptr;   // Gaussians in depth order
+    const uint32_t* sorted_tile = nullptr;
+    const uint32_t* sorted_inst = nullptr;
+    uint64_t* h_count = nullptr;          // pinned: I, overflow
+    gl_status init();
+    void release();
+};
+
+struct gl_ctx_impl {
+    cudaStream_t stream = nullptr;
+    View view;
+    DevBuf pose_part;   // per-block pose partials
+    DevBuf loss_part;   // per-block loss partials
+    int has_forward = 0;
+    int deg = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (each returns GL_OK or an error; all work on `stream`).
+// ---------------------------------------------------------------------------
+
+// Preprocess + depth sort + scan + duplicate + tile sort + ranges: fills
+// `v` for the Gaussians `p` seen by `cam` (tiles of side Ts).  Synchronises
+// once to size the instance buffers.
+gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream_t s);
+
+// Forward raster of a binned view into (rgb, depth, opacity) device images
+// (depth/opacity may be null) plus T_final / n_contrib in `v`.
+gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s);
+
+// Backward raster: per-instance 2-D gradients into v.igrad.
+gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
+                          const float* dL_dopac, cudaStream_t s);
+
+// Chain rule from per-instance 2-D gradients to parameters.
+struct AdamArgs {
+    GMut m, v;                 // moments
+    float lr_pos, lr_dc, lr_rest, lr_op, lr_scale, lr_rot;
+    float b1, b2, eps, bc1, bc2;   // bias corrections 1-b^t
+    int sparse;
+};
+// mode 0: write gradients into `grad` (+ pose partials if pose_part != null).
+gl_status params_backward(View& v, const GParams& p, GMut grad, float* pose_part, int npart,
+                          cudaStream_t s);
+// mode 1: fused Adam update of `upd` (same storage as p) with moments.
+gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cudaStream_t s);
+int pose_partials_needed(int64_t n);
+gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s);
+
+// Photometric loss (Eq. 9): writes dL/drgb and per-block partials; then the
+// final reduction writes loss and dL/dE and, if adam != null, updates E.
+struct ExpAdam {
+    float* E;          // device 12
+    float* m;          // device 12
+    float* v;          // device 12
+    float lr, b1, b2, eps, bc1, bc2;
+};
+int loss_partials_needed(int W, int H);
+gl_status photometric_loss(const float* rgb, const float* target, const float* E, int W, int H,
+                           float lambda, float* dL_drgb, float* part, float* loss_out,
+                           float* dE_out, const ExpAdam* adam, cudaStream_t s);
+
+// Apply C_hat = A C + b (E34 by value) from src to dst (device images).
+gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P,
+                         cudaStream_t s);
+
+// Radix sort of (u32 key, u32 value) pairs over bits [0, bits); n on device.
+// Returns in *out_k/*out_v the buffers holding the result.
+gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                         const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
+                         uint32_t** out_k, uint32_t** out_v, cudaStream_t s);
+
+// Sorted instances as (tile << 32 | depth bits) keys and owning Gaussians.
+gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+
+// Map-side kernels.
+gl_status sky_create(float* means, float* log_scales, float* quats, float* logits, float* sh,
+                     int K, int64_t n, double radius, uint64_t seed, float opacity,
+                     cudaStream_t s);
+gl_status expand_points(const float* xyz, const float* rgb, int64_t n, const Cam& cam,
+                        const float* opacity_map, float tau, int use_mask, float opacity_fg,
+                        int K, GMut dst, int64_t dst_offset, int64_t dst_cap, DevBuf& flags,
+                        DevBuf& scan, int64_t* n_added, cudaStream_t s);
+
+}  // namespace gl

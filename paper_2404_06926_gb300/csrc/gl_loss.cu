@@ -1,0 +1,273 @@
+// gl_loss.cu -- exposure-compensated photometric loss (Eq. 9) and its adjoint.
+//
+// L = (1 - lambda) mean |E[C] - C_bar| + lambda (1 - mean SSIM(E[C], C_bar)),
+// E[C] = A C + b with the 3x4 exposure [A | b] of the view (Sec. III-C 3).
+// SSIM uses an 11x11 Gaussian window (sigma 1.5), zero padding, C1 = 0.01^2,
+// C2 = 0.03^2 -- the D-SSIM of 3DGS the paper cites.
+//
+// One CTA per 32x32 output tile does everything in shared memory: it loads the
+// exposed colour and the target over the tile plus a 10-pixel halo, blurs the
+// five moment maps separably over a 5-pixel halo, forms the SSIM map and its
+// partials w.r.t. (mu_x, E[x^2], E[xy]), blurs those back (the adjoint of a
+// zero-padded symmetric correlation is the same correlation) and writes
+// dL/dC = A^T dL/dE[C].  Per-CTA partial sums of |.|, SSIM and dL/dE are
+// reduced afterwards in a fixed order, in double.
+#include "gl_internal.h"
+
+#include <algorithm>
+
+namespace gl {
+
+namespace {
+
+constexpr int LT = 32;
+constexpr int HW = 5;                 // window half width
+constexpr int RA = LT + 4 * HW;       // 52
+constexpr int RB = LT + 2 * HW;       // 42
+constexpr int kThreads = 256;
+constexpr int kNP = 14;               // partials per CTA: 12 dL/dE, sum|d|, sum SSIM
+constexpr float kC1 = 0.01f * 0.01f;
+constexpr float kC2 = 0.03f * 0.03f;
+
+constexpr size_t kSmemFloats = 2 * RA * RA + 5 * RA * RB + 3 * RB * RB + 3 * LT * LT;
+
+__global__ void __launch_bounds__(kThreads)
+k_loss(const float* __restrict__ rgb, const float* __restrict__ target, const float* __restrict__ E,
+       int W, int H, float lambda, float* __restrict__ dL_drgb, float* __restrict__ part)
+{
+    extern __shared__ float sm[];
+    float* xs = sm;
+    float* ys = xs + RA * RA;
+    float* hm = ys + RA * RA;          // 5 maps, RA rows x RB cols
+    float* gmap = hm + 5 * RA * RB;    // 3 maps, RB x RB
+    float* dch = gmap + 3 * RB * RB;   // 3 channels, LT x LT
+    float* hg = hm;                    // 3 maps, RB rows x LT cols (reuses hm)
+    __shared__ float wt[11];
+    __shared__ float Es[12];
+    __shared__ float red[kNP][kThreads / 32];
+    const int tid = threadIdx.x;
+    if (tid < 11) {
+        float s = 0.0f;
+        for (int k = 0; k < 11; k++) s += expf(-(float)((k - HW) * (k - HW)) / 4.5f);
+        wt[tid] = expf(-(float)((tid - HW) * (tid - HW)) / 4.5f) / s;
+    }
+    if (tid < 12) Es[tid] = E[tid];
+    __syncthreads();
+    const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
+    const float invN = 1.0f / (3.0f * (float)W * (float)H);
+    const float gS = -lambda * invN;
+    const float gL1 = (1.0f - lambda) * invN;
+    float l1acc = 0.0f, sacc = 0.0f;
+
+    for (int ch = 0; ch < 3; ch++) {
+        const float e0 = Es[4 * ch], e1 = Es[4 * ch + 1], e2 = Es[4 * ch + 2], e3 = Es[4 * ch + 3];
+        for (int e = tid; e < RA * RA; e += kThreads) {
+            const int gx = ox - 2 * HW + e % RA, gy = oy - 2 * HW + e / RA;
+            float x = 0.0f, y = 0.0f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const size_t p = (size_t)gy * W + gx;
+                x = e0 * rgb[3 * p] + e1 * rgb[3 * p + 1] + e2 * rgb[3 * p + 2] + e3;
+                y = target[3 * p + ch];
+            }
+            xs[e] = x;
+            ys[e] = y;
+        }
+        __syncthreads();
+        for (int e = tid; e < RA * RB; e += kThreads) {
+            const int r = e / RB, c = e % RB;
+            float s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+#pragma unroll
+            for (int k = 0; k < 11; k++) {
+                const float xv = xs[r * RA + c + k], yv = ys[r * RA + c + k], wk = wt[k];
+                s0 += wk * xv; s1 += wk * yv; s2 += wk * xv * xv; s3 += wk * yv * yv; s4 += wk * xv * yv;
+            }
+            hm[e] = s0; hm[RA * RB + e] = s1; hm[2 * RA * RB + e] = s2;
+            hm[3 * RA * RB + e] = s3; hm[4 * RA * RB + e] = s4;
+        }
+        __syncthreads();
+        for (int e = tid; e < RB * RB; e += kThreads) {
+            const int r = e / RB, c = e % RB;
+            const int gx = ox - HW + c, gy = oy - HW + r;
+            float ga = 0.0f, gb = 0.0f, gc = 0.0f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+#pragma unroll
+                for (int k = 0; k < 11; k++) {
+                    const int i = (r + k) * RB + c;
+                    const float wk = wt[k];
+                    mx += wk * hm[i]; my += wk * hm[RA * RB + i]; exx += wk * hm[2 * RA * RB + i];
+                    eyy += wk * hm[3 * RA * RB + i]; exy += wk * hm[4 * RA * RB + i];
+                }
+                const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                const float N1 = 2.f * mx * my + kC1, N2 = 2.f * sxy + kC2;
+                const float D1 = mx * mx + my * my + kC1, D2 = sxx + syy + kC2;
+                const float iD = 1.0f / (D1 * D2);
+                const float S = N1 * N2 * iD;
+                if (r >= HW && r < HW + LT && c >= HW && c < HW + LT) sacc += S;
+                const float dN1 = N2 * iD, dN2 = N1 * iD, dD1 = -S / D1, dD2 = -S / D2;
+                const float dmx = dN1 * 2.f * my - dN2 * 2.f * my + dD1 * 2.f * mx - dD2 * 2.f * mx;
+                ga = gS * dmx;
+                gb = gS * dD2;
+                gc = gS * 2.f * dN2;
+            }
+            gmap[e] = ga; gmap[RB * RB + e] = gb; gmap[2 * RB * RB + e] = gc;
+        }
+        __syncthreads();
+        for (int e = tid; e < RB * LT; e += kThreads) {
+            const int r = e / LT, c = e % LT;
+            float a = 0, b = 0, cc = 0;
+#pragma unroll
+            for (int k = 0; k < 11; k++) {
+                const int i = r * RB + c + k;
+                const float wk = wt[k];
+                a += wk * gmap[i]; b += wk * gmap[RB * RB + i]; cc += wk * gmap[2 * RB * RB + i];
+            }
+            hg[e] = a; hg[RB * LT + e] = b; hg[2 * RB * LT + e] = cc;
+        }
+        __syncthreads();
+        for (int e = tid; e < LT * LT; e += kThreads) {
+            const int r = e / LT, c = e % LT;
+            const int gx = ox + c, gy = oy + r;
+            float g = 0.0f;
+            if (gx < W && gy < H) {
+                float a = 0, b = 0, cc = 0;
+#pragma unroll
+                for (int k = 0; k < 11; k++) {
+                    const int i = (r + k) * LT + c;
+                    const float wk = wt[k];
+                    a += wk * hg[i]; b += wk * hg[RB * LT + i]; cc += wk * hg[2 * RB * LT + i];
+                }
+                const float x = xs[(r + 2 * HW) * RA + c + 2 * HW], y = ys[(r + 2 * HW) * RA + c + 2 * HW];
+                const float d = x - y;
+                l1acc += fabsf(d);
+                g = a + 2.f * x * b + y * cc + gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
+            }
+            dch[ch * LT * LT + e] = g;
+        }
+        __syncthreads();
+    }
+
+    float pe[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) pe[i] = 0.0f;
+    for (int e = tid; e < LT * LT; e += kThreads) {
+        const int gx = ox + e % LT, gy = oy + e / LT;
+        if (gx >= W || gy >= H) continue;
+        const size_t p = (size_t)gy * W + gx;
+        const float c0 = rgb[3 * p], c1 = rgb[3 * p + 1], c2 = rgb[3 * p + 2];
+        const float g0 = dch[e], g1 = dch[LT * LT + e], g2 = dch[2 * LT * LT + e];
+        dL_drgb[3 * p] = Es[0] * g0 + Es[4] * g1 + Es[8] * g2;
+        dL_drgb[3 * p + 1] = Es[1] * g0 + Es[5] * g1 + Es[9] * g2;
+        dL_drgb[3 * p + 2] = Es[2] * g0 + Es[6] * g1 + Es[10] * g2;
+        const float gg[3] = {g0, g1, g2};
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            pe[4 * i] += gg[i] * c0; pe[4 * i + 1] += gg[i] * c1; pe[4 * i + 2] += gg[i] * c2;
+            pe[4 * i + 3] += gg[i];
+        }
+    }
+    float vals[kNP];
+#pragma unroll
+    for (int i = 0; i < 12; i++) vals[i] = pe[i];
+    vals[12] = l1acc;
+    vals[13] = sacc;
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < kNP; i++) {
+        float v = vals[i];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (tid < kNP) {
+        float v = 0.0f;
+        for (int ww = 0; ww < kThreads / 32; ww++) v += red[tid][ww];
+        const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        part[blk * kNP + tid] = v;
+    }
+}
+
+__global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, int H, float lambda,
+                             float* __restrict__ loss_out, float* __restrict__ dE_out, ExpAdam ad,
+                             int do_adam)
+{
+    // one warp per partial slot, fixed order, double accumulation
+    __shared__ double tot[kNP];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k < kNP) {
+        double acc = 0.0;
+        for (int i = lane; i < nblk; i += 32) acc += part[(size_t)i * kNP + k];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+        if (lane == 0) tot[k] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double invN = 1.0 / (3.0 * (double)W * (double)H);
+        const double L = (1.0 - lambda) * tot[12] * invN + lambda * (1.0 - tot[13] * invN);
+        if (loss_out) *loss_out = (float)L;
+    }
+    if (threadIdx.x < 12) {
+        const float g = (float)tot[threadIdx.x];
+        if (dE_out) dE_out[threadIdx.x] = g;
+        if (do_adam) {
+            const int i = threadIdx.x;
+            float m = ad.b1 * ad.m[i] + (1.0f - ad.b1) * g;
+            float v = ad.b2 * ad.v[i] + (1.0f - ad.b2) * g * g;
+            ad.m[i] = m;
+            ad.v[i] = v;
+            ad.E[i] -= ad.lr * (m / ad.bc1) / (sqrtf(v / ad.bc2) + ad.eps);
+        }
+    }
+}
+
+__global__ void k_apply_exposure(const float* __restrict__ src, float* __restrict__ dst, int64_t P,
+                                 float e0, float e1, float e2, float e3, float e4, float e5, float e6,
+                                 float e7, float e8, float e9, float e10, float e11)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const float c0 = src[3 * p], c1 = src[3 * p + 1], c2 = src[3 * p + 2];
+        dst[3 * p] = e0 * c0 + e1 * c1 + e2 * c2 + e3;
+        dst[3 * p + 1] = e4 * c0 + e5 * c1 + e6 * c2 + e7;
+        dst[3 * p + 2] = e8 * c0 + e9 * c1 + e10 * c2 + e11;
+    }
+}
+
+}  // namespace
+
+int loss_partials_needed(int W, int H)
+{
+    return ((W + LT - 1) / LT) * ((H + LT - 1) / LT) * kNP;
+}
+
+gl_status photometric_loss(const float* rgb, const float* target, const float* E, int W, int H,
+                           float lambda, float* dL_drgb, float* part, float* loss_out, float* dE_out,
+                           const ExpAdam* adam, cudaStream_t s)
+{
+    static bool attr_set = false;
+    const size_t smem = kSmemFloats * sizeof(float);
+    if (!attr_set) {
+        GL_CUDA_TRY(cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT);
+    k_loss<<<grid, kThreads, smem, s>>>(rgb, target, E, W, H, lambda, dL_drgb, part);
+    ExpAdam a{};
+    if (adam) a = *adam;
+    k_loss_final<<<1, 32 * kNP, 0, s>>>(part, (int)(grid.x * grid.y), W, H, lambda, loss_out, dE_out, a,
+                                        adam ? 1 : 0);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P, cudaStream_t s)
+{
+    int blocks = (int)std::min<int64_t>(8 * 152, (P + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    k_apply_exposure<<<blocks, 256, 0, s>>>(src, dst, P, E[0], E[1], E[2], E[3], E[4], E[5], E[6], E[7],
+                                            E[8], E[9], E[10], E[11]);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+}  // namespace gl

@@ -1,0 +1,372 @@
+// gl_params.cu -- backward of the projection and colour (Eq. 1-3, SH) from the
+// per-instance screen-space gradients to every Gaussian attribute and to the
+// camera pose, and the fused (sparse) Adam update (Sec. III-D 2).
+//
+// One thread per Gaussian.  It sums the gradients of its (Gaussian, tile)
+// instances -- contiguous, because instances are emitted per Gaussian --
+// recomputes the forward geometry in registers, applies the chain rule and
+// either writes the gradients (differentiable API) or updates the parameters
+// and both Adam moments in place, so the 59-float gradient never reaches
+// memory on the optimisation path.
+#include "gl_internal.h"
+
+#include <algorithm>
+
+namespace gl {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNG = 10;
+
+struct Geo {
+    float x, y, z, iz;
+    float s[3], qn[4], qnorm, Rq[9], M[9], Sig[9];
+    float J00, J02, J11, J12;
+    bool clx, cly;
+    float T[6], a, b, c, A, B, C;
+    float o;
+    float dir[3], dnorm;
+};
+
+__device__ __forceinline__ void geometry(const float mu[3], const float ls[3], const float q[4],
+                                         float logit, const Cam& cam, Geo& G)
+{
+    const float* R = cam.R;
+    G.x = R[0] * mu[0] + R[1] * mu[1] + R[2] * mu[2] + cam.t[0];
+    G.y = R[3] * mu[0] + R[4] * mu[1] + R[5] * mu[2] + cam.t[1];
+    G.z = R[6] * mu[0] + R[7] * mu[1] + R[8] * mu[2] + cam.t[2];
+    G.iz = 1.0f / G.z;
+    for (int i = 0; i < 3; i++) G.s[i] = expf(ls[i]);
+    float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    G.qnorm = sqrtf(qq);
+    float inv = 1.0f / G.qnorm;
+    for (int i = 0; i < 4; i++) G.qn[i] = q[i] * inv;
+    const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+    G.Rq[0] = 1.f - 2.f * (y * y + z * z); G.Rq[1] = 2.f * (x * y - w * z); G.Rq[2] = 2.f * (x * z + w * y);
+    G.Rq[3] = 2.f * (x * y + w * z); G.Rq[4] = 1.f - 2.f * (x * x + z * z); G.Rq[5] = 2.f * (y * z - w * x);
+    G.Rq[6] = 2.f * (x * z - w * y); G.Rq[7] = 2.f * (y * z + w * x); G.Rq[8] = 1.f - 2.f * (x * x + y * y);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) G.M[i * 3 + j] = G.Rq[i * 3 + j] * G.s[j];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            G.Sig[i * 3 + j] = G.M[i * 3] * G.M[j * 3] + G.M[i * 3 + 1] * G.M[j * 3 + 1] + G.M[i * 3 + 2] * G.M[j * 3 + 2];
+    const float limx = kJacClamp * (0.5f * (float)cam.W / cam.fx);
+    const float limy = kJacClamp * (0.5f * (float)cam.H / cam.fy);
+    const float xz = G.x * G.iz, yz = G.y * G.iz;
+    G.clx = xz < -limx || xz > limx;
+    G.cly = yz < -limy || yz > limy;
+    const float cxz = fminf(fmaxf(xz, -limx), limx), cyz = fminf(fmaxf(yz, -limy), limy);
+    G.J00 = cam.fx * G.iz;
+    G.J02 = -cam.fx * cxz * G.iz;
+    G.J11 = cam.fy * G.iz;
+    G.J12 = -cam.fy * cyz * G.iz;
+    for (int k = 0; k < 3; k++) {
+        G.T[k] = G.J00 * R[k] + G.J02 * R[6 + k];
+        G.T[3 + k] = G.J11 * R[3 + k] + G.J12 * R[6 + k];
+    }
+    float U[6];
+    for (int i = 0; i < 2; i++)
+        for (int k = 0; k < 3; k++)
+            U[i * 3 + k] = G.T[i * 3] * G.Sig[k] + G.T[i * 3 + 1] * G.Sig[3 + k] + G.T[i * 3 + 2] * G.Sig[6 + k];
+    G.a = U[0] * G.T[0] + U[1] * G.T[1] + U[2] * G.T[2] + kDilation;
+    G.b = U[0] * G.T[3] + U[1] * G.T[4] + U[2] * G.T[5];
+    G.c = U[3] * G.T[3] + U[4] * G.T[4] + U[5] * G.T[5] + kDilation;
+    const float idet = 1.0f / (G.a * G.c - G.b * G.b);
+    G.A = G.c * idet;
+    G.B = -G.b * idet;
+    G.C = G.a * idet;
+    G.o = 1.0f / (1.0f + expf(-logit));
+    const float cw0 = -(R[0] * cam.t[0] + R[3] * cam.t[1] + R[6] * cam.t[2]);
+    const float cw1 = -(R[1] * cam.t[0] + R[4] * cam.t[1] + R[7] * cam.t[2]);
+    const float cw2 = -(R[2] * cam.t[0] + R[5] * cam.t[1] + R[8] * cam.t[2]);
+    const float d0 = mu[0] - cw0, d1 = mu[1] - cw1, d2 = mu[2] - cw2;
+    G.dnorm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    const float idn = 1.0f / G.dnorm;
+    G.dir[0] = d0 * idn; G.dir[1] = d1 * idn; G.dir[2] = d2 * idn;
+}
+
+__device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, float lr, const AdamArgs& a)
+{
+    m = a.b1 * m + (1.0f - a.b1) * g;
+    v = a.b2 * v + (1.0f - a.b2) * g * g;
+    p -= lr * (m / a.bc1) / (sqrtf(v / a.bc2) + a.eps);
+}
+
+template <int DEG, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const uint32_t* __restrict__ touched,
+             const uint32_t* __restrict__ dup_off, const float* __restrict__ igrad, GMut out,
+             AdamArgs ad, float* __restrict__ pose_part)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    const bool valid = g < p.n;
+    const bool vis = valid && radius[g] > 0;
+
+    float gm[3] = {0, 0, 0}, gl3[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glg = 0.0f;
+    float grgb[3] = {0, 0, 0};
+    float Y[16];
+    for (int k = 0; k < 16; k++) Y[k] = 0.0f;
+
+    if (vis) {
+        float mu[3] = {p.means[3 * g], p.means[3 * g + 1], p.means[3 * g + 2]};
+        float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
+        const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
+        float q[4] = {q4.x, q4.y, q4.z, q4.w};
+        Geo G;
+        geometry(mu, ls, q, p.logits[g], cam, G);
+
+        // screen-space gradients of this Gaussian: sum over its instances
+        float s[kNG];
+        for (int k = 0; k < kNG; k++) s[k] = 0.0f;
+        const uint32_t n_i = touched[g];
+        const float* src = igrad + (size_t)dup_off[g] * kNG;
+        for (uint32_t i = 0; i < n_i; i++)
+            for (int k = 0; k < kNG; k++) s[k] += src[(size_t)i * kNG + k];
+        const float du = -G.A * s[4] - G.B * s[5];
+        const float dv = -G.C * s[5] - G.B * s[4];
+        const float dA = -0.5f * s[6], dB = -s[7], dC = -0.5f * s[8];
+        const float dop = s[3] / G.o;
+        const float dz = s[9];
+
+        // opacity
+        glg = dop * G.o * (1.0f - G.o);
+
+        // colour -> SH and view direction (clamped channels pass no gradient)
+        sh_eval<DEG>(G.dir[0], G.dir[1], G.dir[2], Y);
+        const float* sh = p.sh + (size_t)g * K * 3;
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < K; k++)
+            for (int c = 0; c < 3; c++) raw[c] += Y[k] * sh[3 * k + c];
+        for (int c = 0; c < 3; c++) grgb[c] = raw[c] < 0.0f ? 0.0f : s[c];
+        float gdir[3] = {0, 0, 0};
+        if (DEG > 0) {
+            float dY[16][3];
+            sh_grad<DEG>(G.dir[0], G.dir[1], G.dir[2], dY);
+            for (int k = 1; k < K; k++) {
+                const float cf = sh[3 * k] * grgb[0] + sh[3 * k + 1] * grgb[1] + sh[3 * k + 2] * grgb[2];
+                gdir[0] += cf * dY[k][0]; gdir[1] += cf * dY[k][1]; gdir[2] += cf * dY[k][2];
+            }
+        }
+        const float dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
+        float gdu[3];
+        for (int j = 0; j < 3; j++) gdu[j] = (gdir[j] - G.dir[j] * dd) / G.dnorm;
+        for (int j = 0; j < 3; j++) gm[j] += gdu[j];
+        const float* R = cam.R;
+        for (int i = 0; i < 3; i++) pose[i] += R[i * 3] * gdu[0] + R[i * 3 + 1] * gdu[1] + R[i * 3 + 2] * gdu[2];
+
+        // conic -> Sigma' (a, b, c), written with the conic to avoid det^2
+        const float A = G.A, B = G.B, C = G.C;
+        const float ga = -A * A * dA - A * B * dB - B * B * dC;
+        const float gb = -2.f * A * B * dA - (A * C + B * B) * dB - 2.f * B * C * dC;
+        const float gc = -B * B * dA - B * C * dB - C * C * dC;
+        const float Gm[4] = {ga, 0.5f * gb, 0.5f * gb, gc};
+        // Sigma' = T Sigma T^T
+        float gSig[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const float t0i = G.T[i], t1i = G.T[3 + i], t0j = G.T[j], t1j = G.T[3 + j];
+                gSig[i * 3 + j] = t0i * (Gm[0] * t0j + Gm[1] * t1j) + t1i * (Gm[2] * t0j + Gm[3] * t1j);
+            }
+        float TS[6];
+        for (int r = 0; r < 2; r++)
+            for (int j = 0; j < 3; j++)
+                TS[r * 3 + j] = G.T[r * 3] * G.Sig[j] + G.T[r * 3 + 1] * G.Sig[3 + j] + G.T[r * 3 + 2] * G.Sig[6 + j];
+        float gT[6];
+        for (int r = 0; r < 2; r++)
+            for (int j = 0; j < 3; j++)
+                gT[r * 3 + j] = 2.f * (Gm[r * 2] * TS[j] + Gm[r * 2 + 1] * TS[3 + j]);
+        // Sigma = M M^T, M = Rq diag(s)
+        float gRq[9];
+        for (int j = 0; j < 3; j++) {
+            float acc = 0.0f;
+            for (int i = 0; i < 3; i++) {
+                const float gMij = 2.f * (gSig[i * 3] * G.M[j] + gSig[i * 3 + 1] * G.M[3 + j] + gSig[i * 3 + 2] * G.M[6 + j]);
+                acc += gMij * G.Rq[i * 3 + j];
+                gRq[i * 3 + j] = gMij * G.s[j];
+            }
+            gl3[j] = acc * G.s[j];
+        }
+        {
+            const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+            float gn[4];
+            gn[0] = 2.f * (-z * gRq[1] + y * gRq[2] + z * gRq[3] - x * gRq[5] - y * gRq[6] + x * gRq[7]);
+            gn[1] = 2.f * (y * gRq[1] + z * gRq[2] + y * gRq[3] - 2.f * x * gRq[4] - w * gRq[5]
+                           + z * gRq[6] + w * gRq[7] - 2.f * x * gRq[8]);
+            gn[2] = 2.f * (-2.f * y * gRq[0] + x * gRq[1] + w * gRq[2] + x * gRq[3] + z * gRq[5]
+                           - w * gRq[6] + z * gRq[7] - 2.f * y * gRq[8]);
+            gn[3] = 2.f * (-2.f * z * gRq[0] - w * gRq[1] + x * gRq[2] + w * gRq[3] - 2.f * z * gRq[4]
+                           + y * gRq[5] + x * gRq[6] + y * gRq[7]);
+            const float qd = w * gn[0] + x * gn[1] + y * gn[2] + z * gn[3];
+            for (int i = 0; i < 4; i++) gq[i] = (gn[i] - G.qn[i] * qd) / G.qnorm;
+        }
+        // T = J W
+        float gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+        for (int k = 0; k < 3; k++) {
+            gJ00 += gT[k] * R[k];
+            gJ02 += gT[k] * R[6 + k];
+            gJ11 += gT[3 + k] * R[3 + k];
+            gJ12 += gT[3 + k] * R[6 + k];
+        }
+        // camera-space mean through mu', J and the depth output
+        const float x = G.x, y = G.y, z = G.z, iz = G.iz, iz2 = iz * iz;
+        float gmc[3];
+        gmc[0] = du * cam.fx * iz;
+        gmc[1] = dv * cam.fy * iz;
+        gmc[2] = -(du * cam.fx * x + dv * cam.fy * y) * iz2 + dz;
+        gmc[2] += -(gJ00 * cam.fx + gJ11 * cam.fy) * iz2;
+        if (!G.clx) { gmc[0] += -gJ02 * cam.fx * iz2; gmc[2] += 2.f * gJ02 * cam.fx * x * iz2 * iz; }
+        else { gmc[2] += -gJ02 * G.J02 * iz; }
+        if (!G.cly) { gmc[1] += -gJ12 * cam.fy * iz2; gmc[2] += 2.f * gJ12 * cam.fy * y * iz2 * iz; }
+        else { gmc[2] += -gJ12 * G.J12 * iz; }
+        for (int j = 0; j < 3; j++) gm[j] += R[j] * gmc[0] + R[3 + j] * gmc[1] + R[6 + j] * gmc[2];
+        pose[0] += gmc[0]; pose[1] += gmc[1]; pose[2] += gmc[2];
+        pose[3] += y * gmc[2] - z * gmc[1];
+        pose[4] += z * gmc[0] - x * gmc[2];
+        pose[5] += x * gmc[1] - y * gmc[0];
+        // dW = phi^ W: P = W gW^T with gW = J^T gT
+        float gW[9];
+        for (int k = 0; k < 3; k++) {
+            gW[0 * 3 + k] = G.J00 * gT[k];
+            gW[1 * 3 + k] = G.J11 * gT[3 + k];
+            gW[2 * 3 + k] = G.J02 * gT[k] + G.J12 * gT[3 + k];
+        }
+        float P[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                P[i * 3 + j] = R[i * 3] * gW[j * 3] + R[i * 3 + 1] * gW[j * 3 + 1] + R[i * 3 + 2] * gW[j * 3 + 2];
+        pose[3] += P[5] - P[7];
+        pose[4] += P[6] - P[2];
+        pose[5] += P[1] - P[3];
+    }
+
+    if (MODE == 0) {
+        if (valid) {
+            for (int j = 0; j < 3; j++) { out.means[3 * g + j] = gm[j]; out.log_scales[3 * g + j] = gl3[j]; }
+            reinterpret_cast<float4*>(out.quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+            out.logits[g] = glg;
+            float* o = out.sh + (size_t)g * K * 3;
+            for (int k = 0; k < K; k++)
+                for (int c = 0; c < 3; c++) o[3 * k + c] = Y[k] * grgb[c];
+        }
+        if (pose_part) {
+            __shared__ float red[6][kThreads / 32];
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            for (int k = 0; k < 6; k++) {
+                float v = pose[k];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+                if (lane == 0) red[k][w] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 6) {
+                float v = 0.0f;
+                for (int ww = 0; ww < kThreads / 32; ww++) v += red[threadIdx.x][ww];
+                pose_part[blockIdx.x * 6 + threadIdx.x] = v;
+            }
+        }
+    } else {
+        if (!valid || (ad.sparse && !vis)) return;
+        // p (out) shares storage with the parameters read above
+        for (int j = 0; j < 3; j++) {
+            adam1(out.means[3 * g + j], ad.m.means[3 * g + j], ad.v.means[3 * g + j], gm[j], ad.lr_pos, ad);
+            adam1(out.log_scales[3 * g + j], ad.m.log_scales[3 * g + j], ad.v.log_scales[3 * g + j], gl3[j], ad.lr_scale, ad);
+        }
+        {
+            float4 pq = reinterpret_cast<float4*>(out.quats)[g];
+            float4 mq = reinterpret_cast<float4*>(ad.m.quats)[g];
+            float4 vq = reinterpret_cast<float4*>(ad.v.quats)[g];
+            adam1(pq.x, mq.x, vq.x, gq[0], ad.lr_rot, ad);
+            adam1(pq.y, mq.y, vq.y, gq[1], ad.lr_rot, ad);
+            adam1(pq.z, mq.z, vq.z, gq[2], ad.lr_rot, ad);
+            adam1(pq.w, mq.w, vq.w, gq[3], ad.lr_rot, ad);
+            reinterpret_cast<float4*>(out.quats)[g] = pq;
+            reinterpret_cast<float4*>(ad.m.quats)[g] = mq;
+            reinterpret_cast<float4*>(ad.v.quats)[g] = vq;
+        }
+        adam1(out.logits[g], ad.m.logits[g], ad.v.logits[g], glg, ad.lr_op, ad);
+        float* ps = out.sh + (size_t)g * K * 3;
+        float* ms = ad.m.sh + (size_t)g * K * 3;
+        float* vs = ad.v.sh + (size_t)g * K * 3;
+        if ((K * 3) % 4 == 0) {
+#pragma unroll
+            for (int i = 0; i < K * 3 / 4; i++) {
+                float4 pp = reinterpret_cast<float4*>(ps)[i];
+                float4 mm = reinterpret_cast<float4*>(ms)[i];
+                float4 vv = reinterpret_cast<float4*>(vs)[i];
+                float* pa = &pp.x; float* ma = &mm.x; float* va = &vv.x;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int idx = 4 * i + e, k = idx / 3, c = idx % 3;
+                    adam1(pa[e], ma[e], va[e], Y[k] * grgb[c], k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+                }
+                reinterpret_cast<float4*>(ps)[i] = pp;
+                reinterpret_cast<float4*>(ms)[i] = mm;
+                reinterpret_cast<float4*>(vs)[i] = vv;
+            }
+        } else {
+            for (int k = 0; k < K; k++)
+                for (int c = 0; c < 3; c++)
+                    adam1(ps[3 * k + c], ms[3 * k + c], vs[3 * k + c], Y[k] * grgb[c],
+                          k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+        }
+    }
+}
+
+__global__ void k_pose_reduce(const float* __restrict__ part, int npart, float* __restrict__ out6)
+{
+    // one warp per component, fixed summation order
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= 6) return;
+    double acc = 0.0;
+    for (int i = lane; i < npart; i += 32) acc += part[i * 6 + k];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if (lane == 0) out6[k] = (float)acc;
+}
+
+template <int MODE>
+gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* pose_part, cudaStream_t s)
+{
+    if (p.n == 0) return GL_OK;
+    const unsigned grid = (unsigned)((p.n + kThreads - 1) / kThreads);
+#define GL_PB(D_)                                                                            \
+    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.cam, v.radius.as<int>(),            \
+                                                     v.touched.as<uint32_t>(), v.dup_off.as<uint32_t>(), \
+                                                     v.igrad.as<float>(), o, a, pose_part)
+    switch (p.deg) {
+        case 0: GL_PB(0); break;
+        case 1: GL_PB(1); break;
+        case 2: GL_PB(2); break;
+        case 3: GL_PB(3); break;
+        default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
+    }
+#undef GL_PB
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+}  // namespace
+
+int pose_partials_needed(int64_t n) { return (int)std::max<int64_t>(1, (n + kThreads - 1) / kThreads); }
+
+gl_status params_backward(View& v, const GParams& p, GMut grad, float* pose_part, int npart, cudaStream_t s)
+{
+    (void)npart;
+    AdamArgs a{};
+    return launch<0>(v, p, grad, a, pose_part, s);
+}
+
+gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cudaStream_t s)
+{
+    return launch<1>(v, p, upd, a, nullptr, s);
+}
+
+gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s)
+{
+    k_pose_reduce<<<1, 192, 0, s>>>(part, npart, out6);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+}  // namespace gl
