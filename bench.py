@@ -1,0 +1,449 @@
+"""Benchmark: map optimisation steps/s on the outdoor LiDAR-camera workload.
+
+Workload: a synthetic street scene shaped like the paper's LiDAR-camera
+sequences (Sec. IV-A): 900,000 coloured LiDAR + visual points from a 100-pose
+trajectory initialised as Gaussians (Sec. III-C 1) plus 100,000 sky Gaussians,
+i.e. 1,000,000 Gaussians with SH degree 3, optimised against 1280x1024 keyframe
+images with per-image exposure.  One step = forward, exposure-compensated
+L1 + D-SSIM loss, backward and sparse Adam for one keyframe view (plain
+single-view path, Sec. III-C 3).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded crop of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "optimise steps/s (plain single-view), 1M Gaussians 1280x1024"
+UNIT = "steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="250k Gaussians at 640x512 (profiling case)")
+    ap.add_argument("--updates", type=int, default=8, help="keyframe updates for the latency figure")
+    ap.add_argument("--update-steps", type=int, default=100, help="optimise steps per keyframe update (K)")
+    ap.add_argument("--keyframes", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas: every rank runs the whole workload)
+# ----------------------------------------------------------------------------
+def dist_setup(n):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def workload_sizes(small):
+    if small:
+        return dict(n_points=225_000, n_sky=25_000, W=640, H=512, f=500.0)
+    return dict(n_points=900_000, n_sky=100_000, W=1280, H=1024, f=1000.0)
+
+
+def build_map(binding, torch, small, n_kf):
+    from paper_2404_06926_gb300 import scenes
+    ws = workload_sizes(small)
+    sc = scenes.Outdoor(seed=2, width=ws["W"], img_height=ws["H"], f=ws["f"])
+    xyz, rgb, idx = sc.point_cloud(ws["n_points"])
+    cfg = binding.default_config(n_sky=ws["n_sky"], sh_degree=3, tile_size=16,
+                                 capacity_hint=ws["n_points"] + ws["n_sky"] + 200_000)
+    m = binding.Map(cfg)
+    # initialise from every capture pose's points (scale d/f with d in that pose)
+    for i, s in enumerate(sc.traj_x):
+        sel = np.nonzero(idx == i)[0]
+        if len(sel):
+            m.add_points(np.ascontiguousarray(xyz[sel]), np.ascontiguousarray(rgb[sel]), sc.camera_at(s),
+                         use_mask=False, kind=0)
+    # keyframes spread along the trajectory
+    pos = np.linspace(sc.traj_x[2], sc.traj_x[-12], n_kf)
+    cams, imgs = [], []
+    for k, s in enumerate(pos):
+        cam = sc.camera_at(float(s))
+        img = sc.target_image_torch(cam, device="cuda")
+        m.add_keyframe(k, cam, img)
+        cams.append(cam)
+        imgs.append(img)
+    return sc, m, cams, imgs, ws
+
+
+def algorithmic_bytes(st, n_total):
+    """Algorithmic bytes per launch of each phase (fp32, SH degree 3)."""
+    N, Nv, I, P = n_total, st["n_visible"], st["n_instances"], st["pixels"]
+    return {
+        "preprocess": N * 16 + Nv * (220 + 52),
+        "depth_sort": N * 16,
+        "scan_duplicate": N * 8 + I * 12,
+        "tile_sort": I * 16,
+        "tile_ranges": I * 8,
+        "raster_forward": I * 40 + P * 28,
+        "loss": P * 36,
+        "raster_backward": I * 40 + P * 20 + Nv * 36,
+        "params_adam": Nv * (236 + 472 + 40 + 236 + 472),
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gl_raster.cu", "gl_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2404_06926_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch_full_size")
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded crop of the same view
+# ----------------------------------------------------------------------------
+def oracle_step_on_crop(params, cam, target, E, crop):
+    import oracle
+    cw, ch = crop
+    x0, y0 = cam["width"] // 2 - cw // 2, cam["height"] // 2 - ch // 2
+    c2 = dict(cam, width=cw, height=ch, cx=cam["cx"] - x0, cy=cam["cy"] - y0)
+    tgt = np.ascontiguousarray(target[y0:y0 + ch, x0:x0 + cw])
+    t0 = time.perf_counter()
+    pre = oracle.preprocess(params, c2, 16)
+    t1 = time.perf_counter()
+    bins = oracle.bin_instances(pre, c2)
+    img = oracle.render(pre, bins, c2)
+    L = oracle.loss(img["color"], tgt, E)
+    oracle.backward(params, c2, pre, bins, L["dL_dC"])
+    t2 = time.perf_counter()
+    scale = (cam["width"] * cam["height"]) / float(cw * ch)
+    full = (t1 - t0) + scale * (t2 - t1)
+    return full, t2 - t0
+
+
+def cpu_baseline(m, cams, imgs, crop, reps=1):
+    import oracle
+    oracle.build()
+    params = {k: v.astype(np.float64) for k, v in m.get_params().items()}
+    E = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
+    fulls, walls = [], []
+    for r in range(reps):
+        k = r % len(cams)
+        full, wall = oracle_step_on_crop(params, cams[k], imgs[k].cpu().numpy(), E, crop)
+        fulls.append(full)
+        walls.append(wall)
+    return 1.0 / float(np.mean(fulls)), float(np.sum(walls))
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    """The oracle as it stands, on host cores, on a bounded crop per step."""
+    rank, ws, local, dist = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import oracle
+    from paper_2404_06926_gb300 import scenes
+    oracle.build()
+    wsz = workload_sizes(args.small)
+    sc = scenes.Outdoor(seed=2, width=wsz["W"], img_height=wsz["H"], f=wsz["f"])
+    xyz, rgb, idx = sc.point_cloud(wsz["n_points"])
+    deps = np.zeros(len(xyz), np.float32)
+    for i, s in enumerate(sc.traj_x):
+        sel = idx == i
+        _, d, _ = oracle.expand_mask(xyz[sel], sc.camera_at(s), None)
+        deps[sel] = d
+    p = oracle.init_gaussians(xyz, rgb, deps, wsz["f"])
+    sxyz, nn = oracle.sky_points(wsz["n_sky"], 1e4, seed=0x5eed)
+    ps = oracle.init_gaussians(sxyz, np.ones_like(sxyz), None, wsz["f"], opacity=0.7, scale=nn)
+    params = {k: np.concatenate([p[k], ps[k]]).astype(np.float64) for k in p}
+    cam = sc.camera_at(float(sc.traj_x[30]))
+    target = sc.target_image(cam)[0]
+    E = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
+    crop = (160, 128)
+    for _ in range(args.warmup):
+        oracle_step_on_crop(params, cam, target, E, crop)
+    t0 = time.perf_counter()
+    fulls = []
+    for _ in range(args.steps):
+        fulls.append(oracle_step_on_crop(params, cam, target, E, crop)[0])
+    wall = time.perf_counter() - t0
+    v = 1.0 / float(np.mean(fulls))
+    sample = (f"oracle (C, 1 thread) one step on a {crop[0]}x{crop[1]} centre crop of the 1280x1024 view "
+              f"with all {len(params['logits'])} Gaussians preprocessed; steps/s extrapolated as "
+              f"1/(t_preprocess + (full pixels / crop pixels) * t_rest)")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "outdoor LiDAR street, 1M Gaussians, SH3, 1280x1024, plain single-view step",
+                      "parallelism": "replicas"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "wall_s": wall},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, ws, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2404_06926_gb300 import binding
+    n_kf = args.keyframes
+    sc, m, cams, imgs, wsz = build_map(binding, torch, args.small, n_kf)
+    n_total = len(m)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(100 + rank)
+    order = rng.integers(0, n_kf, size=args.warmup + args.steps + 1)
+
+    def step(k, img=None, want=False):
+        return m.optimize_step([(int(k), cams[int(k)], img)], want_loss=want)
+
+    for i in range(args.warmup):
+        step(order[i])
+    torch.cuda.synchronize()
+    m.set_timing(True)
+    launches0 = binding.kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(order[args.warmup + i])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    launches = binding.kernel_launches() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    st = m.stats()
+    m.set_timing(False)
+    ms_max = max_over_ranks(ms_total, dist)
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned host target in,
+    # loss out, every step
+    e2e = None
+    if not args.no_e2e:
+        host_imgs = [im.cpu().pin_memory() for im in imgs]
+        for i in range(2):
+            step(order[i], host_imgs[order[i]], True)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            k = order[args.warmup + i]
+            step(k, host_imgs[k], True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e_ms = max_over_ranks((t1 - t0) * 1e3, dist)
+        e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(imgs[0].numel() * 4), "d2h_bytes_per_step": 4}
+
+    # keyframe-update latency (Sec. III-C 2-3): expansion from a new frame's
+    # points through the opacity mask, then K optimise steps over random keyframes
+    lat = []
+    if args.updates > 0:
+        for u in range(args.updates):
+            s_new = float(sc.traj_x[5 + (u * 7) % 80] + 0.5)
+            pts, col = sc.lidar_sweep(s_new, rng=np.random.default_rng(1000 + u))
+            vp, vc = sc.visual_points(s_new, 400, rng=np.random.default_rng(2000 + u))
+            pts = np.ascontiguousarray(np.concatenate([pts, vp]))
+            col = np.ascontiguousarray(np.concatenate([col, vc]))
+            ks = rng.integers(0, n_kf, size=args.update_steps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.add_points(pts, col, sc.camera_at(s_new), use_mask=True, kind=0)
+            for k in ks:
+                step(k)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t0) * 1e3)
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    hbm_peak, sm_max, peak_src = load_peaks()
+    phases = st["phases"]
+    byts = algorithmic_bytes(st, n_total)
+    per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in phases.items()}
+    dom = max((k for k in per_launch if k in byts), key=lambda k: phases[k][0])
+    t_launch = per_launch[dom] / 1e3
+    kp = st["sum_contrib"]
+    flops_per_pair = {"raster_forward": 20.0, "raster_backward": 70.0}
+    if dom in flops_per_pair:
+        peak = fp32_peak_tflops(sm_max)
+        ach = flops_per_pair[dom] * kp / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": ncu_traffic(dom), "kernel": dom,
+                "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "hbm": {"achieved": byts[dom] / t_launch / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": byts[dom] / t_launch / 1e9 / hbm_peak, "peak_source": peak_src}}
+    else:
+        ach = byts[dom] / t_launch / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": ncu_traffic(dom), "kernel": dom, "peak_source": peak_src}
+    kernels = {k: {"ms_per_launch": per_launch[k], "share": phases[k][0] / max(1e-9, sum(v[0] for v in phases.values())),
+                   "gbs": (byts[k] / (per_launch[k] / 1e3) / 1e9) if (k in byts and per_launch[k] > 0) else None}
+               for k in phases if phases[k][1]}
+
+    cpu = None
+    if not args.no_cpu_baseline and args.gpus == 1 and not args.small:
+        crop = (320, 256)
+        v, wall = cpu_baseline(m, cams, imgs, crop)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle step on a {crop[0]}x{crop[1]} centre crop of a 1280x1024 keyframe "
+                         f"with all {n_total} Gaussians preprocessed; steps/s extrapolated as "
+                         f"1/(t_preprocess + 16 * t_rest); wall {wall:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (procedural LiDAR-camera street scene, seeded)",
+        "config": {"workload": ("outdoor LiDAR street, %d Gaussians (%d LiDAR+visual, %d sky), SH3, %dx%d, "
+                                "plain single-view step" % (n_total, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"])),
+                   "n_gaussians": n_total, "width": wsz["W"], "height": wsz["H"], "tile": 16,
+                   "keyframes": n_kf, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (params + Adam moments %.2f GB)" % (n_total * 708 / 1e9),
+                   "visible": st["n_visible"], "instances": st["n_instances"],
+                   "pairs_backward": st["sum_contrib"]},
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "keyframe_update": ({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "updates": len(lat), "steps_per_update": args.update_steps,
+                             "map_size_after": len(m)} if lat else None),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -194,6 +194,39 @@ GL_API gl_status gl_map_get_moments(gl_map* map, int32_t which, gl_gaussians* ou
 GL_API gl_status gl_map_get_exposure(gl_map* map, int64_t id, float* E34_out);
 
 /* ---------------------------------------------------------------------- */
+/* Instrumentation (not in the paper, which reports only run times,      */
+/* Table II): per-phase CUDA-event timers and counts of the last view.    */
+/* ---------------------------------------------------------------------- */
+#define GL_NUM_PHASES 10
+
+typedef struct {
+    int64_t n_gaussians;   /* map size                                          */
+    int64_t n_visible;     /* Gaussians with a non-zero screen radius, last view */
+    int64_t n_instances;   /* (Gaussian, tile) instances of the last view        */
+    int64_t sum_contrib;   /* sum over pixels of the contributor count, i.e. the
+                              (pixel, Gaussian) pairs the backward walks         */
+    int64_t pixels;        /* pixels of the last view                           */
+    int64_t steps;         /* optimisation steps taken (Adam step counter)      */
+    double phase_ms[GL_NUM_PHASES];     /* summed device time per phase         */
+    int64_t phase_calls[GL_NUM_PHASES]; /* timed launches per phase             */
+} gl_stats;
+
+/* Turn the per-phase timers on (1) or off (0); either way they restart from
+ * zero.  When on, every phase of every call is bracketed by CUDA events on
+ * the map's stream (no extra synchronisation). */
+GL_API gl_status gl_map_set_timing(gl_map* map, int32_t enable);
+
+/* Counts of the last rendered view and the accumulated phase times.
+ * Synchronises the map's stream. */
+GL_API gl_status gl_map_get_stats(gl_map* map, gl_stats* out);
+
+/* Name of phase i (0 <= i < GL_NUM_PHASES), e.g. "raster_backward". */
+GL_API const char* gl_phase_name(int32_t i);
+
+/* Number of kernels this library has launched in this process so far. */
+GL_API int64_t gl_kernel_launch_count(void);
+
+/* ---------------------------------------------------------------------- */
 /* Stateless differentiable API (one view), for autograd wrappers and     */
 /* tests.  A gl_ctx owns the scratch of one forward/backward pair.         */
 /* ---------------------------------------------------------------------- */

@@ -51,6 +51,15 @@ class Config(C.Structure):
                 ("adam_eps", C.c_float), ("capacity_hint", C.c_int64)]
 
 
+NUM_PHASES = 10
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_gaussians", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
+                ("sum_contrib", C.c_int64), ("pixels", C.c_int64), ("steps", C.c_int64),
+                ("phase_ms", C.c_double * NUM_PHASES), ("phase_calls", C.c_int64 * NUM_PHASES)]
+
+
 class Gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("reserved", C.c_int32),
                 ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
@@ -89,6 +98,10 @@ def lib():
             "gl_ctx_num_instances": ([P, P], i32),
             "gl_ctx_get_instances": ([P, P, P, P], i32),
             "gl_ctx_get_pixel_state": ([P, P, P], i32),
+            "gl_map_set_timing": ([P, i32], i32),
+            "gl_map_get_stats": ([P, P], i32),
+            "gl_phase_name": ([i32], C.c_char_p),
+            "gl_kernel_launch_count": ([], i64),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -249,6 +262,11 @@ class Ctx:
         return T, n
 
 
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().gl_kernel_launch_count())
+
+
 def keyframe(kid: int, cam: dict, image=None) -> Keyframe:
     k = Keyframe()
     k.id = int(kid)
@@ -339,6 +357,18 @@ class Map:
         out = self._alloc(n)
         g = gaussians(out, n)
         check(lib().gl_map_get_moments(self._h, int(which), C.byref(g)))
+        return out
+
+    def set_timing(self, on: bool):
+        check(lib().gl_map_set_timing(self._h, int(bool(on))))
+
+    def stats(self) -> dict:
+        st = Stats()
+        check(lib().gl_map_get_stats(self._h, C.byref(st)))
+        out = {k: getattr(st, k) for k in ("n_gaussians", "n_visible", "n_instances", "sum_contrib",
+                                           "pixels", "steps")}
+        out["phases"] = {lib().gl_phase_name(i).decode(): (st.phase_ms[i], st.phase_calls[i])
+                         for i in range(NUM_PHASES)}
         return out
 
     def exposure(self, kid: int):

@@ -354,6 +354,23 @@ __global__ void k_export(const uint32_t* __restrict__ stile, const uint32_t* __r
     }
 }
 
+__global__ void k_view_counts(const int* __restrict__ radius, int64_t n, const uint32_t* __restrict__ ncon,
+                              int64_t P, unsigned long long* out)
+{
+    unsigned long long vis = 0, sc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) vis += radius[i] > 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += stride) sc += ncon[i];
+    for (int off = 16; off > 0; off >>= 1) {
+        vis += __shfl_xor_sync(kFull, vis, off);
+        sc += __shfl_xor_sync(kFull, sc, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, vis);
+        atomicAdd(out + 1, sc);
+    }
+}
+
 int ceil_log2(int64_t x)
 {
     int b = 0;
@@ -375,6 +392,7 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
         k_sort_scan<<<1, 1024, 0, s>>>(hist.as<uint32_t>(), 256 * nblocks);
         k_sort_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, nblocks,
                                                         hist.as<uint32_t>());
+        count_launches(3);
         std::swap(ki, ko);
         std::swap(vi, vo);
     }
@@ -384,12 +402,32 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
     return GL_OK;
 }
 
+gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s)
+{
+    *n_visible = 0;
+    *sum_contrib = 0;
+    const int64_t P = (int64_t)v.W * v.H;
+    if (v.n == 0 && P == 0) return GL_OK;
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(v.count.as<uint64_t>() + 4);
+    GL_CUDA_TRY(cudaMemsetAsync(d, 0, 16, s));
+    k_view_counts<<<4 * 152, 256, 0, s>>>(v.radius.as<int>(), v.n, v.ncon.as<uint32_t>(), v.ncon.p ? P : 0, d);
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    unsigned long long h[2];
+    GL_CUDA_TRY(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, s));
+    GL_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_visible = (int64_t)h[0];
+    *sum_contrib = (int64_t)h[1];
+    return GL_OK;
+}
+
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s)
 {
     if (v.I == 0) return GL_OK;
     int blocks = (int)std::min<int64_t>(4 * 152, (v.I + 255) / 256);
     k_export<<<blocks, 256, 0, s>>>(v.sorted_tile, v.sorted_inst, v.iowner.as<uint32_t>(),
                                     v.rec0.as<float4>(), v.I, keys, vals);
+    count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -426,11 +464,15 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     if (n == 0) {
         v.I = 0;
         k_set_u64<<<1, 1, 0, s>>>(count, 0, 0);
+        count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());
         return GL_OK;
     }
     const int TX = v.TX, TY = v.TY;
     dim3 grid((unsigned)((n + kPreThreads - 1) / kPreThreads));
+    {
+    PhaseScope ps(v.prof, PH_PREPROCESS, s);
+    count_launches(1);
     switch (p.deg) {
         case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
         case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
@@ -439,18 +481,25 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
+    }
 
     // depth order of the Gaussians (culled ones carry key 0xffffffff and go last)
-    k_set_u64<<<1, 1, 0, s>>>(count + 2, (uint64_t)n, 0);
     uint32_t *sk, *sv;
-    GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
-                          v.gidx2.as<uint32_t>(), count + 2, n, 32, v.hist, &sk, &sv, s));
+    {
+        PhaseScope ps(v.prof, PH_DEPTH_SORT, s);
+        k_set_u64<<<1, 1, 0, s>>>(count + 2, (uint64_t)n, 0);
+        count_launches(1);
+        GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
+                              v.gidx2.as<uint32_t>(), count + 2, n, 32, v.hist, &sk, &sv, s));
+    }
     v.sorted_g = sv;
 
     // instance offsets in depth order
     const uint64_t cap = v.itile.bytes / 4;
+    PhaseScope ps_scan(v.prof, PH_SCAN_DUP, s);
     k_scan_count<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), n, v.bsum.as<uint64_t>());
     k_scan_top<<<1, 1024, 0, s>>>(v.bsum.as<uint64_t>(), nb, cap, count);
+    count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, 16, cudaMemcpyDeviceToHost, s));
     GL_CUDA_TRY(cudaStreamSynchronize(s));
@@ -473,7 +522,9 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
                                            v.bsum.as<uint64_t>(), n, TX, cap2, v.dup_off.as<uint32_t>(),
                                            v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.iowner.as<uint32_t>());
+    count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
+    ps_scan.close();
     if (I == 0) {
         v.sorted_tile = v.itile.as<uint32_t>();
         v.sorted_inst = v.ival.as<uint32_t>();
@@ -481,13 +532,20 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     }
     // stable sort of the instances by tile id
     const int tbits = std::max(1, ceil_log2(v.ntiles));
-    GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
-                          v.ival2.as<uint32_t>(), count, (int64_t)I, tbits, v.hist, &sk, &sv, s));
+    {
+        PhaseScope ps(v.prof, PH_TILE_SORT, s);
+        GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
+                              v.ival2.as<uint32_t>(), count, (int64_t)I, tbits, v.hist, &sk, &sv, s));
+    }
     v.sorted_tile = sk;
     v.sorted_inst = sv;
-    int rb = (int)std::min<uint64_t>(4 * 152, (I + 255) / 256);
-    k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
-    GL_CUDA_TRY(cudaGetLastError());
+    {
+        PhaseScope ps(v.prof, PH_RANGES, s);
+        int rb = (int)std::min<uint64_t>(4 * 152, (I + 255) / 256);
+        k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
+        count_launches(1);
+        GL_CUDA_TRY(cudaGetLastError());
+    }
     return GL_OK;
 }
 

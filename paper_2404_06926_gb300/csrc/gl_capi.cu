@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -24,6 +26,80 @@ thread_local std::string g_err;
 }
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+const char* kPhaseNames[PH_COUNT] = {"preprocess", "depth_sort", "scan_duplicate", "tile_sort",
+                                     "tile_ranges", "raster_forward", "loss", "raster_backward",
+                                     "params_adam", "expand"};
+}
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaEvent_t Prof::begin(cudaStream_t s)
+{
+    cudaEvent_t e;
+    if (npool > 0) e = pool[--npool];
+    else if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, s);
+    return e;
+}
+
+void Prof::end(int phase, cudaEvent_t a, cudaStream_t s)
+{
+    cudaEvent_t b;
+    if (npool > 0) b = pool[--npool];
+    else if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(b, s);
+    if (npend == cap) {
+        int nc = cap ? 2 * cap : 256;
+        Pending* np = static_cast<Pending*>(realloc(pend, sizeof(Pending) * nc));
+        if (!np) return;
+        pend = np;
+        cap = nc;
+    }
+    pend[npend++] = Pending{phase, a, b};
+}
+
+void Prof::harvest()
+{
+    for (int i = 0; i < npend; i++) {
+        float t = 0.f;
+        cudaEventSynchronize(pend[i].b);
+        if (cudaEventElapsedTime(&t, pend[i].a, pend[i].b) == cudaSuccess) {
+            ms[pend[i].phase] += t;
+            calls[pend[i].phase] += 1;
+        }
+        for (cudaEvent_t e : {pend[i].a, pend[i].b}) {
+            if (npool == poolcap) {
+                int nc = poolcap ? 2 * poolcap : 512;
+                cudaEvent_t* np = static_cast<cudaEvent_t*>(realloc(pool, sizeof(cudaEvent_t) * nc));
+                if (!np) { cudaEventDestroy(e); continue; }
+                pool = np;
+                poolcap = nc;
+            }
+            pool[npool++] = e;
+        }
+    }
+    npend = 0;
+}
+
+void Prof::reset()
+{
+    harvest();
+    for (int i = 0; i < PH_COUNT; i++) { ms[i] = 0; calls[i] = 0; }
+}
+
+void Prof::release()
+{
+    harvest();
+    for (int i = 0; i < npool; i++) cudaEventDestroy(pool[i]);
+    free(pool);
+    free(pend);
+    pool = nullptr;
+    pend = nullptr;
+    npool = poolcap = npend = cap = 0;
+}
 
 gl_status DevBuf::reserve(size_t need)
 {
@@ -353,6 +429,7 @@ struct gl_map {
     DevBuf flags, scan;
     float* h_loss = nullptr;
     std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
+    Prof prof;
 
     size_t row_floats(int which) const
     {
@@ -491,6 +568,7 @@ extern "C" gl_status gl_map_create(const gl_config* cfg, void* stream, gl_map** 
     m->deg = cfg->sh_degree;
     m->K = (m->deg + 1) * (m->deg + 1);
     m->ctx.stream = m->stream;
+    m->ctx.view.prof = &m->prof;
     GL_TRY(m->ctx.view.init());
     GL_CUDA_TRY(cudaMallocHost(&m->h_loss, 16));
     GL_TRY(m->loss_dev.reserve(16));
@@ -520,6 +598,7 @@ extern "C" gl_status gl_map_destroy(gl_map* m)
     m->flags.release(); m->scan.release();
     for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
     if (m->h_loss) cudaFreeHost(m->h_loss);
+    m->prof.release();
     delete m;
     return GL_OK;
 }
@@ -563,6 +642,7 @@ extern "C" gl_status gl_map_add_points(gl_map* m, const float* xyz, const float*
         opac = m->ctx.view.opac.as<float>();
     }
     int64_t added = 0;
+    PhaseScope ps(&m->prof, PH_EXPAND, m->stream);
     GMut none{};
     GL_TRY(expand_points(dx, dc, n, cam, opac, m->cfg.tau, use_mask ? 1 : 0, m->cfg.opacity_fg, m->K, none, 0, 0,
                          m->flags, m->scan, &added, m->stream));
@@ -655,8 +735,11 @@ extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32
     ea.lr = c.lr_exposure; ea.b1 = c.adam_b1; ea.b2 = c.adam_b2; ea.eps = c.adam_eps;
     ea.bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
     ea.bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
-    GL_TRY(photometric_loss(v.rgb.as<float>(), target, e, cam.W, cam.H, c.lambda_dssim, m->dLdC.as<float>(),
-                            m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), nullptr, &ea, m->stream));
+    {
+        PhaseScope ps(&m->prof, PH_LOSS, m->stream);
+        GL_TRY(photometric_loss(v.rgb.as<float>(), target, e, cam.W, cam.H, c.lambda_dssim, m->dLdC.as<float>(),
+                                m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), nullptr, &ea, m->stream));
+    }
     GL_TRY(raster_backward(v, m->dLdC.as<float>(), nullptr, nullptr, m->stream));
     AdamArgs a;
     a.m = gl_map::mut(m->mom1);
@@ -732,3 +815,39 @@ extern "C" gl_status gl_map_get_exposure(gl_map* m, int64_t id, float* E34_out)
     GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
     return GL_OK;
 }
+
+extern "C" gl_status gl_map_set_timing(gl_map* m, int32_t enable)
+{
+    if (!m) { set_error("null map"); return GL_ERR_INVALID; }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    m->prof.reset();
+    m->prof.on = enable != 0;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_stats(gl_map* m, gl_stats* out)
+{
+    if (!m || !out) { set_error("null argument"); return GL_ERR_INVALID; }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    m->prof.harvest();
+    std::memset(out, 0, sizeof(*out));
+    out->n_gaussians = m->n;
+    out->steps = m->step;
+    const View& v = m->ctx.view;
+    out->n_instances = v.I;
+    out->pixels = (int64_t)v.W * v.H;
+    GL_TRY(view_counts(v, &out->n_visible, &out->sum_contrib, m->stream));
+    for (int i = 0; i < PH_COUNT && i < GL_NUM_PHASES; i++) {
+        out->phase_ms[i] = m->prof.ms[i];
+        out->phase_calls[i] = m->prof.calls[i];
+    }
+    return GL_OK;
+}
+
+extern "C" const char* gl_phase_name(int32_t i)
+{
+    if (i < 0 || i >= PH_COUNT) return "";
+    return kPhaseNames[i];
+}
+
+extern "C" int64_t gl_kernel_launch_count(void) { return g_launches.load(); }

@@ -30,6 +30,51 @@ void set_error(const std::string& msg);
         if (_s != GL_OK) return _s;          \
     } while (0)
 
+// Kernel launch accounting (process-wide).
+void count_launches(int64_t n);
+
+// Phases timed by the optional CUDA-event profiler.
+enum Phase {
+    PH_PREPROCESS = 0, PH_DEPTH_SORT, PH_SCAN_DUP, PH_TILE_SORT, PH_RANGES, PH_RASTER_FWD, PH_LOSS,
+    PH_RASTER_BWD, PH_PARAMS, PH_EXPAND, PH_COUNT
+};
+
+// Event-pair timers: begin/end record events on the stream; harvest() waits
+// for them and accumulates elapsed time per phase.  Events are pooled.
+struct Prof {
+    bool on = false;
+    struct Pending { int phase; cudaEvent_t a, b; };
+    Pending* pend = nullptr;
+    int npend = 0, cap = 0;
+    cudaEvent_t* pool = nullptr;
+    int npool = 0, poolcap = 0;
+    double ms[PH_COUNT] = {0};
+    int64_t calls[PH_COUNT] = {0};
+    cudaEvent_t begin(cudaStream_t s);
+    void end(int phase, cudaEvent_t a, cudaStream_t s);
+    void harvest();
+    void reset();
+    void release();
+};
+
+// RAII bracket of one phase (no-op when the profiler is off or null).
+struct PhaseScope {
+    Prof* p;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(Prof* p_, int ph, cudaStream_t s_) : p(p_), phase(ph), s(s_)
+    {
+        if (p && p->on) a = p->begin(s);
+    }
+    void close()
+    {
+        if (p && p->on && a) p->end(phase, a, s);
+        p = nullptr;
+    }
+    ~PhaseScope() { close(); }
+};
+
 // Grow-only device allocation.  Contents are not preserved on growth.
 struct DevBuf {
     void* p = nullptr;
@@ -70,6 +115,7 @@ struct View {
     const uint32_t* sorted_tile = nullptr;
     const uint32_t* sorted_inst = nullptr;
     uint64_t* h_count = nullptr;          // pinned: I, overflow
+    Prof* prof = nullptr;                 // optional phase timers
     gl_status init();
     void release();
 };
@@ -137,6 +183,9 @@ gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
                          uint32_t** out_k, uint32_t** out_v, cudaStream_t s);
+
+// Visible Gaussians and the summed contributor count of the last view.
+gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s);
 
 // Sorted instances as (tile << 32 | depth bits) keys and owning Gaussians.
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s);

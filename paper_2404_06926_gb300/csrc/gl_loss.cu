@@ -256,6 +256,7 @@ gl_status photometric_loss(const float* rgb, const float* target, const float* E
     if (adam) a = *adam;
     k_loss_final<<<1, 32 * kNP, 0, s>>>(part, (int)(grid.x * grid.y), W, H, lambda, loss_out, dE_out, a,
                                         adam ? 1 : 0);
+    count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -266,6 +267,7 @@ gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_
     if (blocks < 1) blocks = 1;
     k_apply_exposure<<<blocks, 256, 0, s>>>(src, dst, P, E[0], E[1], E[2], E[3], E[4], E[5], E[6], E[7],
                                             E[8], E[9], E[10], E[11]);
+    count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }

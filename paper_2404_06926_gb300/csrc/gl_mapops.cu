@@ -201,6 +201,7 @@ gl_status sky_create(float* means, float* log_scales, float* quats, float* logit
     k_sky_points<<<grid, kThreads, 0, s>>>(means, n, radius, seed);
     const float logit = logf(opacity / (1.0f - opacity));
     k_sky_init<<<grid, kThreads, 0, s>>>(means, n, log_scales, quats, logits, sh, K, logit);
+    count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -221,6 +222,7 @@ gl_status expand_points(const float* xyz, const float* rgb, int64_t n, const Cam
     if (dst.means == nullptr) {
         k_expand_flags<<<nb, kThreads, 0, s>>>(xyz, n, cam, opacity_map, tau, use_mask, fl, depth, bs);
         k_expand_scan<<<1, 1024, 0, s>>>(bs, nb, bs + nb);
+        count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
         uint64_t tot = 0;
         GL_CUDA_TRY(cudaMemcpyAsync(&tot, bs + nb, 8, cudaMemcpyDeviceToHost, s));
@@ -231,6 +233,7 @@ gl_status expand_points(const float* xyz, const float* rgb, int64_t n, const Cam
     const float logit = logf(opacity_fg / (1.0f - opacity_fg));
     k_expand_emit<<<nb, kThreads, 0, s>>>(xyz, rgb, n, fl, depth, bs, cam.fx, logit, K, dst, dst_offset,
                                           dst_cap);
+    count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }

@@ -330,6 +330,8 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
 {
     if (p.n == 0) return GL_OK;
     const unsigned grid = (unsigned)((p.n + kThreads - 1) / kThreads);
+    PhaseScope ps(v.prof, PH_PARAMS, s);
+    count_launches(1);
 #define GL_PB(D_)                                                                            \
     k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.cam, v.radius.as<int>(),            \
                                                      v.touched.as<uint32_t>(), v.dup_off.as<uint32_t>(), \
@@ -365,6 +367,7 @@ gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cu
 gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s)
 {
     k_pose_reduce<<<1, 192, 0, s>>>(part, npart, out6);
+    count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }

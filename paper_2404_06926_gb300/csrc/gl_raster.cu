@@ -277,6 +277,8 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     GL_TRY(v.Tfin.reserve(4 * P));
     GL_TRY(v.ncon.reserve(4 * P));
     if (v.ntiles == 0) return GL_OK;
+    PhaseScope ps(v.prof, PH_RASTER_FWD, s);
+    count_launches(1);
     const uint32_t* own = v.iowner.as<uint32_t>();
 #define GL_FWD(TS_)                                                                          \
     k_raster_fwd<TS_><<<v.ntiles, RCfg<TS_>::NT, 0, s>>>(                                    \
@@ -299,6 +301,8 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
 {
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     const bool extra = dL_ddepth != nullptr || dL_dopac != nullptr;
+    PhaseScope ps(v.prof, PH_RASTER_BWD, s);
+    count_launches(1);
     const uint32_t* own = v.iowner.as<uint32_t>();
 #define GL_BWD(TS_, EX_)                                                                      \
     k_raster_bwd<TS_, EX_><<<v.ntiles, RCfg<TS_>::NT, 0, s>>>(                                \

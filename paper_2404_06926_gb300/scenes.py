@@ -150,6 +150,10 @@ class Outdoor:
     # -- ray casting against the plane and the boxes ---------------------------
     def cast(self, o, d):
         """Nearest hit of rays o + s d (s > 0): returns (s, colour, hit mask)."""
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return self._cast(o, d)
+
+    def _cast(self, o, d):
         n = d.shape[0]
         best = np.full(n, np.inf)
         col = np.zeros((n, 3))
@@ -184,6 +188,58 @@ class Outdoor:
             col[hit] = self.box_col[b][None] * pat[:, None]
         return best, col, np.isfinite(best)
 
+    def target_image_torch(self, cam, device="cuda", rng=None, exposure=True):
+        """The same analytic ray cast as target_image, evaluated with torch on
+        `device` (float32) for large images; returns a device tensor."""
+        import torch
+        W, H = cam["width"], cam["height"]
+        f32 = dict(dtype=torch.float32, device=device)
+        v, u = torch.meshgrid(torch.arange(H, **f32), torch.arange(W, **f32), indexing="ij")
+        dc = torch.stack([(u - cam["cx"]) / cam["fx"], (v - cam["cy"]) / cam["fy"], torch.ones_like(u)], -1)
+        R = torch.tensor(np.asarray(cam["R"]), **f32)
+        t = torch.tensor(np.asarray(cam["t"]), **f32)
+        d = dc.reshape(-1, 3) @ R
+        d = d / d.norm(dim=1, keepdim=True)
+        o = -(R.T @ t)
+        best = torch.full((d.shape[0],), float("inf"), **f32)
+        col = torch.zeros((d.shape[0], 3), **f32)
+        s = -o[2] / d[:, 2]
+        hx = o[0] + s * d[:, 0]
+        hy = o[1] + s * d[:, 1]
+        ok = (s > 0) & torch.isfinite(s) & (hx > -20) & (hx < 420) & (hy.abs() < 60)
+        best = torch.where(ok, s, best)
+        tex = 0.75 + 0.25 * torch.remainder(torch.floor(hx / 2.0) + torch.floor(hy / 2.0), 2)
+        road = self.amp * torch.sin(2 * np.pi * hx / self.period)
+        lane = ((hy - road).abs() < 0.15).float() * 0.4
+        gcol = torch.tensor(self.ground_col, **f32)[None] * tex[:, None] + lane[:, None]
+        col = torch.where(ok[:, None], gcol, col)
+        dd = torch.where(d.abs() < 1e-12, torch.full_like(d, 1e-12), d)
+        inv = 1.0 / dd
+        lo = torch.tensor(self.box_lo, **f32)
+        hi = torch.tensor(self.box_hi, **f32)
+        for b in range(lo.shape[0]):
+            t0 = (lo[b] - o) * inv
+            t1 = (hi[b] - o) * inv
+            tmin = torch.minimum(t0, t1).max(1).values
+            tmax = torch.maximum(t0, t1).min(1).values
+            hit = (tmax >= tmin) & (tmin > 0) & (tmin < best)
+            p = o + tmin[:, None] * d
+            fr = float(self.box_freq[b])
+            pat = 0.7 + 0.3 * torch.remainder(torch.floor(p[:, 0] * fr) + torch.floor(p[:, 1] * fr)
+                                              + torch.floor(p[:, 2] * fr * 0.7), 2)
+            best = torch.where(hit, tmin, best)
+            bc = torch.tensor(self.box_col[b], **f32)
+            col = torch.where(hit[:, None], bc[None] * pat[:, None], col)
+        e = d[:, 2].clamp(0, 1)[:, None]
+        sky = (1 - e) * torch.tensor([0.75, 0.85, 0.95], **f32) + e * torch.tensor([0.35, 0.55, 0.9], **f32)
+        hitm = torch.isfinite(best)
+        img = torch.where(hitm[:, None], col, sky)
+        if exposure:
+            rng = self.rng if rng is None else rng
+            a, b = rng.uniform(0.7, 1.3), rng.uniform(-0.05, 0.05)
+            img = (a * img + b).clamp(0, 1)
+        return img.reshape(H, W, 3).contiguous()
+
     def sky_colour(self, d):
         e = np.clip(d[:, 2], 0, 1)[:, None]
         return (1 - e) * np.array([0.75, 0.85, 0.95]) + e * np.array([0.35, 0.55, 0.9])
@@ -210,7 +266,7 @@ class Outdoor:
             img = np.clip(a * img + b, 0, 1)
         return img.reshape(H, W, 3).astype(np.float32), (~hit).reshape(H, W), (a, b)
 
-    def lidar_sweep(self, s, keep=0.1, beams=32, fov_deg=15.0, n_az=15600, noise=0.02, rng=None,
+    def lidar_sweep(self, s, keep=0.1, beams=32, fov_deg=15.0, n_az=17600, noise=0.02, rng=None,
                     hfov=None):
         """One spinning-LiDAR sweep at pose s, kept 1/`keep`, cropped to the camera
         FoV, coloured by the surface albedo.  Rays are drawn at random so the
@@ -257,7 +313,7 @@ class Outdoor:
         Returns (xyz, rgb, pose index of capture)."""
         poses = self.traj_x if poses is None else poses
         xs, cs, ks = [], [], []
-        per_pose = int(np.ceil(n_total / len(poses)))
+        per_pose = int(np.ceil(1.03 * n_total / len(poses)))
         for i, s in enumerate(poses):
             p, c = self.lidar_sweep(s)
             nv = int(per_pose * visual_frac)
