@@ -268,6 +268,30 @@ GL_API gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const float*
                               int32_t width, int32_t height, float lambda_dssim,
                               float* loss_out, float* dL_drgb, float* dL_dE);
 
+/* The photometric loss above without any device allocation.  The paper has
+ * no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory while they run: a real-time tracking or serving
+ * thread for which cudaMalloc's implicit device-wide synchronisation would
+ * stall the other work on the GPU, or a process whose device memory is all
+ * owned by another allocator (a framework's caching allocator, a fixed
+ * memory budget).  Arguments and results are those of gl_photometric_loss,
+ * with the stream passed directly (cudaStream_t, NULL for the legacy
+ * default stream) instead of through a gl_ctx.
+ * Scratch: the per-tile partial sums live in one fixed array inside the
+ * library (917,504 bytes), which every GPU that loads the library holds
+ * until the process exits.  Limit: at most 16,384 tiles of 32x32 pixels
+ * (e.g. 4096 x 4096); larger images are rejected with GL_ERR_INVALID before
+ * any work is enqueued.  The first call on each device looks up the array's
+ * device address once; make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents; calls
+ * that overlap on the GPU (on different streams, or from different threads)
+ * race on it, so serialise them.  Allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine. */
+GL_API gl_status gl_photometric_loss_noalloc(const float* rgb, const float* target, const float* E34,
+                                             int32_t width, int32_t height, float lambda_dssim,
+                                             float* loss_out, float* dL_drgb, float* dL_dE,
+                                             void* cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Introspection of the last forward on a ctx (tests; not a user API).     */
 /* All outputs are device arrays; n = number of Gaussians of the forward.  */

@@ -102,6 +102,7 @@ def lib():
             "gl_map_get_stats": ([P, P], i32),
             "gl_phase_name": ([i32], C.c_char_p),
             "gl_kernel_launch_count": ([], i64),
+            "gl_photometric_loss_noalloc": ([P, P, P, i32, i32, f32, P, P, P, P], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -260,6 +261,19 @@ class Ctx:
         n = torch.empty((H, W), dtype=torch.int32, device=device)
         check(lib().gl_ctx_get_pixel_state(self._h, _ptr(T), _ptr(n)))
         return T, n
+
+
+def photometric_loss_noalloc(rgb, target, E, lam: float = 0.2, stream=None):
+    """Eq. 9 loss through the entry point that allocates no device memory
+    (its scratch is a fixed array inside the library)."""
+    import torch
+    H, W = rgb.shape[:2]
+    loss = torch.empty(1, dtype=torch.float32, device=rgb.device)
+    dC = torch.empty_like(rgb)
+    dE = torch.empty(12, dtype=torch.float32, device=rgb.device)
+    check(lib().gl_photometric_loss_noalloc(_ptr(rgb), _ptr(target), _ptr(E), int(W), int(H), float(lam),
+                                            _ptr(loss), _ptr(dC), _ptr(dE), _stream_ptr(stream)))
+    return loss, dC, dE.view(3, 4)
 
 
 def kernel_launches() -> int:
