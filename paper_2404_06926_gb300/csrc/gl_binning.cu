@@ -74,7 +74,8 @@ __device__ __forceinline__ T block_sum(T x, T* sm)
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
 k_preprocess(GParams p, Cam cam, int Ts, int TX, int TY, float4* __restrict__ rec0,
-             float4* __restrict__ rec1, float4* __restrict__ rec2, int* __restrict__ radius,
+             float4* __restrict__ rec1, float4* __restrict__ rec2, float4* __restrict__ rec3,
+             int* __restrict__ radius,
              int4* __restrict__ rect, uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
              uint32_t* __restrict__ gidx)
 {
@@ -125,9 +126,19 @@ k_preprocess(GParams p, Cam cam, int Ts, int TX, int TY, float4* __restrict__ re
             c0 += Y[k] * sh[3 * k]; c1 += Y[k] * sh[3 * k + 1]; c2 += Y[k] * sh[3 * k + 2];
         }
     }
-    rec0[g] = make_float4(D.u, D.v, D.z, o);
-    rec1[g] = make_float4(D.c * id, -D.b * id, D.a * id, 0.0f);
+    // log2-domain conic and opacity for the raster kernels
+    const float A = D.c * id, B = -D.b * id, C = D.a * id;
+    rec0[g] = make_float4(D.u, D.v, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
+    rec1[g] = make_float4(-kLog2e * B, log2f(o), D.z, o);
     rec2[g] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
+    // conservative box of {alpha >= 1/255}: the ellipse d^T Sigma'^-1 d <= 2 ln(255 o)
+    const float kappa = 2.0f * logf(255.0f * o);
+    if (kappa > 0.0f) {
+        const float hx = sqrtf(kappa * D.a) * 1.001f + 0.01f, hy = sqrtf(kappa * D.c) * 1.001f + 0.01f;
+        rec3[g] = make_float4(D.u - hx, D.u + hx, D.v - hy, D.v + hy);
+    } else {
+        rec3[g] = make_float4(3.0e38f, -3.0e38f, 3.0e38f, -3.0e38f);
+    }
     radius[g] = D.r;
     rect[g] = make_int4(D.x0, D.y0, D.x1, D.y1);
     touched[g] = (uint32_t)((D.x1 - D.x0) * (D.y1 - D.y0));
@@ -173,34 +184,44 @@ k_sort_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int shift, 
     hist[tid * nblocks + blockIdx.x] = h[tid];
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int total)
+// Exclusive scan of one digit's row of per-block counts (one CTA per digit);
+// the row total goes to totals[digit].
+__global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ hist, int nblocks,
+                                                     uint32_t* __restrict__ totals)
 {
-    __shared__ uint32_t sm[33];
-    const int per = (total + 1023) / 1024;
-    const int b = min(total, (int)threadIdx.x * per), e = min(total, b + per);
-    uint32_t s = 0;
-    for (int i = b; i < e; i++) s += hist[i];
-    uint32_t tot;
-    uint32_t ex = block_exclusive_scan<uint32_t, 1024>(s, sm, &tot);
-    for (int i = b; i < e; i++) {
-        uint32_t x = hist[i];
-        hist[i] = ex;
-        ex += x;
+    __shared__ uint32_t sm[256 / 32 + 1];
+    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
+    uint32_t carry = 0;
+    for (int base = 0; base < nblocks; base += 256) {
+        const int i = base + threadIdx.x;
+        const uint32_t x = i < nblocks ? row[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<uint32_t, 256>(x, sm, &tot);
+        if (i < nblocks) row[i] = carry + ex;
+        carry += tot;
     }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint64_t* n_dev,
-               int shift, int nblocks, const uint32_t* __restrict__ hist)
+               int shift, int nblocks, const uint32_t* __restrict__ hist,
+               const uint32_t* __restrict__ totals)
 {
     __shared__ uint32_t wcnt[kSortThreads / 32][256];
     __shared__ uint32_t doff[256];
     __shared__ uint32_t tcnt[256];
+    __shared__ uint32_t sm[kSortThreads / 32 + 1];
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     uint64_t begin, end;
     sort_chunk(*n_dev, nblocks, begin, end);
-    doff[tid] = hist[tid * nblocks + blockIdx.x];
+    {
+        // digit base = exclusive scan of the digit totals; plus this block's row prefix
+        uint32_t tot;
+        const uint32_t base = block_exclusive_scan<uint32_t, kSortThreads>(totals[tid], sm, &tot);
+        doff[tid] = base + hist[tid * nblocks + blockIdx.x];
+    }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     for (uint64_t base = begin; base < end; base += kSortTile) {
@@ -331,6 +352,34 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
     }
 }
 
+// Tile launch order: heaviest lists first (log2 buckets of the list length,
+// longest-processing-time first), so long tiles start early instead of
+// forming the tail.  Order within a bucket is arbitrary; tiles are
+// independent, so results do not depend on it.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
+                                                     uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t cnt[33], off[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        const int b = 32 - __clz(len);   // 0 for empty, 1..32 otherwise
+        atomicAdd(&cnt[32 - b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int b = 0; b < 33; b++) { off[b] = s; s += cnt[b]; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        const int b = 32 - __clz(len);
+        order[atomicAdd(&off[32 - b], 1u)] = (uint32_t)t;
+    }
+}
+
 __global__ void k_ranges(const uint32_t* __restrict__ stile, const uint64_t* n_dev,
                          uint32_t* __restrict__ ranges)
 {
@@ -344,13 +393,33 @@ __global__ void k_ranges(const uint32_t* __restrict__ stile, const uint64_t* n_d
 }
 
 __global__ void k_export(const uint32_t* __restrict__ stile, const uint32_t* __restrict__ sinst,
-                         const uint32_t* __restrict__ owner, const float4* __restrict__ rec0, int64_t I,
+                         const uint32_t* __restrict__ owner, const float4* __restrict__ rec1, int64_t I,
                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t g = owner[sinst[i]];
-        if (keys) keys[i] = ((uint64_t)stile[i] << 32) | (uint64_t)__float_as_uint(rec0[g].z);
+        if (keys) keys[i] = ((uint64_t)stile[i] << 32) | (uint64_t)__float_as_uint(rec1[g].z);
         if (vals) vals[i] = g;
+    }
+}
+
+// Projected quantities in plain form (mu', conic, opacity, rgb, depth).
+__global__ void k_export_pre(const float4* __restrict__ rec0, const float4* __restrict__ rec1,
+                             const float4* __restrict__ rec2, int64_t n, float* __restrict__ mean2d,
+                             float* __restrict__ conic, float* __restrict__ opacity, float* __restrict__ rgb,
+                             float* __restrict__ depth)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = rec0[g], b = rec1[g], c = rec2[g];
+        if (mean2d) { mean2d[2 * g] = a.x; mean2d[2 * g + 1] = a.y; }
+        if (conic) {
+            conic[3 * g] = a.z / (-0.5f * kLog2e);
+            conic[3 * g + 1] = b.x / -kLog2e;
+            conic[3 * g + 2] = a.w / (-0.5f * kLog2e);
+        }
+        if (opacity) opacity[g] = b.w;
+        if (depth) depth[g] = b.z;
+        if (rgb) { rgb[3 * g] = c.x; rgb[3 * g + 1] = c.y; rgb[3 * g + 2] = c.z; }
     }
 }
 
@@ -385,13 +454,14 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
 {
     int nblocks = (int)std::min<int64_t>(kSortMaxBlocks, std::max<int64_t>(1, (n_max + kSortTile - 1) / kSortTile));
-    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * (size_t)nblocks));
+    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * ((size_t)nblocks + 1)));
+    uint32_t* totals = hist.as<uint32_t>() + 256 * (size_t)nblocks;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int shift = 0; shift < bits; shift += 8) {
         k_sort_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_dev, shift, nblocks, hist.as<uint32_t>());
-        k_sort_scan<<<1, 1024, 0, s>>>(hist.as<uint32_t>(), 256 * nblocks);
+        k_sort_rowscan<<<256, 256, 0, s>>>(hist.as<uint32_t>(), nblocks, totals);
         k_sort_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, nblocks,
-                                                        hist.as<uint32_t>());
+                                                        hist.as<uint32_t>(), totals);
         count_launches(3);
         std::swap(ki, ko);
         std::swap(vi, vo);
@@ -421,12 +491,24 @@ gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, c
     return GL_OK;
 }
 
+gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* opacity, float* rgb,
+                            float* depth, cudaStream_t s)
+{
+    if (v.n == 0) return GL_OK;
+    int blocks = (int)std::min<int64_t>(4 * 152, (v.n + 255) / 256);
+    k_export_pre<<<blocks, 256, 0, s>>>(v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.n,
+                                        mean2d, conic, opacity, rgb, depth);
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s)
 {
     if (v.I == 0) return GL_OK;
     int blocks = (int)std::min<int64_t>(4 * 152, (v.I + 255) / 256);
     k_export<<<blocks, 256, 0, s>>>(v.sorted_tile, v.sorted_inst, v.iowner.as<uint32_t>(),
-                                    v.rec0.as<float4>(), v.I, keys, vals);
+                                    v.rec1.as<float4>(), v.I, keys, vals);
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
@@ -447,6 +529,7 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     GL_TRY(v.rec0.reserve(16 * nn));
     GL_TRY(v.rec1.reserve(16 * nn));
     GL_TRY(v.rec2.reserve(16 * nn));
+    GL_TRY(v.rec3.reserve(16 * nn));
     GL_TRY(v.radius.reserve(4 * nn));
     GL_TRY(v.rect.reserve(16 * nn));
     GL_TRY(v.touched.reserve(4 * nn));
@@ -464,7 +547,9 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     if (n == 0) {
         v.I = 0;
         k_set_u64<<<1, 1, 0, s>>>(count, 0, 0);
-        count_launches(1);
+        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
+        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
+        count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
         return GL_OK;
     }
@@ -474,10 +559,10 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     PhaseScope ps(v.prof, PH_PREPROCESS, s);
     count_launches(1);
     switch (p.deg) {
-        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
@@ -516,7 +601,6 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
         GL_TRY(v.itile2.reserve(4 * want));
         GL_TRY(v.ival2.reserve(4 * want));
         GL_TRY(v.iowner.reserve(4 * want));
-        GL_TRY(v.igrad.reserve(40 * want));
     }
     const uint64_t cap2 = v.itile.bytes / 4;
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
@@ -528,6 +612,10 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     if (I == 0) {
         v.sorted_tile = v.itile.as<uint32_t>();
         v.sorted_inst = v.ival.as<uint32_t>();
+        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
+        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
+        count_launches(1);
+        GL_CUDA_TRY(cudaGetLastError());
         return GL_OK;
     }
     // stable sort of the instances by tile id
@@ -543,8 +631,11 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
         PhaseScope ps(v.prof, PH_RANGES, s);
         int rb = (int)std::min<uint64_t>(4 * 152, (I + 255) / 256);
         k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
-        count_launches(1);
+        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
+        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
+        count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
+        GL_TRY(permute_records(v, s));
     }
     return GL_OK;
 }

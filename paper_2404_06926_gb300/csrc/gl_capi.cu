@@ -90,6 +90,24 @@ void Prof::reset()
     for (int i = 0; i < PH_COUNT; i++) { ms[i] = 0; calls[i] = 0; }
 }
 
+void Prof::prefill(int count)
+{
+    // Creating events inside a timed region stalls the host while the GPU
+    // idles; create them up front.
+    while (npool < count) {
+        if (npool == poolcap) {
+            int nc = poolcap ? 2 * poolcap : 512;
+            cudaEvent_t* np = static_cast<cudaEvent_t*>(realloc(pool, sizeof(cudaEvent_t) * nc));
+            if (!np) return;
+            pool = np;
+            poolcap = nc;
+        }
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        pool[npool++] = e;
+    }
+}
+
 void Prof::release()
 {
     harvest();
@@ -136,9 +154,9 @@ gl_status View::init()
 
 void View::release()
 {
-    DevBuf* all[] = {&rec0, &rec1, &rec2, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
-                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &igrad,
-                     &hist, &ranges, &Tfin, &ncon, &rgb, &depth, &opac};
+    DevBuf* all[] = {&rec0, &rec1, &rec2, &rec3, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
+                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d,
+                     &hist, &ranges, &tile_order, &Tfin, &ncon, &rgb, &depth, &opac};
     for (DevBuf* b : all) b->release();
     if (h_count) cudaFreeHost(h_count);
     h_count = nullptr;
@@ -357,17 +375,9 @@ extern "C" gl_status gl_ctx_get_preprocess(gl_ctx* ctx, int32_t* radius, int32_t
     cudaStream_t s = ctx->impl.stream;
     const size_t n = (size_t)v.n;
     if (n == 0) return GL_OK;
-    const char* r0 = static_cast<const char*>(v.rec0.p);
-    const char* r1 = static_cast<const char*>(v.rec1.p);
-    const char* r2 = static_cast<const char*>(v.rec2.p);
     if (radius) GL_CUDA_TRY(cudaMemcpyAsync(radius, v.radius.p, 4 * n, cudaMemcpyDeviceToDevice, s));
     if (rect) GL_CUDA_TRY(cudaMemcpyAsync(rect, v.rect.p, 16 * n, cudaMemcpyDeviceToDevice, s));
-    if (mean2d) GL_CUDA_TRY(cudaMemcpy2DAsync(mean2d, 8, r0, 16, 8, n, cudaMemcpyDeviceToDevice, s));
-    if (depth) GL_CUDA_TRY(cudaMemcpy2DAsync(depth, 4, r0 + 8, 16, 4, n, cudaMemcpyDeviceToDevice, s));
-    if (opacity) GL_CUDA_TRY(cudaMemcpy2DAsync(opacity, 4, r0 + 12, 16, 4, n, cudaMemcpyDeviceToDevice, s));
-    if (conic) GL_CUDA_TRY(cudaMemcpy2DAsync(conic, 12, r1, 16, 12, n, cudaMemcpyDeviceToDevice, s));
-    if (rgb) GL_CUDA_TRY(cudaMemcpy2DAsync(rgb, 12, r2, 16, 12, n, cudaMemcpyDeviceToDevice, s));
-    return GL_OK;
+    return export_preprocess(v, mean2d, conic, opacity, rgb, depth, s);
 }
 
 extern "C" gl_status gl_ctx_num_instances(gl_ctx* ctx, int64_t* I_out)
@@ -822,6 +832,7 @@ extern "C" gl_status gl_map_set_timing(gl_map* m, int32_t enable)
     GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
     m->prof.reset();
     m->prof.on = enable != 0;
+    if (m->prof.on) m->prof.prefill(8192);
     return GL_OK;
 }
 

@@ -228,23 +228,36 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, float dY[16][
 
 // ---------------------------------------------------------------------------
 // Per-pair blending weight (Eq. 4) shared by the forward and the backward
-// raster kernels.  Explicitly rounded operations keep the skip decisions of
-// the two kernels identical.  rec0 = (u, v, depth, opacity), rec1 = conic.
+// raster kernels, evaluated in the log2 domain:
+//   e = log2(o exp(power)) = A' dx^2 + C' dy^2 + B' dx dy + log2(o),
+// with A' = -A log2(e)/2, C' = -C log2(e)/2, B' = -B log2(e) precomputed per
+// Gaussian.  The pair is skipped when e < log2(1/255) (alpha below 1/255) or
+// when e > log2(o) (power > 0, possible only through rounding).  Explicitly
+// rounded operations keep the decisions of the two kernels identical.
+// Record layout: r0 = (u, v, A', C'), r1 = (B', log2 o, depth, o).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool pair_alpha(const float4 r0, const float4 r1, float px, float py,
-                                           float& dx, float& dy, float& alpha, float& G,
-                                           bool& capped)
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLog2AlphaMin = -7.994353436858858f;   // log2(1/255)
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ bool pair_eval(const float4 r0, const float4 r1, float px, float py,
+                                          float& dx, float& dy, float& alpha, bool& capped)
 {
     dx = __fsub_rn(r0.x, px);
     dy = __fsub_rn(r0.y, py);
-    float quad = __fmaf_rn(r1.x, __fmul_rn(dx, dx), __fmul_rn(r1.z, __fmul_rn(dy, dy)));
-    float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(r1.y, __fmul_rn(dx, dy)));
-    if (power > 0.0f) return false;
-    G = __expf(power);
-    float araw = __fmul_rn(r0.w, G);
+    const float e = __fmaf_rn(__fmul_rn(r0.z, dx), dx,
+                              __fmaf_rn(__fmul_rn(r0.w, dy), dy, __fmaf_rn(__fmul_rn(r1.x, dx), dy, r1.y)));
+    if (!(e >= kLog2AlphaMin) || e > r1.y) return false;
+    const float araw = ex2_approx(e);
     capped = araw >= kAlphaMax;
     alpha = fminf(kAlphaMax, araw);
-    return alpha >= kAlphaMin;
+    return true;
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

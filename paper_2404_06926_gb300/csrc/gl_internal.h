@@ -54,6 +54,7 @@ struct Prof {
     void end(int phase, cudaEvent_t a, cudaStream_t s);
     void harvest();
     void reset();
+    void prefill(int count);
     void release();
 };
 
@@ -91,7 +92,7 @@ struct View {
     int64_t I = 0;            // (Gaussian, tile) instances
     Cam cam{};
     // per Gaussian
-    DevBuf rec0, rec1, rec2;  // float4: (u,v,z,o), (A,B,C,-), (r,g,b,-)
+    DevBuf rec0, rec1, rec2, rec3;  // float4: (u,v,A',C'), (B',log2 o,z,o), (r,g,b,-), alpha box
     DevBuf radius;            // int
     DevBuf rect;              // int4 (x0,y0,x1,y1)
     DevBuf touched;           // u32
@@ -104,9 +105,12 @@ struct View {
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 tile id, u32 instance id (sort)
     DevBuf iowner;            // u32 owning Gaussian per instance id
-    DevBuf igrad;             // float[10] per instance id (backward)
+    DevBuf srec0, srec1, srec2, srec3;  // records in sorted-instance order
+    DevBuf sgid;              // u32 owning Gaussian per sorted instance
+    DevBuf g2d;               // float[10] screen-space gradient accumulators per Gaussian
     DevBuf hist;              // radix histograms
     DevBuf ranges;            // uint2 per tile
+    DevBuf tile_order;        // u32 tile launch order (heaviest first)
     // per pixel
     DevBuf Tfin, ncon;        // float, u32
     DevBuf rgb, depth, opac;  // internal render targets when needed
@@ -142,7 +146,10 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
 // (depth/opacity may be null) plus T_final / n_contrib in `v`.
 gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s);
 
-// Backward raster: per-instance 2-D gradients into v.igrad.
+// Records gathered into sorted-instance order (after binning).
+gl_status permute_records(View& v, cudaStream_t s);
+
+// Backward raster: per-Gaussian screen-space gradients into v.g2d.
 gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
                           const float* dL_dopac, cudaStream_t s);
 
@@ -186,6 +193,10 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
 
 // Visible Gaussians and the summed contributor count of the last view.
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s);
+
+// Projected quantities of the last view in plain form (null outputs skipped).
+gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* opacity, float* rgb,
+                            float* depth, cudaStream_t s);
 
 // Sorted instances as (tile << 32 | depth bits) keys and owning Gaussians.
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s);

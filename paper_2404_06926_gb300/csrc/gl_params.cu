@@ -95,12 +95,18 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
 
 template <int DEG, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const uint32_t* __restrict__ touched,
-             const uint32_t* __restrict__ dup_off, const float* __restrict__ igrad, GMut out,
+k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __restrict__ g2d, GMut out,
              AdamArgs ad, float* __restrict__ pose_part)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const int64_t g = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    constexpr int KF = K * 3;   // SH floats per Gaussian
+    // per-Gaussian factors of the SH gradient dL/dsh[k][c] = Y[k] * grgb[c],
+    // staged so the block can stream the SH arrays with coalesced accesses
+    __shared__ float sY[kThreads][K];
+    __shared__ float sG[kThreads][3];
+    __shared__ uint8_t sUpd[kThreads];
+    const int64_t g0 = blockIdx.x * (int64_t)kThreads;
+    const int64_t g = g0 + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     const bool valid = g < p.n;
     const bool vis = valid && radius[g] > 0;
@@ -118,13 +124,9 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const uint32_t*
         Geo G;
         geometry(mu, ls, q, p.logits[g], cam, G);
 
-        // screen-space gradients of this Gaussian: sum over its instances
+        // screen-space gradients of this Gaussian, accumulated by the raster backward
         float s[kNG];
-        for (int k = 0; k < kNG; k++) s[k] = 0.0f;
-        const uint32_t n_i = touched[g];
-        const float* src = igrad + (size_t)dup_off[g] * kNG;
-        for (uint32_t i = 0; i < n_i; i++)
-            for (int k = 0; k < kNG; k++) s[k] += src[(size_t)i * kNG + k];
+        for (int k = 0; k < kNG; k++) s[k] = g2d[(size_t)g * kNG + k];
         const float du = -G.A * s[4] - G.B * s[5];
         const float dv = -G.C * s[5] - G.B * s[4];
         const float dA = -0.5f * s[6], dB = -s[7], dC = -0.5f * s[8];
@@ -242,74 +244,93 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const uint32_t*
         pose[5] += P[1] - P[3];
     }
 
+    for (int k = 0; k < K; k++) sY[threadIdx.x][k] = Y[k];
+    for (int c = 0; c < 3; c++) sG[threadIdx.x][c] = grgb[c];
+    const bool upd = valid && (MODE == 0 || !ad.sparse || vis);
+    sUpd[threadIdx.x] = upd ? 1 : 0;
+
     if (MODE == 0) {
         if (valid) {
             for (int j = 0; j < 3; j++) { out.means[3 * g + j] = gm[j]; out.log_scales[3 * g + j] = gl3[j]; }
             reinterpret_cast<float4*>(out.quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
             out.logits[g] = glg;
-            float* o = out.sh + (size_t)g * K * 3;
-            for (int k = 0; k < K; k++)
-                for (int c = 0; c < 3; c++) o[3 * k + c] = Y[k] * grgb[c];
         }
-        if (pose_part) {
-            __shared__ float red[6][kThreads / 32];
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-            for (int k = 0; k < 6; k++) {
-                float v = pose[k];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-                if (lane == 0) red[k][w] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x < 6) {
-                float v = 0.0f;
-                for (int ww = 0; ww < kThreads / 32; ww++) v += red[threadIdx.x][ww];
-                pose_part[blockIdx.x * 6 + threadIdx.x] = v;
-            }
-        }
-    } else {
-        if (!valid || (ad.sparse && !vis)) return;
-        // p (out) shares storage with the parameters read above
+    } else if (upd) {
         for (int j = 0; j < 3; j++) {
             adam1(out.means[3 * g + j], ad.m.means[3 * g + j], ad.v.means[3 * g + j], gm[j], ad.lr_pos, ad);
             adam1(out.log_scales[3 * g + j], ad.m.log_scales[3 * g + j], ad.v.log_scales[3 * g + j], gl3[j], ad.lr_scale, ad);
         }
-        {
-            float4 pq = reinterpret_cast<float4*>(out.quats)[g];
-            float4 mq = reinterpret_cast<float4*>(ad.m.quats)[g];
-            float4 vq = reinterpret_cast<float4*>(ad.v.quats)[g];
-            adam1(pq.x, mq.x, vq.x, gq[0], ad.lr_rot, ad);
-            adam1(pq.y, mq.y, vq.y, gq[1], ad.lr_rot, ad);
-            adam1(pq.z, mq.z, vq.z, gq[2], ad.lr_rot, ad);
-            adam1(pq.w, mq.w, vq.w, gq[3], ad.lr_rot, ad);
-            reinterpret_cast<float4*>(out.quats)[g] = pq;
-            reinterpret_cast<float4*>(ad.m.quats)[g] = mq;
-            reinterpret_cast<float4*>(ad.v.quats)[g] = vq;
-        }
+        float4 pq = reinterpret_cast<float4*>(out.quats)[g];
+        float4 mq = reinterpret_cast<float4*>(ad.m.quats)[g];
+        float4 vq = reinterpret_cast<float4*>(ad.v.quats)[g];
+        adam1(pq.x, mq.x, vq.x, gq[0], ad.lr_rot, ad);
+        adam1(pq.y, mq.y, vq.y, gq[1], ad.lr_rot, ad);
+        adam1(pq.z, mq.z, vq.z, gq[2], ad.lr_rot, ad);
+        adam1(pq.w, mq.w, vq.w, gq[3], ad.lr_rot, ad);
+        reinterpret_cast<float4*>(out.quats)[g] = pq;
+        reinterpret_cast<float4*>(ad.m.quats)[g] = mq;
+        reinterpret_cast<float4*>(ad.v.quats)[g] = vq;
         adam1(out.logits[g], ad.m.logits[g], ad.v.logits[g], glg, ad.lr_op, ad);
-        float* ps = out.sh + (size_t)g * K * 3;
-        float* ms = ad.m.sh + (size_t)g * K * 3;
-        float* vs = ad.v.sh + (size_t)g * K * 3;
-        if ((K * 3) % 4 == 0) {
-#pragma unroll
-            for (int i = 0; i < K * 3 / 4; i++) {
-                float4 pp = reinterpret_cast<float4*>(ps)[i];
-                float4 mm = reinterpret_cast<float4*>(ms)[i];
-                float4 vv = reinterpret_cast<float4*>(vs)[i];
-                float* pa = &pp.x; float* ma = &mm.x; float* va = &vv.x;
+    }
+    __syncthreads();
+
+    // SH of the block's Gaussians: one contiguous span of cnt * KF floats
+    const int cnt = (int)min((int64_t)kThreads, p.n - g0);
+    if (cnt > 0) {
+        const size_t base = (size_t)g0 * KF;
+        if (KF % 4 == 0) {
+            const int nv = cnt * KF / 4;
+            for (int f = threadIdx.x; f < nv; f += kThreads) {
+                const int e0 = 4 * f, loc = e0 / KF;
+                if (!sUpd[loc]) continue;
+                float gr[4];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const int idx = 4 * i + e, k = idx / 3, c = idx % 3;
-                    adam1(pa[e], ma[e], va[e], Y[k] * grgb[c], k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+                    const int w = e0 % KF + e, k = w / 3, c = w % 3;
+                    gr[e] = sY[loc][k] * sG[loc][c];
                 }
-                reinterpret_cast<float4*>(ps)[i] = pp;
-                reinterpret_cast<float4*>(ms)[i] = mm;
-                reinterpret_cast<float4*>(vs)[i] = vv;
+                if (MODE == 0) {
+                    reinterpret_cast<float4*>(out.sh + base)[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+                } else {
+                    float4 pp = reinterpret_cast<float4*>(out.sh + base)[f];
+                    float4 mm = reinterpret_cast<float4*>(ad.m.sh + base)[f];
+                    float4 vv = reinterpret_cast<float4*>(ad.v.sh + base)[f];
+                    float* pa = &pp.x; float* ma = &mm.x; float* va = &vv.x;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int k = (e0 % KF + e) / 3;
+                        adam1(pa[e], ma[e], va[e], gr[e], k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+                    }
+                    reinterpret_cast<float4*>(out.sh + base)[f] = pp;
+                    reinterpret_cast<float4*>(ad.m.sh + base)[f] = mm;
+                    reinterpret_cast<float4*>(ad.v.sh + base)[f] = vv;
+                }
             }
         } else {
-            for (int k = 0; k < K; k++)
-                for (int c = 0; c < 3; c++)
-                    adam1(ps[3 * k + c], ms[3 * k + c], vs[3 * k + c], Y[k] * grgb[c],
-                          k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+            const int ne = cnt * KF;
+            for (int e = threadIdx.x; e < ne; e += kThreads) {
+                const int loc = e / KF, w = e % KF, k = w / 3, c = w % 3;
+                if (!sUpd[loc]) continue;
+                const float gr = sY[loc][k] * sG[loc][c];
+                if (MODE == 0) out.sh[base + e] = gr;
+                else adam1(out.sh[base + e], ad.m.sh[base + e], ad.v.sh[base + e], gr, k == 0 ? ad.lr_dc : ad.lr_rest, ad);
+            }
+        }
+    }
+
+    if (MODE == 0 && pose_part) {
+        __shared__ float red[6][kThreads / 32];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int k = 0; k < 6; k++) {
+            float v = pose[k];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+            if (lane == 0) red[k][w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            float v = 0.0f;
+            for (int ww = 0; ww < kThreads / 32; ww++) v += red[threadIdx.x][ww];
+            pose_part[blockIdx.x * 6 + threadIdx.x] = v;
         }
     }
 }
@@ -333,9 +354,8 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
     PhaseScope ps(v.prof, PH_PARAMS, s);
     count_launches(1);
 #define GL_PB(D_)                                                                            \
-    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.cam, v.radius.as<int>(),            \
-                                                     v.touched.as<uint32_t>(), v.dup_off.as<uint32_t>(), \
-                                                     v.igrad.as<float>(), o, a, pose_part)
+    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.cam, v.radius.as<int>(), v.g2d.as<float>(), \
+                                                     o, a, pose_part)
     switch (p.deg) {
         case 0: GL_PB(0); break;
         case 1: GL_PB(1); break;

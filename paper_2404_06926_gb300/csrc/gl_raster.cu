@@ -1,103 +1,123 @@
-// gl_raster.cu -- per-tile front-to-back compositing (Eq. 4-7) and its adjoint.
+// gl_raster.cu -- front-to-back compositing (Eq. 4-7) and its adjoint.
 //
-// Forward: one CTA per screen tile; the tile's depth-sorted Gaussians are
-// staged batch by batch into shared memory (gathered through the sorted
-// instance list) and every thread blends its pixel(s) front to back until the
-// transmittance would fall below 1e-4.  Per pixel it keeps the final
-// transmittance and the position of the last blended Gaussian, so the
-// backward recomputes T by division instead of storing it per pair.
+// Work unit: one warp per (screen tile, 8x4 pixel block).  Binning is done
+// per tile (TS x TS), but every 8x4 block of a tile is rendered by its own
+// warp, independently: a heavy tile is spread over TS*TS/32 warps instead of
+// being the critical path of one CTA.  Units are launched heaviest tile first.
 //
-// Backward: the same tiles walked back to front.  Each pixel produces ten
-// per-Gaussian partial sums (colour 3, dL/dpower moments 6, depth 1); a warp
-// folds its 32 pixels with a transposed butterfly (16 shuffles for 16 slots),
-// warps are summed in a fixed order in shared memory, and the result is
-// written once per (Gaussian, tile) instance -- no atomics, so the gradients
-// are deterministic.
+// Records are permuted into sorted-instance order after binning, so a tile's
+// Gaussians are contiguous: each lane loads one Gaussian per batch of 32
+// (prefetched one batch ahead), the warp ballots which Gaussians' alpha boxes
+// touch its pixel block, compacts those hits in shared memory in depth order
+// and evaluates only them.  A Gaussian outside the block's box fails the
+// alpha test at every pixel of the block, so skipping it changes no result.
+//
+// Forward: per pixel, blend until the transmittance would fall below 1e-4;
+// keep the final transmittance and the position (in the tile's list) of the
+// last blended Gaussian, so the backward recomputes T by division.
+// Backward: the same units walked back to front; per hit, the warp folds its
+// 32 pixels' ten partial sums (colour 3, dL/dpower moments 6, depth 1) with a
+// transposed butterfly and ten lanes add them to the Gaussian's accumulator.
 #include "gl_internal.h"
 
 namespace gl {
 
 namespace {
 
-template <int TS>
-struct RCfg {
-    static constexpr int NT = (TS * TS < 256) ? TS * TS : 256;
-    static constexpr int PPT = TS * TS / NT;
-    static constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
+constexpr int kWarpsPerBlock = 8;
+constexpr int kNG = 10;   // screen-space gradient slots per Gaussian
+
+struct Unit {
+    int tile, x0, y0;      // tile and the absolute pixel origin of the 8x4 block
+    uint32_t rs, re;       // the tile's list
 };
 
-template <int TS>
-__global__ void __launch_bounds__(RCfg<TS>::NT)
-k_raster_fwd(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ sinst,
-             const uint32_t* __restrict__ owner, const float4* __restrict__ rec0,
-             const float4* __restrict__ rec1, const float4* __restrict__ rec2, int W, int H, int TX,
-             float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_opac,
-             float* __restrict__ Tfin, uint32_t* __restrict__ ncon)
+__device__ __forceinline__ bool unit_of(int u, int TS, int TX, const uint32_t* __restrict__ order,
+                                        const uint32_t* __restrict__ ranges, Unit& U)
 {
-    constexpr int NT = RCfg<TS>::NT, PPT = RCfg<TS>::PPT;
-    __shared__ float4 s0[NT], s1[NT], s2[NT];
-    const int tid = threadIdx.x;
-    const int tile = blockIdx.x, tx = tile % TX, ty = tile / TX;
-    const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
-    float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], Dd[PPT], Oo[PPT];
-    uint32_t last[PPT];
-    bool done[PPT], inside[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int local = tid + k * NT;
-        const int x = tx * TS + local % TS, y = ty * TS + local / TS;
-        px[k] = (float)x; py[k] = (float)y;
-        inside[k] = x < W && y < H;
-        done[k] = !inside[k];
-        T[k] = 1.0f; C0[k] = C1[k] = C2[k] = Dd[k] = Oo[k] = 0.0f;
-        last[k] = 0;
+    const int wb_per_tile = TS * TS / 32, bpr = TS / 8;
+    const int tile = (int)order[u / wb_per_tile], wb = u % wb_per_tile;
+    U.tile = tile;
+    U.x0 = (tile % TX) * TS + (wb % bpr) * 8;
+    U.y0 = (tile / TX) * TS + (wb / bpr) * 4;
+    U.rs = ranges[2 * tile];
+    U.re = ranges[2 * tile + 1];
+    return true;
+}
+
+__device__ __forceinline__ bool box_hit(const float4 box, float bx0, float bx1, float by0, float by1)
+{
+    return !(box.y < bx0 || box.x > bx1 || box.w < by0 || box.z > by1);
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k_raster_fwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint32_t* __restrict__ ranges,
+             const float4* __restrict__ s0g, const float4* __restrict__ s1g, const float4* __restrict__ s2g,
+             const float4* __restrict__ s3g, int W, int H, int TX, float* __restrict__ out_rgb,
+             float* __restrict__ out_depth, float* __restrict__ out_opac, float* __restrict__ Tfin,
+             uint32_t* __restrict__ ncon)
+{
+    __shared__ float4 sr0[kWarpsPerBlock][32], sr1[kWarpsPerBlock][32], sr2[kWarpsPerBlock][32];
+    __shared__ uint32_t spos[kWarpsPerBlock][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u = blockIdx.x * kWarpsPerBlock + w;
+    if (u >= nunits) return;
+    Unit U;
+    unit_of(u, TS, TX, order, ranges, U);
+    const int x = U.x0 + (lane & 7), y = U.y0 + (lane >> 3);
+    const bool inside = x < W && y < H;
+    const float px = (float)x, py = (float)y;
+    const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 3);
+    const unsigned lt = (1u << lane) - 1u;
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dd = 0.f, Oo = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    // prefetch of the first batch
+    float4 n0, n1, n2, n3;
+    {
+        const uint32_t i = U.rs + lane;
+        if (i < U.re) { n0 = s0g[i]; n1 = s1g[i]; n2 = s2g[i]; n3 = s3g[i]; }
     }
-    for (uint32_t base = rs; base < re; base += NT) {
-        bool mine = true;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) mine = mine && done[k];
-        if (__syncthreads_and(mine)) break;
-        const uint32_t i = base + tid;
-        if (i < re) {
-            const uint32_t g = owner[sinst[i]];
-            s0[tid] = rec0[g];
-            s1[tid] = rec1[g];
-            s2[tid] = rec2[g];
+    for (uint32_t base = U.rs; base < U.re; base += 32) {
+        if (__all_sync(kFull, done)) break;
+        const float4 c0 = n0, c1 = n1, c2 = n2, c3 = n3;
+        const uint32_t i = base + lane;
+        const bool valid = i < U.re;
+        const uint32_t ni = i + 32;
+        if (ni < U.re) { n0 = s0g[ni]; n1 = s1g[ni]; n2 = s2g[ni]; n3 = s3g[ni]; }
+        const bool hit = valid && box_hit(c3, bx0, bx1, by0, by1);
+        const unsigned mask = __ballot_sync(kFull, hit);
+        if (hit) {
+            const int k = __popc(mask & lt);
+            sr0[w][k] = c0; sr1[w][k] = c1; sr2[w][k] = c2;
+            spos[w][k] = i - U.rs;
         }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)NT, re - base);
-        for (int j = 0; j < cnt; j++) {
-            const float4 a = s0[j], b = s1[j];
-            bool alldone = true;
-#pragma unroll
-            for (int k = 0; k < PPT; k++) {
-                if (done[k]) continue;
-                alldone = false;
-                float dx, dy, alpha, G;
-                bool capped;
-                if (!pair_alpha(a, b, px[k], py[k], dx, dy, alpha, G, capped)) continue;
-                const float tT = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
-                if (tT < kTransMin) { done[k] = true; continue; }
-                const float w = alpha * T[k];
-                const float4 c = s2[j];
-                C0[k] += c.x * w; C1[k] += c.y * w; C2[k] += c.z * w;
-                Dd[k] += a.z * w; Oo[k] += w;
-                T[k] = tT;
-                last[k] = base + j - rs + 1;
-            }
-            if (alldone) break;
+        __syncwarp();
+        const int nh = __popc(mask);
+        for (int k = 0; k < nh; k++) {
+            if (done) break;
+            float dx, dy, alpha;
+            bool capped;
+            const float4 a = sr0[w][k], b = sr1[w][k];
+            if (!pair_eval(a, b, px, py, dx, dy, alpha, capped)) continue;
+            const float tT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (tT < kTransMin) { done = true; break; }
+            const float wgt = alpha * T;
+            const float4 c = sr2[w][k];
+            C0 += c.x * wgt; C1 += c.y * wgt; C2 += c.z * wgt;
+            Dd += b.z * wgt; Oo += wgt;
+            T = tT;
+            last = spos[w][k] + 1;
         }
+        __syncwarp();
     }
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        if (!inside[k]) continue;
-        const size_t p = (size_t)py[k] * W + (size_t)px[k];
-        out_rgb[3 * p] = C0[k]; out_rgb[3 * p + 1] = C1[k]; out_rgb[3 * p + 2] = C2[k];
-        if (out_depth) out_depth[p] = Dd[k];
-        if (out_opac) out_opac[p] = Oo[k];
-        Tfin[p] = T[k];
-        ncon[p] = last[k];
-    }
+    if (!inside) return;
+    const size_t p = (size_t)y * W + x;
+    out_rgb[3 * p] = C0; out_rgb[3 * p + 1] = C1; out_rgb[3 * p + 2] = C2;
+    if (out_depth) out_depth[p] = Dd;
+    if (out_opac) out_opac[p] = Oo;
+    Tfin[p] = T;
+    ncon[p] = last;
 }
 
 // Sum 16 per-lane values over the warp.  On return lane l holds the total of
@@ -141,135 +161,146 @@ __device__ __forceinline__ float warp_transpose_reduce16(float (&v)[16])
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-constexpr int kNG = 10;   // per-instance gradient slots
-constexpr int kSub = 32;  // Gaussians per flush of the warp partials
-
-template <int TS, bool EXTRA>
-__global__ void __launch_bounds__(RCfg<TS>::NT)
-k_raster_bwd(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ sinst,
-             const uint32_t* __restrict__ owner, const float4* __restrict__ rec0,
-             const float4* __restrict__ rec1, const float4* __restrict__ rec2, int W, int H, int TX,
+template <bool EXTRA>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k_raster_bwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint32_t* __restrict__ ranges,
+             const float4* __restrict__ s0g, const float4* __restrict__ s1g, const float4* __restrict__ s2g,
+             const float4* __restrict__ s3g, const uint32_t* __restrict__ sgid, int W, int H, int TX,
              const float* __restrict__ Tfin, const uint32_t* __restrict__ ncon,
              const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
-             const float* __restrict__ dL_dopac, float* __restrict__ igrad)
+             const float* __restrict__ dL_dopac, float* __restrict__ g2d)
 {
-    constexpr int NT = RCfg<TS>::NT, PPT = RCfg<TS>::PPT, NW = RCfg<TS>::NW;
-    __shared__ float4 s0[NT], s1[NT], s2[NT];
-    __shared__ uint32_t sd[NT];
-    __shared__ float part[NW][kSub][kNG];
-    __shared__ uint32_t s_max;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int tile = blockIdx.x, tx = tile % TX, ty = tile / TX;
-    const uint32_t rs = ranges[2 * tile], re = ranges[2 * tile + 1];
+    __shared__ float4 sr0[kWarpsPerBlock][32], sr1[kWarpsPerBlock][32], sr2[kWarpsPerBlock][32];
+    __shared__ uint32_t spos[kWarpsPerBlock][32], sg[kWarpsPerBlock][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u = blockIdx.x * kWarpsPerBlock + w;
+    if (u >= nunits) return;
+    Unit U;
+    unit_of(u, TS, TX, order, ranges, U);
+    const int x = U.x0 + (lane & 7), y = U.y0 + (lane >> 3);
+    const bool inside = x < W && y < H;
+    const float px = (float)x, py = (float)y;
+    const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 3);
+    const unsigned lt = (1u << lane) - 1u;
+    float T = 1.0f, R0 = 0.f, R1 = 0.f, R2 = 0.f, RD = 0.f, RO = 0.f;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, gO = 0.f;
+    uint32_t last = 0;
+    if (inside) {
+        const size_t p = (size_t)y * W + x;
+        T = Tfin[p];
+        last = ncon[p];
+        g0 = dL_drgb[3 * p]; g1 = dL_drgb[3 * p + 1]; g2 = dL_drgb[3 * p + 2];
+        if (EXTRA) {
+            gD = dL_ddepth ? dL_ddepth[p] : 0.0f;
+            gO = dL_dopac ? dL_dopac[p] : 0.0f;
+        }
+    }
+    uint32_t wmax = last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, off));
+    const uint32_t end = U.rs + wmax;   // positions at or beyond this reach no pixel of the block
+    if (end == U.rs) return;
+    // batches from the back: [bstart, bstart + 32) with bstart = end - 32 k, clipped at rs
+    int64_t bstart = (int64_t)end - 32;
+    float4 n0, n1, n2, n3;
+    uint32_t ng = 0;
+    {
+        const int64_t i = bstart + lane;
+        if (i >= (int64_t)U.rs) { n0 = s0g[i]; n1 = s1g[i]; n2 = s2g[i]; n3 = s3g[i]; ng = sgid[i]; }
+    }
+    for (; bstart + 32 > (int64_t)U.rs; bstart -= 32) {
+        const float4 c0 = n0, c1 = n1, c2 = n2, c3 = n3;
+        const uint32_t cg = ng;
+        const int64_t i = bstart + lane;
+        const bool valid = i >= (int64_t)U.rs;
+        const int64_t ni = i - 32;
+        if (ni >= (int64_t)U.rs) { n0 = s0g[ni]; n1 = s1g[ni]; n2 = s2g[ni]; n3 = s3g[ni]; ng = sgid[ni]; }
+        const bool hit = valid && box_hit(c3, bx0, bx1, by0, by1);
+        const unsigned mask = __ballot_sync(kFull, hit);
+        if (hit) {
+            const int k = __popc(mask & lt);
+            sr0[w][k] = c0; sr1[w][k] = c1; sr2[w][k] = c2;
+            spos[w][k] = (uint32_t)(i - U.rs);
+            sg[w][k] = cg;
+        }
+        __syncwarp();
+        const int nh = __popc(mask);
+        for (int k = nh - 1; k >= 0; k--) {
+            const float4 a = sr0[w][k], b = sr1[w][k], c = sr2[w][k];
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = 0.0f;
+            bool any = false;
+            float dx, dy, alpha;
+            bool capped;
+            if (spos[w][k] < last && pair_eval(a, b, px, py, dx, dy, alpha, capped)) {
+                const float om = 1.0f - alpha;
+                T = __fdividef(T, om);
+                const float wgt = alpha * T;
+                float ga = g0 * (c.x - R0) + g1 * (c.y - R1) + g2 * (c.z - R2);
+                if (EXTRA) ga += gD * (b.z - RD) + gO * (1.0f - RO);
+                ga *= T;
+                R0 = alpha * c.x + om * R0;
+                R1 = alpha * c.y + om * R1;
+                R2 = alpha * c.z + om * R2;
+                if (EXTRA) {
+                    RD = alpha * b.z + om * RD;
+                    RO = alpha + om * RO;
+                }
+                const float gp = capped ? 0.0f : ga * alpha;
+                v[0] = wgt * g0; v[1] = wgt * g1; v[2] = wgt * g2;
+                v[3] = gp;
+                v[4] = gp * dx; v[5] = gp * dy;
+                v[6] = gp * dx * dx; v[7] = gp * dx * dy; v[8] = gp * dy * dy;
+                if (EXTRA) v[9] = wgt * gD;
+                any = true;
+            }
+            if (__any_sync(kFull, any)) {
+                const float r = warp_transpose_reduce16(v);
+                const int q = lane >> 1;
+                if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1))
+                    atomicAdd(g2d + (size_t)sg[w][k] * kNG + q, r);
+            }
+        }
+        __syncwarp();
+    }
+}
 
-    float px[PPT], py[PPT], T[PPT], R0[PPT], R1[PPT], R2[PPT], RD[PPT], RO[PPT];
-    float g0[PPT], g1[PPT], g2[PPT], gD[PPT], gO[PPT];
-    uint32_t last[PPT];
-    if (tid == 0) s_max = 0;
-    __syncthreads();
-    uint32_t mymax = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int local = tid + k * NT;
-        const int x = tx * TS + local % TS, y = ty * TS + local / TS;
-        px[k] = (float)x; py[k] = (float)y;
-        R0[k] = R1[k] = R2[k] = RD[k] = RO[k] = 0.0f;
-        g0[k] = g1[k] = g2[k] = gD[k] = gO[k] = 0.0f;
-        T[k] = 1.0f;
-        last[k] = 0;
-        if (x < W && y < H) {
-            const size_t p = (size_t)y * W + x;
-            T[k] = Tfin[p];
-            last[k] = ncon[p];
-            g0[k] = dL_drgb[3 * p]; g1[k] = dL_drgb[3 * p + 1]; g2[k] = dL_drgb[3 * p + 2];
-            if (EXTRA) {
-                gD[k] = dL_ddepth ? dL_ddepth[p] : 0.0f;
-                gO[k] = dL_dopac ? dL_dopac[p] : 0.0f;
-            }
-        }
-        mymax = max(mymax, last[k]);
-    }
-    atomicMax(&s_max, mymax);
-    __syncthreads();
-    const uint32_t end = rs + s_max;
-    // instances no pixel reached get zero gradients
-    for (uint32_t i = end + tid; i < re; i += NT) {
-        float* o = igrad + (size_t)sinst[i] * kNG;
-#pragma unroll
-        for (int q = 0; q < kNG; q++) o[q] = 0.0f;
-    }
-    for (int64_t bend = end; bend > (int64_t)rs; bend -= NT) {
-        const int64_t bstart = bend - NT > (int64_t)rs ? bend - NT : (int64_t)rs;
-        const int cnt = (int)(bend - bstart);
-        __syncthreads();
-        if (tid < cnt) {
-            const uint32_t d = sinst[bstart + tid];
-            const uint32_t g = owner[d];
-            sd[tid] = d;
-            s0[tid] = rec0[g];
-            s1[tid] = rec1[g];
-            s2[tid] = rec2[g];
-        }
-        __syncthreads();
-        for (int sub_end = cnt; sub_end > 0; sub_end -= kSub) {
-            const int sub_start = sub_end - kSub > 0 ? sub_end - kSub : 0;
-            for (int j = sub_end - 1; j >= sub_start; j--) {
-                const float4 a = s0[j], b = s1[j], c = s2[j];
-                const uint32_t pos = (uint32_t)(bstart + j) - rs;
-                float v[16];
-#pragma unroll
-                for (int q = 0; q < 16; q++) v[q] = 0.0f;
-                bool any = false;
-#pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    if (pos >= last[k]) continue;
-                    float dx, dy, alpha, G;
-                    bool capped;
-                    if (!pair_alpha(a, b, px[k], py[k], dx, dy, alpha, G, capped)) continue;
-                    T[k] = __fdiv_rn(T[k], __fsub_rn(1.0f, alpha));
-                    const float wgt = alpha * T[k];
-                    float ga = g0[k] * (c.x - R0[k]) + g1[k] * (c.y - R1[k]) + g2[k] * (c.z - R2[k]);
-                    if (EXTRA) ga += gD[k] * (a.z - RD[k]) + gO[k] * (1.0f - RO[k]);
-                    ga *= T[k];
-                    const float om = 1.0f - alpha;
-                    R0[k] = alpha * c.x + om * R0[k];
-                    R1[k] = alpha * c.y + om * R1[k];
-                    R2[k] = alpha * c.z + om * R2[k];
-                    if (EXTRA) {
-                        RD[k] = alpha * a.z + om * RD[k];
-                        RO[k] = alpha + om * RO[k];
-                    }
-                    const float gp = capped ? 0.0f : ga * alpha;
-                    v[0] += wgt * g0[k]; v[1] += wgt * g1[k]; v[2] += wgt * g2[k];
-                    v[3] += gp;
-                    v[4] += gp * dx; v[5] += gp * dy;
-                    v[6] += gp * dx * dx; v[7] += gp * dx * dy; v[8] += gp * dy * dy;
-                    if (EXTRA) v[9] += wgt * gD[k];
-                    any = true;
-                }
-                const int jj = j - sub_start;
-                if (__any_sync(kFull, any)) {
-                    const float r = warp_transpose_reduce16(v);
-                    if ((lane & 1) == 0 && (lane >> 1) < kNG) part[w][jj][lane >> 1] = r;
-                } else if (lane < kNG) {
-                    part[w][jj][lane] = 0.0f;
-                }
-            }
-            __syncthreads();
-            const int nsub = sub_end - sub_start;
-            for (int e = tid; e < nsub * kNG; e += NT) {
-                const int jj = e / kNG, q = e % kNG;
-                float s = 0.0f;
-#pragma unroll
-                for (int ww = 0; ww < NW; ww++) s += part[ww][jj][q];
-                igrad[(size_t)sd[sub_start + jj] * kNG + q] = s;
-            }
-            __syncthreads();
-        }
+// Records in sorted-instance order (and the owning Gaussian of each).
+__global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __restrict__ sinst,
+                          const uint32_t* __restrict__ owner, const float4* __restrict__ r0,
+                          const float4* __restrict__ r1, const float4* __restrict__ r2,
+                          const float4* __restrict__ r3, float4* __restrict__ s0, float4* __restrict__ s1,
+                          float4* __restrict__ s2, float4* __restrict__ s3, uint32_t* __restrict__ sg)
+{
+    const uint64_t I = *n_dev;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < I; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = owner[sinst[i]];
+        s0[i] = r0[g]; s1[i] = r1[g]; s2[i] = r2[g]; s3[i] = r3[g];
+        sg[i] = g;
     }
 }
 
 }  // namespace
+
+gl_status permute_records(View& v, cudaStream_t s)
+{
+    if (v.I == 0) return GL_OK;
+    const size_t I = (size_t)v.I;
+    GL_TRY(v.srec0.reserve(16 * I));
+    GL_TRY(v.srec1.reserve(16 * I));
+    GL_TRY(v.srec2.reserve(16 * I));
+    GL_TRY(v.srec3.reserve(16 * I));
+    GL_TRY(v.sgid.reserve(4 * I));
+    const int blocks = (int)std::min<size_t>(8 * 152, (I + 255) / 256);
+    k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.sorted_inst, v.iowner.as<uint32_t>(),
+                                     v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(),
+                                     v.rec3.as<float4>(), v.srec0.as<float4>(), v.srec1.as<float4>(),
+                                     v.srec2.as<float4>(), v.srec3.as<float4>(), v.sgid.as<uint32_t>());
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
 
 gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s)
 {
@@ -277,21 +308,15 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     GL_TRY(v.Tfin.reserve(4 * P));
     GL_TRY(v.ncon.reserve(4 * P));
     if (v.ntiles == 0) return GL_OK;
+    if (v.Ts != 8 && v.Ts != 16 && v.Ts != 32) { set_error("tile_size must be 8, 16 or 32"); return GL_ERR_INVALID; }
     PhaseScope ps(v.prof, PH_RASTER_FWD, s);
+    const int nunits = v.ntiles * (v.Ts * v.Ts / 32);
+    const int blocks = (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_raster_fwd<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(
+        nunits, v.Ts, v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.srec0.as<float4>(),
+        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.W, v.H, v.TX, rgb, depth, opac,
+        v.Tfin.as<float>(), v.ncon.as<uint32_t>());
     count_launches(1);
-    const uint32_t* own = v.iowner.as<uint32_t>();
-#define GL_FWD(TS_)                                                                          \
-    k_raster_fwd<TS_><<<v.ntiles, RCfg<TS_>::NT, 0, s>>>(                                    \
-        v.ranges.as<uint32_t>(), v.sorted_inst, own, v.rec0.as<float4>(), v.rec1.as<float4>(), \
-        v.rec2.as<float4>(), v.W, v.H, v.TX, rgb, depth, opac, v.Tfin.as<float>(),           \
-        v.ncon.as<uint32_t>())
-    switch (v.Ts) {
-        case 8: GL_FWD(8); break;
-        case 16: GL_FWD(16); break;
-        case 32: GL_FWD(32); break;
-        default: set_error("tile_size must be 8, 16 or 32"); return GL_ERR_INVALID;
-    }
-#undef GL_FWD
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -299,23 +324,21 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
 gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
                           const float* dL_dopac, cudaStream_t s)
 {
+    GL_TRY(v.g2d.reserve(sizeof(float) * kNG * (size_t)std::max<int64_t>(v.n, 1)));
+    PhaseScope ps(v.prof, PH_RASTER_BWD, s);
+    GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * (size_t)v.n, s));
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     const bool extra = dL_ddepth != nullptr || dL_dopac != nullptr;
-    PhaseScope ps(v.prof, PH_RASTER_BWD, s);
+    const int nunits = v.ntiles * (v.Ts * v.Ts / 32);
+    const int blocks = (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock;
+#define GL_BWD_ARGS                                                                                     \
+    nunits, v.Ts, v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.srec0.as<float4>(),           \
+        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.sgid.as<uint32_t>(), v.W, v.H, \
+        v.TX, v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>()
+    if (extra) k_raster_bwd<true><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(GL_BWD_ARGS);
+    else k_raster_bwd<false><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(GL_BWD_ARGS);
+#undef GL_BWD_ARGS
     count_launches(1);
-    const uint32_t* own = v.iowner.as<uint32_t>();
-#define GL_BWD(TS_, EX_)                                                                      \
-    k_raster_bwd<TS_, EX_><<<v.ntiles, RCfg<TS_>::NT, 0, s>>>(                                \
-        v.ranges.as<uint32_t>(), v.sorted_inst, own, v.rec0.as<float4>(), v.rec1.as<float4>(),  \
-        v.rec2.as<float4>(), v.W, v.H, v.TX, v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, \
-        dL_ddepth, dL_dopac, v.igrad.as<float>())
-    switch (v.Ts) {
-        case 8: if (extra) GL_BWD(8, true); else GL_BWD(8, false); break;
-        case 16: if (extra) GL_BWD(16, true); else GL_BWD(16, false); break;
-        case 32: if (extra) GL_BWD(32, true); else GL_BWD(32, false); break;
-        default: set_error("tile_size must be 8, 16 or 32"); return GL_ERR_INVALID;
-    }
-#undef GL_BWD
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
