@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--updates", type=int, default=8, help="keyframe updates for the latency figure")
     ap.add_argument("--update-steps", type=int, default=100, help="optimise steps per keyframe update (K)")
     ap.add_argument("--keyframes", type=int, default=16)
+    ap.add_argument("--window", type=int, default=8, help="views per batched window step (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -348,6 +349,29 @@ def run_ours(args):
     st = m.stats()
     m.set_timing(False)
 
+    # batched: windows of several keyframes rendered and back-propagated
+    # together, one Adam step per window (mean of the views' losses)
+    batched = None
+    if args.window > 1:
+        wv = min(args.window, n_kf)
+        nwin = max(5, args.steps // wv)
+        wins = [rng.choice(n_kf, wv, replace=False) for _ in range(nwin + 2)]
+
+        def wstep(ks):
+            m.optimize_step([(int(k), cams[int(k)], None) for k in ks])
+        for i in range(2):
+            wstep(wins[i])
+        torch.cuda.synchronize()
+        barrier(dist)
+        ev0.record(stream)
+        for i in range(nwin):
+            wstep(wins[2 + i])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        w_ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+        batched = {"views_per_window": wv, "windows": nwin, "ms_per_window": w_ms / nwin,
+                   "windows_per_s": ws * nwin / (w_ms / 1e3), "views_per_s": ws * nwin * wv / (w_ms / 1e3)}
+
     # end to end through the C ABI with host buffers: pinned host target in,
     # loss out, every step
     e2e = None
@@ -438,6 +462,7 @@ def run_ours(args):
         "kernels_pass_ms_per_step": ms_timed / args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": int(launches),
         "clocks": clk,
         "keyframe_update": ({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),

@@ -88,6 +88,8 @@ def _load():
         lib.orc_backward_2d.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, P, P, i64, P]
         lib.orc_backward_params.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_adam.argtypes = [i64, i32, P, P, P, P, P, dbl, dbl, dbl, dbl, i64]
+        lib.orc_expf_decision.argtypes = [C.c_float]
+        lib.orc_expf_decision.restype = C.c_float
         lib.orc_uniform.argtypes = [C.c_uint64, C.c_uint64]
         lib.orc_uniform.restype = dbl
         lib.orc_sky.argtypes = [i64, dbl, C.c_uint64, P, P]
@@ -262,6 +264,11 @@ def adam_update(p, m, v, g, lr, step, mask=None, b1=0.9, b2=0.999, eps=1e-15):
     lib.orc_adam(p.size, stride, _p(mk), _p(p), _p(m), _p(v), _p(g), lr, b1, b2, eps, int(step))
 
 
+def expf_decision(x: float) -> float:
+    """exp as the float32 decision path evaluates it (see gl_oracle.c)."""
+    return float(_load().orc_expf_decision(float(x)))
+
+
 def uniform(seed: int, i: int) -> float:
     return _load().orc_uniform(C.c_uint64(seed), C.c_uint64(i))
 
@@ -357,3 +364,52 @@ def new_state(params: dict, E=None) -> dict:
                         np.float64).reshape(3, 4).copy()
     return dict(p=p, m={k: np.zeros_like(v) for k, v in p.items()},
                 v={k: np.zeros_like(v) for k, v in p.items()})
+
+
+def optimize_window(params: dict, state: dict, cams, targets, step: int, Ts: int = 16,
+                    lr: dict | None = None, sparse: bool = True, lam: float = LAMBDA_DSSIM,
+                    exposure_steps=None) -> dict:
+    """One window step over several keyframe views: the loss is the mean of the
+    per-view losses (Eq. 9 with each view's exposure), the Gaussians take one
+    Adam step on the mean gradient (sparse: Gaussians visible in any view), and
+    each view's exposure takes one Adam step on its own (1/n-weighted) gradient.
+    `state["p"]["E"]` is a list of the views' 3x4 exposures (moments alike)."""
+    lr = dict(DEFAULT_LR, **(lr or {}))
+    n = len(cams)
+    exposure_steps = exposure_steps or [1] * n
+    acc, vis, losses, dEs = None, None, [], []
+    for v in range(n):
+        r = loss_and_grads(params, cams[v], targets[v], state["p"]["E"][v], Ts, lam)
+        g = r["grads"]
+        if acc is None:
+            acc = {k: g[k] / n for k in ("means", "log_scales", "quats", "logits", "sh")}
+            vis = r["pre"]["radius"] > 0
+        else:
+            for k in acc:
+                acc[k] = acc[k] + g[k] / n
+            vis = vis | (r["pre"]["radius"] > 0)
+        losses.append(r["loss"]["loss"])
+        dEs.append(r["loss"]["dL_dE"] / n)
+    mask = vis.astype(np.uint8) if sparse else None
+    for name in ("means", "log_scales", "quats", "logits"):
+        adam_update(state["p"][name], state["m"][name], state["v"][name], acc[name], lr[name], step, mask)
+    sh_p, sh_m, sh_v = state["p"]["sh"], state["m"]["sh"], state["v"]["sh"]
+    for sl, key in ((slice(0, 1), "sh_dc"), (slice(1, None), "sh_rest")):
+        if sh_p[:, sl].size == 0:
+            continue
+        pp, mm, vv = (np.ascontiguousarray(a[:, sl]) for a in (sh_p, sh_m, sh_v))
+        adam_update(pp, mm, vv, np.ascontiguousarray(acc["sh"][:, sl]), lr[key], step, mask)
+        sh_p[:, sl], sh_m[:, sl], sh_v[:, sl] = pp, mm, vv
+    for v in range(n):
+        adam_update(state["p"]["E"][v], state["m"]["E"][v], state["v"]["E"][v], dEs[v], lr["exposure"],
+                    exposure_steps[v])
+    return dict(loss=float(np.mean(losses)), losses=losses, visible=vis, grads=acc)
+
+
+def new_window_state(params: dict, n_views: int) -> dict:
+    p = {k: np.asarray(v, np.float64).copy() for k, v in params.items()}
+    I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
+    st = dict(p=p, m={k: np.zeros_like(v) for k, v in p.items()}, v={k: np.zeros_like(v) for k, v in p.items()})
+    for d in ("p", "m", "v"):
+        st[d]["E"] = [(I34.copy() if d == "p" else np.zeros((3, 4))) for _ in range(n_views)]
+    return st

@@ -122,6 +122,33 @@ void orc_sh_basis(int deg, double x, double y, double z, double* Y, double* dY)
 }
 
 /* ------------------------------------------------------------------------- */
+/* exp in the float32 decision path: Cody-Waite reduction x = k ln2 + r with */
+/* ln2 split into a 16-bit head and a tail, then the Taylor polynomial of    */
+/* exp(r) to degree 8 (coefficients 1/j!) by Horner's rule, then 2^k.  A     */
+/* fixed sequence of correctly rounded float32 operations, so any IEEE       */
+/* implementation of the same sequence returns the same bits; accurate to a  */
+/* couple of ulp (|r| <= ln2/2, truncation r^9/9! < 1.4e-10).               */
+/* ------------------------------------------------------------------------- */
+float orc_expf_decision(float x)
+{
+    const float ln2_hi = 0.693145751953125f;      /* 45425 * 2^-16 */
+    const float ln2_lo = 1.42860682030941723212e-6f;
+    const float k = rintf(x * 1.44269504088896340736f);
+    const float r = (x - k * ln2_hi) - k * ln2_lo;
+    float p = 1.0f / 40320.0f;
+    p = p * r + 1.0f / 5040.0f;
+    p = p * r + 1.0f / 720.0f;
+    p = p * r + 1.0f / 120.0f;
+    p = p * r + 1.0f / 24.0f;
+    p = p * r + 1.0f / 6.0f;
+    p = p * r + 0.5f;
+    p = p * r + 1.0f;
+    p = p * r + 1.0f;
+    if (!(k >= -300.0f && k <= 300.0f)) return k > 0.0f ? INFINITY : 0.0f;
+    return ldexpf(p, (int)k);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Float32 decision path: cull, radius, rectangle, depth key (Eq. 2-3).      */
 /* Returns 1 if the Gaussian is kept.                                         */
 /* ------------------------------------------------------------------------- */
@@ -145,11 +172,10 @@ static int project_f32(const double* mud, const double* lsd, const double* qd,
     float v = fy * yz + cy;
     if (!(fabsf(u) <= 3.0e38f) || !(fabsf(v) <= 3.0e38f)) return 0;
 
-    /* Eq. 1: Sigma = R S S^T R^T, S = diag(exp(log-scale)).  exp is taken in  */
-    /* double and rounded once, so both sides round the same real number.      */
-    float s0 = (float)exp((double)ls[0]);
-    float s1 = (float)exp((double)ls[1]);
-    float s2 = (float)exp((double)ls[2]);
+    /* Eq. 1: Sigma = R S S^T R^T, S = diag(exp(log-scale)), exp as above.   */
+    float s0 = orc_expf_decision(ls[0]);
+    float s1 = orc_expf_decision(ls[1]);
+    float s2 = orc_expf_decision(ls[2]);
     float qq = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
     if (!(qq > 0.0f) || !(qq <= 3.0e38f)) return 0;
     float inv = 1.0f / sqrtf(qq);

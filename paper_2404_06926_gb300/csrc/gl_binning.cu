@@ -73,26 +73,30 @@ __device__ __forceinline__ T block_sum(T x, T* sm)
 // ---------------------------------------------------------------------------
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
-k_preprocess(GParams p, Cam cam, int Ts, int TX, int TY, float4* __restrict__ rec0,
-             float4* __restrict__ rec1, float4* __restrict__ rec2, float4* __restrict__ rec3,
-             int* __restrict__ radius,
-             int4* __restrict__ rect, uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
-             uint32_t* __restrict__ gidx)
+k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int Ts,
+             float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
+             float4* __restrict__ rec3, int* __restrict__ radius, int4* __restrict__ rect,
+             uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey, uint32_t* __restrict__ gidx)
 {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= p.n) return;
+    // t indexes (view, Gaussian) pairs: t = view * n + g
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int vw = (int)(t / p.n);
+    const int64_t g = t - (int64_t)vw * p.n;
+    const Cam cam = views[vw].cam;
+    const int TX = views[vw].TX, TY = views[vw].TY;
     constexpr int K = (DEG + 1) * (DEG + 1);
     float mu[3] = {p.means[3 * g], p.means[3 * g + 1], p.means[3 * g + 2]};
     float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
     const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    gidx[g] = (uint32_t)g;
+    gidx[t] = (uint32_t)t;
     Decision D;
     if (!decide(mu, ls, q, cam, Ts, TX, TY, D)) {
-        radius[g] = 0;
-        touched[g] = 0;
-        dkey[g] = 0xffffffffu;
-        rect[g] = make_int4(0, 0, 0, 0);
+        radius[t] = 0;
+        touched[t] = 0;
+        dkey[t] = 0xffffffffu;
+        rect[t] = make_int4(0, 0, 0, 0);
         return;
     }
     const float o = 1.0f / (1.0f + __expf(-p.logits[g]));
@@ -128,21 +132,21 @@ k_preprocess(GParams p, Cam cam, int Ts, int TX, int TY, float4* __restrict__ re
     }
     // log2-domain conic and opacity for the raster kernels
     const float A = D.c * id, B = -D.b * id, C = D.a * id;
-    rec0[g] = make_float4(D.u, D.v, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
-    rec1[g] = make_float4(-kLog2e * B, log2f(o), D.z, o);
-    rec2[g] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
+    rec0[t] = make_float4(D.u, D.v, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
+    rec1[t] = make_float4(-kLog2e * B, log2f(o), D.z, o);
+    rec2[t] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
     // conservative box of {alpha >= 1/255}: the ellipse d^T Sigma'^-1 d <= 2 ln(255 o)
     const float kappa = 2.0f * logf(255.0f * o);
     if (kappa > 0.0f) {
         const float hx = sqrtf(kappa * D.a) * 1.001f + 0.01f, hy = sqrtf(kappa * D.c) * 1.001f + 0.01f;
-        rec3[g] = make_float4(D.u - hx, D.u + hx, D.v - hy, D.v + hy);
+        rec3[t] = make_float4(D.u - hx, D.u + hx, D.v - hy, D.v + hy);
     } else {
-        rec3[g] = make_float4(3.0e38f, -3.0e38f, 3.0e38f, -3.0e38f);
+        rec3[t] = make_float4(3.0e38f, -3.0e38f, 3.0e38f, -3.0e38f);
     }
-    radius[g] = D.r;
-    rect[g] = make_int4(D.x0, D.y0, D.x1, D.y1);
-    touched[g] = (uint32_t)((D.x1 - D.x0) * (D.y1 - D.y0));
-    dkey[g] = __float_as_uint(D.z);
+    radius[t] = D.r;
+    rect[t] = make_int4(D.x0, D.y0, D.x1, D.y1);
+    touched[t] = (uint32_t)((D.x1 - D.x0) * (D.y1 - D.y0));
+    dkey[t] = __float_as_uint(D.z);
 }
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v0, uint64_t v1)
@@ -316,9 +320,10 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint6
 
 __global__ void __launch_bounds__(kPreThreads)
 k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched,
-            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int64_t n, int TX,
-            uint64_t cap, uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile,
-            uint32_t* __restrict__ ival, uint32_t* __restrict__ iowner)
+            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int64_t n,
+            const ViewDesc* __restrict__ views, int64_t per_view, uint64_t cap,
+            uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile, uint32_t* __restrict__ ival,
+            uint32_t* __restrict__ iowner)
 {
     __shared__ uint64_t sm[kPreThreads / 32 + 1];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
@@ -340,10 +345,12 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
         dup_off[g] = (uint32_t)off;
         if (cc[k] && off + cc[k] <= cap) {
             const int4 r = rect[g];
+            const ViewDesc& vd = views[g / per_view];
+            const int TX = vd.TX, base = vd.tile_base;
             uint64_t d = off;
             for (int ty = r.y; ty < r.w; ty++)
                 for (int tx = r.x; tx < r.z; tx++, d++) {
-                    itile[d] = (uint32_t)(ty * TX + tx);
+                    itile[d] = (uint32_t)(base + ty * TX + tx);
                     ival[d] = (uint32_t)d;
                     iowner[d] = g;
                 }
@@ -476,11 +483,11 @@ gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, c
 {
     *n_visible = 0;
     *sum_contrib = 0;
-    const int64_t P = (int64_t)v.W * v.H;
+    const int64_t P = v.P;
     if (v.n == 0 && P == 0) return GL_OK;
     unsigned long long* d = reinterpret_cast<unsigned long long*>(v.count.as<uint64_t>() + 4);
     GL_CUDA_TRY(cudaMemsetAsync(d, 0, 16, s));
-    k_view_counts<<<4 * 152, 256, 0, s>>>(v.radius.as<int>(), v.n, v.ncon.as<uint32_t>(), v.ncon.p ? P : 0, d);
+    k_view_counts<<<4 * 152, 256, 0, s>>>(v.radius.as<int>(), v.n * v.V, v.ncon.as<uint32_t>(), v.ncon.p ? P : 0, d);
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     unsigned long long h[2];
@@ -516,15 +523,49 @@ gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaSt
 
 gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream_t s)
 {
-    const int64_t n = p.n;
-    v.n = n;
-    v.W = cam.W;
-    v.H = cam.H;
+    return bin_views(v, p, &cam, nullptr, 1, Ts, s);
+}
+
+gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra* extra, int V, int Ts,
+                    cudaStream_t s)
+{
+    if (V < 1 || V > kMaxViews) { set_error("1..64 views per step"); return GL_ERR_INVALID; }
+    v.V = V;
+    v.n = p.n;
     v.Ts = Ts;
-    v.TX = (cam.W + Ts - 1) / Ts;
-    v.TY = (cam.H + Ts - 1) / Ts;
-    v.ntiles = v.TX * v.TY;
-    v.cam = cam;
+    v.W = cams[0].W;
+    v.H = cams[0].H;
+    v.TX = (cams[0].W + Ts - 1) / Ts;
+    v.TY = (cams[0].H + Ts - 1) / Ts;
+    v.cam = cams[0];
+    int tiles = 0, ltiles = 0;
+    int64_t pix = 0;
+    for (int i = 0; i < V; i++) {
+        ViewDesc& d = v.hdesc[i];
+        d = ViewDesc{};
+        d.cam = cams[i];
+        d.TX = (cams[i].W + Ts - 1) / Ts;
+        d.TY = (cams[i].H + Ts - 1) / Ts;
+        d.tile_base = tiles;
+        d.ltile_base = ltiles;
+        d.pix_base = pix;
+        const ViewExtra ex = extra ? extra[i] : ViewExtra{};
+        d.target = ex.target;
+        d.E = ex.E;
+        d.Em = ex.Em;
+        d.e_bc1 = ex.e_bc1;
+        d.e_bc2 = ex.e_bc2;
+        d.weight = ex.weight;
+        tiles += d.TX * d.TY;
+        ltiles += ((cams[i].W + 31) / 32) * ((cams[i].H + 31) / 32);
+        pix += (int64_t)cams[i].W * cams[i].H;
+    }
+    v.ntiles = tiles;
+    v.nltiles = ltiles;
+    v.P = pix;
+    GL_TRY(v.upload_descs(s));
+    const ViewDesc* dv = v.d_desc();
+    const int64_t n = p.n * V;   // (view, Gaussian) pairs
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     GL_TRY(v.rec0.reserve(16 * nn));
     GL_TRY(v.rec1.reserve(16 * nn));
@@ -553,16 +594,15 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
         GL_CUDA_TRY(cudaGetLastError());
         return GL_OK;
     }
-    const int TX = v.TX, TY = v.TY;
     dim3 grid((unsigned)((n + kPreThreads - 1) / kPreThreads));
     {
     PhaseScope ps(v.prof, PH_PREPROCESS, s);
     count_launches(1);
     switch (p.deg) {
-        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, cam, Ts, TX, TY, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
@@ -604,7 +644,7 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     }
     const uint64_t cap2 = v.itile.bytes / 4;
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
-                                           v.bsum.as<uint64_t>(), n, TX, cap2, v.dup_off.as<uint32_t>(),
+                                           v.bsum.as<uint64_t>(), n, dv, p.n, cap2, v.dup_off.as<uint32_t>(),
                                            v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.iowner.as<uint32_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());

@@ -149,6 +149,25 @@ gl_status View::init()
 {
     GL_TRY(count.reserve(64));
     if (!h_count) GL_CUDA_TRY(cudaMallocHost(&h_count, 64));
+    if (!hpin) GL_CUDA_TRY(cudaMallocHost(&hpin, sizeof(ViewDesc) * kMaxViews * kDescRing));
+    for (int i = 0; i < kDescRing; i++)
+        if (!pin_ev[i]) GL_CUDA_TRY(cudaEventCreateWithFlags(&pin_ev[i], cudaEventDisableTiming));
+    GL_TRY(desc.reserve(sizeof(ViewDesc) * kMaxViews));
+    return GL_OK;
+}
+
+// Copy hdesc[0..V) to the device through the next pinned slot; a slot is
+// reused only after its previous copy has executed.
+gl_status View::upload_descs(cudaStream_t s)
+{
+    const int slot = pin_slot;
+    pin_slot = (pin_slot + 1) % kDescRing;
+    if (pin_used[slot]) GL_CUDA_TRY(cudaEventSynchronize(pin_ev[slot]));
+    ViewDesc* h = hpin + (size_t)slot * kMaxViews;
+    std::memcpy(h, hdesc, sizeof(ViewDesc) * (size_t)V);
+    GL_CUDA_TRY(cudaMemcpyAsync(desc.p, h, sizeof(ViewDesc) * (size_t)V, cudaMemcpyHostToDevice, s));
+    GL_CUDA_TRY(cudaEventRecord(pin_ev[slot], s));
+    pin_used[slot] = true;
     return GL_OK;
 }
 
@@ -158,8 +177,16 @@ void View::release()
                      &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d,
                      &hist, &ranges, &tile_order, &Tfin, &ncon, &rgb, &depth, &opac};
     for (DevBuf* b : all) b->release();
+    desc.release();
     if (h_count) cudaFreeHost(h_count);
     h_count = nullptr;
+    if (hpin) cudaFreeHost(hpin);
+    hpin = nullptr;
+    for (int i = 0; i < kDescRing; i++) {
+        if (pin_ev[i]) cudaEventDestroy(pin_ev[i]);
+        pin_ev[i] = nullptr;
+        pin_used[i] = false;
+    }
 }
 
 namespace {
@@ -364,7 +391,7 @@ extern "C" gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const fl
     gl_ctx_impl& c = ctx->impl;
     GL_TRY(c.loss_part.reserve(sizeof(float) * (size_t)loss_partials_needed(width, height)));
     return photometric_loss(rgb, target, E34, width, height, lambda_dssim, dL_drgb, c.loss_part.as<float>(),
-                            loss_out, dL_dE, nullptr, c.stream);
+                            loss_out, dL_dE, c.stream);
 }
 
 extern "C" gl_status gl_ctx_get_preprocess(gl_ctx* ctx, int32_t* radius, int32_t* rect, float* mean2d,
@@ -402,7 +429,7 @@ extern "C" gl_status gl_ctx_get_pixel_state(gl_ctx* ctx, float* T_final, uint32_
 {
     if (!ctx || !ctx->impl.has_forward) { set_error("no forward on this ctx"); return GL_ERR_INVALID; }
     View& v = ctx->impl.view;
-    const size_t P = (size_t)v.W * v.H;
+    const size_t P = (size_t)v.P;
     if (T_final) GL_CUDA_TRY(cudaMemcpyAsync(T_final, v.Tfin.p, 4 * P, cudaMemcpyDeviceToDevice, ctx->impl.stream));
     if (n_contrib) GL_CUDA_TRY(cudaMemcpyAsync(n_contrib, v.ncon.p, 4 * P, cudaMemcpyDeviceToDevice, ctx->impl.stream));
     return GL_OK;
@@ -512,16 +539,6 @@ gl_status zero_moments(gl_map* m, int64_t from, int64_t count)
     return GL_OK;
 }
 
-// Copy host-or-device floats to a device pointer (staging host data).
-gl_status to_device(const float* src, size_t count, DevBuf& stage, const float** out, cudaStream_t s)
-{
-    if (is_device_ptr(src)) { *out = src; return GL_OK; }
-    GL_TRY(stage.reserve(4 * count));
-    GL_CUDA_TRY(cudaMemcpyAsync(stage.p, src, 4 * count, cudaMemcpyHostToDevice, s));
-    *out = stage.as<float>();
-    return GL_OK;
-}
-
 gl_status from_device(float* dst, const float* src, size_t count, cudaStream_t s)
 {
     GL_CUDA_TRY(cudaMemcpyAsync(dst, src, 4 * count, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -580,7 +597,7 @@ extern "C" gl_status gl_map_create(const gl_config* cfg, void* stream, gl_map** 
     m->ctx.stream = m->stream;
     m->ctx.view.prof = &m->prof;
     GL_TRY(m->ctx.view.init());
-    GL_CUDA_TRY(cudaMallocHost(&m->h_loss, 16));
+    GL_CUDA_TRY(cudaMallocHost(&m->h_loss, sizeof(float) * kMaxViews));
     GL_TRY(m->loss_dev.reserve(16));
     GL_TRY(map_reserve(m.get(), std::max<int64_t>(cfg->n_sky, 1)));
     if (cfg->n_sky > 0) {
@@ -716,39 +733,70 @@ extern "C" gl_status gl_render(gl_map* m, const gl_pose* pose, const gl_intrinsi
 extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32_t n_views, float* out_loss)
 {
     if (!m || !views || n_views < 1) { set_error("need at least one view"); return GL_ERR_INVALID; }
-    if (n_views != 1) { set_error("multi-view windows go through gl_optimize_window"); return GL_ERR_INVALID; }
-    const gl_keyframe& kv = views[0];
-    Cam cam;
-    GL_TRY(make_cam(&kv.pose, &kv.K, cam));
-    gl_status st;
-    Keyframe* kf = get_kf(m, kv.id, true, &st);
-    if (!kf) return st;
-    const size_t P = (size_t)cam.W * cam.H;
-    const float* target = nullptr;
-    if (kv.image) {
-        GL_TRY(to_device(kv.image, 3 * P, m->stage_img, &target, m->stream));
-    } else {
-        if (!kf->has_image) { set_error("keyframe has no stored image"); return GL_ERR_NOT_FOUND; }
-        if (kf->K.width != cam.W || kf->K.height != cam.H) { set_error("stored image size differs"); return GL_ERR_INVALID; }
-        target = kf->image.as<float>();
+    if (n_views > kMaxViews) { set_error("at most 64 views per step"); return GL_ERR_INVALID; }
+    const int V = n_views;
+    Cam cams[kMaxViews];
+    ViewExtra extra[kMaxViews];
+    Keyframe* kfs[kMaxViews];
+    for (int i = 0; i < V; i++) {
+        GL_TRY(make_cam(&views[i].pose, &views[i].K, cams[i]));
+        for (int j = 0; j < i; j++)
+            if (views[j].id == views[i].id) { set_error("a keyframe appears twice in one window"); return GL_ERR_INVALID; }
+        gl_status st;
+        kfs[i] = get_kf(m, views[i].id, true, &st);
+        if (!kfs[i]) return st;
+        if (!views[i].image) {
+            if (!kfs[i]->has_image) { set_error("keyframe has no stored image"); return GL_ERR_NOT_FOUND; }
+            if (kfs[i]->K.width != cams[i].W || kfs[i]->K.height != cams[i].H) {
+                set_error("stored image size differs");
+                return GL_ERR_INVALID;
+            }
+        }
+    }
+    // targets: registered device copies, caller device images, or caller host
+    // images staged into one buffer at each view's pixel offset
+    int64_t P = 0;
+    for (int i = 0; i < V; i++) P += (int64_t)cams[i].W * cams[i].H;
+    bool need_stage = false;
+    for (int i = 0; i < V; i++)
+        if (views[i].image && !is_device_ptr(views[i].image)) need_stage = true;
+    if (need_stage) GL_TRY(m->stage_img.reserve(12 * (size_t)P));
+    const gl_config& c = m->cfg;
+    int64_t off = 0;
+    for (int i = 0; i < V; i++) {
+        const size_t Pi = (size_t)cams[i].W * cams[i].H;
+        const float* tgt = nullptr;
+        if (!views[i].image) tgt = kfs[i]->image.as<float>();
+        else if (is_device_ptr(views[i].image)) tgt = views[i].image;
+        else {
+            float* dst = m->stage_img.as<float>() + 3 * off;
+            GL_CUDA_TRY(cudaMemcpyAsync(dst, views[i].image, 12 * Pi, cudaMemcpyHostToDevice, m->stream));
+            tgt = dst;
+        }
+        off += (int64_t)Pi;
+        Keyframe* kf = kfs[i];
+        kf->steps++;
+        float* e = kf->expo.as<float>();
+        extra[i].target = tgt;
+        extra[i].E = e;
+        extra[i].Em = e + 12;
+        extra[i].e_bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
+        extra[i].e_bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
+        extra[i].weight = 1.0f / (float)V;
     }
     View& v = m->ctx.view;
-    GL_TRY(render_internal(m, cam, m->cfg.tile_size));
-    GL_TRY(m->dLdC.reserve(12 * P));
-    GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * (size_t)loss_partials_needed(cam.W, cam.H)));
+    GL_TRY(v.rgb.reserve(12 * (size_t)P));
+    GL_TRY(bin_views(v, m->params(), cams, extra, V, c.tile_size, m->stream));
+    GL_TRY(raster_forward(v, v.rgb.as<float>(), nullptr, nullptr, m->stream));
+    GL_TRY(m->dLdC.reserve(12 * (size_t)P));
+    GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * 14 * (size_t)v.nltiles));
+    GL_TRY(m->loss_dev.reserve(sizeof(float) * kMaxViews));
     m->step++;
-    kf->steps++;
-    const gl_config& c = m->cfg;
-    ExpAdam ea;
-    float* e = kf->expo.as<float>();
-    ea.E = e; ea.m = e + 12; ea.v = e + 24;
-    ea.lr = c.lr_exposure; ea.b1 = c.adam_b1; ea.b2 = c.adam_b2; ea.eps = c.adam_eps;
-    ea.bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
-    ea.bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
     {
         PhaseScope ps(&m->prof, PH_LOSS, m->stream);
-        GL_TRY(photometric_loss(v.rgb.as<float>(), target, e, cam.W, cam.H, c.lambda_dssim, m->dLdC.as<float>(),
-                                m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), nullptr, &ea, m->stream));
+        GL_TRY(photometric_loss_views(v, v.rgb.as<float>(), c.lambda_dssim, m->dLdC.as<float>(),
+                                      m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), c.adam_b1, c.adam_b2,
+                                      c.adam_eps, c.lr_exposure, m->stream));
     }
     GL_TRY(raster_backward(v, m->dLdC.as<float>(), nullptr, nullptr, m->stream));
     AdamArgs a;
@@ -757,14 +805,16 @@ extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32
     a.lr_pos = c.lr_pos; a.lr_dc = c.lr_sh_dc; a.lr_rest = c.lr_sh_rest; a.lr_op = c.lr_opacity;
     a.lr_scale = c.lr_scale; a.lr_rot = c.lr_rot;
     a.b1 = c.adam_b1; a.b2 = c.adam_b2; a.eps = c.adam_eps;
-    a.bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)m->step));
-    a.bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)m->step));
+    a.ibc1 = (float)(1.0 / (1.0 - std::pow((double)c.adam_b1, (double)m->step)));
+    a.isbc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)c.adam_b2, (double)m->step)));
     a.sparse = c.sparse_adam;
     GL_TRY(params_adam(v, m->params(), gl_map::mut(m->prm), a, m->stream));
     if (out_loss) {
-        GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4, cudaMemcpyDeviceToHost, m->stream));
+        GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, m->stream));
         GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
-        *out_loss = m->h_loss[0];
+        double s = 0.0;
+        for (int i = 0; i < V; i++) s += m->h_loss[i];
+        *out_loss = (float)(s / V);
     }
     return GL_OK;
 }

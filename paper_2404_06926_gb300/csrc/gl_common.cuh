@@ -43,6 +43,38 @@ struct Cam {
     int W, H;
 };
 
+// One view of a (possibly multi-view) step, read by the kernels from device
+// memory.  Views are concatenated: raster tiles, 32x32 loss tiles and pixels
+// of view v start at tile_base, ltile_base and pix_base.
+struct ViewDesc {
+    Cam cam;
+    int TX, TY;              // raster tiles of the view
+    int tile_base;           // global index of the view's first raster tile
+    int ltile_base;          // global index of the view's first 32x32 loss tile
+    long long pix_base;      // first pixel of the view in the concatenated images
+    const float* target;     // loss target (H*W*3 RGB) or null
+    float* E;                // exposure [A | b] (12) read by the loss; null = identity
+    float* Em;               // Adam moments of E: m (12) then v (12); null = E not updated
+    float e_bc1, e_bc2;      // exposure Adam bias corrections 1 - beta^t for this step
+    float weight;            // weight of the view's loss in the step (1 / views)
+    int pad;
+};
+
+// View of a global raster tile (views are few; linear search over the table).
+__device__ __forceinline__ int view_of_tile(const ViewDesc* __restrict__ views, int V, int tile)
+{
+    int v = 0;
+    while (v + 1 < V && views[v + 1].tile_base <= tile) v++;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_ltile(const ViewDesc* __restrict__ views, int V, int lt)
+{
+    int v = 0;
+    while (v + 1 < V && views[v + 1].ltile_base <= lt) v++;
+    return v;
+}
+
 // Read-only view of Gaussian parameters (device, one row-major array each).
 struct GParams {
     const float* means;       // n*3
@@ -67,8 +99,7 @@ struct GMut {
 // ---------------------------------------------------------------------------
 // Integer-deciding projection (Eq. 2-3): cull, radius, tile rectangle and
 // depth key.  Every operation is an explicitly rounded float32 operation in
-// a fixed order (no contraction), so the decision is reproducible; exp of the
-// log-scale is taken in double and rounded once.
+// a fixed order (no contraction), so the decision is reproducible.
 // ---------------------------------------------------------------------------
 struct Decision {
     float u, v, z;           // mu' and depth
@@ -81,6 +112,29 @@ __device__ __forceinline__ float fmr(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ float far_(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsr(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdr(float a, float b) { return __fdiv_rn(a, b); }
+
+// exp of the decision path: x = k ln2 + r (ln2 as a 16-bit head plus tail),
+// Taylor polynomial of exp(r) to degree 8 by Horner's rule, times 2^k -- a
+// fixed sequence of correctly rounded float32 operations (no FP64, no
+// contraction), accurate to a couple of ulp for |r| <= ln2/2.
+__device__ __forceinline__ float expf_decision(float x)
+{
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.42860682030941723212e-6f;
+    const float k = rintf(__fmul_rn(x, 1.44269504088896340736f));
+    const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(k, ln2_hi)), __fmul_rn(k, ln2_lo));
+    float p = 1.0f / 40320.0f;
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 5040.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 720.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 120.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 24.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 6.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    if (!(k >= -300.0f && k <= 300.0f)) return k > 0.0f ? __int_as_float(0x7f800000) : 0.0f;
+    return ldexpf(p, (int)k);
+}
 
 __device__ __forceinline__ bool decide(const float mu[3], const float ls[3], const float q[4],
                                        const Cam& cam, int Ts, int TX, int TY, Decision& D)
@@ -96,9 +150,9 @@ __device__ __forceinline__ bool decide(const float mu[3], const float ls[3], con
     float v = far_(fmr(cam.fy, yz), cam.cy);
     if (!(fabsf(u) <= 3.0e38f) || !(fabsf(v) <= 3.0e38f)) return false;
 
-    float s0 = (float)exp((double)ls[0]);
-    float s1 = (float)exp((double)ls[1]);
-    float s2 = (float)exp((double)ls[2]);
+    float s0 = expf_decision(ls[0]);
+    float s1 = expf_decision(ls[1]);
+    float s2 = expf_decision(ls[2]);
     float qq = far_(far_(far_(fmr(q[0], q[0]), fmr(q[1], q[1])), fmr(q[2], q[2])), fmr(q[3], q[3]));
     if (!(qq > 0.0f) || !(qq <= 3.0e38f)) return false;
     float inv = fdr(1.0f, __fsqrt_rn(qq));
@@ -194,36 +248,51 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float Y[16])
     }
 }
 
-// dY[k][j] = d Y_k / d dir_j (dir treated as unconstrained).
+// g += sum_k c_k grad Y_k(x, y, z) with c_k = sum_c sh[3k + c] w[c] (dir treated
+// as unconstrained); the basis gradient is never materialised.
 template <int DEG>
-__device__ __forceinline__ void sh_grad(float x, float y, float z, float dY[16][3])
+__device__ __forceinline__ void sh_grad_acc(float x, float y, float z, const float* __restrict__ sh,
+                                            const float w[3], float g[3])
 {
-#pragma unroll
-    for (int k = 0; k < 16; k++) { dY[k][0] = 0.f; dY[k][1] = 0.f; dY[k][2] = 0.f; }
-    if (DEG >= 1) { dY[1][1] = -kSH1; dY[2][2] = kSH1; dY[3][0] = -kSH1; }
-    if (DEG >= 2) {
-        dY[4][0] = kSH2a * y;  dY[4][1] = kSH2a * x;
-        dY[5][1] = -kSH2a * z; dY[5][2] = -kSH2a * y;
-        dY[6][0] = -2.0f * kSH2b * x; dY[6][1] = -2.0f * kSH2b * y; dY[6][2] = 4.0f * kSH2b * z;
-        dY[7][0] = -kSH2a * z; dY[7][2] = -kSH2a * x;
-        dY[8][0] = 2.0f * kSH2c * x; dY[8][1] = -2.0f * kSH2c * y;
-        if (DEG >= 3) {
-            float xx = x * x, yy = y * y, zz = z * z;
-            dY[9][0] = -kSH3a * 6.0f * x * y;        dY[9][1] = -kSH3a * (3.0f * xx - 3.0f * yy);
-            dY[10][0] = kSH3b * y * z; dY[10][1] = kSH3b * x * z; dY[10][2] = kSH3b * x * y;
-            dY[11][0] = kSH3c * 2.0f * x * y;
-            dY[11][1] = -kSH3c * (4.0f * zz - xx - 3.0f * yy);
-            dY[11][2] = -kSH3c * 8.0f * y * z;
-            dY[12][0] = -kSH3d * 6.0f * x * z; dY[12][1] = -kSH3d * 6.0f * y * z;
-            dY[12][2] = kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
-            dY[13][0] = -kSH3c * (4.0f * zz - 3.0f * xx - yy);
-            dY[13][1] = kSH3c * 2.0f * x * y;
-            dY[13][2] = -kSH3c * 8.0f * x * z;
-            dY[14][0] = kSH3e * 2.0f * x * z; dY[14][1] = -kSH3e * 2.0f * y * z;
-            dY[14][2] = kSH3e * (xx - yy);
-            dY[15][0] = -kSH3a * (3.0f * xx - 3.0f * yy); dY[15][1] = kSH3a * 6.0f * x * y;
-        }
+#define GL_CF(k) (sh[3 * (k)] * w[0] + sh[3 * (k) + 1] * w[1] + sh[3 * (k) + 2] * w[2])
+    if (DEG >= 1) {
+        g[1] -= kSH1 * GL_CF(1);
+        g[2] += kSH1 * GL_CF(2);
+        g[0] -= kSH1 * GL_CF(3);
     }
+    if (DEG >= 2) {
+        float c = GL_CF(4);
+        g[0] += c * kSH2a * y; g[1] += c * kSH2a * x;
+        c = GL_CF(5);
+        g[1] -= c * kSH2a * z; g[2] -= c * kSH2a * y;
+        c = GL_CF(6);
+        g[0] -= c * 2.0f * kSH2b * x; g[1] -= c * 2.0f * kSH2b * y; g[2] += c * 4.0f * kSH2b * z;
+        c = GL_CF(7);
+        g[0] -= c * kSH2a * z; g[2] -= c * kSH2a * x;
+        c = GL_CF(8);
+        g[0] += c * 2.0f * kSH2c * x; g[1] -= c * 2.0f * kSH2c * y;
+    }
+    if (DEG >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        float c = GL_CF(9);
+        g[0] -= c * kSH3a * 6.0f * x * y; g[1] -= c * kSH3a * (3.0f * xx - 3.0f * yy);
+        c = GL_CF(10);
+        g[0] += c * kSH3b * y * z; g[1] += c * kSH3b * x * z; g[2] += c * kSH3b * x * y;
+        c = GL_CF(11);
+        g[0] += c * kSH3c * 2.0f * x * y; g[1] -= c * kSH3c * (4.0f * zz - xx - 3.0f * yy);
+        g[2] -= c * kSH3c * 8.0f * y * z;
+        c = GL_CF(12);
+        g[0] -= c * kSH3d * 6.0f * x * z; g[1] -= c * kSH3d * 6.0f * y * z;
+        g[2] += c * kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+        c = GL_CF(13);
+        g[0] -= c * kSH3c * (4.0f * zz - 3.0f * xx - yy); g[1] += c * kSH3c * 2.0f * x * y;
+        g[2] -= c * kSH3c * 8.0f * x * z;
+        c = GL_CF(14);
+        g[0] += c * kSH3e * 2.0f * x * z; g[1] -= c * kSH3e * 2.0f * y * z; g[2] += c * kSH3e * (xx - yy);
+        c = GL_CF(15);
+        g[0] -= c * kSH3a * (3.0f * xx - 3.0f * yy); g[1] += c * kSH3a * 6.0f * x * y;
+    }
+#undef GL_CF
 }
 
 // ---------------------------------------------------------------------------

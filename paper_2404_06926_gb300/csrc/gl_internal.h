@@ -85,42 +85,67 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-// Scratch of one rendered view: projected records, binning, per-pixel state.
+constexpr int kMaxViews = 64;   // views in one step (a keyframe window)
+constexpr int kDescRing = 8;    // pinned upload slots for view descriptors
+
+// Per-view inputs of the loss and the exposure update, set by the caller.
+struct ViewExtra {
+    const float* target = nullptr;
+    float* E = nullptr;
+    float* Em = nullptr;
+    float e_bc1 = 1.f, e_bc2 = 1.f;
+    float weight = 1.f;
+};
+
+// Scratch of one step over V views: projected records (per view and
+// Gaussian, index v * n + g), binning over the concatenated tiles of all
+// views, and per-pixel state over the concatenated pixels.
 struct View {
-    int64_t n = 0;            // Gaussians
-    int W = 0, H = 0, Ts = 16, TX = 0, TY = 0, ntiles = 0;
-    int64_t I = 0;            // (Gaussian, tile) instances
-    Cam cam{};
-    // per Gaussian
+    int V = 0;
+    int64_t n = 0;            // Gaussians (per view)
+    int Ts = 16, ntiles = 0, nltiles = 0;   // totals over the views
+    int64_t P = 0;            // pixels over the views
+    int W = 0, H = 0, TX = 0, TY = 0;       // view 0 (single-view helpers)
+    Cam cam{};                // view 0
+    int64_t I = 0;            // (Gaussian, tile) instances over the views
+    ViewDesc hdesc[kMaxViews];
+    DevBuf desc;              // device copy of hdesc[0..V)
+    ViewDesc* hpin = nullptr; // pinned upload ring (kDescRing x kMaxViews)
+    cudaEvent_t pin_ev[kDescRing] = {};
+    bool pin_used[kDescRing] = {};
+    int pin_slot = 0;
+    // per (view, Gaussian)
     DevBuf rec0, rec1, rec2, rec3;  // float4: (u,v,A',C'), (B',log2 o,z,o), (r,g,b,-), alpha box
     DevBuf radius;            // int
-    DevBuf rect;              // int4 (x0,y0,x1,y1)
+    DevBuf rect;              // int4 (x0,y0,x1,y1), tiles local to the view
     DevBuf touched;           // u32
     DevBuf dkey, gidx;        // u32 depth key, u32 index (sort input)
     DevBuf dkey2, gidx2;      // sort ping-pong
     DevBuf dup_off;           // u32 offset of the Gaussian's first instance
+    DevBuf g2d;               // float[10] screen-space gradient accumulators
     // scan
     DevBuf bsum;              // u64 per scan block
-    DevBuf count;             // u64[4]: I, overflow flag, ...
+    DevBuf count;             // u64[8]: I, overflow flag, N (sort), scratch
     // per instance
-    DevBuf itile, ival, itile2, ival2;  // u32 tile id, u32 instance id (sort)
-    DevBuf iowner;            // u32 owning Gaussian per instance id
+    DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
+    DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
     DevBuf srec0, srec1, srec2, srec3;  // records in sorted-instance order
-    DevBuf sgid;              // u32 owning Gaussian per sorted instance
-    DevBuf g2d;               // float[10] screen-space gradient accumulators per Gaussian
+    DevBuf sgid;              // u32 owning (view, Gaussian) per sorted instance
     DevBuf hist;              // radix histograms
-    DevBuf ranges;            // uint2 per tile
+    DevBuf ranges;            // uint2 per global tile
     DevBuf tile_order;        // u32 tile launch order (heaviest first)
-    // per pixel
+    // per pixel (concatenated over views)
     DevBuf Tfin, ncon;        // float, u32
     DevBuf rgb, depth, opac;  // internal render targets when needed
     // sorted-order results of the last forward (pointers into the buffers above)
-    const uint32_t* sorted_g = nullptr;   // Gaussians in depth order
+    const uint32_t* sorted_g = nullptr;
     const uint32_t* sorted_tile = nullptr;
     const uint32_t* sorted_inst = nullptr;
     uint64_t* h_count = nullptr;          // pinned: I, overflow
     Prof* prof = nullptr;                 // optional phase timers
+    const ViewDesc* d_desc() const { return desc.as<const ViewDesc>(); }
     gl_status init();
+    gl_status upload_descs(cudaStream_t s);
     void release();
 };
 
@@ -137,9 +162,13 @@ struct gl_ctx_impl {
 // Launchers (each returns GL_OK or an error; all work on `stream`).
 // ---------------------------------------------------------------------------
 
-// Preprocess + depth sort + scan + duplicate + tile sort + ranges: fills
-// `v` for the Gaussians `p` seen by `cam` (tiles of side Ts).  Synchronises
+// Describe V views (cameras, tiles, pixel offsets, loss inputs), upload the
+// descriptors, then preprocess + depth sort + scan + duplicate + tile sort +
+// ranges + tile order + record permutation over all of them.  Synchronises
 // once to size the instance buffers.
+gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra* extra, int V, int Ts,
+                    cudaStream_t s);
+// The single-view case.
 gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream_t s);
 
 // Forward raster of a binned view into (rgb, depth, opacity) device images
@@ -157,7 +186,7 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
 struct AdamArgs {
     GMut m, v;                 // moments
     float lr_pos, lr_dc, lr_rest, lr_op, lr_scale, lr_rot;
-    float b1, b2, eps, bc1, bc2;   // bias corrections 1-b^t
+    float b1, b2, eps, ibc1, isbc2;  // 1/(1-b1^t), 1/sqrt(1-b2^t)
     int sparse;
 };
 // mode 0: write gradients into `grad` (+ pose partials if pose_part != null).
@@ -168,18 +197,18 @@ gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cu
 int pose_partials_needed(int64_t n);
 gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s);
 
-// Photometric loss (Eq. 9): writes dL/drgb and per-block partials; then the
-// final reduction writes loss and dL/dE and, if adam != null, updates E.
-struct ExpAdam {
-    float* E;          // device 12
-    float* m;          // device 12
-    float* v;          // device 12
-    float lr, b1, b2, eps, bc1, bc2;
-};
+// Photometric loss (Eq. 9) of one view given by value (no descriptor upload):
+// writes dL/drgb and per-tile partials; then the final reduction writes loss
+// and dL/dE.
 int loss_partials_needed(int W, int H);
 gl_status photometric_loss(const float* rgb, const float* target, const float* E, int W, int H,
                            float lambda, float* dL_drgb, float* part, float* loss_out,
-                           float* dE_out, const ExpAdam* adam, cudaStream_t s);
+                           float* dE_out, cudaStream_t s);
+// The same over all views of `v` (targets, exposures and weights from the
+// descriptors): dL/drgb over the concatenated pixels (already weighted),
+// loss per view into loss_v[V], and the exposure Adam step of views with Em.
+gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, float* dL_drgb, float* part,
+                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s);
 
 // Apply C_hat = A C + b (E34 by value) from src to dst (device images).
 gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P,

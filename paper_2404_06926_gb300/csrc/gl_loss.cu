@@ -31,10 +31,41 @@ constexpr float kC2 = 0.03f * 0.03f;
 
 constexpr size_t kSmemFloats = 2 * RA * RA + 5 * RA * RB + 3 * RB * RB + 3 * LT * LT;
 
+// One view passed by value (the stateless and allocation-free entry points).
+struct LossOne {
+    const float* rgb;
+    const float* target;
+    const float* E;
+    float* dL;
+    int W, H;
+};
+
+// Grid: one CTA per 32x32 loss tile over all views.  With `views` null the
+// single view `one` is used; otherwise view, images, exposure and weight
+// come from the descriptors and images are the concatenated ones.
 __global__ void __launch_bounds__(kThreads)
-k_loss(const float* __restrict__ rgb, const float* __restrict__ target, const float* __restrict__ E,
-       int W, int H, float lambda, float* __restrict__ dL_drgb, float* __restrict__ part)
+k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __restrict__ rgb_all,
+       float* __restrict__ dL_all, float lambda, float* __restrict__ part)
 {
+    const float* rgb = one.rgb;
+    const float* target = one.target;
+    const float* E = one.E;
+    float* dL_drgb = one.dL;
+    int W = one.W, H = one.H;
+    float weight = 1.0f;
+    int lt = blockIdx.x;
+    if (views) {
+        const int v = view_of_ltile(views, V, lt);
+        const ViewDesc& d = views[v];
+        lt -= d.ltile_base;
+        rgb = rgb_all + 3 * d.pix_base;
+        dL_drgb = dL_all + 3 * d.pix_base;
+        target = d.target;
+        E = d.E;
+        W = d.cam.W;
+        H = d.cam.H;
+        weight = d.weight;
+    }
     extern __shared__ float sm[];
     float* xs = sm;
     float* ys = xs + RA * RA;
@@ -51,12 +82,13 @@ k_loss(const float* __restrict__ rgb, const float* __restrict__ target, const fl
         for (int k = 0; k < 11; k++) s += expf(-(float)((k - HW) * (k - HW)) / 4.5f);
         wt[tid] = expf(-(float)((tid - HW) * (tid - HW)) / 4.5f) / s;
     }
-    if (tid < 12) Es[tid] = E[tid];
+    if (tid < 12) Es[tid] = E ? E[tid] : ((tid % 5 == 0) ? 1.0f : 0.0f);
     __syncthreads();
-    const int ox = blockIdx.x * LT, oy = blockIdx.y * LT;
+    const int LTX = (W + LT - 1) / LT;
+    const int ox = (lt % LTX) * LT, oy = (lt / LTX) * LT;
     const float invN = 1.0f / (3.0f * (float)W * (float)H);
-    const float gS = -lambda * invN;
-    const float gL1 = (1.0f - lambda) * invN;
+    const float gS = -lambda * invN * weight;
+    const float gL1 = (1.0f - lambda) * invN * weight;
     float l1acc = 0.0f, sacc = 0.0f;
 
     for (int ch = 0; ch < 3; ch++) {
@@ -182,21 +214,39 @@ k_loss(const float* __restrict__ rgb, const float* __restrict__ target, const fl
     if (tid < kNP) {
         float v = 0.0f;
         for (int ww = 0; ww < kThreads / 32; ww++) v += red[tid][ww];
-        const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-        part[blk * kNP + tid] = v;
+        part[(size_t)blockIdx.x * kNP + tid] = v;
     }
 }
 
+// Sums the per-tile partials in a fixed order (double).  Single view (views
+// null): block 0 over [0, nblk) -> loss_out, dE_out.  Views: block v over the
+// view's loss tiles -> loss_v[v] (unweighted) and, if the view has Em, one
+// Adam step of its exposure on the (already weighted) gradient.
 __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, int H, float lambda,
-                             float* __restrict__ loss_out, float* __restrict__ dE_out, ExpAdam ad,
-                             int do_adam)
+                             float* __restrict__ loss_out, float* __restrict__ dE_out,
+                             const ViewDesc* __restrict__ views, float* __restrict__ loss_v, float b1,
+                             float b2, float eps, float lr)
 {
-    // one warp per partial slot, fixed order, double accumulation
     __shared__ double tot[kNP];
+    int begin = 0;
+    float* Ev = nullptr;
+    float* Em = nullptr;
+    float bc1 = 1.f, bc2 = 1.f;
+    if (views) {
+        const ViewDesc& d = views[blockIdx.x];
+        begin = d.ltile_base;
+        W = d.cam.W;
+        H = d.cam.H;
+        nblk = ((W + LT - 1) / LT) * ((H + LT - 1) / LT);
+        Ev = d.E;
+        Em = d.Em;
+        bc1 = d.e_bc1;
+        bc2 = d.e_bc2;
+    }
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < kNP) {
         double acc = 0.0;
-        for (int i = lane; i < nblk; i += 32) acc += part[(size_t)i * kNP + k];
+        for (int i = lane; i < nblk; i += 32) acc += part[(size_t)(begin + i) * kNP + k];
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
         if (lane == 0) tot[k] = acc;
     }
@@ -204,18 +254,19 @@ __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, in
     if (threadIdx.x == 0) {
         const double invN = 1.0 / (3.0 * (double)W * (double)H);
         const double L = (1.0 - lambda) * tot[12] * invN + lambda * (1.0 - tot[13] * invN);
-        if (loss_out) *loss_out = (float)L;
+        if (views) { if (loss_v) loss_v[blockIdx.x] = (float)L; }
+        else if (loss_out) *loss_out = (float)L;
     }
     if (threadIdx.x < 12) {
-        const float g = (float)tot[threadIdx.x];
-        if (dE_out) dE_out[threadIdx.x] = g;
-        if (do_adam) {
-            const int i = threadIdx.x;
-            float m = ad.b1 * ad.m[i] + (1.0f - ad.b1) * g;
-            float v = ad.b2 * ad.v[i] + (1.0f - ad.b2) * g * g;
-            ad.m[i] = m;
-            ad.v[i] = v;
-            ad.E[i] -= ad.lr * (m / ad.bc1) / (sqrtf(v / ad.bc2) + ad.eps);
+        const int i = threadIdx.x;
+        const float g = (float)tot[i];
+        if (!views && dE_out) dE_out[i] = g;
+        if (Ev && Em) {
+            const float m = b1 * Em[i] + (1.0f - b1) * g;
+            const float v = b2 * Em[12 + i] + (1.0f - b2) * g * g;
+            Em[i] = m;
+            Em[12 + i] = v;
+            Ev[i] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
         }
     }
 }
@@ -240,22 +291,43 @@ int loss_partials_needed(int W, int H)
     return ((W + LT - 1) / LT) * ((H + LT - 1) / LT) * kNP;
 }
 
-gl_status photometric_loss(const float* rgb, const float* target, const float* E, int W, int H,
-                           float lambda, float* dL_drgb, float* part, float* loss_out, float* dE_out,
-                           const ExpAdam* adam, cudaStream_t s)
+namespace {
+gl_status loss_attr()
 {
     static bool attr_set = false;
-    const size_t smem = kSmemFloats * sizeof(float);
     if (!attr_set) {
-        GL_CUDA_TRY(cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GL_CUDA_TRY(cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSmemFloats * sizeof(float))));
         attr_set = true;
     }
-    dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT);
-    k_loss<<<grid, kThreads, smem, s>>>(rgb, target, E, W, H, lambda, dL_drgb, part);
-    ExpAdam a{};
-    if (adam) a = *adam;
-    k_loss_final<<<1, 32 * kNP, 0, s>>>(part, (int)(grid.x * grid.y), W, H, lambda, loss_out, dE_out, a,
-                                        adam ? 1 : 0);
+    return GL_OK;
+}
+}  // namespace
+
+gl_status photometric_loss(const float* rgb, const float* target, const float* E, int W, int H,
+                           float lambda, float* dL_drgb, float* part, float* loss_out, float* dE_out,
+                           cudaStream_t s)
+{
+    GL_TRY(loss_attr());
+    const int nblk = ((W + LT - 1) / LT) * ((H + LT - 1) / LT);
+    LossOne one{rgb, target, E, dL_drgb, W, H};
+    k_loss<<<nblk, kThreads, kSmemFloats * sizeof(float), s>>>(one, nullptr, 0, nullptr, nullptr, lambda, part);
+    k_loss_final<<<1, 32 * kNP, 0, s>>>(part, nblk, W, H, lambda, loss_out, dE_out, nullptr, nullptr, 0.f, 0.f,
+                                        0.f, 0.f);
+    count_launches(2);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
+gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, float* dL_drgb, float* part,
+                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s)
+{
+    GL_TRY(loss_attr());
+    LossOne one{};
+    k_loss<<<v.nltiles, kThreads, kSmemFloats * sizeof(float), s>>>(one, v.d_desc(), v.V, rgb, dL_drgb, lambda,
+                                                                     part);
+    k_loss_final<<<v.V, 32 * kNP, 0, s>>>(part, 0, 0, 0, lambda, nullptr, nullptr, v.d_desc(), loss_v, b1, b2, eps,
+                                          lr);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;

@@ -68,5 +68,5 @@ extern "C" gl_status gl_photometric_loss_noalloc(const float* rgb, const float* 
     // Every partial the reduction reads is written by this call's tile pass,
     // so nothing in the shared array needs clearing first.
     return photometric_loss(rgb, target, E34, width, height, lambda_dssim, dL_drgb, part, loss_out, dL_dE,
-                            nullptr, static_cast<cudaStream_t>(cuda_stream));
+                            static_cast<cudaStream_t>(cuda_stream));
 }

@@ -16,7 +16,7 @@ namespace gl {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kNG = 10;
 
 struct Geo {
@@ -86,37 +86,118 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     G.dir[0] = d0 * idn; G.dir[1] = d1 * idn; G.dir[2] = d2 * idn;
 }
 
+// p -= lr (m / bc1) / (sqrt(v / bc2) + eps), with 1/bc1 and 1/sqrt(bc2)
+// precomputed for the step: the same update with one square root and one
+// fast division per element.
 __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, float lr, const AdamArgs& a)
 {
     m = a.b1 * m + (1.0f - a.b1) * g;
     v = a.b2 * v + (1.0f - a.b2) * g * g;
-    p -= lr * (m / a.bc1) / (sqrtf(v / a.bc2) + a.eps);
+    p -= __fdividef(lr * a.ibc1 * m, sqrtf(v) * a.isbc2 + a.eps);
+}
+
+// Block-cooperative pass over one parameter array of the block's Gaussians
+// (a contiguous span of cnt * WIDTH floats): MODE 0 writes the staged
+// gradients, MODE 1 applies Adam (the first three floats of a row take lr0,
+// the SH DC band; the rest lr).  Rows flagged off in upd are left untouched.
+template <int MODE, int WIDTH, int NR>
+__device__ __forceinline__ void coop_one(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
+                                         size_t base, int e, const float* __restrict__ sR, int off,
+                                         const uint8_t* __restrict__ upd, float lr, float lr0, const AdamArgs& ad)
+{
+    const int loc = e / WIDTH, w = e - loc * WIDTH;
+    if (!upd[loc]) return;
+    const float gr = sR[loc * NR + off + w];
+    if (MODE == 0) P[base + e] = gr;
+    else adam1(P[base + e], Mm[base + e], Vv[base + e], gr, w < 3 ? lr0 : lr, ad);
+}
+
+// Block-cooperative pass over one parameter array of the block's Gaussians
+// (a contiguous span of cnt * WIDTH floats, 16-byte aligned because blocks
+// start at multiples of 128 Gaussians): MODE 0 writes the staged gradients,
+// MODE 1 applies Adam (the first three floats of a row take lr0, the SH DC
+// band; the rest lr).  Rows flagged off in upd are left untouched.  float4
+// accesses, two per thread in flight.
+template <int MODE, int WIDTH, int NR>
+__device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
+                                     int64_t g0, int cnt, const float* __restrict__ sR, int off,
+                                     const uint8_t* __restrict__ upd, float lr, float lr0, const AdamArgs& ad)
+{
+    const size_t base = (size_t)g0 * WIDTH;
+    const int ne = cnt * WIDTH, nv = ne / 4;
+    float4* P4 = reinterpret_cast<float4*>(P + base);
+    float4* M4 = reinterpret_cast<float4*>(Mm + base);
+    float4* V4 = reinterpret_cast<float4*>(Vv + base);
+    for (int f0 = threadIdx.x; f0 < nv; f0 += 2 * kThreads) {
+        float4 pp[2], mm[2], vv[2];
+        bool any[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int f = f0 + u * kThreads;
+            any[u] = false;
+            if (f < nv) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) any[u] = any[u] || upd[(4 * f + e) / WIDTH];
+            }
+            if (any[u] && MODE == 1) { pp[u] = P4[f]; mm[u] = M4[f]; vv[u] = V4[f]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int f = f0 + u * kThreads;
+            if (!any[u]) continue;
+            float* pa = &pp[u].x;
+            float* ma = &mm[u].x;
+            float* va = &vv[u].x;
+            float gr[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int el = 4 * f + e, loc = el / WIDTH, w = el - loc * WIDTH;
+                gr[e] = sR[loc * NR + off + w];
+                if (MODE == 1 && upd[loc]) adam1(pa[e], ma[e], va[e], gr[e], w < 3 ? lr0 : lr, ad);
+            }
+            if (MODE == 0) {
+                // rows not updated still receive their (zero) gradient
+                P4[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+            } else {
+                P4[f] = pp[u]; M4[f] = mm[u]; V4[f] = vv[u];
+            }
+        }
+    }
+    for (int e = 4 * nv + threadIdx.x; e < ne; e += kThreads) coop_one<MODE, WIDTH, NR>(P, Mm, Vv, base, e, sR, off, upd, lr, lr0, ad);
 }
 
 template <int DEG, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __restrict__ g2d, GMut out,
-             AdamArgs ad, float* __restrict__ pose_part)
+__global__ void __launch_bounds__(kThreads, 3)
+k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __restrict__ radius,
+             const float* __restrict__ g2d, GMut out, AdamArgs ad, float* __restrict__ pose_part)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int KF = K * 3;   // SH floats per Gaussian
-    // per-Gaussian factors of the SH gradient dL/dsh[k][c] = Y[k] * grgb[c],
-    // staged so the block can stream the SH arrays with coalesced accesses
-    __shared__ float sY[kThreads][K];
-    __shared__ float sG[kThreads][3];
+    // one row of gradients per Gaussian of the block: means 3, log-scales 3,
+    // quaternion 4, logit 1, SH KF (odd stride against bank conflicts); the
+    // Adam update then streams every parameter array with coalesced accesses
+    constexpr int NR = 11 + KF + ((11 + KF) % 2 == 0 ? 1 : 0);
+    __shared__ float sR[kThreads * NR];
     __shared__ uint8_t sUpd[kThreads];
     const int64_t g0 = blockIdx.x * (int64_t)kThreads;
     const int64_t g = g0 + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     const bool valid = g < p.n;
-    const bool vis = valid && radius[g] > 0;
+    bool vis = false;
 
     float gm[3] = {0, 0, 0}, gl3[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glg = 0.0f;
+    float* dsh = sR + threadIdx.x * NR + 11;   // this Gaussian's SH gradient, accumulated in place
+    for (int k = 0; k < KF; k++) dsh[k] = 0.0f;
+
+    // every view the Gaussian is visible in contributes (window steps sum them)
+    for (int vw = 0; vw < V && valid; vw++) {
+    const int64_t tv = (int64_t)vw * p.n + g;
+    if (radius[tv] <= 0) continue;
+    vis = true;
+    const Cam cam = views[vw].cam;
     float grgb[3] = {0, 0, 0};
     float Y[16];
-    for (int k = 0; k < 16; k++) Y[k] = 0.0f;
-
-    if (vis) {
+    {
         float mu[3] = {p.means[3 * g], p.means[3 * g + 1], p.means[3 * g + 2]};
         float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
         const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
@@ -126,7 +207,7 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
 
         // screen-space gradients of this Gaussian, accumulated by the raster backward
         float s[kNG];
-        for (int k = 0; k < kNG; k++) s[k] = g2d[(size_t)g * kNG + k];
+        for (int k = 0; k < kNG; k++) s[k] = g2d[(size_t)tv * kNG + k];
         const float du = -G.A * s[4] - G.B * s[5];
         const float dv = -G.C * s[5] - G.B * s[4];
         const float dA = -0.5f * s[6], dB = -s[7], dC = -0.5f * s[8];
@@ -134,7 +215,7 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
         const float dz = s[9];
 
         // opacity
-        glg = dop * G.o * (1.0f - G.o);
+        glg += dop * G.o * (1.0f - G.o);
 
         // colour -> SH and view direction (clamped channels pass no gradient)
         sh_eval<DEG>(G.dir[0], G.dir[1], G.dir[2], Y);
@@ -144,14 +225,7 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
             for (int c = 0; c < 3; c++) raw[c] += Y[k] * sh[3 * k + c];
         for (int c = 0; c < 3; c++) grgb[c] = raw[c] < 0.0f ? 0.0f : s[c];
         float gdir[3] = {0, 0, 0};
-        if (DEG > 0) {
-            float dY[16][3];
-            sh_grad<DEG>(G.dir[0], G.dir[1], G.dir[2], dY);
-            for (int k = 1; k < K; k++) {
-                const float cf = sh[3 * k] * grgb[0] + sh[3 * k + 1] * grgb[1] + sh[3 * k + 2] * grgb[2];
-                gdir[0] += cf * dY[k][0]; gdir[1] += cf * dY[k][1]; gdir[2] += cf * dY[k][2];
-            }
-        }
+        if (DEG > 0) sh_grad_acc<DEG>(G.dir[0], G.dir[1], G.dir[2], sh, grgb, gdir);
         const float dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
         float gdu[3];
         for (int j = 0; j < 3; j++) gdu[j] = (gdir[j] - G.dir[j] * dd) / G.dnorm;
@@ -189,7 +263,7 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
                 acc += gMij * G.Rq[i * 3 + j];
                 gRq[i * 3 + j] = gMij * G.s[j];
             }
-            gl3[j] = acc * G.s[j];
+            gl3[j] += acc * G.s[j];
         }
         {
             const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
@@ -202,7 +276,7 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
             gn[3] = 2.f * (-2.f * z * gRq[0] - w * gRq[1] + x * gRq[2] + w * gRq[3] - 2.f * z * gRq[4]
                            + y * gRq[5] + x * gRq[6] + y * gRq[7]);
             const float qd = w * gn[0] + x * gn[1] + y * gn[2] + z * gn[3];
-            for (int i = 0; i < 4; i++) gq[i] = (gn[i] - G.qn[i] * qd) / G.qnorm;
+            for (int i = 0; i < 4; i++) gq[i] += (gn[i] - G.qn[i] * qd) / G.qnorm;
         }
         // T = J W
         float gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
@@ -244,78 +318,30 @@ k_params_bwd(GParams p, Cam cam, const int* __restrict__ radius, const float* __
         pose[5] += P[1] - P[3];
     }
 
-    for (int k = 0; k < K; k++) sY[threadIdx.x][k] = Y[k];
-    for (int c = 0; c < 3; c++) sG[threadIdx.x][c] = grgb[c];
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) dsh[3 * k + c] += Y[k] * grgb[c];
+    }
+
     const bool upd = valid && (MODE == 0 || !ad.sparse || vis);
     sUpd[threadIdx.x] = upd ? 1 : 0;
-
-    if (MODE == 0) {
-        if (valid) {
-            for (int j = 0; j < 3; j++) { out.means[3 * g + j] = gm[j]; out.log_scales[3 * g + j] = gl3[j]; }
-            reinterpret_cast<float4*>(out.quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-            out.logits[g] = glg;
-        }
-    } else if (upd) {
-        for (int j = 0; j < 3; j++) {
-            adam1(out.means[3 * g + j], ad.m.means[3 * g + j], ad.v.means[3 * g + j], gm[j], ad.lr_pos, ad);
-            adam1(out.log_scales[3 * g + j], ad.m.log_scales[3 * g + j], ad.v.log_scales[3 * g + j], gl3[j], ad.lr_scale, ad);
-        }
-        float4 pq = reinterpret_cast<float4*>(out.quats)[g];
-        float4 mq = reinterpret_cast<float4*>(ad.m.quats)[g];
-        float4 vq = reinterpret_cast<float4*>(ad.v.quats)[g];
-        adam1(pq.x, mq.x, vq.x, gq[0], ad.lr_rot, ad);
-        adam1(pq.y, mq.y, vq.y, gq[1], ad.lr_rot, ad);
-        adam1(pq.z, mq.z, vq.z, gq[2], ad.lr_rot, ad);
-        adam1(pq.w, mq.w, vq.w, gq[3], ad.lr_rot, ad);
-        reinterpret_cast<float4*>(out.quats)[g] = pq;
-        reinterpret_cast<float4*>(ad.m.quats)[g] = mq;
-        reinterpret_cast<float4*>(ad.v.quats)[g] = vq;
-        adam1(out.logits[g], ad.m.logits[g], ad.v.logits[g], glg, ad.lr_op, ad);
+    {
+        float* row = sR + threadIdx.x * NR;
+        row[0] = gm[0]; row[1] = gm[1]; row[2] = gm[2];
+        row[3] = gl3[0]; row[4] = gl3[1]; row[5] = gl3[2];
+        row[6] = gq[0]; row[7] = gq[1]; row[8] = gq[2]; row[9] = gq[3];
+        row[10] = glg;
     }
     __syncthreads();
-
-    // SH of the block's Gaussians: one contiguous span of cnt * KF floats
     const int cnt = (int)min((int64_t)kThreads, p.n - g0);
     if (cnt > 0) {
-        const size_t base = (size_t)g0 * KF;
-        if (KF % 4 == 0) {
-            const int nv = cnt * KF / 4;
-            for (int f = threadIdx.x; f < nv; f += kThreads) {
-                const int e0 = 4 * f, loc = e0 / KF;
-                if (!sUpd[loc]) continue;
-                float gr[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int w = e0 % KF + e, k = w / 3, c = w % 3;
-                    gr[e] = sY[loc][k] * sG[loc][c];
-                }
-                if (MODE == 0) {
-                    reinterpret_cast<float4*>(out.sh + base)[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
-                } else {
-                    float4 pp = reinterpret_cast<float4*>(out.sh + base)[f];
-                    float4 mm = reinterpret_cast<float4*>(ad.m.sh + base)[f];
-                    float4 vv = reinterpret_cast<float4*>(ad.v.sh + base)[f];
-                    float* pa = &pp.x; float* ma = &mm.x; float* va = &vv.x;
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int k = (e0 % KF + e) / 3;
-                        adam1(pa[e], ma[e], va[e], gr[e], k == 0 ? ad.lr_dc : ad.lr_rest, ad);
-                    }
-                    reinterpret_cast<float4*>(out.sh + base)[f] = pp;
-                    reinterpret_cast<float4*>(ad.m.sh + base)[f] = mm;
-                    reinterpret_cast<float4*>(ad.v.sh + base)[f] = vv;
-                }
-            }
-        } else {
-            const int ne = cnt * KF;
-            for (int e = threadIdx.x; e < ne; e += kThreads) {
-                const int loc = e / KF, w = e % KF, k = w / 3, c = w % 3;
-                if (!sUpd[loc]) continue;
-                const float gr = sY[loc][k] * sG[loc][c];
-                if (MODE == 0) out.sh[base + e] = gr;
-                else adam1(out.sh[base + e], ad.m.sh[base + e], ad.v.sh[base + e], gr, k == 0 ? ad.lr_dc : ad.lr_rest, ad);
-            }
-        }
+        coop<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sR, 0, sUpd, ad.lr_pos, ad.lr_pos, ad);
+        coop<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sR, 3, sUpd, ad.lr_scale,
+                          ad.lr_scale, ad);
+        coop<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sR, 6, sUpd, ad.lr_rot, ad.lr_rot, ad);
+        coop<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sR, 10, sUpd, ad.lr_op, ad.lr_op, ad);
+        coop<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sR, 11, sUpd, ad.lr_rest, ad.lr_dc, ad);
     }
 
     if (MODE == 0 && pose_part) {
@@ -354,7 +380,7 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
     PhaseScope ps(v.prof, PH_PARAMS, s);
     count_launches(1);
 #define GL_PB(D_)                                                                            \
-    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.cam, v.radius.as<int>(), v.g2d.as<float>(), \
+    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), \
                                                      o, a, pose_part)
     switch (p.deg) {
         case 0: GL_PB(0); break;

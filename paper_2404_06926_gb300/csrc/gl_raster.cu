@@ -28,21 +28,28 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kNG = 10;   // screen-space gradient slots per Gaussian
 
 struct Unit {
-    int tile, x0, y0;      // tile and the absolute pixel origin of the 8x4 block
+    int x0, y0;            // absolute pixel origin of the 8x4 block in its view
+    int W, H;              // the view's image size
+    long long pix_base;    // the view's first pixel in the concatenated images
     uint32_t rs, re;       // the tile's list
 };
 
-__device__ __forceinline__ bool unit_of(int u, int TS, int TX, const uint32_t* __restrict__ order,
+__device__ __forceinline__ void unit_of(int u, int TS, const ViewDesc* __restrict__ views, int V,
+                                        const uint32_t* __restrict__ order,
                                         const uint32_t* __restrict__ ranges, Unit& U)
 {
     const int wb_per_tile = TS * TS / 32, bpr = TS / 8;
     const int tile = (int)order[u / wb_per_tile], wb = u % wb_per_tile;
-    U.tile = tile;
-    U.x0 = (tile % TX) * TS + (wb % bpr) * 8;
-    U.y0 = (tile / TX) * TS + (wb / bpr) * 4;
+    const int v = view_of_tile(views, V, tile);
+    const ViewDesc& d = views[v];
+    const int lt = tile - d.tile_base;
+    U.x0 = (lt % d.TX) * TS + (wb % bpr) * 8;
+    U.y0 = (lt / d.TX) * TS + (wb / bpr) * 4;
+    U.W = d.cam.W;
+    U.H = d.cam.H;
+    U.pix_base = d.pix_base;
     U.rs = ranges[2 * tile];
     U.re = ranges[2 * tile + 1];
-    return true;
 }
 
 __device__ __forceinline__ bool box_hit(const float4 box, float bx0, float bx1, float by0, float by1)
@@ -53,7 +60,8 @@ __device__ __forceinline__ bool box_hit(const float4 box, float bx0, float bx1, 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_raster_fwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint32_t* __restrict__ ranges,
              const float4* __restrict__ s0g, const float4* __restrict__ s1g, const float4* __restrict__ s2g,
-             const float4* __restrict__ s3g, int W, int H, int TX, float* __restrict__ out_rgb,
+             const float4* __restrict__ s3g, const ViewDesc* __restrict__ views, int V,
+             float* __restrict__ out_rgb,
              float* __restrict__ out_depth, float* __restrict__ out_opac, float* __restrict__ Tfin,
              uint32_t* __restrict__ ncon)
 {
@@ -63,9 +71,9 @@ k_raster_fwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint3
     const int u = blockIdx.x * kWarpsPerBlock + w;
     if (u >= nunits) return;
     Unit U;
-    unit_of(u, TS, TX, order, ranges, U);
+    unit_of(u, TS, views, V, order, ranges, U);
     const int x = U.x0 + (lane & 7), y = U.y0 + (lane >> 3);
-    const bool inside = x < W && y < H;
+    const bool inside = x < U.W && y < U.H;
     const float px = (float)x, py = (float)y;
     const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 3);
     const unsigned lt = (1u << lane) - 1u;
@@ -112,7 +120,7 @@ k_raster_fwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint3
         __syncwarp();
     }
     if (!inside) return;
-    const size_t p = (size_t)y * W + x;
+    const size_t p = (size_t)U.pix_base + (size_t)y * U.W + x;
     out_rgb[3 * p] = C0; out_rgb[3 * p + 1] = C1; out_rgb[3 * p + 2] = C2;
     if (out_depth) out_depth[p] = Dd;
     if (out_opac) out_opac[p] = Oo;
@@ -165,7 +173,8 @@ template <bool EXTRA>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_raster_bwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint32_t* __restrict__ ranges,
              const float4* __restrict__ s0g, const float4* __restrict__ s1g, const float4* __restrict__ s2g,
-             const float4* __restrict__ s3g, const uint32_t* __restrict__ sgid, int W, int H, int TX,
+             const float4* __restrict__ s3g, const uint32_t* __restrict__ sgid,
+             const ViewDesc* __restrict__ views, int V,
              const float* __restrict__ Tfin, const uint32_t* __restrict__ ncon,
              const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
              const float* __restrict__ dL_dopac, float* __restrict__ g2d)
@@ -176,9 +185,9 @@ k_raster_bwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint3
     const int u = blockIdx.x * kWarpsPerBlock + w;
     if (u >= nunits) return;
     Unit U;
-    unit_of(u, TS, TX, order, ranges, U);
+    unit_of(u, TS, views, V, order, ranges, U);
     const int x = U.x0 + (lane & 7), y = U.y0 + (lane >> 3);
-    const bool inside = x < W && y < H;
+    const bool inside = x < U.W && y < U.H;
     const float px = (float)x, py = (float)y;
     const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 3);
     const unsigned lt = (1u << lane) - 1u;
@@ -186,7 +195,7 @@ k_raster_bwd(int nunits, int TS, const uint32_t* __restrict__ order, const uint3
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, gO = 0.f;
     uint32_t last = 0;
     if (inside) {
-        const size_t p = (size_t)y * W + x;
+        const size_t p = (size_t)U.pix_base + (size_t)y * U.W + x;
         T = Tfin[p];
         last = ncon[p];
         g0 = dL_drgb[3 * p]; g1 = dL_drgb[3 * p + 1]; g2 = dL_drgb[3 * p + 2];
@@ -304,7 +313,7 @@ gl_status permute_records(View& v, cudaStream_t s)
 
 gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s)
 {
-    const size_t P = (size_t)v.W * v.H;
+    const size_t P = (size_t)v.P;
     GL_TRY(v.Tfin.reserve(4 * P));
     GL_TRY(v.ncon.reserve(4 * P));
     if (v.ntiles == 0) return GL_OK;
@@ -314,7 +323,7 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     const int blocks = (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_raster_fwd<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(
         nunits, v.Ts, v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.srec0.as<float4>(),
-        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.W, v.H, v.TX, rgb, depth, opac,
+        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.d_desc(), v.V, rgb, depth, opac,
         v.Tfin.as<float>(), v.ncon.as<uint32_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
@@ -324,17 +333,18 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
 gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
                           const float* dL_dopac, cudaStream_t s)
 {
-    GL_TRY(v.g2d.reserve(sizeof(float) * kNG * (size_t)std::max<int64_t>(v.n, 1)));
+    const size_t pairs = (size_t)v.n * v.V;
+    GL_TRY(v.g2d.reserve(sizeof(float) * kNG * std::max<size_t>(pairs, 1)));
     PhaseScope ps(v.prof, PH_RASTER_BWD, s);
-    GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * (size_t)v.n, s));
+    GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * pairs, s));
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     const bool extra = dL_ddepth != nullptr || dL_dopac != nullptr;
     const int nunits = v.ntiles * (v.Ts * v.Ts / 32);
     const int blocks = (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock;
 #define GL_BWD_ARGS                                                                                     \
     nunits, v.Ts, v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.srec0.as<float4>(),           \
-        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.sgid.as<uint32_t>(), v.W, v.H, \
-        v.TX, v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>()
+        v.srec1.as<float4>(), v.srec2.as<float4>(), v.srec3.as<float4>(), v.sgid.as<uint32_t>(), v.d_desc(), \
+        v.V, v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>()
     if (extra) k_raster_bwd<true><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(GL_BWD_ARGS);
     else k_raster_bwd<false><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(GL_BWD_ARGS);
 #undef GL_BWD_ARGS

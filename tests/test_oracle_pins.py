@@ -478,3 +478,18 @@ def test_init_gaussians_follows_paper():
     assert np.allclose(1 / (1 + np.exp(-g["logits"].astype(np.float64))), 0.1, atol=1e-7)
     assert np.allclose(g["sh"][0, 0] * oracle.SH_C0 + 0.5, rgb[0], atol=1e-6)
     assert np.all(g["sh"][0, 1:] == 0)
+
+
+def test_decision_exp_within_two_ulp_of_exp():
+    """The float32 exp of the decision path is within 2 ulp of the exact
+    exponential (evaluated in double) over the range log-scales take."""
+    xs = np.concatenate([np.linspace(-30, 30, 4001), np.random.default_rng(0).uniform(-12, 8, 4000)])
+    xs = xs.astype(np.float32)
+    for x in xs:
+        y = oracle.expf_decision(x)
+        ref = np.exp(np.float64(x))
+        ulp = np.spacing(np.float32(ref))
+        assert abs(y - ref) <= 2 * ulp, (x, y, ref)
+    assert oracle.expf_decision(0.0) == 1.0
+    assert oracle.expf_decision(np.float32(np.log(2.0))) == np.float32(2.0) or \
+        abs(oracle.expf_decision(np.float32(np.log(2.0))) - 2.0) <= 2 * np.spacing(np.float32(2.0))
