@@ -69,12 +69,19 @@ def barrier(dist):
 
 
 def max_over_ranks(x, dist):
+    """Largest value of x over the ranks (the job's time is its slowest rank's)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 # ----------------------------------------------------------------------------
@@ -204,9 +211,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
-    was taken on the current source (else None)."""
+def ncu_traffic(kernel, alg_full):
+    """Per-launch DRAM bytes of `kernel` at full size, from the committed ncu
+    counters of a smaller case of the same workload scaled by the ratio of
+    algorithmic bytes; None unless they were taken on the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -214,7 +222,7 @@ def ncu_traffic(kernel):
     e = d.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("bytes_per_launch_full_size")
+    return (e["dram_read_bytes"] + e["dram_write_bytes"]) * alg_full / e["algorithmic_bytes"]
 
 
 # ----------------------------------------------------------------------------
@@ -335,7 +343,7 @@ def run_ours(args):
     launches = binding.kernel_launches() - launches0
     ms_total = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms_total, dist)
-    value = ws * args.steps / (ms_max / 1e3)
+    value = job_throughput(args.steps, ws, ms_max)
 
     # per-kernel device times: the same steps again with the library's
     # CUDA-event phase timers on (events pre-created, recorded on the map's stream)
@@ -425,14 +433,14 @@ def run_ours(args):
         peak = fp32_peak_tflops(sm_max)
         ach = flops_per_pair[dom] * kp / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": ncu_traffic(dom), "kernel": dom,
+                "traffic": ncu_traffic(dom, byts[dom]), "kernel": dom,
                 "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "hbm": {"achieved": byts[dom] / t_launch / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": byts[dom] / t_launch / 1e9 / hbm_peak, "peak_source": peak_src}}
     else:
         ach = byts[dom] / t_launch / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": ncu_traffic(dom), "kernel": dom, "peak_source": peak_src}
+                "traffic": ncu_traffic(dom, byts[dom]), "kernel": dom, "peak_source": peak_src}
     kernels = {k: {"ms_per_launch": per_launch[k], "share": phases[k][0] / max(1e-9, sum(v[0] for v in phases.values())),
                    "gbs": (byts[k] / (per_launch[k] / 1e3) / 1e9) if (k in byts and per_launch[k] > 0) else None}
                for k in phases if phases[k][1]}

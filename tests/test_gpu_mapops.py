@@ -1,0 +1,87 @@
+"""Map creation with sky Gaussians (Sec. III-C 1) and map expansion through
+the opacity mask (Sec. III-C 2, Eq. 8), against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_06926_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_sky_creation_matches_oracle():
+    from paper_2404_06926_gb300 import binding
+    n, seed = 3000, 1234
+    m = binding.Map(binding.default_config(n_sky=n, seed=seed, sh_degree=3, capacity_hint=4096))
+    assert len(m) == n
+    p = m.get_params()
+    xyz, nn = oracle.sky_points(n, 1e4, seed=seed)
+    # same counter-based draws; cos/sin in double on both sides, rounded once
+    assert np.allclose(p["means"], xyz, rtol=0, atol=2e-3)
+    assert np.allclose(p["log_scales"], np.log(nn)[:, None], atol=1e-5)
+    assert np.allclose(p["quats"], [[1, 0, 0, 0]])
+    assert np.allclose(p["logits"], np.log(0.7 / 0.3), atol=1e-6)
+    assert np.allclose(p["sh"][:, 0], 0.5 / oracle.SH_C0, atol=1e-5)
+    assert np.all(p["sh"][:, 1:] == 0)
+
+
+def _points(rng, cam, n):
+    """Points in the camera frustum at depths 0.1..8 m (some in front of z_near)."""
+    W, H = cam["width"], cam["height"]
+    u = rng.uniform(-5, W + 5, n)
+    v = rng.uniform(-5, H + 5, n)
+    z = rng.uniform(0.1, 8.0, n)
+    xc = np.stack([(u - cam["cx"]) * z / cam["fx"], (v - cam["cy"]) * z / cam["fy"], z], 1)
+    xw = (xc - np.asarray(cam["t"])) @ np.asarray(cam["R"])
+    return xw.astype(np.float32), rng.uniform(0, 1, (n, 3)).astype(np.float32)
+
+
+@pytest.mark.parametrize("use_mask", [False, True])
+def test_expansion_matches_oracle(use_mask):
+    from paper_2404_06926_gb300 import binding
+    sc = scenes.diff_check()
+    cam = sc["cam"]
+    sparse = {k: np.ascontiguousarray(v[:300]) for k, v in sc["params"].items()}   # partly transparent
+    m = binding.Map(binding.default_config(n_sky=0, sh_degree=3, capacity_hint=8192))
+    m.set_params(sparse)
+    n0 = len(m)
+    xyz, rgb = _points(np.random.default_rng(5), cam, 20000)
+    added = m.add_points(xyz, rgb, cam, use_mask=use_mask, kind=1)
+    opac = None
+    if use_mask:
+        opac = oracle.forward(sparse, cam, 16)[2]["opacity"]
+        assert 0.05 < (opac < 0.99).mean() < 0.95
+    keep, depth, k = oracle.expand_mask(xyz, cam, opac)
+    if use_mask:
+        assert 0 < k < len(xyz)
+    # a point whose pixel opacity sits within rounding of tau may be decided
+    # either way (float32 render vs double oracle): allow a handful
+    assert abs(added - k) <= (3 if use_mask else 0)
+    got = m.get_params()
+    assert len(m) == n0 + added
+    if added == k:
+        ref = oracle.init_gaussians(xyz[keep], rgb[keep], depth[keep].astype(np.float64), cam["fx"], sh_deg=3)
+        new = {kk: v[n0:] for kk, v in got.items()}
+        assert np.array_equal(new["means"], ref["means"])
+        assert np.allclose(new["log_scales"], ref["log_scales"], atol=2e-6)
+        assert np.allclose(new["quats"], ref["quats"])
+        assert np.allclose(new["logits"], ref["logits"], atol=1e-6)
+        assert np.allclose(new["sh"], ref["sh"], atol=2e-5)
+    # new Gaussians start with zero moments
+    m1 = m.get_moments(1)
+    assert np.all(m1["means"][n0:] == 0) and np.all(m1["sh"][n0:] == 0)
+
+
+def test_expansion_rejects_everything_under_an_opaque_map():
+    """A second expansion with the same points, after they were added, keeps
+    few: the map now covers their pixels (O >= tau)."""
+    from paper_2404_06926_gb300 import binding
+    sc = scenes.diff_check()
+    cam = sc["cam"]
+    m = binding.Map(binding.default_config(n_sky=0, sh_degree=3, capacity_hint=8192, opacity_fg=0.999))
+    m.set_params({k: np.ascontiguousarray(v[:300]) for k, v in sc["params"].items()})
+    xyz, rgb = _points(np.random.default_rng(7), cam, 5000)
+    a1 = m.add_points(xyz, rgb, cam, use_mask=True)
+    a2 = m.add_points(xyz, rgb, cam, use_mask=True)
+    assert a1 > 0 and a2 < 0.5 * a1
