@@ -180,6 +180,49 @@ GL_API gl_status gl_render(gl_map* map, const gl_pose* pose, const gl_intrinsics
 GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t n_views,
                            float* out_loss);
 
+/* How optimisation steps execute (none of this is in the paper; none of it
+ * changes a result except tile_size, which sets the binning tiles and so
+ * the 3-sigma tile rectangles of Sec. III-A):
+ *   use_graphs       1: after one eager step of a given shape (views and
+ *                    their sizes, map size, the fields below) the step is
+ *                    captured into a CUDA graph and later steps of that
+ *                    shape replay it.  Binning then reads nothing back: the
+ *                    instance buffers keep 25% headroom, a step whose
+ *                    instances do not fit updates nothing, is detected when
+ *                    the replay ends and is re-run eagerly (growing them).
+ *                    Graph steps synchronise the map's stream once, at the
+ *                    end.  Ignored while timers are on.
+ *   persistent       1: both raster kernels run one grid of resident warps
+ *                    that take (tile, pixel block) units from a counter.
+ *   batch_depth      records a warp stages per batch: 32 or 64.
+ *   pixels_per_lane  1, 2 or 4 pixels of a column per lane; 4 x this must
+ *                    not exceed the tile size.
+ *   tile_size        0: gl_config's; else 8, 16 or 32.
+ * gl_map_create starts with {0, 0, 32, 1, 0}.  Errors: GL_ERR_INVALID. */
+typedef struct {
+    int32_t use_graphs;
+    int32_t persistent;
+    int32_t batch_depth;
+    int32_t pixels_per_lane;
+    int32_t tile_size;
+    int32_t reserved;
+} gl_exec_config;
+
+GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
+GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
+
+/* Autotuner for one window shape: for each candidate execution (tile size
+ * 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4 x persistent or not,
+ * graphs on) time `reps` optimisation steps of `views` (as gl_optimize_step)
+ * with CUDA events, putting the Gaussians, their Adam moments, the views'
+ * exposures and the step counters back after each trial.  With
+ * keep_tile_size != 0 only gl_config's tile size is tried.  The fastest
+ * candidate is installed with gl_map_set_exec and returned in *best, its
+ * device time per step in *best_ms (nullable).  The map ends as it started.
+ * Errors: as gl_optimize_step, GL_ERR_OOM for the state snapshot. */
+GL_API gl_status gl_map_autotune(gl_map* map, const gl_keyframe* views, int32_t n_views, int32_t reps,
+                                 int32_t keep_tile_size, gl_exec_config* best, float* best_ms);
+
 /* Copy the Gaussians (out->n must be >= the map size; pointers host or
  * device; out->sh_degree must equal the map's).  *n_out gets the size. */
 GL_API gl_status gl_map_get_params(gl_map* map, gl_gaussians* out, int64_t* n_out);
@@ -209,6 +252,9 @@ typedef struct {
     int64_t steps;         /* optimisation steps taken (Adam step counter)      */
     double phase_ms[GL_NUM_PHASES];     /* summed device time per phase         */
     int64_t phase_calls[GL_NUM_PHASES]; /* timed launches per phase             */
+    int64_t graph_captures;  /* step graphs captured                             */
+    int64_t graph_replays;   /* steps run by replaying a graph                   */
+    int64_t graph_reruns;    /* replays whose instances overflowed (re-run eagerly) */
 } gl_stats;
 
 /* Turn the per-phase timers on (1) or off (0); either way they restart from

@@ -57,7 +57,16 @@ NUM_PHASES = 10
 class Stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("sum_contrib", C.c_int64), ("pixels", C.c_int64), ("steps", C.c_int64),
-                ("phase_ms", C.c_double * NUM_PHASES), ("phase_calls", C.c_int64 * NUM_PHASES)]
+                ("phase_ms", C.c_double * NUM_PHASES), ("phase_calls", C.c_int64 * NUM_PHASES),
+                ("graph_captures", C.c_int64), ("graph_replays", C.c_int64), ("graph_reruns", C.c_int64)]
+
+
+class ExecConfig(C.Structure):
+    _fields_ = [("use_graphs", C.c_int32), ("persistent", C.c_int32), ("batch_depth", C.c_int32),
+                ("pixels_per_lane", C.c_int32), ("tile_size", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
 
 
 class Gaussians(C.Structure):
@@ -103,6 +112,9 @@ def lib():
             "gl_phase_name": ([i32], C.c_char_p),
             "gl_kernel_launch_count": ([], i64),
             "gl_photometric_loss_noalloc": ([P, P, P, i32, i32, f32, P, P, P, P], i32),
+            "gl_map_set_exec": ([P, P], i32),
+            "gl_map_get_exec": ([P, P], i32),
+            "gl_map_autotune": ([P, P, i32, i32, i32, P, P], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -376,11 +388,41 @@ class Map:
     def set_timing(self, on: bool):
         check(lib().gl_map_set_timing(self._h, int(bool(on))))
 
+    def set_exec(self, use_graphs=None, persistent=None, batch_depth=None, pixels_per_lane=None,
+                 tile_size=None):
+        """Change how steps execute (fields left as None keep their value)."""
+        e = ExecConfig()
+        check(lib().gl_map_get_exec(self._h, C.byref(e)))
+        for k, v in dict(use_graphs=use_graphs, persistent=persistent, batch_depth=batch_depth,
+                         pixels_per_lane=pixels_per_lane, tile_size=tile_size).items():
+            if v is not None:
+                setattr(e, k, int(v))
+        check(lib().gl_map_set_exec(self._h, C.byref(e)))
+        return e.as_dict()
+
+    def get_exec(self) -> dict:
+        e = ExecConfig()
+        check(lib().gl_map_get_exec(self._h, C.byref(e)))
+        return e.as_dict()
+
+    def autotune(self, views, reps: int = 3, keep_tile_size: bool = False):
+        """Time every execution candidate on the window `views` (list of
+        (id, cam, image-or-None)), install the fastest; returns (config, ms)."""
+        arr = (Keyframe * len(views))()
+        for i, (kid, cam, img) in enumerate(views):
+            arr[i] = keyframe(kid, cam, img)
+        e = ExecConfig()
+        ms = C.c_float()
+        check(lib().gl_map_autotune(self._h, arr, len(views), int(reps), int(bool(keep_tile_size)), C.byref(e),
+                                    C.byref(ms)))
+        return e.as_dict(), ms.value
+
     def stats(self) -> dict:
         st = Stats()
         check(lib().gl_map_get_stats(self._h, C.byref(st)))
         out = {k: getattr(st, k) for k in ("n_gaussians", "n_visible", "n_instances", "sum_contrib",
-                                           "pixels", "steps")}
+                                           "pixels", "steps", "graph_captures", "graph_replays",
+                                           "graph_reruns")}
         out["phases"] = {lib().gl_phase_name(i).decode(): (st.phase_ms[i], st.phase_calls[i])
                          for i in range(NUM_PHASES)}
         return out

@@ -296,7 +296,9 @@ k_scan_count(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums; count[0] = I, count[1] = overflow flag.
+// Exclusive scan of the block sums.  count[3] = instances needed; if they
+// fit in `cap` (and in 32 bits) count[0] = that number and count[1] = 0,
+// else count[0] = 0 (nothing downstream runs) and count[1] = 1.
 __global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint64_t cap,
                                                    uint64_t* count)
 {
@@ -313,8 +315,10 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint6
         ex += x;
     }
     if (threadIdx.x == 0) {
-        count[0] = tot;
-        count[1] = (tot > cap || tot > 0xffffffffull) ? 1ull : 0ull;
+        const bool ovf = tot > cap || tot > 0xffffffffull;
+        count[0] = ovf ? 0ull : tot;
+        count[1] = ovf ? 1ull : 0ull;
+        count[3] = tot;
     }
 }
 
@@ -461,7 +465,9 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
 {
     int nblocks = (int)std::min<int64_t>(kSortMaxBlocks, std::max<int64_t>(1, (n_max + kSortTile - 1) / kSortTile));
-    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * ((size_t)nblocks + 1)));
+    // sized for the largest grid, so that no later sort (graph steps
+    // included) has to grow it
+    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * ((size_t)kSortMaxBlocks + 1)));
     uint32_t* totals = hist.as<uint32_t>() + 256 * (size_t)nblocks;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int shift = 0; shift < bits; shift += 8) {
@@ -526,26 +532,23 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
     return bin_views(v, p, &cam, nullptr, 1, Ts, s);
 }
 
-gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra* extra, int V, int Ts,
-                    cudaStream_t s)
+void View::set_views(const Cam* cams, const ViewExtra* extra, int nv, int ts)
 {
-    if (V < 1 || V > kMaxViews) { set_error("1..64 views per step"); return GL_ERR_INVALID; }
-    v.V = V;
-    v.n = p.n;
-    v.Ts = Ts;
-    v.W = cams[0].W;
-    v.H = cams[0].H;
-    v.TX = (cams[0].W + Ts - 1) / Ts;
-    v.TY = (cams[0].H + Ts - 1) / Ts;
-    v.cam = cams[0];
+    V = nv;
+    Ts = ts;
+    W = cams[0].W;
+    H = cams[0].H;
+    TX = (cams[0].W + ts - 1) / ts;
+    TY = (cams[0].H + ts - 1) / ts;
+    cam = cams[0];
     int tiles = 0, ltiles = 0;
     int64_t pix = 0;
-    for (int i = 0; i < V; i++) {
-        ViewDesc& d = v.hdesc[i];
+    for (int i = 0; i < nv; i++) {
+        ViewDesc& d = hdesc[i];
         d = ViewDesc{};
         d.cam = cams[i];
-        d.TX = (cams[i].W + Ts - 1) / Ts;
-        d.TY = (cams[i].H + Ts - 1) / Ts;
+        d.TX = (cams[i].W + ts - 1) / ts;
+        d.TY = (cams[i].H + ts - 1) / ts;
         d.tile_base = tiles;
         d.ltile_base = ltiles;
         d.pix_base = pix;
@@ -560,10 +563,24 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         ltiles += ((cams[i].W + 31) / 32) * ((cams[i].H + 31) / 32);
         pix += (int64_t)cams[i].W * cams[i].H;
     }
-    v.ntiles = tiles;
-    v.nltiles = ltiles;
-    v.P = pix;
-    GL_TRY(v.upload_descs(s));
+    ntiles = tiles;
+    nltiles = ltiles;
+    P = pix;
+}
+
+gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra* extra, int V, int Ts,
+                    cudaStream_t s, bool sync_free)
+{
+    if (V < 1 || V > kMaxViews) { set_error("1..64 views per step"); return GL_ERR_INVALID; }
+    v.n = p.n;
+    if (!sync_free) {
+        v.set_views(cams, extra, V, Ts);
+        GL_TRY(v.upload_descs(s));
+    } else if (v.V != V || v.Ts != Ts) {
+        set_error("view descriptors not set for this step");
+        return GL_ERR_INVALID;
+    }
+
     const ViewDesc* dv = v.d_desc();
     const int64_t n = p.n * V;   // (view, Gaussian) pairs
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -621,26 +638,40 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
 
     // instance offsets in depth order
     const uint64_t cap = v.itile.bytes / 4;
+    if (sync_free && cap == 0) {
+        set_error("graph steps need instance buffers sized by an earlier step");
+        return GL_ERR_INVALID;
+    }
     PhaseScope ps_scan(v.prof, PH_SCAN_DUP, s);
     k_scan_count<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), n, v.bsum.as<uint64_t>());
     k_scan_top<<<1, 1024, 0, s>>>(v.bsum.as<uint64_t>(), nb, cap, count);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
-    GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, 16, cudaMemcpyDeviceToHost, s));
-    GL_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint64_t I = v.h_count[0];
-    if (I > 0xffffffffull) {
-        set_error("more than 2^32-1 (Gaussian, tile) instances in one view");
-        return GL_ERR_CAPACITY;
-    }
-    v.I = (int64_t)I;
-    if (I > cap) {
-        size_t want = (size_t)(I + I / 4 + 1024);
-        GL_TRY(v.itile.reserve(4 * want));
-        GL_TRY(v.ival.reserve(4 * want));
-        GL_TRY(v.itile2.reserve(4 * want));
-        GL_TRY(v.ival2.reserve(4 * want));
-        GL_TRY(v.iowner.reserve(4 * want));
+    int64_t nmax;   // bound on the instance count the device holds in count[0]
+    if (sync_free) {
+        v.I = -1;   // known on the device only
+        nmax = (int64_t)cap;
+    } else {
+        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, 32, cudaMemcpyDeviceToHost, s));
+        GL_CUDA_TRY(cudaStreamSynchronize(s));
+        const uint64_t I = v.h_count[3];
+        if (I > 0xffffffffull) {
+            set_error("more than 2^32-1 (Gaussian, tile) instances in one step");
+            return GL_ERR_CAPACITY;
+        }
+        v.I = (int64_t)I;
+        if (I > cap) {
+            // grow with headroom, so that later graph steps rarely overflow
+            const size_t want = (size_t)(I + I / 4 + 1024);
+            GL_TRY(v.itile.reserve(4 * want));
+            GL_TRY(v.ival.reserve(4 * want));
+            GL_TRY(v.itile2.reserve(4 * want));
+            GL_TRY(v.ival2.reserve(4 * want));
+            GL_TRY(v.iowner.reserve(4 * want));
+            k_set_u64<<<1, 1, 0, s>>>(count, I, 0);
+            count_launches(1);
+        }
+        nmax = (int64_t)I;
     }
     const uint64_t cap2 = v.itile.bytes / 4;
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
@@ -649,10 +680,10 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     ps_scan.close();
-    if (I == 0) {
+    GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
+    if (nmax == 0) {
         v.sorted_tile = v.itile.as<uint32_t>();
         v.sorted_inst = v.ival.as<uint32_t>();
-        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
         k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
         count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());
@@ -663,19 +694,20 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     {
         PhaseScope ps(v.prof, PH_TILE_SORT, s);
         GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
-                              v.ival2.as<uint32_t>(), count, (int64_t)I, tbits, v.hist, &sk, &sv, s));
+                              v.ival2.as<uint32_t>(), count, nmax, tbits, v.hist, &sk, &sv, s));
     }
     v.sorted_tile = sk;
     v.sorted_inst = sv;
     {
         PhaseScope ps(v.prof, PH_RANGES, s);
-        int rb = (int)std::min<uint64_t>(4 * 152, (I + 255) / 256);
+        int rb = (int)std::min<int64_t>(4 * 152, (nmax + 255) / 256);
         k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
-        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
         k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
         count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
-        GL_TRY(permute_records(v, s));
+        // the sorted records always get the full capacity, so that graph
+        // steps (which size nothing) find room for any count that fits
+        GL_TRY(permute_records(v, (int64_t)(v.itile.bytes / 4), s));
     }
     return GL_OK;
 }

@@ -119,9 +119,20 @@ void Prof::release()
     npool = poolcap = npend = cap = 0;
 }
 
+namespace {
+thread_local int t_freeze = 0;
+}
+AllocFreeze::AllocFreeze() { t_freeze++; }
+AllocFreeze::~AllocFreeze() { t_freeze--; }
+bool alloc_frozen() { return t_freeze > 0; }
+
 gl_status DevBuf::reserve(size_t need)
 {
     if (need <= bytes && p) return GL_OK;
+    if (t_freeze) {
+        set_error("buffer growth while capturing a step graph");
+        return GL_ERR_CAPACITY;
+    }
     if (p) {
         cudaFree(p);
         p = nullptr;
@@ -149,10 +160,10 @@ gl_status View::init()
 {
     GL_TRY(count.reserve(64));
     if (!h_count) GL_CUDA_TRY(cudaMallocHost(&h_count, 64));
-    if (!hpin) GL_CUDA_TRY(cudaMallocHost(&hpin, sizeof(ViewDesc) * kMaxViews * kDescRing));
+    if (!hpin) GL_CUDA_TRY(cudaMallocHost(&hpin, kDescBlock * kDescRing));
     for (int i = 0; i < kDescRing; i++)
         if (!pin_ev[i]) GL_CUDA_TRY(cudaEventCreateWithFlags(&pin_ev[i], cudaEventDisableTiming));
-    GL_TRY(desc.reserve(sizeof(ViewDesc) * kMaxViews));
+    GL_TRY(desc.reserve(kDescBlock));
     return GL_OK;
 }
 
@@ -163,9 +174,11 @@ gl_status View::upload_descs(cudaStream_t s)
     const int slot = pin_slot;
     pin_slot = (pin_slot + 1) % kDescRing;
     if (pin_used[slot]) GL_CUDA_TRY(cudaEventSynchronize(pin_ev[slot]));
-    ViewDesc* h = hpin + (size_t)slot * kMaxViews;
-    std::memcpy(h, hdesc, sizeof(ViewDesc) * (size_t)V);
-    GL_CUDA_TRY(cudaMemcpyAsync(desc.p, h, sizeof(ViewDesc) * (size_t)V, cudaMemcpyHostToDevice, s));
+    char* h = hpin + (size_t)slot * kDescBlock;
+    std::memcpy(h, &hscal, sizeof(StepScalars));
+    std::memcpy(h + sizeof(StepScalars), hdesc, sizeof(ViewDesc) * (size_t)V);
+    const size_t bytes = sizeof(StepScalars) + sizeof(ViewDesc) * (size_t)V;
+    GL_CUDA_TRY(cudaMemcpyAsync(desc.p, h, bytes, cudaMemcpyHostToDevice, s));
     GL_CUDA_TRY(cudaEventRecord(pin_ev[slot], s));
     pin_used[slot] = true;
     return GL_OK;
@@ -280,7 +293,7 @@ using namespace gl;
 // ===========================================================================
 extern "C" const char* gl_last_error(void) { return g_err.c_str(); }
 
-extern "C" int32_t gl_version(void) { return 100; }
+extern "C" int32_t gl_version(void) { return 101; }
 
 extern "C" gl_status gl_config_default(gl_config* c)
 {
@@ -467,6 +480,13 @@ struct gl_map {
     float* h_loss = nullptr;
     std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
     Prof prof;
+    // step execution and the captured step graph
+    gl_exec_config exec{0, 0, 32, 1, 0, 0};
+    cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int64_t> gkey;           // the step shape gexec was captured for
+    int64_t gnodes = 0;                  // kernels per replay
+    int64_t graph_captures = 0, graph_replays = 0, graph_reruns = 0;
 
     size_t row_floats(int which) const
     {
@@ -572,6 +592,9 @@ gl_status render_internal(gl_map* m, const Cam& cam, int Ts)
     GL_TRY(v.rgb.reserve(12 * P));
     GL_TRY(v.depth.reserve(4 * P));
     GL_TRY(v.opac.reserve(4 * P));
+    v.nb = m->exec.batch_depth == 64 ? 2 : 1;
+    v.pd = std::min(m->exec.pixels_per_lane, Ts / 4);
+    v.persistent = m->exec.persistent != 0;
     GL_TRY(bin_view(v, m->params(), cam, Ts, m->stream));
     return raster_forward(v, v.rgb.as<float>(), v.depth.as<float>(), v.opac.as<float>(), m->stream);
 }
@@ -625,6 +648,8 @@ extern "C" gl_status gl_map_destroy(gl_map* m)
     m->flags.release(); m->scan.release();
     for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
     if (m->h_loss) cudaFreeHost(m->h_loss);
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->gstream) cudaStreamDestroy(m->gstream);
     m->prof.release();
     delete m;
     return GL_OK;
@@ -730,43 +755,49 @@ extern "C" gl_status gl_render(gl_map* m, const gl_pose* pose, const gl_intrinsi
     return GL_OK;
 }
 
-extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32_t n_views, float* out_loss)
-{
-    if (!m || !views || n_views < 1) { set_error("need at least one view"); return GL_ERR_INVALID; }
-    if (n_views > kMaxViews) { set_error("at most 64 views per step"); return GL_ERR_INVALID; }
-    const int V = n_views;
+namespace {
+
+// Host side of one step: cameras, keyframes and targets (caller host images
+// are staged into one device buffer at each view's pixel offset).
+struct StepPlan {
+    int V = 0;
+    int64_t P = 0;
     Cam cams[kMaxViews];
     ViewExtra extra[kMaxViews];
     Keyframe* kfs[kMaxViews];
+};
+
+gl_status plan_step(gl_map* m, const gl_keyframe* views, int V, StepPlan& sp)
+{
+    if (!m || !views || V < 1) { set_error("need at least one view"); return GL_ERR_INVALID; }
+    if (V > kMaxViews) { set_error("at most 64 views per step"); return GL_ERR_INVALID; }
+    sp.V = V;
     for (int i = 0; i < V; i++) {
-        GL_TRY(make_cam(&views[i].pose, &views[i].K, cams[i]));
+        GL_TRY(make_cam(&views[i].pose, &views[i].K, sp.cams[i]));
         for (int j = 0; j < i; j++)
             if (views[j].id == views[i].id) { set_error("a keyframe appears twice in one window"); return GL_ERR_INVALID; }
         gl_status st;
-        kfs[i] = get_kf(m, views[i].id, true, &st);
-        if (!kfs[i]) return st;
+        sp.kfs[i] = get_kf(m, views[i].id, true, &st);
+        if (!sp.kfs[i]) return st;
         if (!views[i].image) {
-            if (!kfs[i]->has_image) { set_error("keyframe has no stored image"); return GL_ERR_NOT_FOUND; }
-            if (kfs[i]->K.width != cams[i].W || kfs[i]->K.height != cams[i].H) {
+            if (!sp.kfs[i]->has_image) { set_error("keyframe has no stored image"); return GL_ERR_NOT_FOUND; }
+            if (sp.kfs[i]->K.width != sp.cams[i].W || sp.kfs[i]->K.height != sp.cams[i].H) {
                 set_error("stored image size differs");
                 return GL_ERR_INVALID;
             }
         }
     }
-    // targets: registered device copies, caller device images, or caller host
-    // images staged into one buffer at each view's pixel offset
-    int64_t P = 0;
-    for (int i = 0; i < V; i++) P += (int64_t)cams[i].W * cams[i].H;
+    sp.P = 0;
+    for (int i = 0; i < V; i++) sp.P += (int64_t)sp.cams[i].W * sp.cams[i].H;
     bool need_stage = false;
     for (int i = 0; i < V; i++)
         if (views[i].image && !is_device_ptr(views[i].image)) need_stage = true;
-    if (need_stage) GL_TRY(m->stage_img.reserve(12 * (size_t)P));
-    const gl_config& c = m->cfg;
+    if (need_stage) GL_TRY(m->stage_img.reserve(12 * (size_t)sp.P));
     int64_t off = 0;
     for (int i = 0; i < V; i++) {
-        const size_t Pi = (size_t)cams[i].W * cams[i].H;
+        const size_t Pi = (size_t)sp.cams[i].W * sp.cams[i].H;
         const float* tgt = nullptr;
-        if (!views[i].image) tgt = kfs[i]->image.as<float>();
+        if (!views[i].image) tgt = sp.kfs[i]->image.as<float>();
         else if (is_device_ptr(views[i].image)) tgt = views[i].image;
         else {
             float* dst = m->stage_img.as<float>() + 3 * off;
@@ -774,49 +805,211 @@ extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32
             tgt = dst;
         }
         off += (int64_t)Pi;
-        Keyframe* kf = kfs[i];
-        kf->steps++;
-        float* e = kf->expo.as<float>();
-        extra[i].target = tgt;
-        extra[i].E = e;
-        extra[i].Em = e + 12;
-        extra[i].e_bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
-        extra[i].e_bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
-        extra[i].weight = 1.0f / (float)V;
+        float* e = sp.kfs[i]->expo.as<float>();
+        sp.extra[i].target = tgt;
+        sp.extra[i].E = e;
+        sp.extra[i].Em = e + 12;
+        sp.extra[i].weight = 1.0f / (float)V;
     }
+    return GL_OK;
+}
+
+// Advance the Adam step counters (the map's and each view's exposure) and
+// set the exposure bias corrections of the plan.
+void begin_step(gl_map* m, StepPlan& sp)
+{
+    const gl_config& c = m->cfg;
+    m->step++;
+    for (int i = 0; i < sp.V; i++) {
+        Keyframe* kf = sp.kfs[i];
+        kf->steps++;
+        sp.extra[i].e_bc1 = (float)(1.0 - std::pow((double)c.adam_b1, (double)kf->steps));
+        sp.extra[i].e_bc2 = (float)(1.0 - std::pow((double)c.adam_b2, (double)kf->steps));
+    }
+}
+
+StepScalars step_scalars(const gl_map* m)
+{
+    const gl_config& c = m->cfg;
+    StepScalars sc;
+    sc.ibc1 = (float)(1.0 / (1.0 - std::pow((double)c.adam_b1, (double)m->step)));
+    sc.isbc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)c.adam_b2, (double)m->step)));
+    return sc;
+}
+
+int step_tile(const gl_map* m) { return m->exec.tile_size ? m->exec.tile_size : m->cfg.tile_size; }
+
+void apply_exec(gl_map* m)
+{
     View& v = m->ctx.view;
-    GL_TRY(v.rgb.reserve(12 * (size_t)P));
-    GL_TRY(bin_views(v, m->params(), cams, extra, V, c.tile_size, m->stream));
-    GL_TRY(raster_forward(v, v.rgb.as<float>(), nullptr, nullptr, m->stream));
-    GL_TRY(m->dLdC.reserve(12 * (size_t)P));
+    v.nb = m->exec.batch_depth == 64 ? 2 : 1;
+    v.pd = m->exec.pixels_per_lane;
+    v.persistent = m->exec.persistent != 0;
+}
+
+// Enqueue the whole step on `s`.  sync_free: the descriptors were uploaded by
+// the caller, nothing is read back (the step being captured into a graph).
+gl_status enqueue_step(gl_map* m, const StepPlan& sp, cudaStream_t s, bool sync_free)
+{
+    const gl_config& c = m->cfg;
+    View& v = m->ctx.view;
+    const int V = sp.V;
+    GL_TRY(v.rgb.reserve(12 * (size_t)sp.P));
+    GL_TRY(bin_views(v, m->params(), sp.cams, sp.extra, V, step_tile(m), s, sync_free));
+    GL_TRY(raster_forward(v, v.rgb.as<float>(), nullptr, nullptr, s));
+    GL_TRY(m->dLdC.reserve(12 * (size_t)sp.P));
     GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * 14 * (size_t)v.nltiles));
     GL_TRY(m->loss_dev.reserve(sizeof(float) * kMaxViews));
-    m->step++;
+    const uint64_t* ctl = v.count.as<uint64_t>();
     {
-        PhaseScope ps(&m->prof, PH_LOSS, m->stream);
+        PhaseScope ps(&m->prof, PH_LOSS, s);
         GL_TRY(photometric_loss_views(v, v.rgb.as<float>(), c.lambda_dssim, m->dLdC.as<float>(),
                                       m->ctx.loss_part.as<float>(), m->loss_dev.as<float>(), c.adam_b1, c.adam_b2,
-                                      c.adam_eps, c.lr_exposure, m->stream));
+                                      c.adam_eps, c.lr_exposure, s, ctl));
     }
-    GL_TRY(raster_backward(v, m->dLdC.as<float>(), nullptr, nullptr, m->stream));
+    GL_TRY(raster_backward(v, m->dLdC.as<float>(), nullptr, nullptr, s));
     AdamArgs a;
     a.m = gl_map::mut(m->mom1);
     a.v = gl_map::mut(m->mom2);
     a.lr_pos = c.lr_pos; a.lr_dc = c.lr_sh_dc; a.lr_rest = c.lr_sh_rest; a.lr_op = c.lr_opacity;
     a.lr_scale = c.lr_scale; a.lr_rot = c.lr_rot;
     a.b1 = c.adam_b1; a.b2 = c.adam_b2; a.eps = c.adam_eps;
-    a.ibc1 = (float)(1.0 / (1.0 - std::pow((double)c.adam_b1, (double)m->step)));
-    a.isbc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)c.adam_b2, (double)m->step)));
+    const StepScalars sc = step_scalars(m);
+    a.ibc1 = sc.ibc1;
+    a.isbc2 = sc.isbc2;
     a.sparse = c.sparse_adam;
-    GL_TRY(params_adam(v, m->params(), gl_map::mut(m->prm), a, m->stream));
-    if (out_loss) {
-        GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, m->stream));
-        GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
-        double s = 0.0;
-        for (int i = 0; i < V; i++) s += m->h_loss[i];
-        *out_loss = (float)(s / V);
+    a.abort = ctl;
+    if (sync_free) a.bc = v.d_scal();
+    GL_TRY(params_adam(v, m->params(), gl_map::mut(m->prm), a, s));
+    if (sync_free) {
+        GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, s));
+        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, v.count.p, 32, cudaMemcpyDeviceToHost, s));
     }
     return GL_OK;
+}
+
+gl_status read_loss(gl_map* m, int V, bool copy, float* out_loss)
+{
+    if (!out_loss) return GL_OK;
+    if (copy) GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, m->stream));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    double sum = 0.0;
+    for (int i = 0; i < V; i++) sum += m->h_loss[i];
+    *out_loss = (float)(sum / V);
+    return GL_OK;
+}
+
+// Everything a captured step bakes in: its shape, the execution knobs and
+// the address and size of every buffer its kernels touch directly (targets
+// and exposures are reached through the descriptors, uploaded per replay).
+std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
+{
+    std::vector<int64_t> k = {sp.V, step_tile(m), m->exec.batch_depth, m->exec.pixels_per_lane,
+                              m->exec.persistent, m->n, m->deg, m->cfg.sparse_adam};
+    for (int i = 0; i < sp.V; i++) {
+        k.push_back(sp.cams[i].W);
+        k.push_back(sp.cams[i].H);
+    }
+    const View& v = m->ctx.view;
+    const DevBuf* bufs[] = {&v.rec0, &v.rec1, &v.rec2, &v.rec3, &v.radius, &v.rect, &v.touched, &v.dkey,
+                            &v.gidx, &v.dkey2, &v.gidx2, &v.dup_off, &v.g2d, &v.bsum, &v.count, &v.itile,
+                            &v.ival, &v.itile2, &v.ival2, &v.iowner, &v.srec0, &v.srec1, &v.srec2, &v.srec3,
+                            &v.sgid, &v.hist, &v.ranges, &v.tile_order, &v.Tfin, &v.ncon, &v.rgb, &v.work,
+                            &v.desc, &m->dLdC, &m->ctx.loss_part, &m->loss_dev};
+    for (const DevBuf* b : bufs) {
+        k.push_back((int64_t)(uintptr_t)b->p);
+        k.push_back((int64_t)b->bytes);
+    }
+    for (int w = 0; w < NPARAM; w++) {
+        k.push_back((int64_t)(uintptr_t)m->prm[w].p);
+        k.push_back((int64_t)(uintptr_t)m->mom1[w].p);
+        k.push_back((int64_t)(uintptr_t)m->mom2[w].p);
+    }
+    return k;
+}
+
+void drop_graph(gl_map* m)
+{
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+    m->gkey.clear();
+}
+
+// Capture the step shape of `sp` (sized by the eager step just taken).  A
+// failure leaves no graph and is not an error: steps stay eager.
+void capture_step(gl_map* m, const StepPlan& sp)
+{
+    drop_graph(m);
+    if (!m->gstream && cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking) != cudaSuccess) {
+        m->gstream = nullptr;
+        return;
+    }
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return;
+    const int64_t l0 = g_launches.load();
+    cudaGraph_t g = nullptr;
+    gl_status st;
+    {
+        AllocFreeze freeze;
+        if (cudaStreamBeginCapture(m->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return;
+        st = enqueue_step(m, sp, m->gstream, true);
+        const cudaError_t e = cudaStreamEndCapture(m->gstream, &g);
+        if (e != cudaSuccess) st = GL_ERR_CUDA;
+    }
+    const int64_t nodes = g_launches.load() - l0;
+    count_launches(-nodes);   // nothing ran yet
+    cudaGetLastError();
+    if (st != GL_OK || !g) {
+        if (g) cudaGraphDestroy(g);
+        return;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    m->gexec = ex;
+    m->gkey = graph_key(m, sp);
+    m->gnodes = nodes;
+    m->graph_captures++;
+}
+
+gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
+{
+    apply_exec(m);
+    begin_step(m, sp);
+    View& v = m->ctx.view;
+    const bool graphs = m->exec.use_graphs && !m->prof.on;
+    if (graphs && m->gexec && graph_key(m, sp) == m->gkey) {
+        v.set_views(sp.cams, sp.extra, sp.V, step_tile(m));
+        v.hscal = step_scalars(m);
+        GL_TRY(v.upload_descs(m->stream));
+        GL_CUDA_TRY(cudaGraphLaunch(m->gexec, m->stream));
+        count_launches(m->gnodes);
+        m->graph_replays++;
+        GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        if (v.h_count[1] == 0) {
+            if (out_loss) GL_TRY(read_loss(m, sp.V, false, out_loss));
+            return GL_OK;
+        }
+        // the instances outgrew the buffers: the replay updated nothing; run
+        // the same step (same counters) eagerly, which grows them
+        m->graph_reruns++;
+    }
+    GL_TRY(enqueue_step(m, sp, m->stream, false));
+    GL_TRY(read_loss(m, sp.V, true, out_loss));
+    if (graphs) capture_step(m, sp);
+    return GL_OK;
+}
+
+}  // namespace
+
+extern "C" gl_status gl_optimize_step(gl_map* m, const gl_keyframe* views, int32_t n_views, float* out_loss)
+{
+    StepPlan sp;
+    GL_TRY(plan_step(m, views, n_views, sp));
+    return run_step(m, sp, out_loss);
 }
 
 extern "C" gl_status gl_map_get_params(gl_map* m, gl_gaussians* out, int64_t* n_out)
@@ -896,6 +1089,14 @@ extern "C" gl_status gl_map_get_stats(gl_map* m, gl_stats* out)
     out->steps = m->step;
     const View& v = m->ctx.view;
     out->n_instances = v.I;
+    if (v.I < 0) {   // a graph step: the count lives on the device
+        uint64_t c = 0;
+        GL_CUDA_TRY(cudaMemcpy(&c, v.count.p, sizeof(c), cudaMemcpyDeviceToHost));
+        out->n_instances = (int64_t)c;
+    }
+    out->graph_captures = m->graph_captures;
+    out->graph_replays = m->graph_replays;
+    out->graph_reruns = m->graph_reruns;
     out->pixels = (int64_t)v.W * v.H;
     GL_TRY(view_counts(v, &out->n_visible, &out->sum_contrib, m->stream));
     for (int i = 0; i < PH_COUNT && i < GL_NUM_PHASES; i++) {
@@ -912,3 +1113,161 @@ extern "C" const char* gl_phase_name(int32_t i)
 }
 
 extern "C" int64_t gl_kernel_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// Step execution and the autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
+{
+    const int ts = e.tile_size ? e.tile_size : m->cfg.tile_size;
+    if (e.tile_size != 0 && e.tile_size != 8 && e.tile_size != 16 && e.tile_size != 32) {
+        set_error("tile_size must be 0, 8, 16 or 32");
+        return GL_ERR_INVALID;
+    }
+    if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
+    if ((e.pixels_per_lane != 1 && e.pixels_per_lane != 2 && e.pixels_per_lane != 4) || 4 * e.pixels_per_lane > ts) {
+        set_error("pixels_per_lane must be 1, 2 or 4 with 4 x pixels_per_lane <= tile size");
+        return GL_ERR_INVALID;
+    }
+    return GL_OK;
+}
+
+// Device copy of everything a step changes: the Gaussians, both Adam
+// moments, the views' exposures (E, m, v) and the step counters.
+struct Snapshot {
+    DevBuf rows[3][NPARAM];
+    DevBuf expo;
+    int64_t step = 0, n = 0;
+    std::vector<int64_t> kf_steps;
+};
+
+gl_status snap_take(gl_map* m, const StepPlan& sp, Snapshot& S)
+{
+    S.step = m->step;
+    S.n = m->n;
+    S.kf_steps.resize(sp.V);
+    GL_TRY(S.expo.reserve(36 * 4 * (size_t)sp.V));
+    for (int i = 0; i < sp.V; i++) {
+        S.kf_steps[i] = sp.kfs[i]->steps;
+        GL_CUDA_TRY(cudaMemcpyAsync(S.expo.as<float>() + 36 * i, sp.kfs[i]->expo.p, 36 * 4, cudaMemcpyDeviceToDevice,
+                                    m->stream));
+    }
+    for (int set = 0; set < 3; set++) {
+        DevBuf* arr = set == 0 ? m->prm : (set == 1 ? m->mom1 : m->mom2);
+        for (int w = 0; w < NPARAM; w++) {
+            const size_t bytes = 4 * m->row_floats(w) * (size_t)m->n;
+            GL_TRY(S.rows[set][w].reserve(bytes));
+            GL_CUDA_TRY(cudaMemcpyAsync(S.rows[set][w].p, arr[w].p, bytes, cudaMemcpyDeviceToDevice, m->stream));
+        }
+    }
+    return GL_OK;
+}
+
+gl_status snap_restore(gl_map* m, const StepPlan& sp, const Snapshot& S)
+{
+    m->step = S.step;
+    for (int i = 0; i < sp.V; i++) {
+        sp.kfs[i]->steps = S.kf_steps[i];
+        GL_CUDA_TRY(cudaMemcpyAsync(sp.kfs[i]->expo.p, S.expo.as<float>() + 36 * i, 36 * 4, cudaMemcpyDeviceToDevice,
+                                    m->stream));
+    }
+    for (int set = 0; set < 3; set++) {
+        DevBuf* arr = set == 0 ? m->prm : (set == 1 ? m->mom1 : m->mom2);
+        for (int w = 0; w < NPARAM; w++) {
+            const size_t bytes = 4 * m->row_floats(w) * (size_t)S.n;
+            GL_CUDA_TRY(cudaMemcpyAsync(arr[w].p, S.rows[set][w].p, bytes, cudaMemcpyDeviceToDevice, m->stream));
+        }
+    }
+    return GL_OK;
+}
+
+void snap_release(Snapshot& S)
+{
+    for (auto& set : S.rows)
+        for (DevBuf& b : set) b.release();
+    S.expo.release();
+}
+
+}  // namespace
+
+extern "C" gl_status gl_map_set_exec(gl_map* m, const gl_exec_config* e)
+{
+    if (!m || !e) { set_error("null argument"); return GL_ERR_INVALID; }
+    GL_TRY(check_exec_config(m, *e));
+    m->exec = *e;
+    m->exec.reserved = 0;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_exec(gl_map* m, gl_exec_config* e)
+{
+    if (!m || !e) { set_error("null argument"); return GL_ERR_INVALID; }
+    *e = m->exec;
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_t n_views, int32_t reps,
+                                     int32_t keep_tile_size, gl_exec_config* best, float* best_ms)
+{
+    if (!m || !best) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (reps < 1) { set_error("reps must be >= 1"); return GL_ERR_INVALID; }
+    StepPlan sp;
+    GL_TRY(plan_step(m, views, n_views, sp));
+    const gl_exec_config saved = m->exec;
+    const bool timing = m->prof.on;
+    m->prof.on = false;
+    Snapshot S;
+    gl_status st = snap_take(m, sp, S);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == GL_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        set_error("event creation failed");
+        st = GL_ERR_CUDA;
+    }
+    float best_t = -1.0f;
+    gl_exec_config best_e = saved;
+    const int tiles[3] = {8, 16, 32};
+    for (int ti = 0; ti < 3 && st == GL_OK; ti++) {
+        const int ts = tiles[ti];
+        if (keep_tile_size && ts != m->cfg.tile_size) continue;
+        for (int bd = 32; bd <= 64 && st == GL_OK; bd *= 2)
+            for (int ppl = 1; ppl <= 4 && st == GL_OK; ppl *= 2)
+                for (int pers = 0; pers <= 1 && st == GL_OK; pers++) {
+                    if (4 * ppl > ts) continue;
+                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, 0};
+                    m->exec = cand;
+                    // one eager step (sizes buffers, captures the graph), one replay, then reps timed replays
+                    for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, sp, nullptr);
+                    if (st != GL_OK) break;
+                    cudaEventRecord(e0, m->stream);
+                    for (int r = 0; r < reps && st == GL_OK; r++) st = run_step(m, sp, nullptr);
+                    cudaEventRecord(e1, m->stream);
+                    if (st != GL_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = GL_ERR_CUDA; break; }
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)reps;
+                    if (best_t < 0.0f || ms < best_t) {
+                        best_t = ms;
+                        best_e = cand;
+                    }
+                    st = snap_restore(m, sp, S);
+                }
+    }
+    if (st == GL_OK) st = snap_restore(m, sp, S);
+    cudaStreamSynchronize(m->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    snap_release(S);
+    drop_graph(m);
+    m->prof.on = timing;
+    if (st != GL_OK) {
+        m->exec = saved;
+        return st;
+    }
+    m->exec = best_e;
+    *best = best_e;
+    if (best_ms) *best_ms = best_t;
+    return GL_OK;
+}

@@ -77,6 +77,9 @@ struct PhaseScope {
 };
 
 // Grow-only device allocation.  Contents are not preserved on growth.
+// While a thread captures a CUDA graph (AllocFreeze in scope) a reserve that
+// would have to grow fails with GL_ERR_CAPACITY instead of reallocating a
+// buffer that captured work already points at.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -84,6 +87,12 @@ struct DevBuf {
     void release();
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
+
+struct AllocFreeze {
+    AllocFreeze();
+    ~AllocFreeze();
+};
+bool alloc_frozen();
 
 constexpr int kMaxViews = 64;   // views in one step (a keyframe window)
 constexpr int kDescRing = 8;    // pinned upload slots for view descriptors
@@ -97,6 +106,14 @@ struct ViewExtra {
     float weight = 1.f;
 };
 
+// Per-step scalars uploaded with the view descriptors (read on the device by
+// steps replayed from a CUDA graph).
+struct StepScalars {
+    float ibc1 = 1.f, isbc2 = 1.f;   // Adam bias corrections 1/(1-b1^t), 1/sqrt(1-b2^t)
+    float pad[14] = {};
+};
+static_assert(sizeof(StepScalars) == 64, "descriptor block layout");
+
 // Scratch of one step over V views: projected records (per view and
 // Gaussian, index v * n + g), binning over the concatenated tiles of all
 // views, and per-pixel state over the concatenated pixels.
@@ -109,8 +126,9 @@ struct View {
     Cam cam{};                // view 0
     int64_t I = 0;            // (Gaussian, tile) instances over the views
     ViewDesc hdesc[kMaxViews];
-    DevBuf desc;              // device copy of hdesc[0..V)
-    ViewDesc* hpin = nullptr; // pinned upload ring (kDescRing x kMaxViews)
+    StepScalars hscal;
+    DevBuf desc;              // device copy of [hscal][hdesc[0..V)]
+    char* hpin = nullptr;     // pinned upload ring (kDescRing blocks of that layout)
     cudaEvent_t pin_ev[kDescRing] = {};
     bool pin_used[kDescRing] = {};
     int pin_slot = 0;
@@ -125,7 +143,8 @@ struct View {
     DevBuf g2d;               // float[10] screen-space gradient accumulators
     // scan
     DevBuf bsum;              // u64 per scan block
-    DevBuf count;             // u64[8]: I, overflow flag, N (sort), scratch
+    DevBuf count;             // u64[8]: I (0 after an overflow), overflow flag, N (depth
+                              // sort), instances needed, view-count scratch [4..5]
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
@@ -143,7 +162,19 @@ struct View {
     const uint32_t* sorted_inst = nullptr;
     uint64_t* h_count = nullptr;          // pinned: I, overflow
     Prof* prof = nullptr;                 // optional phase timers
-    const ViewDesc* d_desc() const { return desc.as<const ViewDesc>(); }
+    // raster execution: records per lane per batch (1: 32, 2: 64), pixels per
+    // lane (1, 2, 4), persistent grid with a unit counter in `work`
+    int nb = 1, pd = 1;
+    bool persistent = false;
+    DevBuf work;              // int[2] unit counters (forward, backward)
+    const ViewDesc* d_desc() const
+    {
+        return reinterpret_cast<const ViewDesc*>(desc.as<const char>() + sizeof(StepScalars));
+    }
+    const float* d_scal() const { return desc.as<const float>(); }
+    static constexpr size_t kDescBlock = sizeof(StepScalars) + sizeof(ViewDesc) * kMaxViews;
+    // Fill hdesc and the tile / pixel totals for V views (host only).
+    void set_views(const Cam* cams, const ViewExtra* extra, int V, int Ts);
     gl_status init();
     gl_status upload_descs(cudaStream_t s);
     void release();
@@ -166,8 +197,13 @@ struct gl_ctx_impl {
 // descriptors, then preprocess + depth sort + scan + duplicate + tile sort +
 // ranges + tile order + record permutation over all of them.  Synchronises
 // once to size the instance buffers.
+// sync_free: the descriptors were set and uploaded by the caller (set_views,
+// upload_descs) and nothing is read back: instances beyond the current
+// capacity set the overflow flag (count[1]), every later kernel of the step
+// sees zero instances, and the Adam updates skip themselves; the caller
+// checks the flag after the step.  Used for steps captured in a CUDA graph.
 gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra* extra, int V, int Ts,
-                    cudaStream_t s);
+                    cudaStream_t s, bool sync_free = false);
 // The single-view case.
 gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream_t s);
 
@@ -176,7 +212,8 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
 gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s);
 
 // Records gathered into sorted-instance order (after binning).
-gl_status permute_records(View& v, cudaStream_t s);
+// nmax bounds the instance count (which is read on the device).
+gl_status permute_records(View& v, int64_t nmax, cudaStream_t s);
 
 // Backward raster: per-Gaussian screen-space gradients into v.g2d.
 gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
@@ -188,6 +225,8 @@ struct AdamArgs {
     float lr_pos, lr_dc, lr_rest, lr_op, lr_scale, lr_rot;
     float b1, b2, eps, ibc1, isbc2;  // 1/(1-b1^t), 1/sqrt(1-b2^t)
     int sparse;
+    const float* bc = nullptr;       // if set: (ibc1, isbc2) read on the device
+    const uint64_t* abort = nullptr; // if set and abort[1] != 0: no update
 };
 // mode 0: write gradients into `grad` (+ pose partials if pose_part != null).
 gl_status params_backward(View& v, const GParams& p, GMut grad, float* pose_part, int npart,
@@ -207,8 +246,10 @@ gl_status photometric_loss(const float* rgb, const float* target, const float* E
 // The same over all views of `v` (targets, exposures and weights from the
 // descriptors): dL/drgb over the concatenated pixels (already weighted),
 // loss per view into loss_v[V], and the exposure Adam step of views with Em.
+// With abort set and abort[1] != 0, the exposure update is skipped.
 gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, float* dL_drgb, float* part,
-                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s);
+                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s,
+                                 const uint64_t* abort = nullptr);
 
 // Apply C_hat = A C + b (E34 by value) from src to dst (device images).
 gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P,

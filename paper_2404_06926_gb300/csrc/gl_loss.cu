@@ -225,7 +225,7 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
 __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, int H, float lambda,
                              float* __restrict__ loss_out, float* __restrict__ dE_out,
                              const ViewDesc* __restrict__ views, float* __restrict__ loss_v, float b1,
-                             float b2, float eps, float lr)
+                             float b2, float eps, float lr, const uint64_t* __restrict__ abort)
 {
     __shared__ double tot[kNP];
     int begin = 0;
@@ -261,7 +261,7 @@ __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, in
         const int i = threadIdx.x;
         const float g = (float)tot[i];
         if (!views && dE_out) dE_out[i] = g;
-        if (Ev && Em) {
+        if (Ev && Em && !(abort && abort[1])) {
             const float m = b1 * Em[i] + (1.0f - b1) * g;
             const float v = b2 * Em[12 + i] + (1.0f - b2) * g * g;
             Em[i] = m;
@@ -313,21 +313,22 @@ gl_status photometric_loss(const float* rgb, const float* target, const float* E
     LossOne one{rgb, target, E, dL_drgb, W, H};
     k_loss<<<nblk, kThreads, kSmemFloats * sizeof(float), s>>>(one, nullptr, 0, nullptr, nullptr, lambda, part);
     k_loss_final<<<1, 32 * kNP, 0, s>>>(part, nblk, W, H, lambda, loss_out, dE_out, nullptr, nullptr, 0.f, 0.f,
-                                        0.f, 0.f);
+                                        0.f, 0.f, nullptr);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
 
 gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, float* dL_drgb, float* part,
-                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s)
+                                 float* loss_v, float b1, float b2, float eps, float lr, cudaStream_t s,
+                                 const uint64_t* abort)
 {
     GL_TRY(loss_attr());
     LossOne one{};
     k_loss<<<v.nltiles, kThreads, kSmemFloats * sizeof(float), s>>>(one, v.d_desc(), v.V, rgb, dL_drgb, lambda,
                                                                      part);
     k_loss_final<<<v.V, 32 * kNP, 0, s>>>(part, 0, 0, 0, lambda, nullptr, nullptr, v.d_desc(), loss_v, b1, b2, eps,
-                                          lr);
+                                          lr, abort);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;

@@ -177,6 +177,11 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
     // quaternion 4, logit 1, SH KF (odd stride against bank conflicts); the
     // Adam update then streams every parameter array with coalesced accesses
     constexpr int NR = 11 + KF + ((11 + KF) % 2 == 0 ? 1 : 0);
+    if (MODE == 1) {
+        // a step whose binning overflowed its buffers updates nothing (it is re-run)
+        if (ad.abort && ad.abort[1]) return;
+        if (ad.bc) { ad.ibc1 = ad.bc[0]; ad.isbc2 = ad.bc[1]; }
+    }
     __shared__ float sR[kThreads * NR];
     __shared__ uint8_t sUpd[kThreads];
     const int64_t g0 = blockIdx.x * (int64_t)kThreads;

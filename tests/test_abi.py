@@ -47,12 +47,15 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     """No compute call: only calls that validate arguments before touching CUDA."""
     from paper_2404_06926_gb300 import binding
     L = binding.lib()
-    assert L.gl_version() == 100
+    assert L.gl_version() == 101
     cfg = binding.default_config()
     assert cfg.sh_degree == 3 and cfg.tile_size == 16 and abs(cfg.lambda_dssim - 0.2) < 1e-7
     assert abs(cfg.tau - 0.99) < 1e-7 and cfg.n_sky == 100000
     assert L.gl_map_create(None, None, None) == 1
     assert b"null" in L.gl_last_error()
+    e = binding.ExecConfig(1, 0, 32, 1, 0, 0)
+    assert L.gl_map_set_exec(None, ctypes.byref(e)) == 1
+    assert L.gl_map_autotune(None, None, 1, 1, 0, None, None) == 1
 
 
 def test_struct_layouts_match_c(libpath, tmp_path):
@@ -63,8 +66,8 @@ def test_struct_layouts_match_c(libpath, tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(gl_intrinsics), sizeof(gl_pose), sizeof(gl_keyframe),
-         sizeof(gl_config), sizeof(gl_gaussians));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gl_intrinsics), sizeof(gl_pose), sizeof(gl_keyframe),
+         sizeof(gl_config), sizeof(gl_gaussians), sizeof(gl_stats), sizeof(gl_exec_config));
   printf("%zu %zu %zu %zu\\n", offsetof(gl_keyframe, image), offsetof(gl_config, n_sky),
          offsetof(gl_config, capacity_hint), offsetof(gl_gaussians, sh));
   return 0;
@@ -75,7 +78,8 @@ int main(void) {{
     a, b = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")[:2]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
-    assert sizes == [ctypes.sizeof(t) for t in (B.Intrinsics, B.Pose, B.Keyframe, B.Config, B.Gaussians)]
+    assert sizes == [ctypes.sizeof(t) for t in (B.Intrinsics, B.Pose, B.Keyframe, B.Config, B.Gaussians, B.Stats,
+                                                 B.ExecConfig)]
     assert offs == [B.Keyframe.image.offset, B.Config.n_sky.offset, B.Config.capacity_hint.offset,
                     B.Gaussians.sh.offset]
 

@@ -1,0 +1,174 @@
+"""How optimisation steps execute: records staged per warp batch (32/64),
+pixels per lane (1/2/4), persistent raster grids, the binning tile size and
+CUDA-graph replay of whole steps.
+
+Batch depth, pixels per lane and persistence change no rendered pixel
+(bit-exact) and no step result beyond the atomic-order tolerance; the tile
+size changes the 3-sigma tile rectangles, and each size matches the oracle
+run at that size; a replayed step equals an eager one, including the step
+that overflows its instance buffers and is re-run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_06926_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EXECS = [dict(batch_depth=bd, pixels_per_lane=pp, persistent=pe)
+         for bd in (32, 64) for pp in (1, 2, 4) for pe in (0, 1)]
+
+
+def _map(params, tile=16):
+    from paper_2404_06926_gb300 import binding
+    m = binding.Map(binding.default_config(n_sky=0, sh_degree=3, tile_size=tile, capacity_hint=8192))
+    m.set_params(params)
+    return m
+
+
+def _window_scene():
+    sc = scenes.diff_check()
+    base = sc["cam"]
+    rng = np.random.default_rng(31)
+    cams, targets = [], []
+    for (W, H, f) in ((256, 192, 200.0), (192, 128, 150.0), (160, 160, 170.0)):
+        w = rng.normal(0, 0.02, 3)
+        R = scenes._rodrigues(w) @ np.asarray(base["R"])
+        t = np.asarray(base["t"]) + rng.normal(0, 0.05, 3)
+        cams.append(scenes.camera(W, H, f, f, W / 2, H / 2, R=R, t=t))
+        targets.append(rng.uniform(0, 1, (H, W, 3)).astype(np.float32))
+    return sc["params"], cams, targets
+
+
+def _agree(a, b, p0, lr, frac=0.99):
+    """Fraction of entries whose moves from p0 agree within 1e-3 lr."""
+    out = {}
+    for name in ("means", "log_scales", "quats", "logits", "sh"):
+        da = a[name].astype(np.float64) - p0[name]
+        db = b[name].astype(np.float64) - p0[name]
+        moved = (da != 0) | (db != 0)
+        if not moved.any():
+            out[name] = 1.0
+            continue
+        out[name] = float((np.abs(da - db)[moved] <= 1e-3 * lr[name if name != "sh" else "sh_dc"] + 1e-7).mean())
+    return out
+
+
+@pytest.mark.parametrize("ex", EXECS, ids=lambda e: f"b{e['batch_depth']}p{e['pixels_per_lane']}s{e['persistent']}")
+def test_render_bit_identical_across_exec(ex):
+    sc = scenes.diff_check()
+    cam = sc["cam"]
+    m = _map(sc["params"])
+    H, W = cam["height"], cam["width"]
+    ref = [np.empty((H, W, 3), np.float32), np.empty((H, W), np.float32), np.empty((H, W), np.float32)]
+    m.render(cam, out_rgb=ref[0], out_depth=ref[1], out_opacity=ref[2])
+    m.set_exec(**ex)
+    got = [np.empty_like(x) for x in ref]
+    m.render(cam, out_rgb=got[0], out_depth=got[1], out_opacity=got[2])
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile,ex", [(8, dict(batch_depth=32, pixels_per_lane=2, persistent=1)),
+                                     (16, dict(batch_depth=64, pixels_per_lane=4, persistent=1)),
+                                     (16, dict(batch_depth=32, pixels_per_lane=1, persistent=0)),
+                                     (32, dict(batch_depth=64, pixels_per_lane=2, persistent=0)),
+                                     (32, dict(batch_depth=32, pixels_per_lane=4, persistent=1))])
+def test_window_step_parity_under_exec(tile, ex):
+    """The mixed-resolution window step equals the oracle at the same tile
+    size for every execution."""
+    params, cams, targets = _window_scene()
+    m = _map(params)
+    m.set_exec(tile_size=tile, **ex)
+    views = [(10 + i, cams[i], targets[i]) for i in range(3)]
+    loss = m.optimize_step(views, want_loss=True)
+    st = oracle.new_window_state(params, 3)
+    r = oracle.optimize_window(params, st, cams, targets, step=1, Ts=tile)
+    assert abs(loss - r["loss"]) <= 2e-5 * r["loss"]
+    got = m.get_params()
+    vis = r["visible"]
+    lr = oracle.DEFAULT_LR
+    for name in ("means", "log_scales", "quats", "logits"):
+        d_gpu = got[name].astype(np.float64) - params[name]
+        d_or = st["p"][name] - params[name]
+        assert np.all(d_gpu[~vis] == 0), name
+        gref = r["grads"][name][vis]
+        clear = np.abs(gref) > 1e-3 * np.sqrt(np.mean(gref ** 2))
+        agree = np.abs(d_gpu[vis] - d_or[vis])[clear] <= 1e-3 * lr[name] + 1e-7
+        assert agree.mean() > 0.99, (name, agree.mean())
+    for i in range(3):
+        assert np.allclose(m.exposure(10 + i), st["p"]["E"][i], atol=1e-6)
+
+
+def test_graph_replay_equals_eager_over_steps():
+    params, cams, targets = _window_scene()
+    a, b = _map(params), _map(params)
+    b.set_exec(use_graphs=1)
+    views = [(10 + i, cams[i], targets[i]) for i in range(3)]
+    la, lb = [], []
+    for _ in range(6):
+        la.append(a.optimize_step(views, want_loss=True))
+        lb.append(b.optimize_step(views, want_loss=True))
+    assert np.allclose(la, lb, rtol=1e-4)
+    s = b.stats()
+    assert s["graph_captures"] == 1 and s["graph_replays"] == 5
+    frac = _agree(a.get_params(), b.get_params(), params, oracle.DEFAULT_LR)
+    for name, f in frac.items():
+        assert f > 0.98, (name, f)
+    for i in range(3):
+        assert np.allclose(a.exposure(10 + i), b.exposure(10 + i), atol=1e-5)
+
+
+def test_graph_overflow_is_rerun_once():
+    """A replay whose view needs more instances than the captured step left
+    room for updates nothing and is re-run eagerly: the results equal an
+    eager map taking the same steps."""
+    sc = scenes.diff_check()
+    cam = sc["cam"]
+    far = dict(cam, t=np.asarray(cam["t"]) + np.array([2.2, 0.0, 0.0]))   # sees a sliver of the scene
+    tgt = np.ascontiguousarray(sc["target"])
+    a, b = _map(sc["params"]), _map(sc["params"])
+    b.set_exec(use_graphs=1)
+    for m in (a, b):
+        m.optimize_step([(1, far, tgt)])
+    n_far = b.stats()["n_instances"]
+    for m in (a, b):
+        m.optimize_step([(2, cam, tgt)])
+    s = b.stats()
+    assert s["n_instances"] > 1.25 * n_far + 1024, (s["n_instances"], n_far)
+    assert s["graph_captures"] >= 1 and s["graph_replays"] == 1 and s["graph_reruns"] == 1
+    frac = _agree(a.get_params(), b.get_params(), sc["params"], oracle.DEFAULT_LR)
+    for name, f in frac.items():
+        assert f > 0.98, (name, f)
+    assert np.allclose(a.exposure(2), b.exposure(2), atol=1e-5)
+    assert np.allclose(a.exposure(1), b.exposure(1), atol=1e-5)
+
+
+def test_autotune_picks_a_valid_config_and_restores_the_map():
+    params, cams, targets = _window_scene()
+    m = _map(params)
+    views = [(10 + i, cams[i], targets[i]) for i in range(3)]
+    m.optimize_step(views)
+    before = m.get_params()
+    mom = [m.get_moments(1), m.get_moments(2)]
+    E = [m.exposure(10 + i) for i in range(3)]
+    steps = m.stats()["steps"]
+    best, ms = m.autotune(views, reps=2)
+    assert ms > 0
+    assert best["use_graphs"] == 1 and best["tile_size"] in (8, 16, 32)
+    assert best["batch_depth"] in (32, 64) and best["pixels_per_lane"] in (1, 2, 4)
+    assert 4 * best["pixels_per_lane"] <= best["tile_size"]
+    assert m.get_exec() == best
+    after = m.get_params()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    for w in (1, 2):
+        got = m.get_moments(w)
+        for k in got:
+            assert np.array_equal(got[k], mom[w - 1][k]), (w, k)
+    for i in range(3):
+        assert np.array_equal(m.exposure(10 + i), E[i])
+    assert m.stats()["steps"] == steps
+    # and the map keeps optimising with the chosen execution
+    m.optimize_step(views)
