@@ -41,7 +41,14 @@ def parse():
     ap.add_argument("--updates", type=int, default=8, help="keyframe updates for the latency figure")
     ap.add_argument("--update-steps", type=int, default=100, help="optimise steps per keyframe update (K)")
     ap.add_argument("--keyframes", type=int, default=16)
-    ap.add_argument("--window", type=int, default=8, help="views per batched window step (0: skip)")
+    ap.add_argument("--window", type=int, default=8, help="views per window in the equal-PSNR comparison")
+    ap.add_argument("--exec", default="auto", choices=["auto", "eager", "graphs"],
+                    help="auto: CUDA-graph steps with autotuned raster knobs (plain keeps tile 16)")
+    ap.add_argument("--batched-views", type=int, default=12,
+                    help="mixed-resolution window of the batched workload, 2M Gaussians (0: skip)")
+    ap.add_argument("--batched-windows", type=int, default=30)
+    ap.add_argument("--psnr-steps", type=int, default=500,
+                    help="plain steps of the equal-PSNR comparison on held-out views (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -149,13 +156,25 @@ def workload_sizes(small):
     return dict(n_points=900_000, n_sky=100_000, W=1280, H=1024, f=1000.0)
 
 
-def build_map(binding, torch, small, n_kf):
+def batched_sizes(small, n_views):
+    """2M Gaussians and keyframes of three resolutions (the same field of
+    view, fx = 0.78125 W), cycled along the trajectory."""
+    res = [(1280, 1024), (1024, 768), (640, 512)]
+    if small:
+        res = [(w // 2, h // 2) for w, h in res]
+        return dict(n_points=450_000, n_sky=50_000, views=[res[i % 3] for i in range(n_views)])
+    return dict(n_points=1_800_000, n_sky=200_000, views=[res[i % 3] for i in range(n_views)])
+
+
+def build_map(binding, torch, n_points, n_sky, W, H, f, kf_sizes, seed=2, keep=0.1):
+    """The street scene's point cloud initialised as Gaussians (Sec. III-C 1)
+    plus sky, and keyframes (id k: size kf_sizes[k], evenly along the
+    trajectory) registered with their ray-cast target images."""
     from paper_2404_06926_gb300 import scenes
-    ws = workload_sizes(small)
-    sc = scenes.Outdoor(seed=2, width=ws["W"], img_height=ws["H"], f=ws["f"])
-    xyz, rgb, idx = sc.point_cloud(ws["n_points"])
-    cfg = binding.default_config(n_sky=ws["n_sky"], sh_degree=3, tile_size=16,
-                                 capacity_hint=ws["n_points"] + ws["n_sky"] + 200_000)
+    sc = scenes.Outdoor(seed=seed, width=W, img_height=H, f=f)
+    xyz, rgb, idx = sc.point_cloud(n_points, keep=keep)
+    cfg = binding.default_config(n_sky=n_sky, sh_degree=3, tile_size=16,
+                                 capacity_hint=n_points + n_sky + 200_000)
     m = binding.Map(cfg)
     # initialise from every capture pose's points (scale d/f with d in that pose)
     for i, s in enumerate(sc.traj_x):
@@ -163,16 +182,50 @@ def build_map(binding, torch, small, n_kf):
         if len(sel):
             m.add_points(np.ascontiguousarray(xyz[sel]), np.ascontiguousarray(rgb[sel]), sc.camera_at(s),
                          use_mask=False, kind=0)
-    # keyframes spread along the trajectory
-    pos = np.linspace(sc.traj_x[2], sc.traj_x[-12], n_kf)
+    pos = np.linspace(sc.traj_x[2], sc.traj_x[-12], len(kf_sizes))
     cams, imgs = [], []
-    for k, s in enumerate(pos):
-        cam = sc.camera_at(float(s))
+    for k, (s, (kw, kh)) in enumerate(zip(pos, kf_sizes)):
+        cam = sc.camera_at(float(s), width=kw, height=kh, f=0.78125 * kw)
         img = sc.target_image_torch(cam, device="cuda")
         m.add_keyframe(k, cam, img)
         cams.append(cam)
         imgs.append(img)
-    return sc, m, cams, imgs, ws
+    return sc, m, cams, imgs
+
+
+def held_out(sc, n, W, H, f, torch):
+    """Views midway between trajectory poses inside the keyframe span, with
+    exposure-free targets."""
+    xs = sc.traj_x
+    idx = np.linspace(2, len(xs) - 13, n).astype(int)
+    views = []
+    for i in idx:
+        cam = sc.camera_at(float(0.5 * (xs[i] + xs[i + 1])), width=W, height=H, f=f)
+        views.append((cam, sc.target_image_torch(cam, device="cuda", exposure=False)))
+    return views
+
+
+def mean_psnr(m, views, torch):
+    out = []
+    for cam, tgt in views:
+        img = torch.empty_like(tgt)
+        m.render(cam, out_rgb=img)
+        mse = torch.mean((img.clamp(0, 1) - tgt) ** 2).item()
+        out.append(10.0 * np.log10(1.0 / max(mse, 1e-12)))
+    return float(np.mean(out))
+
+
+def set_exec(m, mode, views, keep_tile):
+    """Execution of the map's steps: eager defaults, graphs with default
+    knobs, or graphs with the autotuner's pick for the window `views`."""
+    if mode == "eager":
+        m.set_exec(use_graphs=0, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0)
+        return m.get_exec(), None
+    if mode == "graphs":
+        m.set_exec(use_graphs=1, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0)
+        return m.get_exec(), None
+    best, ms = m.autotune(views, reps=3, keep_tile_size=keep_tile)
+    return best, ms
 
 
 def algorithmic_bytes(st, n_total):
@@ -261,6 +314,105 @@ def cpu_baseline(m, cams, imgs, crop, reps=1):
     return 1.0 / float(np.mean(fulls)), float(np.sum(walls))
 
 
+def timed(torch, fn):
+    """Device time (ms) of fn() on the current stream."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist):
+    """Wall (device) time for plain single-view steps to reach their PSNR on
+    held-out views after `psnr_steps` steps, against windows of `window`
+    views from the same starting state (the map's checkpoint)."""
+    n_kf = len(cams)
+    views = held_out(sc, 20, wsz["W"], wsz["H"], wsz["f"], torch)
+    ck = m.save(with_images=True)
+    plain_exec = m.get_exec()
+    p0 = mean_psnr(m, views, torch)
+    # plain: a random keyframe per step
+    order = rng.integers(0, n_kf, size=args.psnr_steps)
+    curve, ms_plain = [], 0.0
+    chunk = 100
+    for c0 in range(0, args.psnr_steps, chunk):
+        ks = order[c0:c0 + chunk]
+        ms_plain += timed(torch, lambda: [m.optimize_step([(int(k), cams[int(k)], None)]) for k in ks])
+        curve.append((c0 + len(ks), mean_psnr(m, views, torch)))
+    target = curve[-1][1]
+    # batched: windows of distinct random keyframes, autotuned execution
+    m.load(ck)
+    wv = min(args.window, n_kf)
+    win = [(k, cams[k], None) for k in range(wv)]
+    w_exec, _ = set_exec(m, args.exec, win, keep_tile=False)
+    m.load(ck)
+    runs = {}
+    for exp in (0.0, 0.5):
+        m.set_config(lr_window_exp=exp)
+        ms_win, nwin, reached, wcurve = 0.0, 0, False, []
+        every = 10
+        while nwin < args.psnr_steps and not reached:
+            wins = [rng.choice(n_kf, wv, replace=False) for _ in range(every)]
+            ms_win += timed(torch, lambda: [m.optimize_step([(int(k), cams[int(k)], None) for k in w]) for w in wins])
+            nwin += every
+            q = mean_psnr(m, views, torch)
+            wcurve.append((nwin, q))
+            reached = q >= target
+        runs[exp] = {"views_per_window": wv, "lr_window_exp": exp, "windows": nwin, "views": nwin * wv,
+                     "ms": ms_win, "reached": reached, "exec": w_exec,
+                     "curve": [(int(a), round(b, 3)) for a, b in wcurve],
+                     "time_ratio_plain_over_batched": (ms_plain / ms_win) if reached else None}
+        m.load(ck)
+    m.set_config(lr_window_exp=0.0)
+    m.load(ck)
+    m.set_exec(**plain_exec)
+    return {"held_out_views": len(views), "psnr_start": p0, "target_psnr": target,
+            "plain": {"steps": args.psnr_steps, "ms": ms_plain, "views": args.psnr_steps,
+                      "curve": [(int(a), round(b, 3)) for a, b in curve]},
+            "batched_paper_lr": runs[0.0], "batched_sqrt_lr": runs[0.5]}
+
+
+def run_batched(args, binding, torch, dist, ws):
+    """Keyframe window of mixed resolutions on a 2M-Gaussian map: one step =
+    render + backward of every view and one Adam step; autotuned tile size,
+    batch depth, pixels per lane and persistence, CUDA-graph replay."""
+    bsz = batched_sizes(args.small, args.batched_views)
+    W0, H0 = bsz["views"][0]
+    sc, m, cams, imgs = build_map(binding, torch, bsz["n_points"], bsz["n_sky"], W0, H0, 0.78125 * W0,
+                                  bsz["views"], seed=4, keep=0.25)
+    n = len(cams)
+    win = [(k, cams[k], None) for k in range(n)]
+    m.optimize_step(win)
+    best, tune_ms = set_exec(m, args.exec, win, keep_tile=False)
+    for _ in range(3):
+        m.optimize_step(win)
+    torch.cuda.synchronize()
+    barrier(dist)
+    nw = args.batched_windows
+    w_ms = max_over_ranks(timed(torch, lambda: [m.optimize_step(win) for _ in range(nw)]), dist)
+    st = m.stats()
+    # the same views as plain single-view steps on the same map (tile 16, autotuned knobs)
+    plain_exec, _ = set_exec(m, args.exec, [win[0]], keep_tile=True)
+    for k in range(n):
+        m.optimize_step([win[k]])
+    reps = max(1, nw // 2)
+    p_ms = max_over_ranks(timed(torch, lambda: [m.optimize_step([win[k]]) for _ in range(reps) for k in range(n)]),
+                          dist)
+    px = sum(w * h for w, h in bsz["views"])
+    out = {"workload": "outdoor LiDAR street, %d Gaussians (%d LiDAR+visual, %d sky), SH3, window of %d views "
+                       "(%s), %d pixels" % (len(m), len(m) - bsz["n_sky"], bsz["n_sky"], n,
+                                            ", ".join("%dx%d" % v for v in bsz["views"]), px),
+           "views_per_window": n, "windows": nw, "ms_per_window": w_ms / nw,
+           "windows_per_s": ws * nw / (w_ms / 1e3), "views_per_s": ws * nw * n / (w_ms / 1e3),
+           "exec": best, "autotune_ms_per_window": tune_ms, "graph_replays": st["graph_replays"],
+           "plain_same_views": {"views_per_s": ws * reps * n / (p_ms / 1e3), "exec": plain_exec}}
+    m.close()
+    return out
+
+
 # ----------------------------------------------------------------------------
 def run_reference(args):
     """The oracle as it stands, on host cores, on a bounded crop per step."""
@@ -314,7 +466,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2404_06926_gb300 import binding
     n_kf = args.keyframes
-    sc, m, cams, imgs, wsz = build_map(binding, torch, args.small, n_kf)
+    wsz = workload_sizes(args.small)
+    sc, m, cams, imgs = build_map(binding, torch, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"], wsz["f"],
+                                  [(wsz["W"], wsz["H"])] * n_kf)
     n_total = len(m)
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(100 + rank)
@@ -324,6 +478,12 @@ def run_ours(args):
         return m.optimize_step([(int(k), cams[int(k)], img)], want_loss=want)
 
     for i in range(args.warmup):
+        step(order[i])
+    # execution of the plain step: the autotuner times the raster knobs with
+    # graph replay on one keyframe, keeping the 16-pixel tiles
+    k0 = int(order[0])
+    exec_cfg, tune_ms = set_exec(m, args.exec, [(k0, cams[k0], None)], keep_tile=True)
+    for i in range(max(3, args.warmup)):
         step(order[i])
     torch.cuda.synchronize()
     launches0 = binding.kernel_launches()
@@ -357,28 +517,12 @@ def run_ours(args):
     st = m.stats()
     m.set_timing(False)
 
-    # batched: windows of several keyframes rendered and back-propagated
-    # together, one Adam step per window (mean of the views' losses)
-    batched = None
-    if args.window > 1:
-        wv = min(args.window, n_kf)
-        nwin = max(5, args.steps // wv)
-        wins = [rng.choice(n_kf, wv, replace=False) for _ in range(nwin + 2)]
-
-        def wstep(ks):
-            m.optimize_step([(int(k), cams[int(k)], None) for k in ks])
-        for i in range(2):
-            wstep(wins[i])
-        torch.cuda.synchronize()
-        barrier(dist)
-        ev0.record(stream)
-        for i in range(nwin):
-            wstep(wins[2 + i])
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        w_ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
-        batched = {"views_per_window": wv, "windows": nwin, "ms_per_window": w_ms / nwin,
-                   "windows_per_s": ws * nwin / (w_ms / 1e3), "views_per_s": ws * nwin * wv / (w_ms / 1e3)}
+    # equal-PSNR comparison on held-out views: plain single-view steps against
+    # windows of several views (one Adam step per window), both from the same
+    # starting state
+    psnr = None
+    if args.psnr_steps > 0:
+        psnr = psnr_compare(args, m, cams, sc, wsz, rng, torch, dist)
 
     # end to end through the C ABI with host buffers: pinned host target in,
     # loss out, every step
@@ -453,6 +597,11 @@ def run_ours(args):
                "sample": f"one oracle step on a {crop[0]}x{crop[1]} centre crop of a 1280x1024 keyframe "
                          f"with all {n_total} Gaussians preprocessed; steps/s extrapolated as "
                          f"1/(t_preprocess + 16 * t_rest); wall {wall:.1f} s"}
+    map_after = len(m)
+    batched = None
+    if args.batched_views > 1:
+        m.close()
+        batched = run_batched(args, binding, torch, dist, ws)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -462,6 +611,7 @@ def run_ours(args):
                                 "plain single-view step" % (n_total, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"])),
                    "n_gaussians": n_total, "width": wsz["W"], "height": wsz["H"], "tile": 16,
                    "keyframes": n_kf, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "exec": exec_cfg, "autotune_ms_per_step": tune_ms,
                    "l2": "inputs larger than L2 (params + Adam moments %.2f GB)" % (n_total * 708 / 1e9),
                    "visible": st["n_visible"], "instances": st["n_instances"],
                    "pairs_backward": st["sum_contrib"]},
@@ -471,11 +621,12 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "equal_psnr": psnr,
         "gpu_launches": int(launches),
         "clocks": clk,
         "keyframe_update": ({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                              "updates": len(lat), "steps_per_update": args.update_steps,
-                             "map_size_after": len(m)} if lat else None),
+                             "map_size_after": map_after} if lat else None),
     }
     print(json.dumps(out), flush=True)
 

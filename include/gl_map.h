@@ -92,6 +92,12 @@ typedef struct {
     float lr_pos, lr_sh_dc, lr_sh_rest, lr_opacity, lr_scale, lr_rot, lr_exposure;
     float adam_b1, adam_b2, adam_eps;
     int64_t capacity_hint;  /* initial Gaussian capacity                    */
+    float lr_window_exp;    /* Gaussian learning rates of an n-view window
+                               step are scaled by n^lr_window_exp: 0 keeps
+                               the paper's rates for any window (default);
+                               0.5 is square-root scaling for the mean
+                               gradient's lower variance.  Not in the paper. */
+    int32_t reserved2;
 } gl_config;
 
 /* Gaussian parameters in caller memory, one array per attribute, row-major:
@@ -222,6 +228,31 @@ GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
  * Errors: as gl_optimize_step, GL_ERR_OOM for the state snapshot. */
 GL_API gl_status gl_map_autotune(gl_map* map, const gl_keyframe* views, int32_t n_views, int32_t reps,
                                  int32_t keep_tile_size, gl_exec_config* best, float* best_ms);
+
+/* Change the configuration of an existing map: learning rates, Adam
+ * constants, lambda_dssim, tau, opacity_fg, sparse_adam, tile_size and
+ * lr_window_exp take effect from the next call; sh_degree must equal the
+ * map's; seed, n_sky, sky_radius, opacity_sky and capacity_hint only act at
+ * creation and are kept.  Errors: GL_ERR_INVALID (the map is unchanged). */
+GL_API gl_status gl_map_set_config(gl_map* map, const gl_config* cfg);
+GL_API gl_status gl_map_get_config(gl_map* map, gl_config* cfg);
+
+/* Checkpoint (not in the paper): the whole optimisation state -- the
+ * Gaussians and their kinds (LiDAR, visual, sky), both Adam moments, the
+ * Adam step counter, and every keyframe (id, pose, intrinsics, exposure E
+ * with its Adam moments and step count, and its stored image when
+ * with_images != 0) -- in one host byte buffer: a header (magic "GLMAPCK1",
+ * version 1, SH degree, counts), the parameter arrays, the moments, the
+ * kinds, then the keyframes by ascending id; little-endian, as both target
+ * hosts are.  gl_map_checkpoint_size gives the bytes gl_map_save writes.
+ * gl_map_load replaces the map's contents with such a buffer (same SH
+ * degree); it validates the whole buffer first and leaves the map untouched
+ * on GL_ERR_INVALID.  Pageable or pinned host memory; synchronous.
+ * Errors: GL_ERR_INVALID (null, short buffer, wrong magic/version/degree,
+ * bad keyframe camera), GL_ERR_OOM. */
+GL_API gl_status gl_map_checkpoint_size(gl_map* map, int32_t with_images, int64_t* bytes);
+GL_API gl_status gl_map_save(gl_map* map, int32_t with_images, void* host_buf, int64_t bytes);
+GL_API gl_status gl_map_load(gl_map* map, const void* host_buf, int64_t bytes);
 
 /* Copy the Gaussians (out->n must be >= the map size; pointers host or
  * device; out->sh_degree must equal the map's).  *n_out gets the size. */

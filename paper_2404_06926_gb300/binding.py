@@ -48,7 +48,8 @@ class Config(C.Structure):
                 ("lr_pos", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
                 ("lr_opacity", C.c_float), ("lr_scale", C.c_float), ("lr_rot", C.c_float),
                 ("lr_exposure", C.c_float), ("adam_b1", C.c_float), ("adam_b2", C.c_float),
-                ("adam_eps", C.c_float), ("capacity_hint", C.c_int64)]
+                ("adam_eps", C.c_float), ("capacity_hint", C.c_int64), ("lr_window_exp", C.c_float),
+                ("reserved2", C.c_int32)]
 
 
 NUM_PHASES = 10
@@ -115,6 +116,11 @@ def lib():
             "gl_map_set_exec": ([P, P], i32),
             "gl_map_get_exec": ([P, P], i32),
             "gl_map_autotune": ([P, P, i32, i32, i32, P, P], i32),
+            "gl_map_checkpoint_size": ([P, i32, P], i32),
+            "gl_map_set_config": ([P, P], i32),
+            "gl_map_get_config": ([P, P], i32),
+            "gl_map_save": ([P, i32, P, i64], i32),
+            "gl_map_load": ([P, P, i64], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -399,6 +405,29 @@ class Map:
                 setattr(e, k, int(v))
         check(lib().gl_map_set_exec(self._h, C.byref(e)))
         return e.as_dict()
+
+    def set_config(self, **over):
+        """Change run-time fields of the map's configuration (see gl_map_set_config)."""
+        cfg = Config()
+        check(lib().gl_map_get_config(self._h, C.byref(cfg)))
+        for k, v in over.items():
+            setattr(cfg, k, v)
+        check(lib().gl_map_set_config(self._h, C.byref(cfg)))
+        self.config = cfg
+
+    def save(self, with_images: bool = False) -> np.ndarray:
+        """The map's whole optimisation state as a host byte array."""
+        n = C.c_int64()
+        check(lib().gl_map_checkpoint_size(self._h, int(bool(with_images)), C.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        check(lib().gl_map_save(self._h, int(bool(with_images)), buf.ctypes.data, n.value))
+        return buf
+
+    def load(self, buf) -> None:
+        """Replace the map's state with a buffer written by save()."""
+        buf = np.ascontiguousarray(np.frombuffer(buf, np.uint8) if isinstance(buf, (bytes, bytearray)) else buf,
+                                   dtype=np.uint8)
+        check(lib().gl_map_load(self._h, buf.ctypes.data, buf.nbytes))
 
     def get_exec(self) -> dict:
         e = ExecConfig()

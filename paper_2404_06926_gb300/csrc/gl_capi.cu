@@ -483,9 +483,13 @@ struct gl_map {
     // step execution and the captured step graph
     gl_exec_config exec{0, 0, 32, 1, 0, 0};
     cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<int64_t> gkey;           // the step shape gexec was captured for
-    int64_t gnodes = 0;                  // kernels per replay
+    struct StepGraph {
+        std::vector<int64_t> key;        // the step shape it was captured for
+        cudaGraphExec_t exec = nullptr;
+        int64_t nodes = 0;               // kernels per replay
+    };
+    std::vector<StepGraph> graphs;       // most recently used last, at most kMaxGraphs
+    static constexpr size_t kMaxGraphs = 8;
     int64_t graph_captures = 0, graph_replays = 0, graph_reruns = 0;
 
     size_t row_floats(int which) const
@@ -601,11 +605,28 @@ gl_status render_internal(gl_map* m, const Cam& cam, int Ts)
 
 }  // namespace
 
+gl_status check_runtime_config(const gl_config* cfg)
+{
+    GL_TRY(check_tile(cfg->tile_size));
+    const float lrs[] = {cfg->lr_pos, cfg->lr_sh_dc, cfg->lr_sh_rest, cfg->lr_opacity, cfg->lr_scale, cfg->lr_rot,
+                         cfg->lr_exposure};
+    for (float x : lrs)
+        if (!(x >= 0.f) || !std::isfinite(x)) { set_error("learning rates must be finite and >= 0"); return GL_ERR_INVALID; }
+    if (!(cfg->adam_b1 >= 0.f && cfg->adam_b1 < 1.f) || !(cfg->adam_b2 >= 0.f && cfg->adam_b2 < 1.f) ||
+        !(cfg->adam_eps >= 0.f) || !(cfg->lambda_dssim >= 0.f && cfg->lambda_dssim <= 1.f) ||
+        !(cfg->tau > 0.f && cfg->tau <= 1.f) || !(cfg->opacity_fg > 0.f && cfg->opacity_fg < 1.f) ||
+        !std::isfinite(cfg->lr_window_exp) || cfg->lr_window_exp < -2.f || cfg->lr_window_exp > 2.f) {
+        set_error("invalid config value");
+        return GL_ERR_INVALID;
+    }
+    return GL_OK;
+}
+
 extern "C" gl_status gl_map_create(const gl_config* cfg, void* stream, gl_map** out)
 {
     if (!cfg || !out) { set_error("null argument"); return GL_ERR_INVALID; }
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3) { set_error("sh_degree must be 0..3"); return GL_ERR_INVALID; }
-    GL_TRY(check_tile(cfg->tile_size));
+    GL_TRY(check_runtime_config(cfg));
     if (cfg->n_sky < 0 || !(cfg->sky_radius > 0.f) || !(cfg->opacity_sky > 0.f && cfg->opacity_sky < 1.f) ||
         !(cfg->opacity_fg > 0.f && cfg->opacity_fg < 1.f) || !(cfg->adam_b1 >= 0.f && cfg->adam_b1 < 1.f) ||
         !(cfg->adam_b2 >= 0.f && cfg->adam_b2 < 1.f)) {
@@ -648,7 +669,7 @@ extern "C" gl_status gl_map_destroy(gl_map* m)
     m->flags.release(); m->scan.release();
     for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
     if (m->h_loss) cudaFreeHost(m->h_loss);
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);
     if (m->gstream) cudaStreamDestroy(m->gstream);
     m->prof.release();
     delete m;
@@ -874,6 +895,10 @@ gl_status enqueue_step(gl_map* m, const StepPlan& sp, cudaStream_t s, bool sync_
     a.lr_pos = c.lr_pos; a.lr_dc = c.lr_sh_dc; a.lr_rest = c.lr_sh_rest; a.lr_op = c.lr_opacity;
     a.lr_scale = c.lr_scale; a.lr_rot = c.lr_rot;
     a.b1 = c.adam_b1; a.b2 = c.adam_b2; a.eps = c.adam_eps;
+    if (c.lr_window_exp != 0.0f && V > 1) {
+        const float f = std::pow((float)V, c.lr_window_exp);
+        a.lr_pos *= f; a.lr_dc *= f; a.lr_rest *= f; a.lr_op *= f; a.lr_scale *= f; a.lr_rot *= f;
+    }
     const StepScalars sc = step_scalars(m);
     a.ibc1 = sc.ibc1;
     a.isbc2 = sc.isbc2;
@@ -930,16 +955,27 @@ std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
 
 void drop_graph(gl_map* m)
 {
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    m->gexec = nullptr;
-    m->gkey.clear();
+    for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);
+    m->graphs.clear();
+}
+
+// The cached graph of this key (moved to most recently used), or null.
+gl_map::StepGraph* find_graph(gl_map* m, const std::vector<int64_t>& key)
+{
+    for (size_t i = 0; i < m->graphs.size(); i++)
+        if (m->graphs[i].key == key) {
+            gl_map::StepGraph g = std::move(m->graphs[i]);
+            m->graphs.erase(m->graphs.begin() + i);
+            m->graphs.push_back(std::move(g));
+            return &m->graphs.back();
+        }
+    return nullptr;
 }
 
 // Capture the step shape of `sp` (sized by the eager step just taken).  A
 // failure leaves no graph and is not an error: steps stay eager.
 void capture_step(gl_map* m, const StepPlan& sp)
 {
-    drop_graph(m);
     if (!m->gstream && cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking) != cudaSuccess) {
         m->gstream = nullptr;
         return;
@@ -969,9 +1005,22 @@ void capture_step(gl_map* m, const StepPlan& sp)
         cudaGetLastError();
         return;
     }
-    m->gexec = ex;
-    m->gkey = graph_key(m, sp);
-    m->gnodes = nodes;
+    std::vector<int64_t> key = graph_key(m, sp);
+    for (size_t i = 0; i < m->graphs.size(); i++)
+        if (m->graphs[i].key == key) {   // replaces a stale entry of the same shape
+            cudaGraphExecDestroy(m->graphs[i].exec);
+            m->graphs.erase(m->graphs.begin() + i);
+            break;
+        }
+    if (m->graphs.size() >= gl_map::kMaxGraphs) {
+        cudaGraphExecDestroy(m->graphs.front().exec);
+        m->graphs.erase(m->graphs.begin());
+    }
+    gl_map::StepGraph entry;
+    entry.key = std::move(key);
+    entry.exec = ex;
+    entry.nodes = nodes;
+    m->graphs.push_back(std::move(entry));
     m->graph_captures++;
 }
 
@@ -981,12 +1030,13 @@ gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
     begin_step(m, sp);
     View& v = m->ctx.view;
     const bool graphs = m->exec.use_graphs && !m->prof.on;
-    if (graphs && m->gexec && graph_key(m, sp) == m->gkey) {
+    gl_map::StepGraph* g = graphs ? find_graph(m, graph_key(m, sp)) : nullptr;
+    if (g) {
         v.set_views(sp.cams, sp.extra, sp.V, step_tile(m));
         v.hscal = step_scalars(m);
         GL_TRY(v.upload_descs(m->stream));
-        GL_CUDA_TRY(cudaGraphLaunch(m->gexec, m->stream));
-        count_launches(m->gnodes);
+        GL_CUDA_TRY(cudaGraphLaunch(g->exec, m->stream));
+        count_launches(g->nodes);
         m->graph_replays++;
         GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
         if (v.h_count[1] == 0) {
@@ -1269,5 +1319,206 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
     m->exec = best_e;
     *best = best_e;
     if (best_ms) *best_ms = best_t;
+    return GL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint: the whole optimisation state in one host byte buffer
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkMagic[8] = {'G', 'L', 'M', 'A', 'P', 'C', 'K', '1'};
+constexpr uint32_t kCkVersion = 1;
+
+struct CkHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t deg;
+    int64_t n, step, n_kf;
+    int32_t with_images, reserved;
+};
+
+struct CkKeyframe {
+    int64_t id;
+    gl_pose pose;
+    gl_intrinsics K;
+    int64_t steps;
+    float expo[36];
+    int32_t has_image, reserved;
+};
+
+size_t pad8(size_t x) { return (x + 7) & ~size_t(7); }
+
+int64_t ck_bytes(const gl_map* m, bool with_images)
+{
+    size_t b = sizeof(CkHeader);
+    for (int w = 0; w < NPARAM; w++) b += 3 * 4 * m->row_floats(w) * (size_t)m->n;
+    b += pad8((size_t)m->n);
+    for (const auto& kv : m->kfs) {
+        b += sizeof(CkKeyframe);
+        if (with_images && kv.second->has_image) b += 12 * (size_t)kv.second->K.width * kv.second->K.height;
+    }
+    return (int64_t)b;
+}
+
+std::vector<int64_t> sorted_ids(const gl_map* m)
+{
+    std::vector<int64_t> ids;
+    for (const auto& kv : m->kfs) ids.push_back(kv.first);
+    std::sort(ids.begin(), ids.end());
+    return ids;
+}
+
+}  // namespace
+
+extern "C" gl_status gl_map_checkpoint_size(gl_map* m, int32_t with_images, int64_t* bytes)
+{
+    if (!m || !bytes) { set_error("null argument"); return GL_ERR_INVALID; }
+    *bytes = ck_bytes(m, with_images != 0);
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_save(gl_map* m, int32_t with_images, void* host_buf, int64_t bytes)
+{
+    if (!m || !host_buf) { set_error("null argument"); return GL_ERR_INVALID; }
+    const bool wi = with_images != 0;
+    if (bytes < ck_bytes(m, wi)) { set_error("checkpoint buffer too small"); return GL_ERR_INVALID; }
+    char* out = static_cast<char*>(host_buf);
+    CkHeader h{};
+    std::memcpy(h.magic, kCkMagic, 8);
+    h.version = kCkVersion;
+    h.deg = m->deg;
+    h.n = m->n;
+    h.step = m->step;
+    h.n_kf = (int64_t)m->kfs.size();
+    h.with_images = wi ? 1 : 0;
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (int set = 0; set < 3; set++) {
+        DevBuf* arr = set == 0 ? m->prm : (set == 1 ? m->mom1 : m->mom2);
+        for (int w = 0; w < NPARAM; w++) {
+            const size_t b = 4 * m->row_floats(w) * (size_t)m->n;
+            if (b) GL_CUDA_TRY(cudaMemcpyAsync(out + off, arr[w].p, b, cudaMemcpyDeviceToHost, m->stream));
+            off += b;
+        }
+    }
+    if (m->n) GL_CUDA_TRY(cudaMemcpyAsync(out + off, m->kind.p, (size_t)m->n, cudaMemcpyDeviceToHost, m->stream));
+    std::memset(out + off + m->n, 0, pad8((size_t)m->n) - (size_t)m->n);
+    off += pad8((size_t)m->n);
+    for (int64_t id : sorted_ids(m)) {
+        const Keyframe& k = *m->kfs[id];
+        CkKeyframe c{};
+        c.id = id;
+        c.pose = k.pose;
+        c.K = k.K;
+        c.steps = k.steps;
+        c.has_image = (wi && k.has_image) ? 1 : 0;
+        GL_CUDA_TRY(cudaMemcpyAsync(c.expo, k.expo.p, sizeof(c.expo), cudaMemcpyDeviceToHost, m->stream));
+        GL_CUDA_TRY(cudaStreamSynchronize(m->stream));   // c lives on this stack frame
+        std::memcpy(out + off, &c, sizeof(c));
+        off += sizeof(c);
+        if (c.has_image) {
+            const size_t b = 12 * (size_t)k.K.width * k.K.height;
+            GL_CUDA_TRY(cudaMemcpyAsync(out + off, k.image.p, b, cudaMemcpyDeviceToHost, m->stream));
+            off += b;
+        }
+    }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_load(gl_map* m, const void* host_buf, int64_t bytes)
+{
+    if (!m || !host_buf) { set_error("null argument"); return GL_ERR_INVALID; }
+    const char* in = static_cast<const char*>(host_buf);
+    if (bytes < (int64_t)sizeof(CkHeader)) { set_error("checkpoint too short"); return GL_ERR_INVALID; }
+    CkHeader h;
+    std::memcpy(&h, in, sizeof(h));
+    if (std::memcmp(h.magic, kCkMagic, 8) != 0 || h.version != kCkVersion) {
+        set_error("not a map checkpoint of this version");
+        return GL_ERR_INVALID;
+    }
+    if (h.deg != m->deg) { set_error("checkpoint SH degree differs from the map's"); return GL_ERR_INVALID; }
+    if (h.n < 0 || h.n_kf < 0 || h.step < 0) { set_error("corrupt checkpoint header"); return GL_ERR_INVALID; }
+    // validate the whole layout before touching the map
+    size_t need = sizeof(CkHeader);
+    for (int w = 0; w < NPARAM; w++) need += 3 * 4 * m->row_floats(w) * (size_t)h.n;
+    need += pad8((size_t)h.n);
+    {
+        size_t off = need;
+        for (int64_t i = 0; i < h.n_kf; i++) {
+            if ((int64_t)(off + sizeof(CkKeyframe)) > bytes) { set_error("checkpoint truncated"); return GL_ERR_INVALID; }
+            CkKeyframe c;
+            std::memcpy(&c, in + off, sizeof(c));
+            off += sizeof(c);
+            Cam tmp;
+            GL_TRY(make_cam(&c.pose, &c.K, tmp));
+            if (c.has_image) off += 12 * (size_t)c.K.width * c.K.height;
+        }
+        if ((int64_t)off > bytes) { set_error("checkpoint truncated"); return GL_ERR_INVALID; }
+    }
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    GL_TRY(map_reserve(m, std::max<int64_t>(h.n, 1)));
+    size_t off = sizeof(CkHeader);
+    for (int set = 0; set < 3; set++) {
+        DevBuf* arr = set == 0 ? m->prm : (set == 1 ? m->mom1 : m->mom2);
+        for (int w = 0; w < NPARAM; w++) {
+            const size_t b = 4 * m->row_floats(w) * (size_t)h.n;
+            if (b) GL_CUDA_TRY(cudaMemcpyAsync(arr[w].p, in + off, b, cudaMemcpyHostToDevice, m->stream));
+            off += b;
+        }
+    }
+    if (h.n) GL_CUDA_TRY(cudaMemcpyAsync(m->kind.p, in + off, (size_t)h.n, cudaMemcpyHostToDevice, m->stream));
+    off += pad8((size_t)h.n);
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
+    m->kfs.clear();
+    for (int64_t i = 0; i < h.n_kf; i++) {
+        CkKeyframe c;
+        std::memcpy(&c, in + off, sizeof(c));
+        off += sizeof(c);
+        gl_status st;
+        Keyframe* k = get_kf(m, c.id, true, &st);
+        if (!k) return st;
+        k->pose = c.pose;
+        k->K = c.K;
+        k->steps = c.steps;
+        GL_CUDA_TRY(cudaMemcpyAsync(k->expo.p, in + off - sizeof(c) + offsetof(CkKeyframe, expo), sizeof(c.expo),
+                                    cudaMemcpyHostToDevice, m->stream));
+        if (c.has_image) {
+            const size_t b = 12 * (size_t)c.K.width * c.K.height;
+            GL_TRY(k->image.reserve(b));
+            GL_CUDA_TRY(cudaMemcpyAsync(k->image.p, in + off, b, cudaMemcpyHostToDevice, m->stream));
+            k->has_image = true;
+            off += b;
+        }
+    }
+    m->n = h.n;
+    m->step = h.step;
+    drop_graph(m);
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_set_config(gl_map* m, const gl_config* cfg)
+{
+    if (!m || !cfg) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (cfg->sh_degree != m->deg) { set_error("sh_degree cannot change"); return GL_ERR_INVALID; }
+    GL_TRY(check_runtime_config(cfg));
+    gl_config c = *cfg;
+    c.seed = m->cfg.seed;
+    c.n_sky = m->cfg.n_sky;
+    c.sky_radius = m->cfg.sky_radius;
+    c.opacity_sky = m->cfg.opacity_sky;
+    c.capacity_hint = m->cfg.capacity_hint;
+    m->cfg = c;
+    drop_graph(m);   // learning rates and flags are baked into captured steps
+    return GL_OK;
+}
+
+extern "C" gl_status gl_map_get_config(gl_map* m, gl_config* cfg)
+{
+    if (!m || !cfg) { set_error("null argument"); return GL_ERR_INVALID; }
+    *cfg = m->cfg;
     return GL_OK;
 }

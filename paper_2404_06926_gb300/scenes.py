@@ -308,14 +308,15 @@ class Outdoor:
         pts, col = pts[upper][:n], col[hit][upper][:n]
         return pts.astype(np.float32), col.astype(np.float32)
 
-    def point_cloud(self, n_total, poses=None, visual_frac=0.05):
-        """LiDAR + visual points along the trajectory, truncated to n_total.
+    def point_cloud(self, n_total, poses=None, visual_frac=0.05, keep=0.1):
+        """LiDAR + visual points along the trajectory, truncated to n_total
+        (`keep`: fraction of LiDAR rays kept per sweep, 1/10 in the paper).
         Returns (xyz, rgb, pose index of capture)."""
         poses = self.traj_x if poses is None else poses
         xs, cs, ks = [], [], []
         per_pose = int(np.ceil(1.03 * n_total / len(poses)))
         for i, s in enumerate(poses):
-            p, c = self.lidar_sweep(s)
+            p, c = self.lidar_sweep(s, keep=keep)
             nv = int(per_pose * visual_frac)
             vp, vc = self.visual_points(s, nv)
             p = np.concatenate([p[: per_pose - len(vp)], vp])

@@ -56,6 +56,8 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     e = binding.ExecConfig(1, 0, 32, 1, 0, 0)
     assert L.gl_map_set_exec(None, ctypes.byref(e)) == 1
     assert L.gl_map_autotune(None, None, 1, 1, 0, None, None) == 1
+    assert L.gl_map_load(None, None, 0) == 1
+    assert L.gl_map_save(None, 0, None, 0) == 1
 
 
 def test_struct_layouts_match_c(libpath, tmp_path):

@@ -172,3 +172,44 @@ def test_autotune_picks_a_valid_config_and_restores_the_map():
     assert m.stats()["steps"] == steps
     # and the map keeps optimising with the chosen execution
     m.optimize_step(views)
+
+
+def test_window_learning_rate_scaling():
+    """lr_window_exp = 0.5 scales the Gaussians' learning rates of a 3-view
+    window by sqrt(3) (the exposures keep theirs): equal to the oracle step
+    with those rates."""
+    params, cams, targets = _window_scene()
+    m = _map(params)
+    m.set_config(lr_window_exp=0.5)
+    m.optimize_step([(10 + i, cams[i], targets[i]) for i in range(3)])
+    f = np.sqrt(3.0)
+    lr = {k: (v * f if k != "exposure" else v) for k, v in oracle.DEFAULT_LR.items()}
+    st = oracle.new_window_state(params, 3)
+    r = oracle.optimize_window(params, st, cams, targets, step=1, Ts=16, lr=lr)
+    got = m.get_params()
+    vis = r["visible"]
+    for name in ("means", "log_scales", "quats", "logits"):
+        d_gpu = got[name].astype(np.float64) - params[name]
+        d_or = st["p"][name] - params[name]
+        gref = r["grads"][name][vis]
+        clear = np.abs(gref) > 1e-3 * np.sqrt(np.mean(gref ** 2))
+        agree = np.abs(d_gpu[vis] - d_or[vis])[clear] <= 1e-3 * lr[name] + 1e-7
+        assert agree.mean() > 0.99, (name, agree.mean())
+        # and the moves are sqrt(3) times those at the paper's rates
+        assert np.median(np.abs(d_gpu[vis])[clear]) > 1.5 * oracle.DEFAULT_LR[name]
+    for i in range(3):
+        assert np.allclose(m.exposure(10 + i), st["p"]["E"][i], atol=1e-6)
+
+
+def test_set_config_rejects_bad_values_and_keeps_the_map():
+    from paper_2404_06926_gb300 import binding
+    params, cams, targets = _window_scene()
+    m = _map(params)
+    before = m.get_exec()
+    for bad in (dict(lr_pos=-1.0), dict(tile_size=12), dict(sh_degree=0), dict(lambda_dssim=2.0)):
+        with pytest.raises(binding.GLError):
+            m.set_config(**bad)
+    m2 = binding.Config()
+    binding.lib().gl_map_get_config(m._h, binding.C.byref(m2))
+    assert abs(m2.lr_pos - 1.6e-4) < 1e-10 and m2.tile_size == 16
+    assert m.get_exec() == before
