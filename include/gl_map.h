@@ -204,14 +204,22 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *   pixels_per_lane  1, 2 or 4 pixels of a column per lane; 4 x this must
  *                    not exceed the tile size.
  *   tile_size        0: gl_config's; else 8, 16 or 32.
- * gl_map_create starts with {0, 0, 32, 1, 0}.  Errors: GL_ERR_INVALID. */
+ *   deterministic    1: the backward writes each pixel block's sums per
+ *                    (Gaussian, tile) instance and adds them per Gaussian
+ *                    in a fixed order instead of with float atomics, so a
+ *                    step's results are bit-identical from run to run (at
+ *                    the cost of one more pass over 40 bytes per instance
+ *                    and pixel block); batch_depth is then 32.
+ * Apart from deterministic = 1, results differ between runs only by the
+ * order of the backward's float atomics.
+ * gl_map_create starts with {0, 0, 32, 1, 0, 0}.  Errors: GL_ERR_INVALID. */
 typedef struct {
     int32_t use_graphs;
     int32_t persistent;
     int32_t batch_depth;
     int32_t pixels_per_lane;
     int32_t tile_size;
-    int32_t reserved;
+    int32_t deterministic;
 } gl_exec_config;
 
 GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
@@ -302,6 +310,106 @@ GL_API const char* gl_phase_name(int32_t i);
 
 /* Number of kernels this library has launched in this process so far. */
 GL_API int64_t gl_kernel_launch_count(void);
+
+/* ---------------------------------------------------------------------- */
+/* Serving loop (not in the paper, which runs the mapping thread of        */
+/* Sec. III-C beside tracking): a request loop over one map that keeps    */
+/* the map on the device, serialises the requests that change it and      */
+/* batches novel-view renders.                                             */
+/*                                                                         */
+/* Mutating requests (KEYFRAME_UPDATE, OPTIMIZE) run on the map's stream   */
+/* in submission order; each one that succeeds commits a new map version   */
+/* (1, 2, ...; 0 is the map as the server found it).  After each commit    */
+/* the Gaussians are copied into one of two snapshot buffers.  RENDER      */
+/* requests read the snapshot of the latest committed version at the time */
+/* they are admitted; all renders admitted together (up to                 */
+/* render_batch) are rendered by one multi-view launch on the server's own */
+/* stream, so their work overlaps the mutations' on the device.  A        */
+/* request is admitted only while the device has free memory for it (its  */
+/* estimated need plus reserve_bytes); it waits otherwise and fails with   */
+/* GL_ERR_OOM only if it cannot fit with nothing else in flight.           */
+/*                                                                         */
+/* KEYFRAME_UPDATE (Sec. III-C 2-3): add the points through the opacity     */
+/* mask of the keyframe's view (gl_map_add_points, use_mask = 1, or all    */
+/* points if the map is empty), register the keyframe (gl_map_add_keyframe) */
+/* and take n_steps optimisation steps.  OPTIMIZE: n_steps steps.  Each     */
+/* step uses `window` distinct registered keyframes (1 = the plain step),  */
+/* drawn by a SplitMix64 counter generator seeded with `seed` over the     */
+/* registered ids in ascending order, so a request's steps depend only on */
+/* the map version it starts from and its own fields.                      */
+/* ---------------------------------------------------------------------- */
+typedef struct gl_server gl_server;
+
+enum { GL_REQ_KEYFRAME_UPDATE = 1, GL_REQ_OPTIMIZE = 2, GL_REQ_RENDER = 3 };
+
+typedef struct {
+    int32_t queue_capacity;      /* pending requests before GL_ERR_BUSY (default 256)  */
+    int32_t render_batch;        /* renders per batched launch (default 8, <= 64)       */
+    int64_t reserve_bytes;       /* device memory kept free (default 1 GiB)             */
+    int32_t record_versions;     /* 1: keep a checkpoint (gl_map_save layout, with      */
+                                 /*    images) of every committed version, for tests    */
+    int32_t reserved;
+} gl_server_config;
+
+typedef struct {
+    int32_t kind;                /* GL_REQ_*                                            */
+    int32_t n_steps;             /* optimisation steps (KEYFRAME_UPDATE, OPTIMIZE)      */
+    int32_t window;              /* keyframes per step (>= 1)                           */
+    int32_t point_kind;          /* 0 LiDAR, 1 visual (KEYFRAME_UPDATE)                 */
+    uint64_t seed;               /* keyframe sampling                                   */
+    const float* xyz;            /* KEYFRAME_UPDATE: n_points * 3, host; copied at      */
+    const float* rgb;            /*   submission                                        */
+    int64_t n_points;
+    gl_keyframe keyframe;        /* KEYFRAME_UPDATE: id, pose, K, host image (copied);  */
+                                 /* RENDER: pose and K (image ignored)                  */
+    float* out_rgb;              /* RENDER: H*W*3, host or device, written before the   */
+                                 /*   request completes; caller keeps it valid          */
+} gl_request;
+
+typedef struct {
+    int32_t status;              /* gl_status of the request                            */
+    int32_t kind;
+    int64_t version;             /* RENDER: version read; others: version committed     */
+    double t_submit, t_admit, t_done;   /* seconds since gl_server_create               */
+    float loss;                  /* mean loss of the request's last optimisation step   */
+    int32_t batch;               /* RENDER: renders in its launch                       */
+    int64_t n_added;             /* KEYFRAME_UPDATE: Gaussians added                    */
+} gl_result;
+
+typedef struct {
+    int64_t submitted[4], completed[4], failed[4];   /* indexed by GL_REQ_* (0 unused)   */
+    double p50_ms[4], p99_ms[4], mean_ms[4];         /* latency submit -> done           */
+    int64_t steps;               /* optimisation steps taken                            */
+    double steps_per_s;          /* steps / (last completion - first submission)        */
+    double renders_per_s;
+    double mean_render_batch;
+    int64_t memory_waits;        /* admissions deferred for device memory               */
+    int64_t busy_rejects;        /* submissions refused with GL_ERR_BUSY                */
+    int64_t version;             /* latest committed version                            */
+    int64_t map_size;
+} gl_server_stats;
+
+/* gl_server_config_default fills the defaults above. */
+GL_API gl_status gl_server_config_default(gl_server_config* cfg);
+/* Start the loop's two worker threads over `map`.  While the server lives,
+ * the map must not be used directly.  Errors: GL_ERR_INVALID, GL_ERR_OOM. */
+GL_API gl_status gl_server_create(gl_map* map, const gl_server_config* cfg, gl_server** out);
+/* Queue a request; *ticket identifies it.  Errors: GL_ERR_INVALID (bad
+ * request), GL_ERR_BUSY (queue full). */
+GL_API gl_status gl_server_submit(gl_server* srv, const gl_request* req, uint64_t* ticket);
+/* Wait up to timeout_s seconds (< 0: forever) for a request and take its
+ * result (each ticket can be taken once).  Errors: GL_ERR_TIMEOUT,
+ * GL_ERR_NOT_FOUND (unknown or already taken). */
+GL_API gl_status gl_server_wait(gl_server* srv, uint64_t ticket, double timeout_s, gl_result* out);
+/* Wait until every submitted request has completed. */
+GL_API gl_status gl_server_drain(gl_server* srv);
+GL_API gl_status gl_server_get_stats(gl_server* srv, gl_server_stats* out);
+/* With record_versions: the checkpoint of committed version v (v = 0 is
+ * the map as the server found it).  *bytes gets its size; buf (nullable)
+ * receives it if cap is large enough.  Errors: GL_ERR_NOT_FOUND. */
+GL_API gl_status gl_server_get_version(gl_server* srv, int64_t v, void* buf, int64_t cap, int64_t* bytes);
+/* Drain, stop the workers and free the server (not the map). */
+GL_API gl_status gl_server_destroy(gl_server* srv);
 
 /* ---------------------------------------------------------------------- */
 /* Stateless differentiable API (one view), for autograd wrappers and     */

@@ -64,10 +64,10 @@ class Stats(C.Structure):
 
 class ExecConfig(C.Structure):
     _fields_ = [("use_graphs", C.c_int32), ("persistent", C.c_int32), ("batch_depth", C.c_int32),
-                ("pixels_per_lane", C.c_int32), ("tile_size", C.c_int32), ("reserved", C.c_int32)]
+                ("pixels_per_lane", C.c_int32), ("tile_size", C.c_int32), ("deterministic", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Gaussians(C.Structure):
@@ -118,6 +118,14 @@ def lib():
             "gl_map_autotune": ([P, P, i32, i32, i32, P, P], i32),
             "gl_map_checkpoint_size": ([P, i32, P], i32),
             "gl_map_set_config": ([P, P], i32),
+            "gl_server_config_default": ([P], i32),
+            "gl_server_create": ([P, P, P], i32),
+            "gl_server_submit": ([P, P, P], i32),
+            "gl_server_wait": ([P, C.c_uint64, C.c_double, P], i32),
+            "gl_server_drain": ([P], i32),
+            "gl_server_get_stats": ([P, P], i32),
+            "gl_server_get_version": ([P, i64, P, i64, P], i32),
+            "gl_server_destroy": ([P], i32),
             "gl_map_get_config": ([P, P], i32),
             "gl_map_save": ([P, i32, P, i64], i32),
             "gl_map_load": ([P, P, i64], i32),
@@ -395,12 +403,12 @@ class Map:
         check(lib().gl_map_set_timing(self._h, int(bool(on))))
 
     def set_exec(self, use_graphs=None, persistent=None, batch_depth=None, pixels_per_lane=None,
-                 tile_size=None):
+                 tile_size=None, deterministic=None):
         """Change how steps execute (fields left as None keep their value)."""
         e = ExecConfig()
         check(lib().gl_map_get_exec(self._h, C.byref(e)))
         for k, v in dict(use_graphs=use_graphs, persistent=persistent, batch_depth=batch_depth,
-                         pixels_per_lane=pixels_per_lane, tile_size=tile_size).items():
+                         pixels_per_lane=pixels_per_lane, tile_size=tile_size, deterministic=deterministic).items():
             if v is not None:
                 setattr(e, k, int(v))
         check(lib().gl_map_set_exec(self._h, C.byref(e)))
@@ -460,3 +468,118 @@ class Map:
         E = np.zeros(12, np.float32)
         check(lib().gl_map_get_exposure(self._h, int(kid), E.ctypes.data))
         return E.reshape(3, 4)
+
+
+# ---------------------------------------------------------------------------
+# Serving loop
+# ---------------------------------------------------------------------------
+REQ_KEYFRAME_UPDATE, REQ_OPTIMIZE, REQ_RENDER = 1, 2, 3
+REQ_NAMES = {1: "keyframe_update", 2: "optimize", 3: "render"}
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("queue_capacity", C.c_int32), ("render_batch", C.c_int32), ("reserve_bytes", C.c_int64),
+                ("record_versions", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_steps", C.c_int32), ("window", C.c_int32), ("point_kind", C.c_int32),
+                ("seed", C.c_uint64), ("xyz", C.c_void_p), ("rgb", C.c_void_p), ("n_points", C.c_int64),
+                ("keyframe", Keyframe), ("out_rgb", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("version", C.c_int64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("loss", C.c_float), ("batch", C.c_int32),
+                ("n_added", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64 * 4), ("completed", C.c_int64 * 4), ("failed", C.c_int64 * 4),
+                ("p50_ms", C.c_double * 4), ("p99_ms", C.c_double * 4), ("mean_ms", C.c_double * 4),
+                ("steps", C.c_int64), ("steps_per_s", C.c_double), ("renders_per_s", C.c_double),
+                ("mean_render_batch", C.c_double), ("memory_waits", C.c_int64), ("busy_rejects", C.c_int64),
+                ("version", C.c_int64), ("map_size", C.c_int64)]
+
+
+class Server:
+    """Request loop over a Map (see gl_server_create).  Host inputs are copied
+    at submission; a render's output array must stay alive until wait()."""
+
+    def __init__(self, m: Map, queue_capacity=256, render_batch=8, reserve_bytes=1 << 30, record_versions=False):
+        cfg = ServerConfig()
+        check(lib().gl_server_config_default(C.byref(cfg)))
+        cfg.queue_capacity, cfg.render_batch = int(queue_capacity), int(render_batch)
+        cfg.reserve_bytes, cfg.record_versions = int(reserve_bytes), int(bool(record_versions))
+        self.map = m
+        self._h = C.c_void_p()
+        self._keep = {}   # ticket -> output arrays kept alive
+        check(lib().gl_server_create(m._h, C.byref(cfg), C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            check(lib().gl_server_destroy(self._h))
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, r: Request, keep=None) -> int:
+        t = C.c_uint64()
+        check(lib().gl_server_submit(self._h, C.byref(r), C.byref(t)))
+        if keep is not None:
+            self._keep[t.value] = keep
+        return t.value
+
+    def keyframe_update(self, kid, cam, image, xyz, rgb, n_steps=0, window=1, seed=0, point_kind=0) -> int:
+        xyz = np.ascontiguousarray(xyz, np.float32)
+        rgb = np.ascontiguousarray(rgb, np.float32)
+        r = Request(kind=REQ_KEYFRAME_UPDATE, n_steps=int(n_steps), window=int(window), point_kind=int(point_kind),
+                    seed=int(seed), xyz=_ptr(xyz), rgb=_ptr(rgb), n_points=len(xyz))
+        r.keyframe = keyframe(kid, cam, image)
+        return self._submit(r)
+
+    def optimize(self, n_steps, window=1, seed=0) -> int:
+        return self._submit(Request(kind=REQ_OPTIMIZE, n_steps=int(n_steps), window=int(window), seed=int(seed)))
+
+    def render(self, cam, out=None) -> int:
+        if out is None:
+            out = np.empty((int(cam["height"]), int(cam["width"]), 3), np.float32)
+        r = Request(kind=REQ_RENDER)
+        r.keyframe = keyframe(-1, cam, None)
+        r.out_rgb = _ptr(out)
+        return self._submit(r, keep=out)
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(result dict, render output or None)."""
+        res = Result()
+        check(lib().gl_server_wait(self._h, int(ticket), float(timeout), C.byref(res)))
+        return res.as_dict(), self._keep.pop(ticket, None)
+
+    def drain(self):
+        check(lib().gl_server_drain(self._h))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().gl_server_get_stats(self._h, C.byref(st)))
+        out = {"steps": st.steps, "steps_per_s": st.steps_per_s, "renders_per_s": st.renders_per_s,
+               "mean_render_batch": st.mean_render_batch, "memory_waits": st.memory_waits,
+               "busy_rejects": st.busy_rejects, "version": st.version, "map_size": st.map_size}
+        for k, name in REQ_NAMES.items():
+            out[name] = {"submitted": st.submitted[k], "completed": st.completed[k], "failed": st.failed[k],
+                         "p50_ms": st.p50_ms[k], "p99_ms": st.p99_ms[k], "mean_ms": st.mean_ms[k]}
+        return out
+
+    def version(self, v: int) -> np.ndarray:
+        n = C.c_int64()
+        check(lib().gl_server_get_version(self._h, int(v), None, 0, C.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        check(lib().gl_server_get_version(self._h, int(v), buf.ctypes.data, n.value, C.byref(n)))
+        return buf

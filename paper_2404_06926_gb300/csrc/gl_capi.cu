@@ -187,7 +187,7 @@ gl_status View::upload_descs(cudaStream_t s)
 void View::release()
 {
     DevBuf* all[] = {&rec0, &rec1, &rec2, &rec3, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
-                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d,
+                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d, &gpart, &work,
                      &hist, &ranges, &tile_order, &Tfin, &ncon, &rgb, &depth, &opac};
     for (DevBuf* b : all) b->release();
     desc.release();
@@ -863,7 +863,8 @@ int step_tile(const gl_map* m) { return m->exec.tile_size ? m->exec.tile_size : 
 void apply_exec(gl_map* m)
 {
     View& v = m->ctx.view;
-    v.nb = m->exec.batch_depth == 64 ? 2 : 1;
+    v.det = m->exec.deterministic != 0;
+    v.nb = (m->exec.batch_depth == 64 && !v.det) ? 2 : 1;
     v.pd = m->exec.pixels_per_lane;
     v.persistent = m->exec.persistent != 0;
 }
@@ -930,7 +931,7 @@ gl_status read_loss(gl_map* m, int V, bool copy, float* out_loss)
 std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
 {
     std::vector<int64_t> k = {sp.V, step_tile(m), m->exec.batch_depth, m->exec.pixels_per_lane,
-                              m->exec.persistent, m->n, m->deg, m->cfg.sparse_adam};
+                              m->exec.persistent, m->exec.deterministic, m->n, m->deg, m->cfg.sparse_adam};
     for (int i = 0; i < sp.V; i++) {
         k.push_back(sp.cams[i].W);
         k.push_back(sp.cams[i].H);
@@ -939,7 +940,7 @@ std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
     const DevBuf* bufs[] = {&v.rec0, &v.rec1, &v.rec2, &v.rec3, &v.radius, &v.rect, &v.touched, &v.dkey,
                             &v.gidx, &v.dkey2, &v.gidx2, &v.dup_off, &v.g2d, &v.bsum, &v.count, &v.itile,
                             &v.ival, &v.itile2, &v.ival2, &v.iowner, &v.srec0, &v.srec1, &v.srec2, &v.srec3,
-                            &v.sgid, &v.hist, &v.ranges, &v.tile_order, &v.Tfin, &v.ncon, &v.rgb, &v.work,
+                            &v.sgid, &v.hist, &v.ranges, &v.tile_order, &v.Tfin, &v.ncon, &v.rgb, &v.work, &v.gpart,
                             &v.desc, &m->dLdC, &m->ctx.loss_part, &m->loss_dev};
     for (const DevBuf* b : bufs) {
         k.push_back((int64_t)(uintptr_t)b->p);
@@ -1177,6 +1178,7 @@ gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
         return GL_ERR_INVALID;
     }
     if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
+    if (e.deterministic != 0 && e.deterministic != 1) { set_error("deterministic must be 0 or 1"); return GL_ERR_INVALID; }
     if ((e.pixels_per_lane != 1 && e.pixels_per_lane != 2 && e.pixels_per_lane != 4) || 4 * e.pixels_per_lane > ts) {
         set_error("pixels_per_lane must be 1, 2 or 4 with 4 x pixels_per_lane <= tile size");
         return GL_ERR_INVALID;
@@ -1247,7 +1249,6 @@ extern "C" gl_status gl_map_set_exec(gl_map* m, const gl_exec_config* e)
     if (!m || !e) { set_error("null argument"); return GL_ERR_INVALID; }
     GL_TRY(check_exec_config(m, *e));
     m->exec = *e;
-    m->exec.reserved = 0;
     return GL_OK;
 }
 
@@ -1281,11 +1282,11 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
     for (int ti = 0; ti < 3 && st == GL_OK; ti++) {
         const int ts = tiles[ti];
         if (keep_tile_size && ts != m->cfg.tile_size) continue;
-        for (int bd = 32; bd <= 64 && st == GL_OK; bd *= 2)
+        for (int bd = 32; bd <= (saved.deterministic ? 32 : 64) && st == GL_OK; bd *= 2)
             for (int ppl = 1; ppl <= 4 && st == GL_OK; ppl *= 2)
                 for (int pers = 0; pers <= 1 && st == GL_OK; pers++) {
                     if (4 * ppl > ts) continue;
-                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, 0};
+                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic};
                     m->exec = cand;
                     // one eager step (sizes buffers, captures the graph), one replay, then reps timed replays
                     for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, sp, nullptr);
@@ -1522,3 +1523,57 @@ extern "C" gl_status gl_map_get_config(gl_map* m, gl_config* cfg)
     *cfg = m->cfg;
     return GL_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Hooks for the serving loop (gl_server.cu)
+// ---------------------------------------------------------------------------
+namespace gl {
+
+gl_status camera_from(const gl_pose* pose, const gl_intrinsics* K, Cam& cam) { return make_cam(pose, K, cam); }
+cudaStream_t map_stream(const gl_map* m) { return m->stream; }
+int map_sh_degree(const gl_map* m) { return m->deg; }
+int map_tile_size(const gl_map* m) { return m->cfg.tile_size; }
+int64_t map_size_now(const gl_map* m) { return m->n; }
+int64_t map_capacity(const gl_map* m) { return m->cap; }
+
+gl_status map_snapshot(gl_map* m, DevBuf* dst, int64_t* n_out, cudaEvent_t done)
+{
+    for (int w = 0; w < NPARAM; w++) {
+        const size_t b = 4 * m->row_floats(w) * (size_t)std::max<int64_t>(m->n, 1);
+        GL_TRY(dst[w].reserve(b));
+        if (m->n) GL_CUDA_TRY(cudaMemcpyAsync(dst[w].p, m->prm[w].p, 4 * m->row_floats(w) * (size_t)m->n,
+                                              cudaMemcpyDeviceToDevice, m->stream));
+    }
+    GL_CUDA_TRY(cudaEventRecord(done, m->stream));
+    *n_out = m->n;
+    return GL_OK;
+}
+
+GParams snapshot_params(const gl_map* m, const DevBuf* src, int64_t n)
+{
+    GParams p;
+    p.means = src[PM].as<float>(); p.log_scales = src[PS].as<float>(); p.quats = src[PQ].as<float>();
+    p.logits = src[PO].as<float>(); p.sh = src[PH].as<float>();
+    p.n = n; p.deg = m->deg; p.K = m->K;
+    return p;
+}
+
+void map_keyframes(const gl_map* m, std::vector<gl_keyframe>& out)
+{
+    out.clear();
+    std::vector<int64_t> ids;
+    for (const auto& kv : m->kfs)
+        if (kv.second->has_image) ids.push_back(kv.first);
+    std::sort(ids.begin(), ids.end());
+    for (int64_t id : ids) {
+        const Keyframe& k = *m->kfs.at(id);
+        gl_keyframe kf{};
+        kf.id = id;
+        kf.pose = k.pose;
+        kf.K = k.K;
+        kf.image = nullptr;
+        out.push_back(kf);
+    }
+}
+
+}  // namespace gl

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gl_common.cuh"
 #include "../../include/gl_map.h"
@@ -167,6 +168,10 @@ struct View {
     int nb = 1, pd = 1;
     bool persistent = false;
     DevBuf work;              // int[2] unit counters (forward, backward)
+    // deterministic backward: per (instance, pixel block) sums, reduced per
+    // (view, Gaussian) in a fixed order (floats: instances x blocks x 10)
+    bool det = false;
+    DevBuf gpart;
     const ViewDesc* d_desc() const
     {
         return reinterpret_cast<const ViewDesc*>(desc.as<const char>() + sizeof(StepScalars));
@@ -270,6 +275,23 @@ gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* o
 
 // Sorted instances as (tile << 32 | depth bits) keys and owning Gaussians.
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+
+// Validated camera of a pose and intrinsics (finite pose, positive focal
+// lengths, image size 1..16384); GL_ERR_INVALID otherwise.
+gl_status camera_from(const gl_pose* pose, const gl_intrinsics* K, Cam& cam);
+
+// Hooks into a map for the serving loop (the map's own code is in gl_capi.cu).
+cudaStream_t map_stream(const gl_map* m);
+int map_sh_degree(const gl_map* m);
+int map_tile_size(const gl_map* m);
+int64_t map_size_now(const gl_map* m);
+int64_t map_capacity(const gl_map* m);
+// Copy the live Gaussians into dst[0..5) (means, log-scales, quats, logits,
+// SH; grown as needed) on the map's stream, then record `done` there.
+gl_status map_snapshot(gl_map* m, DevBuf* dst, int64_t* n_out, cudaEvent_t done);
+GParams snapshot_params(const gl_map* m, const DevBuf* src, int64_t n);
+// Registered keyframes that hold an image, by ascending id (image = null).
+void map_keyframes(const gl_map* m, std::vector<gl_keyframe>& out);
 
 // Map-side kernels.
 gl_status sky_create(float* means, float* log_scales, float* quats, float* logits, float* sh,

@@ -55,10 +55,16 @@ struct RasterGrad {
     const float* Tfin;
     const uint32_t* ncon;
     const float *dL_drgb, *dL_ddepth, *dL_dopac;
-    float* g2d;
+    float* g2d;                  // atomic accumulation per (view, Gaussian)
+    // deterministic mode: per (instance, pixel block) sums, indexed by the
+    // instance's emission index (sinst of its sorted position)
+    float* part;
+    const uint32_t* sinst;
+    int nblk;                    // pixel blocks per tile
 };
 
 struct Unit {
+    int wb;                // pixel block within the tile
     int x0, y0;            // absolute pixel origin of the pixel block in its view
     int W, H;              // the view's image size
     long long pix_base;    // the view's first pixel in the concatenated images
@@ -71,6 +77,7 @@ __device__ __forceinline__ void unit_of(int u, const RasterArgs& A, Unit& U)
     const int TS = A.TS;
     const int wb_per_tile = TS * TS / (32 * D), bpr = TS / 8;
     const int tile = (int)A.order[u / wb_per_tile], wb = u % wb_per_tile;
+    U.wb = wb;
     const int v = view_of_tile(A.views, A.V, tile);
     const ViewDesc& d = A.views[v];
     const int lt = tile - d.tile_base;
@@ -244,7 +251,7 @@ __device__ __forceinline__ float warp_transpose_reduce16(float (&v)[16])
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-template <bool EXTRA, int NB, int D>
+template <bool EXTRA, int NB, int D, bool DET>
 __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const RasterGrad& G, float4* sr0,
                                          float4* sr1, float4* sr2, uint32_t* spos, uint32_t* sg, int lane)
 {
@@ -288,7 +295,10 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
     for (int b = 0; b < NB; b++) {
         const int64_t i = bstart + b * 32 + lane;
         ng[b] = 0;
-        if (i >= (int64_t)U.rs) { n0[b] = A.s0[i]; n1[b] = A.s1[i]; n2[b] = A.s2[i]; n3[b] = A.s3[i]; ng[b] = A.sgid[i]; }
+        if (i >= (int64_t)U.rs) {
+            n0[b] = A.s0[i]; n1[b] = A.s1[i]; n2[b] = A.s2[i]; n3[b] = A.s3[i];
+            ng[b] = DET ? G.sinst[i] : A.sgid[i];
+        }
     }
     for (; bstart + BS > (int64_t)U.rs; bstart -= BS) {
         int nh = 0;
@@ -298,7 +308,10 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
             const uint32_t cg = ng[b];
             const int64_t i = bstart + b * 32 + lane;
             const int64_t ni = i - BS;
-            if (ni >= (int64_t)U.rs) { n0[b] = A.s0[ni]; n1[b] = A.s1[ni]; n2[b] = A.s2[ni]; n3[b] = A.s3[ni]; ng[b] = A.sgid[ni]; }
+            if (ni >= (int64_t)U.rs) {
+                n0[b] = A.s0[ni]; n1[b] = A.s1[ni]; n2[b] = A.s2[ni]; n3[b] = A.s3[ni];
+                ng[b] = DET ? G.sinst[ni] : A.sgid[ni];
+            }
             const bool hit = i >= (int64_t)U.rs && box_hit(c3, bx0, bx1, by0, by1);
             const unsigned mask = __ballot_sync(kFull, hit);
             if (hit) {
@@ -347,15 +360,17 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
             if (__any_sync(kFull, any)) {
                 const float r = warp_transpose_reduce16(v);
                 const int q = lane >> 1;
-                if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1))
-                    atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, r);
+                if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1)) {
+                    if (DET) G.part[((size_t)sg[k] * G.nblk + U.wb) * kNG + q] = r;
+                    else atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, r);
+                }
             }
         }
         __syncwarp();
     }
 }
 
-template <bool EXTRA, int NB, int D>
+template <bool EXTRA, int NB, int D, bool DET>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k_raster_bwd(RasterArgs A, RasterGrad G)
 {
@@ -364,9 +379,35 @@ k_raster_bwd(RasterArgs A, RasterGrad G)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
     while (u < A.nunits) {
-        bwd_unit<EXTRA, NB, D>(u, A, G, sr0[w], sr1[w], sr2[w], spos[w], sg[w], lane);
+        bwd_unit<EXTRA, NB, D, DET>(u, A, G, sr0[w], sr1[w], sr2[w], spos[w], sg[w], lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
+    }
+}
+
+// Deterministic gradient sums: for each (view, Gaussian) pair, its instances
+// (emission indices dup_off .. dup_off + touched) and each instance's pixel
+// blocks in ascending order.
+__global__ void k_part_reduce(const float* __restrict__ part, const uint32_t* __restrict__ touched,
+                              const uint32_t* __restrict__ dup_off, int nblk, int64_t pairs,
+                              const uint64_t* __restrict__ ctl, uint64_t cap, float* __restrict__ g2d)
+{
+    const bool overflow = ctl[1] != 0;   // the step's instances did not fit: nothing was written
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pairs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        float acc[kNG];
+#pragma unroll
+        for (int q = 0; q < kNG; q++) acc[q] = 0.0f;
+        const uint32_t cnt = touched[t];
+        if (cnt && !overflow && (uint64_t)dup_off[t] + cnt <= cap) {
+            const float* p = part + (size_t)dup_off[t] * nblk * kNG;
+            for (uint32_t e = 0; e < cnt * (uint32_t)nblk; e++, p += kNG) {
+#pragma unroll
+                for (int q = 0; q < kNG; q++) acc[q] += p[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kNG; q++) g2d[(size_t)t * kNG + q] = acc[q];
     }
 }
 
@@ -434,28 +475,34 @@ gl_status check_exec(const View& v)
 template <int NB, int D>
 void fwd_launch(const RasterArgs& A, const RasterOut& O, bool persistent, cudaStream_t s)
 {
-    const int grid = grid_for(k_raster_fwd<NB, D>, NB * 8 + D, A.nunits, persistent);
+    const int grid = grid_for(k_raster_fwd<NB, D>, (NB - 1) * 4 + D, A.nunits, persistent);
     k_raster_fwd<NB, D><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, O);
 }
 
-template <bool EXTRA, int NB, int D>
+template <bool EXTRA, int NB, int D, bool DET>
 void bwd_launch(const RasterArgs& A, const RasterGrad& G, bool persistent, cudaStream_t s)
 {
-    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D>, 32 + (EXTRA ? 16 : 0) + NB * 8 + D, A.nunits, persistent);
-    k_raster_bwd<EXTRA, NB, D><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
+    const int variant = 32 + (DET ? 16 : 0) + (EXTRA ? 8 : 0) + (NB - 1) * 4 + D;   // < 64
+    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D, DET>, variant, A.nunits, persistent);
+    k_raster_bwd<EXTRA, NB, D, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
 }
 
 template <bool EXTRA>
-void bwd_dispatch(int nb, int pd, const RasterArgs& A, const RasterGrad& G, bool persistent, cudaStream_t s)
+void bwd_dispatch(int nb, int pd, bool det, const RasterArgs& A, const RasterGrad& G, bool persistent,
+                  cudaStream_t s)
 {
-    if (nb == 1) {
-        if (pd == 1) bwd_launch<EXTRA, 1, 1>(A, G, persistent, s);
-        else if (pd == 2) bwd_launch<EXTRA, 1, 2>(A, G, persistent, s);
-        else bwd_launch<EXTRA, 1, 4>(A, G, persistent, s);
+    if (det) {   // batch depth 32 only
+        if (pd == 1) bwd_launch<EXTRA, 1, 1, true>(A, G, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 1, 2, true>(A, G, persistent, s);
+        else bwd_launch<EXTRA, 1, 4, true>(A, G, persistent, s);
+    } else if (nb == 1) {
+        if (pd == 1) bwd_launch<EXTRA, 1, 1, false>(A, G, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 1, 2, false>(A, G, persistent, s);
+        else bwd_launch<EXTRA, 1, 4, false>(A, G, persistent, s);
     } else {
-        if (pd == 1) bwd_launch<EXTRA, 2, 1>(A, G, persistent, s);
-        else if (pd == 2) bwd_launch<EXTRA, 2, 2>(A, G, persistent, s);
-        else bwd_launch<EXTRA, 2, 4>(A, G, persistent, s);
+        if (pd == 1) bwd_launch<EXTRA, 2, 1, false>(A, G, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 2, 2, false>(A, G, persistent, s);
+        else bwd_launch<EXTRA, 2, 4, false>(A, G, persistent, s);
     }
 }
 
@@ -518,7 +565,9 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     GL_TRY(check_exec(v));
     GL_TRY(v.work.reserve(16));
     PhaseScope ps(v.prof, PH_RASTER_BWD, s);
-    GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * pairs, s));
+    const bool det = v.det && v.ntiles > 0 && v.I != 0;
+    const int nblk = v.Ts * v.Ts / (32 * v.pd);
+    if (!det) GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * pairs, s));
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     int* work = nullptr;
     if (v.persistent) {
@@ -526,10 +575,28 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
         GL_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int), s));
     }
     const RasterArgs A = make_args(v, work);
-    RasterGrad G{v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>()};
-    if (dL_ddepth != nullptr || dL_dopac != nullptr) bwd_dispatch<true>(v.nb, v.pd, A, G, v.persistent, s);
-    else bwd_dispatch<false>(v.nb, v.pd, A, G, v.persistent, s);
+    RasterGrad G{v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>(),
+                 nullptr, v.sorted_inst, nblk};
+    const size_t cap = v.itile.bytes / 4;
+    if (det) {
+        // every instance's block sums, zero where a block has no hit; the
+        // instance count is bounded by the capacity when it is known on the
+        // device only
+        const size_t inst = v.I > 0 ? (size_t)v.I : cap;
+        GL_TRY(v.gpart.reserve(sizeof(float) * kNG * (size_t)nblk * std::max<size_t>(cap, 1)));
+        GL_CUDA_TRY(cudaMemsetAsync(v.gpart.p, 0, sizeof(float) * kNG * (size_t)nblk * inst, s));
+        G.part = v.gpart.as<float>();
+    }
+    if (dL_ddepth != nullptr || dL_dopac != nullptr) bwd_dispatch<true>(v.nb, v.pd, det, A, G, v.persistent, s);
+    else bwd_dispatch<false>(v.nb, v.pd, det, A, G, v.persistent, s);
     count_launches(1);
+    if (det) {
+        const int blocks = (int)std::min<size_t>(8 * 152, (pairs + 255) / 256);
+        k_part_reduce<<<std::max(blocks, 1), 256, 0, s>>>(v.gpart.as<float>(), v.touched.as<uint32_t>(),
+                                                          v.dup_off.as<uint32_t>(), nblk, (int64_t)pairs,
+                                                          v.count.as<uint64_t>(), (uint64_t)cap, v.g2d.as<float>());
+        count_launches(1);
+    }
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }

@@ -57,6 +57,10 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     assert L.gl_map_set_exec(None, ctypes.byref(e)) == 1
     assert L.gl_map_autotune(None, None, 1, 1, 0, None, None) == 1
     assert L.gl_map_load(None, None, 0) == 1
+    sc = binding.ServerConfig()
+    assert L.gl_server_config_default(ctypes.byref(sc)) == 0 and sc.queue_capacity == 256 and sc.render_batch == 8
+    assert L.gl_server_create(None, None, None) == 1
+    assert L.gl_server_submit(None, None, None) == 1
     assert L.gl_map_save(None, 0, None, 0) == 1
 
 
@@ -68,8 +72,9 @@ def test_struct_layouts_match_c(libpath, tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gl_intrinsics), sizeof(gl_pose), sizeof(gl_keyframe),
-         sizeof(gl_config), sizeof(gl_gaussians), sizeof(gl_stats), sizeof(gl_exec_config));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gl_intrinsics), sizeof(gl_pose),
+         sizeof(gl_keyframe), sizeof(gl_config), sizeof(gl_gaussians), sizeof(gl_stats), sizeof(gl_exec_config),
+         sizeof(gl_server_config), sizeof(gl_request), sizeof(gl_result), sizeof(gl_server_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(gl_keyframe, image), offsetof(gl_config, n_sky),
          offsetof(gl_config, capacity_hint), offsetof(gl_gaussians, sh));
   return 0;
@@ -81,7 +86,7 @@ int main(void) {{
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(t) for t in (B.Intrinsics, B.Pose, B.Keyframe, B.Config, B.Gaussians, B.Stats,
-                                                 B.ExecConfig)]
+                                                 B.ExecConfig, B.ServerConfig, B.Request, B.Result, B.ServerStats)]
     assert offs == [B.Keyframe.image.offset, B.Config.n_sky.offset, B.Config.capacity_hint.offset,
                     B.Gaussians.sh.offset]
 

@@ -101,6 +101,40 @@ def test_window_step_parity_under_exec(tile, ex):
         assert np.allclose(m.exposure(10 + i), st["p"]["E"][i], atol=1e-6)
 
 
+@pytest.mark.parametrize("tile,ppl,persistent", [(16, 1, 0), (16, 2, 1), (8, 1, 1)])
+def test_deterministic_steps_are_bit_identical(tile, ppl, persistent):
+    """With the deterministic backward, eager and graph-replayed maps taking
+    the same steps end bit-identical, and the first step equals the oracle."""
+    params, cams, targets = _window_scene()
+    maps = [_map(params), _map(params)]
+    for m, graphs in zip(maps, (0, 1)):
+        m.set_exec(deterministic=1, use_graphs=graphs, tile_size=tile, pixels_per_lane=ppl, persistent=persistent)
+    views = [(10 + i, cams[i], targets[i]) for i in range(3)]
+    losses = [[m.optimize_step(views, want_loss=True) for _ in range(4)] for m in maps]
+    assert losses[0] == losses[1]
+    pa, pb = maps[0].get_params(), maps[1].get_params()
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+    for i in range(3):
+        assert np.array_equal(maps[0].exposure(10 + i), maps[1].exposure(10 + i))
+    assert maps[1].stats()["graph_replays"] == 3
+    # one deterministic step against the oracle
+    m = _map(params)
+    m.set_exec(deterministic=1, tile_size=tile, pixels_per_lane=ppl, persistent=persistent)
+    m.optimize_step(views)
+    st = oracle.new_window_state(params, 3)
+    r = oracle.optimize_window(params, st, cams, targets, step=1, Ts=tile)
+    got = m.get_params()
+    vis = r["visible"]
+    for name in ("means", "log_scales", "quats", "logits"):
+        d_gpu = got[name].astype(np.float64) - params[name]
+        d_or = st["p"][name] - params[name]
+        gref = r["grads"][name][vis]
+        clear = np.abs(gref) > 1e-3 * np.sqrt(np.mean(gref ** 2))
+        agree = np.abs(d_gpu[vis] - d_or[vis])[clear] <= 1e-3 * oracle.DEFAULT_LR[name] + 1e-7
+        assert agree.mean() > 0.99, (name, agree.mean())
+
+
 def test_graph_replay_equals_eager_over_steps():
     params, cams, targets = _window_scene()
     a, b = _map(params), _map(params)

@@ -1,0 +1,163 @@
+"""Serving loop: keyframe updates, optimisation requests and novel-view renders
+submitted together.  Every result equals the same request run alone on the
+map version it saw: renders and point counts exactly; mutations exactly with
+the deterministic backward, and otherwise within the spread that the order
+of the backward's float atomics leaves after Adam (renders of the two
+resulting maps agree to 1e-3 mean, 2e-2 at the 99th percentile).  Memory
+admission and the queue limit refuse work cleanly."""
+import numpy as np
+import pytest
+
+from paper_2404_06926_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, logits=0.05, sh=2.5e-3)
+
+
+def _street():
+    sc = scenes.Outdoor(seed=5, width=160, img_height=128, f=125.0)
+    frames = []
+    for i, s in enumerate(sc.traj_x[2:14:2]):
+        rng = np.random.default_rng(500 + i)
+        pts, col = sc.lidar_sweep(float(s), rng=rng)
+        vp, vc = sc.visual_points(float(s), 200, rng=rng)
+        cam = sc.camera_at(float(s))
+        img = sc.target_image(cam, rng=rng)[0]
+        frames.append((cam, img, np.concatenate([pts, vp]), np.concatenate([col, vc])))
+    novel = [sc.camera_at(float(s) + 0.5, width=w, height=h, f=0.78125 * w)
+             for s, (w, h) in zip(sc.traj_x[3:15:2], [(160, 128), (96, 64), (200, 150)] * 2)]
+    return frames, novel
+
+
+def _map(det=0):
+    from paper_2404_06926_gb300 import binding
+    m = binding.Map(binding.default_config(n_sky=2000, sh_degree=3, tile_size=16, capacity_hint=1 << 16))
+    m.set_exec(deterministic=det)
+    return m
+
+
+def _agree(a, b):
+    out = {}
+    for k, lr in LR.items():
+        d = np.abs(a[k].astype(np.float64) - b[k])
+        out[k] = float((d <= 1e-3 * lr + 1e-6).mean())
+    return out
+
+
+@pytest.mark.parametrize("det", [1, 0])
+def test_results_are_the_same_alone_and_in_the_mix(det):
+    from paper_2404_06926_gb300 import binding
+    frames, novel = _street()
+    m = _map(det)
+    srv = binding.Server(m, record_versions=True, render_batch=4)
+    reqs = []   # (kind, ticket, spec)
+    for i, (cam, img, pts, col) in enumerate(frames):
+        spec = dict(kid=i, cam=cam, image=img, xyz=pts, rgb=col, n_steps=4, window=1 + i % 2, seed=100 + i)
+        reqs.append(("update", srv.keyframe_update(**spec), spec))
+        for j in range(2):
+            c = novel[(2 * i + j) % len(novel)]
+            reqs.append(("render", srv.render(c), c))
+        if i % 3 == 2:
+            spec = dict(n_steps=5, window=2, seed=7 + i)
+            reqs.append(("optimize", srv.optimize(**spec), spec))
+    out = [(kind, srv.wait(t), spec) for kind, t, spec in reqs]
+    st = srv.stats()
+    n_mut = sum(1 for k, _, _ in reqs if k != "render")
+    assert st["version"] == n_mut and st["render"]["completed"] == sum(1 for k, _, _ in reqs if k == "render")
+    for kind, (res, _), _ in out:
+        assert res["status"] == 0, (kind, res)
+    # mutations commit in submission order; renders see non-decreasing versions
+    vers = [res["version"] for kind, (res, _), _ in out if kind != "render"]
+    assert vers == list(range(1, n_mut + 1))
+    rv = [res["version"] for kind, (res, _), _ in out if kind == "render"]
+    assert rv == sorted(rv) and 0 <= rv[0] and rv[-1] <= n_mut
+    ckpt = {v: srv.version(v) for v in range(n_mut + 1)}
+    srv.close()
+
+    # each render alone, on the version it read
+    alone = _map()
+    for kind, (res, img), cam in out:
+        if kind != "render":
+            continue
+        alone.load(ckpt[res["version"]])
+        ref = alone.render(cam)
+        assert np.array_equal(img, ref), res
+
+    # each mutation alone, from the version before it
+    for kind, (res, _), spec in out:
+        if kind == "render":
+            continue
+        v = res["version"]
+        a = _map(det)
+        a.load(ckpt[v - 1])
+        s2 = binding.Server(a)
+        t = s2.keyframe_update(**spec) if kind == "update" else s2.optimize(**spec)
+        r2, _ = s2.wait(t)
+        s2.close()
+        assert r2["status"] == 0 and r2["n_added"] == res["n_added"], (r2, res)
+        b = _map(det)
+        b.load(ckpt[v])
+        assert len(a) == len(b)
+        kid = spec["kid"] if kind == "update" else 0
+        if det:
+            assert r2["loss"] == res["loss"]
+            pa, pb = a.get_params(), b.get_params()
+            for k in pa:
+                assert np.array_equal(pa[k], pb[k]), (kind, v, k)
+            for w in (1, 2):
+                ma, mb = a.get_moments(w), b.get_moments(w)
+                for k in ma:
+                    assert np.array_equal(ma[k], mb[k]), (kind, v, w, k)
+            assert np.array_equal(a.exposure(kid), b.exposure(kid))
+        else:
+            assert abs(r2["loss"] - res["loss"]) <= 1e-3 * abs(res["loss"]) + 1e-6
+            cam = spec["cam"] if kind == "update" else frames[0][0]
+            d = np.abs(a.render(cam) - b.render(cam))
+            assert d.mean() <= 1e-3 and np.percentile(d, 99) <= 2e-2, (kind, v, d.mean(), np.percentile(d, 99))
+            assert np.allclose(a.exposure(kid), b.exposure(kid), atol=1e-3)
+
+
+def test_requests_that_cannot_fit_fail_cleanly():
+    from paper_2404_06926_gb300 import binding
+    frames, novel = _street()
+    m = _map()
+    n0 = len(m)
+    srv = binding.Server(m, reserve_bytes=1 << 52)   # more than any device has free
+    cam, img, pts, col = frames[0]
+    t1 = srv.keyframe_update(0, cam, img, pts, col, n_steps=2)
+    t2 = srv.render(novel[0])
+    r1, _ = srv.wait(t1)
+    r2, _ = srv.wait(t2)
+    assert r1["status"] == 2 and r2["status"] == 2   # GL_ERR_OOM
+    st = srv.stats()
+    assert st["keyframe_update"]["failed"] == 1 and st["render"]["failed"] == 1 and st["version"] == 0
+    srv.close()
+    assert len(m) == n0
+
+
+def test_queue_limit_and_bad_requests():
+    from paper_2404_06926_gb300 import binding
+    frames, novel = _street()
+    m = _map()
+    cam, img, pts, col = frames[0]
+    m.add_points(pts, col, cam, use_mask=False)
+    m.add_keyframe(0, cam, img)
+    srv = binding.Server(m, queue_capacity=2)
+    t1 = srv.optimize(300)
+    t2 = srv.render(novel[0])
+    with pytest.raises(binding.GLError) as e:
+        srv.render(novel[1])
+    assert e.value.status == 6   # GL_ERR_BUSY
+    srv.wait(t1)
+    srv.wait(t2)
+    with pytest.raises(binding.GLError):
+        srv.optimize(3, window=0)
+    bad = dict(novel[0], fx=-1.0)
+    with pytest.raises(binding.GLError):
+        srv.render(bad)
+    with pytest.raises(binding.GLError):
+        srv.wait(12345)   # unknown ticket
+    assert srv.stats()["busy_rejects"] == 1
+    srv.close()
