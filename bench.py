@@ -460,7 +460,8 @@ def run_serving(args, binding, torch):
         ev.append((t, "render"))
     ev.sort()
     n_start = len(m)
-    srv = binding.Server(m, render_batch=8)
+    cap = 750_000 if small else 3_000_000   # the stream's map target; extra points are capped and counted
+    srv = binding.Server(m, render_batch=8, max_gaussians=cap)
     tickets, rejects, kid, ri = [], 0, 100, 0
     t0 = time.perf_counter()
     for (ta, kind) in ev:
@@ -500,7 +501,8 @@ def run_serving(args, binding, torch):
            "wall_s": wall, "map_start": n_start, "map_end": st["map_size"], "versions": st["version"],
            "steps": st["steps"], "steps_per_s": st["steps_per_s"], "renders_per_s": st["renders_per_s"],
            "mean_render_batch": st["mean_render_batch"], "memory_waits": st["memory_waits"],
-           "busy_rejects": rejects, "failed": int(sum(1 for x in statuses if x != 0))}
+           "busy_rejects": rejects, "failed": int(sum(1 for x in statuses if x != 0)),
+           "map_cap": cap, "points_capped": st["points_capped"]}
     for k in ("keyframe_update", "render"):
         out[k] = {kk: st[k][kk] for kk in ("completed", "p50_ms", "p99_ms", "mean_ms")}
     m.close()

@@ -348,7 +348,8 @@ typedef struct {
     int64_t reserve_bytes;       /* device memory kept free (default 1 GiB)             */
     int32_t record_versions;     /* 1: keep a checkpoint (gl_map_save layout, with      */
                                  /*    images) of every committed version, for tests    */
-    int32_t reserved;
+    int32_t max_gaussians;       /* > 0: keyframe updates add at most this many minus   */
+                                 /*    the map size (a prefix of their points); 0: no cap */
 } gl_server_config;
 
 typedef struct {
@@ -387,6 +388,7 @@ typedef struct {
     int64_t busy_rejects;        /* submissions refused with GL_ERR_BUSY                */
     int64_t version;             /* latest committed version                            */
     int64_t map_size;
+    int64_t points_capped;       /* points left out by max_gaussians                    */
 } gl_server_stats;
 
 /* gl_server_config_default fills the defaults above. */

@@ -479,7 +479,7 @@ REQ_NAMES = {1: "keyframe_update", 2: "optimize", 3: "render"}
 
 class ServerConfig(C.Structure):
     _fields_ = [("queue_capacity", C.c_int32), ("render_batch", C.c_int32), ("reserve_bytes", C.c_int64),
-                ("record_versions", C.c_int32), ("reserved", C.c_int32)]
+                ("record_versions", C.c_int32), ("max_gaussians", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -502,18 +502,20 @@ class ServerStats(C.Structure):
                 ("p50_ms", C.c_double * 4), ("p99_ms", C.c_double * 4), ("mean_ms", C.c_double * 4),
                 ("steps", C.c_int64), ("steps_per_s", C.c_double), ("renders_per_s", C.c_double),
                 ("mean_render_batch", C.c_double), ("memory_waits", C.c_int64), ("busy_rejects", C.c_int64),
-                ("version", C.c_int64), ("map_size", C.c_int64)]
+                ("version", C.c_int64), ("map_size", C.c_int64), ("points_capped", C.c_int64)]
 
 
 class Server:
     """Request loop over a Map (see gl_server_create).  Host inputs are copied
     at submission; a render's output array must stay alive until wait()."""
 
-    def __init__(self, m: Map, queue_capacity=256, render_batch=8, reserve_bytes=1 << 30, record_versions=False):
+    def __init__(self, m: Map, queue_capacity=256, render_batch=8, reserve_bytes=1 << 30, record_versions=False,
+                 max_gaussians=0):
         cfg = ServerConfig()
         check(lib().gl_server_config_default(C.byref(cfg)))
         cfg.queue_capacity, cfg.render_batch = int(queue_capacity), int(render_batch)
         cfg.reserve_bytes, cfg.record_versions = int(reserve_bytes), int(bool(record_versions))
+        cfg.max_gaussians = int(max_gaussians)
         self.map = m
         self._h = C.c_void_p()
         self._keep = {}   # ticket -> output arrays kept alive
@@ -571,7 +573,8 @@ class Server:
         check(lib().gl_server_get_stats(self._h, C.byref(st)))
         out = {"steps": st.steps, "steps_per_s": st.steps_per_s, "renders_per_s": st.renders_per_s,
                "mean_render_batch": st.mean_render_batch, "memory_waits": st.memory_waits,
-               "busy_rejects": st.busy_rejects, "version": st.version, "map_size": st.map_size}
+               "busy_rejects": st.busy_rejects, "version": st.version, "map_size": st.map_size,
+               "points_capped": st.points_capped}
         for k, name in REQ_NAMES.items():
             out[name] = {"submitted": st.submitted[k], "completed": st.completed[k], "failed": st.failed[k],
                          "p50_ms": st.p50_ms[k], "p99_ms": st.p99_ms[k], "mean_ms": st.mean_ms[k]}

@@ -102,7 +102,7 @@ struct gl_server {
     // statistics
     std::vector<double> lat[kKinds];
     int64_t submitted[kKinds] = {}, completed[kKinds] = {}, failed[kKinds] = {};
-    int64_t steps = 0, renders = 0, render_batches = 0, memory_waits = 0, busy_rejects = 0;
+    int64_t steps = 0, renders = 0, render_batches = 0, memory_waits = 0, busy_rejects = 0, points_capped = 0;
     double first_submit = -1.0, last_done = 0.0;
     // render side
     cudaStream_t rstream = nullptr;
@@ -236,10 +236,19 @@ gl_status run_mutation(gl_server* s, Req* q, gl_result& res)
     if (r.kind == GL_REQ_KEYFRAME_UPDATE) {
         const gl_keyframe& kf = r.keyframe;
         int64_t added = 0;
-        if (r.n_points > 0) {
+        int64_t np = r.n_points;
+        if (s->cfg.max_gaussians > 0) {
+            const int64_t room = std::max<int64_t>(0, (int64_t)s->cfg.max_gaussians - map_size_now(s->map));
+            if (np > room) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->points_capped += np - room;
+                np = room;
+            }
+        }
+        if (np > 0) {
             const int use_mask = map_size_now(s->map) > 0 ? 1 : 0;
-            GL_TRY(gl_map_add_points(s->map, q->xyz.data(), q->rgb.data(), r.n_points, r.point_kind, &kf.pose,
-                                     &kf.K, use_mask, &added));
+            GL_TRY(gl_map_add_points(s->map, q->xyz.data(), q->rgb.data(), np, r.point_kind, &kf.pose, &kf.K,
+                                     use_mask, &added));
         }
         res.n_added = added;
         gl_keyframe k = kf;
@@ -422,7 +431,8 @@ extern "C" gl_status gl_server_create(gl_map* map, const gl_server_config* cfg, 
     gl_server_config c;
     if (cfg) c = *cfg;
     else gl_server_config_default(&c);
-    if (c.queue_capacity < 1 || c.render_batch < 1 || c.render_batch > kMaxViews || c.reserve_bytes < 0) {
+    if (c.queue_capacity < 1 || c.render_batch < 1 || c.render_batch > kMaxViews || c.reserve_bytes < 0 ||
+        c.max_gaussians < 0) {
         set_error("invalid server config");
         return GL_ERR_INVALID;
     }
@@ -554,6 +564,7 @@ extern "C" gl_status gl_server_get_stats(gl_server* s, gl_server_stats* out)
     out->busy_rejects = s->busy_rejects;
     out->version = s->version;
     out->map_size = map_size_now(s->map);
+    out->points_capped = s->points_capped;
     return GL_OK;
 }
 

@@ -161,3 +161,17 @@ def test_queue_limit_and_bad_requests():
         srv.wait(12345)   # unknown ticket
     assert srv.stats()["busy_rejects"] == 1
     srv.close()
+
+
+def test_map_size_cap():
+    from paper_2404_06926_gb300 import binding
+    frames, _ = _street()
+    m = _map()
+    cap = len(m) + 500
+    srv = binding.Server(m, max_gaussians=cap)
+    for i, (cam, img, pts, col) in enumerate(frames[:3]):
+        r, _ = srv.wait(srv.keyframe_update(i, cam, img, pts, col, n_steps=1))
+        assert r["status"] == 0
+    st = srv.stats()
+    assert st["map_size"] <= cap and st["points_capped"] > 0
+    srv.close()
