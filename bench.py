@@ -480,7 +480,7 @@ def run_serving(args, binding, torch):
                 ri += 1
                 prev = out_owner[wh][slot]
                 if prev is not None:
-                    srv.wait(prev)
+                    srv.wait(prev, 300)
                     tickets.remove(prev)
                 s = float(rng.uniform(sc.traj_x[2], sc.traj_x[-12])) + 0.5
                 cam = sc.camera_at(s, width=wh[0], height=wh[1], f=0.78125 * wh[0])
@@ -491,7 +491,7 @@ def run_serving(args, binding, torch):
             if e.status != 6:
                 raise
             rejects += 1
-    statuses = [srv.wait(tk)[0]["status"] for tk in tickets]
+    statuses = [srv.wait(tk, 300)[0]["status"] for tk in tickets]
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()

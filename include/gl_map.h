@@ -210,9 +210,15 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *                    step's results are bit-identical from run to run (at
  *                    the cost of one more pass over 40 bytes per instance
  *                    and pixel block); batch_depth is then 32.
+ *   segment          0, or a power of two in 64..65536: a tile whose list
+ *                    holds at least 2 x segment Gaussians is rendered and
+ *                    back-propagated as segments of `segment` consecutive
+ *                    Gaussians by separate warps; the transmittance is then
+ *                    a product of per-segment products, equal to the
+ *                    single running product up to float rounding.
  * Apart from deterministic = 1, results differ between runs only by the
  * order of the backward's float atomics.
- * gl_map_create starts with {0, 0, 32, 1, 0, 0}.  Errors: GL_ERR_INVALID. */
+ * gl_map_create starts with {0, 0, 32, 1, 0, 0, 0}.  Errors: GL_ERR_INVALID. */
 typedef struct {
     int32_t use_graphs;
     int32_t persistent;
@@ -220,14 +226,16 @@ typedef struct {
     int32_t pixels_per_lane;
     int32_t tile_size;
     int32_t deterministic;
+    int32_t segment;
+    int32_t reserved;
 } gl_exec_config;
 
 GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
 GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
 
 /* Autotuner for one window shape: for each candidate execution (tile size
- * 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4 x persistent or not,
- * graphs on) time `reps` optimisation steps of `views` (as gl_optimize_step)
+ * 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4 x persistent or not x
+ * segment 0/1024, graphs on, deterministic as set) time `reps` optimisation steps of `views` (as gl_optimize_step)
  * with CUDA events, putting the Gaussians, their Adam moments, the views'
  * exposures and the step counters back after each trial.  With
  * keep_tile_size != 0 only gl_config's tile size is tried.  The fastest
@@ -421,6 +429,13 @@ typedef struct gl_ctx gl_ctx;
 
 GL_API gl_status gl_ctx_create(void* cuda_stream, gl_ctx** out);
 GL_API gl_status gl_ctx_destroy(gl_ctx* ctx);
+
+/* Raster execution of this context's calls: batch_depth, pixels_per_lane,
+ * persistent, deterministic and segment as in gl_exec_config (use_graphs
+ * and tile_size are ignored: the tile size is each call's argument).  A
+ * pixels_per_lane above tile_size / 4 is lowered to it.  Errors:
+ * GL_ERR_INVALID. */
+GL_API gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* exec);
 
 /* Forward (Eq. 1-7) of the Gaussians `g` (device arrays) seen from
  * (pose, K) with square tiles of side tile_size (8, 16 or 32).  Writes the

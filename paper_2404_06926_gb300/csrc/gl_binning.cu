@@ -391,6 +391,40 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
     }
 }
 
+// Work items of the raster kernels, in tile launch order: one per tile, or,
+// for a tile whose list holds at least 2 seg records, one per segment of
+// seg records (seg a power of two, so such tiles sit in the log2 buckets
+// ahead of all others and their items come first).  item = (tile,
+// segment); count[6] = items, count[7] = items of split tiles.
+__global__ void __launch_bounds__(1024) k_seg_items(const uint32_t* __restrict__ order,
+                                                    const uint32_t* __restrict__ ranges, int ntiles, int seg,
+                                                    uint2* __restrict__ items, uint64_t* __restrict__ count)
+{
+    __shared__ uint32_t sm[1024 / 32 + 1];
+    __shared__ uint32_t seg_end;
+    if (threadIdx.x == 0) seg_end = 0;
+    uint32_t carry = 0;
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int k = base + threadIdx.x;
+        uint32_t t = 0, nseg = 0;
+        if (k < ntiles) {
+            t = order[k];
+            const uint32_t L = ranges[2 * t + 1] - ranges[2 * t];
+            nseg = (seg > 0 && L >= 2u * (uint32_t)seg) ? (L + seg - 1) / seg : 1u;
+        }
+        uint32_t tot;
+        const uint32_t off = carry + block_exclusive_scan<uint32_t, 1024>(nseg, sm, &tot);
+        for (uint32_t j = 0; j < nseg; j++) items[off + j] = make_uint2(t, j);
+        if (nseg > 1) atomicMax(&seg_end, off + nseg);
+        carry += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        count[6] = carry;
+        count[7] = seg_end;
+    }
+}
+
 __global__ void k_ranges(const uint32_t* __restrict__ stile, const uint64_t* n_dev,
                          uint32_t* __restrict__ ranges)
 {
@@ -459,6 +493,22 @@ int ceil_log2(int64_t x)
 }
 
 }  // namespace
+
+int64_t work_items_bound(const View& v)
+{
+    const int64_t cap = (int64_t)(v.itile.bytes / 4);
+    return (int64_t)v.ntiles + (v.seg > 0 ? cap / v.seg + 1 : 0);
+}
+
+gl_status build_items(View& v, cudaStream_t s)
+{
+    GL_TRY(v.items.reserve(sizeof(uint2) * (size_t)std::max<int64_t>(work_items_bound(v), 1)));
+    k_seg_items<<<1, 1024, 0, s>>>(v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.ntiles, v.seg,
+                                   v.items.as<uint2>(), v.count.as<uint64_t>());
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
 
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
@@ -609,7 +659,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
         count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
-        return GL_OK;
+        return build_items(v, s);
     }
     dim3 grid((unsigned)((n + kPreThreads - 1) / kPreThreads));
     {
@@ -687,7 +737,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
         count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());
-        return GL_OK;
+        return build_items(v, s);
     }
     // stable sort of the instances by tile id
     const int tbits = std::max(1, ceil_log2(v.ntiles));
@@ -705,6 +755,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
         count_launches(2);
         GL_CUDA_TRY(cudaGetLastError());
+        GL_TRY(build_items(v, s));
         // the sorted records always get the full capacity, so that graph
         // steps (which size nothing) find room for any count that fits
         GL_TRY(permute_records(v, (int64_t)(v.itile.bytes / 4), s));

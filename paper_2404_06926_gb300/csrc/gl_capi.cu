@@ -187,7 +187,7 @@ gl_status View::upload_descs(cudaStream_t s)
 void View::release()
 {
     DevBuf* all[] = {&rec0, &rec1, &rec2, &rec3, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
-                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d, &gpart, &work,
+                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d, &gpart, &work, &items, &segstate,
                      &hist, &ranges, &tile_order, &Tfin, &ncon, &rgb, &depth, &opac};
     for (DevBuf* b : all) b->release();
     desc.release();
@@ -336,6 +336,19 @@ extern "C" gl_status gl_ctx_create(void* stream, gl_ctx** out)
     return GL_OK;
 }
 
+extern "C" gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* e)
+{
+    if (!ctx || !e) { set_error("null argument"); return GL_ERR_INVALID; }
+    if ((e->batch_depth != 32 && e->batch_depth != 64) || (e->deterministic != 0 && e->deterministic != 1) ||
+        (e->pixels_per_lane != 1 && e->pixels_per_lane != 2 && e->pixels_per_lane != 4) ||
+        (e->segment != 0 && (e->segment < 64 || e->segment > 65536 || (e->segment & (e->segment - 1)) != 0))) {
+        set_error("invalid execution config");
+        return GL_ERR_INVALID;
+    }
+    ctx->impl.exec = *e;
+    return GL_OK;
+}
+
 extern "C" gl_status gl_ctx_destroy(gl_ctx* ctx)
 {
     if (!ctx) return GL_OK;
@@ -358,6 +371,11 @@ extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, co
     GL_TRY(make_cam(pose, K, cam));
     gl_ctx_impl& c = ctx->impl;
     c.has_forward = 0;
+    c.view.det = c.exec.deterministic != 0;
+    c.view.nb = (c.exec.batch_depth == 64 && !c.view.det) ? 2 : 1;
+    c.view.pd = std::min(c.exec.pixels_per_lane, tile_size / 4);
+    c.view.persistent = c.exec.persistent != 0;
+    c.view.seg = c.exec.segment;
     GL_TRY(bin_view(c.view, params_of(g), cam, tile_size, c.stream));
     GL_TRY(raster_forward(c.view, out_rgb, out_depth, out_opacity, c.stream));
     c.has_forward = 1;
@@ -481,7 +499,7 @@ struct gl_map {
     std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
     Prof prof;
     // step execution and the captured step graph
-    gl_exec_config exec{0, 0, 32, 1, 0, 0};
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 0};
     cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
     struct StepGraph {
         std::vector<int64_t> key;        // the step shape it was captured for
@@ -596,9 +614,7 @@ gl_status render_internal(gl_map* m, const Cam& cam, int Ts)
     GL_TRY(v.rgb.reserve(12 * P));
     GL_TRY(v.depth.reserve(4 * P));
     GL_TRY(v.opac.reserve(4 * P));
-    v.nb = m->exec.batch_depth == 64 ? 2 : 1;
-    v.pd = std::min(m->exec.pixels_per_lane, Ts / 4);
-    v.persistent = m->exec.persistent != 0;
+    map_exec_knobs(m, v, Ts);
     GL_TRY(bin_view(v, m->params(), cam, Ts, m->stream));
     return raster_forward(v, v.rgb.as<float>(), v.depth.as<float>(), v.opac.as<float>(), m->stream);
 }
@@ -867,6 +883,7 @@ void apply_exec(gl_map* m)
     v.nb = (m->exec.batch_depth == 64 && !v.det) ? 2 : 1;
     v.pd = m->exec.pixels_per_lane;
     v.persistent = m->exec.persistent != 0;
+    v.seg = m->exec.segment;
 }
 
 // Enqueue the whole step on `s`.  sync_free: the descriptors were uploaded by
@@ -931,7 +948,8 @@ gl_status read_loss(gl_map* m, int V, bool copy, float* out_loss)
 std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
 {
     std::vector<int64_t> k = {sp.V, step_tile(m), m->exec.batch_depth, m->exec.pixels_per_lane,
-                              m->exec.persistent, m->exec.deterministic, m->n, m->deg, m->cfg.sparse_adam};
+                              m->exec.persistent, m->exec.deterministic, m->exec.segment, m->n, m->deg,
+                              m->cfg.sparse_adam};
     for (int i = 0; i < sp.V; i++) {
         k.push_back(sp.cams[i].W);
         k.push_back(sp.cams[i].H);
@@ -941,6 +959,7 @@ std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
                             &v.gidx, &v.dkey2, &v.gidx2, &v.dup_off, &v.g2d, &v.bsum, &v.count, &v.itile,
                             &v.ival, &v.itile2, &v.ival2, &v.iowner, &v.srec0, &v.srec1, &v.srec2, &v.srec3,
                             &v.sgid, &v.hist, &v.ranges, &v.tile_order, &v.Tfin, &v.ncon, &v.rgb, &v.work, &v.gpart,
+                            &v.items, &v.segstate,
                             &v.desc, &m->dLdC, &m->ctx.loss_part, &m->loss_dev};
     for (const DevBuf* b : bufs) {
         k.push_back((int64_t)(uintptr_t)b->p);
@@ -1179,6 +1198,10 @@ gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
     }
     if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
     if (e.deterministic != 0 && e.deterministic != 1) { set_error("deterministic must be 0 or 1"); return GL_ERR_INVALID; }
+    if (e.segment != 0 && (e.segment < 64 || e.segment > 65536 || (e.segment & (e.segment - 1)) != 0)) {
+        set_error("segment must be 0 or a power of two in 64..65536");
+        return GL_ERR_INVALID;
+    }
     if ((e.pixels_per_lane != 1 && e.pixels_per_lane != 2 && e.pixels_per_lane != 4) || 4 * e.pixels_per_lane > ts) {
         set_error("pixels_per_lane must be 1, 2 or 4 with 4 x pixels_per_lane <= tile size");
         return GL_ERR_INVALID;
@@ -1284,9 +1307,10 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
         if (keep_tile_size && ts != m->cfg.tile_size) continue;
         for (int bd = 32; bd <= (saved.deterministic ? 32 : 64) && st == GL_OK; bd *= 2)
             for (int ppl = 1; ppl <= 4 && st == GL_OK; ppl *= 2)
-                for (int pers = 0; pers <= 1 && st == GL_OK; pers++) {
+                for (int pers = 0; pers <= 1 && st == GL_OK; pers++)
+                for (int sg = 0; sg <= 1024 && st == GL_OK; sg += 1024) {
                     if (4 * ppl > ts) continue;
-                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic};
+                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic, sg, 0};
                     m->exec = cand;
                     // one eager step (sizes buffers, captures the graph), one replay, then reps timed replays
                     for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, sp, nullptr);
@@ -1531,6 +1555,14 @@ namespace gl {
 
 gl_status camera_from(const gl_pose* pose, const gl_intrinsics* K, Cam& cam) { return make_cam(pose, K, cam); }
 cudaStream_t map_stream(const gl_map* m) { return m->stream; }
+
+void map_exec_knobs(const gl_map* m, View& v, int Ts)
+{
+    v.nb = (m->exec.batch_depth == 64 && !m->exec.deterministic) ? 2 : 1;
+    v.pd = std::min(m->exec.pixels_per_lane, Ts / 4);
+    v.persistent = m->exec.persistent != 0;
+    v.seg = m->exec.segment;
+}
 int map_sh_degree(const gl_map* m) { return m->deg; }
 int map_tile_size(const gl_map* m) { return m->cfg.tile_size; }
 int64_t map_size_now(const gl_map* m) { return m->n; }

@@ -145,7 +145,8 @@ struct View {
     // scan
     DevBuf bsum;              // u64 per scan block
     DevBuf count;             // u64[8]: I (0 after an overflow), overflow flag, N (depth
-                              // sort), instances needed, view-count scratch [4..5]
+                              // sort), instances needed, view-count scratch [4..5],
+                              // work items [6], segment items [7]
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
@@ -172,6 +173,11 @@ struct View {
     // (view, Gaussian) in a fixed order (floats: instances x blocks x 10)
     bool det = false;
     DevBuf gpart;
+    // segmented raster: tiles whose list holds >= 2 seg records are split
+    // into segments of seg records (seg a power of two; 0: never split)
+    int seg = 0;
+    DevBuf items;             // uint2 per work item: (tile, segment), heaviest first
+    DevBuf segstate;          // 8 floats per (segment item, pixel of its tile), see gl_raster.cu
     const ViewDesc* d_desc() const
     {
         return reinterpret_cast<const ViewDesc*>(desc.as<const char>() + sizeof(StepScalars));
@@ -188,6 +194,7 @@ struct View {
 struct gl_ctx_impl {
     cudaStream_t stream = nullptr;
     View view;
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 0};
     DevBuf pose_part;   // per-block pose partials
     DevBuf loss_part;   // per-block loss partials
     int has_forward = 0;
@@ -215,6 +222,12 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
 // Forward raster of a binned view into (rgb, depth, opacity) device images
 // (depth/opacity may be null) plus T_final / n_contrib in `v`.
 gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s);
+
+// Upper bound of the work items of a binned step (every tile once, plus one
+// per seg records of the instance capacity).
+int64_t work_items_bound(const View& v);
+// Build the work items of a binned step (after the tile order).
+gl_status build_items(View& v, cudaStream_t s);
 
 // Records gathered into sorted-instance order (after binning).
 // nmax bounds the instance count (which is read on the device).
@@ -275,6 +288,11 @@ gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* o
 
 // Sorted instances as (tile << 32 | depth bits) keys and owning Gaussians.
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+
+// The map's raster execution knobs (batch depth, pixels per lane,
+// persistence, segment length; pixels per lane capped by the tile size Ts)
+// applied to another view's scratch.
+void map_exec_knobs(const gl_map* m, View& v, int Ts);
 
 // Validated camera of a pose and intrinsics (finite pose, positive focal
 // lengths, image size 1..16384); GL_ERR_INVALID otherwise.

@@ -1,31 +1,54 @@
 // gl_raster.cu -- front-to-back compositing (Eq. 4-7) and its adjoint.
 //
-// Work unit: one warp per (screen tile, block of 8 x 4D pixels).  Binning is
-// per tile (TS x TS); every pixel block of a tile is rendered by its own
-// warp, independently, so a heavy tile is spread over TS*TS/(32 D) warps
-// instead of being the critical path of one CTA.  Units are numbered
-// heaviest tile first.  Lane l owns the D pixels (x0 + l % 8, y0 + l / 8 + 4 j),
-// j < D: the records a warp stages and the warp reduction of the backward are
+// Work unit: one warp per (work item, block of 8 x 4D pixels).  A work item
+// is a screen tile (TS x TS) or, for a tile whose list holds at least 2 seg
+// records, one segment of seg consecutive records of that list.  Every
+// pixel block of a tile is rendered by its own warp, and a long list is
+// split along depth, so neither a heavy tile nor a deep one (the road's
+// vanishing point gathers tens of thousands of far Gaussians in a few
+// tiles) is the critical path of one warp.  Items are numbered heaviest
+// first.  Lane l owns the D pixels (x0 + l % 8, y0 + l / 8 + 4 j), j < D:
+// the records a warp stages and the warp reduction of the backward are
 // shared by D pixels per lane.
 //
-// Records are permuted into sorted-instance order after binning, so a tile's
-// Gaussians are contiguous.  A batch is 32 NB records (NB per lane, the next
-// batch prefetched into registers); the warp ballots which records' alpha
-// boxes touch its pixel block, compacts the hits in shared memory in depth
-// order and evaluates only those.  A Gaussian outside the block's box fails
-// the alpha test at every pixel of the block, so skipping it changes no result.
+// Records are permuted into sorted-instance order after binning, so a
+// tile's Gaussians are contiguous: a batch is 32 NB records (NB per lane, the
+// next batch prefetched into registers); the warp ballots which records'
+// alpha boxes touch its pixel block, compacts the hits in shared memory in
+// depth order and evaluates only those.  A Gaussian outside the block's box
+// fails the alpha test at every pixel of the block, so skipping it changes
+// no result.
 //
-// Scheduling: either one unit per warp of a grid that covers all units, or a
-// persistent grid (sized to the resident warps) whose warps take the next
-// unit from a counter until none is left.
+// Forward of a whole tile: per pixel, blend until the transmittance would
+// fall below 1e-4; keep the final transmittance and the position (in the
+// tile's list) of the last blended Gaussian, so the backward recomputes T by
+// division.
 //
-// Forward: per pixel, blend until the transmittance would fall below 1e-4;
-// keep the final transmittance and the position (in the tile's list) of the
-// last blended Gaussian, so the backward recomputes T by division.
-// Backward: the same units walked back to front; per hit, each lane sums its
-// D pixels' ten partial sums (colour 3, dL/dpower moments 6, depth 1), the
-// warp folds the 32 lanes with a transposed butterfly and ten lanes add the
-// totals to the Gaussian's accumulator.
+// Forward of a split tile, in two launches.  (1) Each segment item blends
+// its records per pixel from T = 1 without the stop rule and stores the
+// segment's transmittance product T_s, colour, depth and opacity sums and
+// last blended position.  (2) A combine pass walks each pixel's segments in
+// order with the incoming transmittance T_in (the product of the earlier
+// T_s): the stop rule fires inside segment s exactly when T_in * T_s falls
+// below 1e-4 (the running value inside s is T_in times the segment's own
+// running product, and that product only decreases), and that one segment
+// is replayed from T_in to find the stop and its truncated sums.  The pass
+// writes the pixel's outputs and, per segment, the backward's starting
+// state: the transmittance after the segment and the normalised colour
+// blended behind it (R = C_next + T_next * R_next over the later segments).
+// The transmittance is the product of the per-segment products, so it can
+// differ from a single running product by float rounding.
+//
+// Backward: every item walked back to front from its starting state (the
+// final transmittance and R = 0 for a whole tile); per hit, each lane sums
+// its D pixels' ten partial sums (colour 3, dL/dpower moments 6, depth 1),
+// the warp folds the 32 lanes with a transposed butterfly and ten lanes add
+// the totals to the Gaussian's accumulator (or, deterministic, store them
+// per instance and pixel block).
+//
+// Scheduling: either one unit per warp of a grid that covers the bound on
+// units, or a persistent grid (sized to the resident warps) whose warps take
+// the next unit from a counter; the number of units is read on the device.
 #include "gl_internal.h"
 
 namespace gl {
@@ -34,15 +57,27 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kNG = 10;   // screen-space gradient slots per Gaussian
+constexpr int kSegFields = 8;   // per (segment item, pixel): see below
 
-// Inputs shared by the forward and backward kernels (passed by value).
+// segstate fields.  After the segment pass: 0 T_s, 1-3 colour, 4 depth,
+// 5 opacity, 6 last position (as bits), 7 the incoming transmittance (set by
+// the combine pass).  After the combine pass: 0 transmittance after the
+// segment, 1-3 R (colour behind it, normalised), 4 R depth, 5 R opacity.
+__device__ __forceinline__ size_t seg_at(int w, int k, int p, int TS)
+{
+    return ((size_t)w * kSegFields + k) * (size_t)(TS * TS) + p;
+}
+
+// Inputs shared by the kernels (passed by value).
 struct RasterArgs {
-    int nunits, TS, V;
-    const uint32_t* order;       // tiles, heaviest first
+    int TS, V, nblk, seg;
+    const uint2* items;          // (tile, segment), heaviest first
+    const uint64_t* ctl;         // ctl[6] work items, ctl[7] items of split tiles
     const uint32_t* ranges;      // [first, last + 1) of each tile's list
     const float4 *s0, *s1, *s2, *s3;
     const uint32_t* sgid;        // owning (view, Gaussian) pair of each sorted instance
     const ViewDesc* views;
+    float* segstate;
     int* work;                   // persistent grid: unit counter; nullptr: one unit per warp
 };
 
@@ -60,34 +95,49 @@ struct RasterGrad {
     // instance's emission index (sinst of its sorted position)
     float* part;
     const uint32_t* sinst;
-    int nblk;                    // pixel blocks per tile
 };
 
 struct Unit {
-    int wb;                // pixel block within the tile
+    int w, wb;             // work item, pixel block within the tile
+    int j, nseg;           // segment of the item and segments of its tile
+    int lx0, ly0;          // pixel block origin within the tile
     int x0, y0;            // absolute pixel origin of the pixel block in its view
     int W, H;              // the view's image size
     long long pix_base;    // the view's first pixel in the concatenated images
-    uint32_t rs, re;       // the tile's list
+    uint32_t trs, tre;     // the tile's whole list
+    uint32_t rs, re;       // the item's part of it
 };
 
 template <int D>
 __device__ __forceinline__ void unit_of(int u, const RasterArgs& A, Unit& U)
 {
-    const int TS = A.TS;
-    const int wb_per_tile = TS * TS / (32 * D), bpr = TS / 8;
-    const int tile = (int)A.order[u / wb_per_tile], wb = u % wb_per_tile;
-    U.wb = wb;
+    const int TS = A.TS, bpr = TS / 8;
+    U.w = u / A.nblk;
+    U.wb = u % A.nblk;
+    const uint2 it = A.items[U.w];
+    const int tile = (int)it.x;
+    U.j = (int)it.y;
     const int v = view_of_tile(A.views, A.V, tile);
     const ViewDesc& d = A.views[v];
     const int lt = tile - d.tile_base;
-    U.x0 = (lt % d.TX) * TS + (wb % bpr) * 8;
-    U.y0 = (lt / d.TX) * TS + (wb / bpr) * 4 * D;
+    U.lx0 = (U.wb % bpr) * 8;
+    U.ly0 = (U.wb / bpr) * 4 * D;
+    U.x0 = (lt % d.TX) * TS + U.lx0;
+    U.y0 = (lt / d.TX) * TS + U.ly0;
     U.W = d.cam.W;
     U.H = d.cam.H;
     U.pix_base = d.pix_base;
-    U.rs = A.ranges[2 * tile];
-    U.re = A.ranges[2 * tile + 1];
+    U.trs = A.ranges[2 * tile];
+    U.tre = A.ranges[2 * tile + 1];
+    const uint32_t L = U.tre - U.trs;
+    U.nseg = (A.seg > 0 && L >= 2u * (uint32_t)A.seg) ? (int)((L + A.seg - 1) / A.seg) : 1;
+    if (U.nseg > 1) {
+        U.rs = U.trs + (uint32_t)U.j * (uint32_t)A.seg;
+        U.re = min(U.tre, U.rs + (uint32_t)A.seg);
+    } else {
+        U.rs = U.trs;
+        U.re = U.tre;
+    }
 }
 
 __device__ __forceinline__ bool box_hit(const float4 box, float bx0, float bx1, float by0, float by1)
@@ -103,55 +153,58 @@ __device__ __forceinline__ int next_unit(int* work, int lane)
     return __shfl_sync(kFull, u, 0);
 }
 
-template <int NB, int D>
-__device__ __forceinline__ void fwd_unit(int u, const RasterArgs& A, const RasterOut& O, float4* sr0, float4* sr1,
-                                         float4* sr2, uint32_t* spos, int lane)
+// Units of this launch: work items (or the split tiles' items) x pixel blocks.
+__device__ __forceinline__ int units_of(const RasterArgs& A, bool split_only)
 {
-    Unit U;
-    unit_of<D>(u, A, U);
-    const int x = U.x0 + (lane & 7), y0 = U.y0 + (lane >> 3);
-    const float px = (float)x;
-    const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 4 * D - 1);
+    return (int)(A.ctl[split_only ? 7 : 6]) * A.nblk;
+}
+
+// Front-to-back blend of the records [a, b) of a tile list for the warp's
+// pixel block.  Per pixel: T (running transmittance), colour, depth and
+// opacity sums and the last blended position (relative to trs).  With
+// `stop`, a pixel stops (without blending) at the first record whose
+// T * (1 - alpha), scaled by its Tin, falls below 1e-4; without it every
+// accepted record is blended and a pixel stops only when T reaches 0.
+// Pixels with done set take no part.
+template <int NB, int D>
+__device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uint32_t b, uint32_t trs, float px,
+                                            const float (&py)[D], float bx0, float bx1, float by0, float by1,
+                                            bool stop, const float (&Tin)[D], bool (&done)[D], float (&T)[D],
+                                            float (&C0)[D], float (&C1)[D], float (&C2)[D], float (&Dd)[D],
+                                            float (&Oo)[D], uint32_t (&last)[D], float4* sr0, float4* sr1,
+                                            float4* sr2, uint32_t* spos, int lane)
+{
     const unsigned lt = (1u << lane) - 1u;
-    float T[D], C0[D], C1[D], C2[D], Dd[D], Oo[D];
-    uint32_t last[D];
-    bool done[D];
-#pragma unroll
-    for (int j = 0; j < D; j++) {
-        T[j] = 1.0f; C0[j] = C1[j] = C2[j] = Dd[j] = Oo[j] = 0.0f;
-        last[j] = 0;
-        done[j] = !(x < U.W && y0 + 4 * j < U.H);
-    }
     float4 n0[NB], n1[NB], n2[NB], n3[NB];
 #pragma unroll
-    for (int b = 0; b < NB; b++) {
-        const uint32_t i = U.rs + b * 32 + lane;
-        if (i < U.re) { n0[b] = A.s0[i]; n1[b] = A.s1[i]; n2[b] = A.s2[i]; n3[b] = A.s3[i]; }
+    for (int q = 0; q < NB; q++) {
+        const uint32_t i = a + q * 32 + lane;
+        if (i < b) { n0[q] = A.s0[i]; n1[q] = A.s1[i]; n2[q] = A.s2[i]; n3[q] = A.s3[i]; }
     }
-    for (uint32_t base = U.rs; base < U.re; base += 32 * NB) {
+    for (uint32_t base = a; base < b; base += 32 * NB) {
         bool lane_done = true;
 #pragma unroll
         for (int j = 0; j < D; j++) lane_done = lane_done && done[j];
         if (__all_sync(kFull, lane_done)) break;
         int nh = 0;
 #pragma unroll
-        for (int b = 0; b < NB; b++) {
-            const float4 c0 = n0[b], c1 = n1[b], c2 = n2[b], c3 = n3[b];
-            const uint32_t i = base + b * 32 + lane;
+        for (int q = 0; q < NB; q++) {
+            const float4 c0 = n0[q], c1 = n1[q], c2 = n2[q], c3 = n3[q];
+            const uint32_t i = base + q * 32 + lane;
             const uint32_t ni = i + 32 * NB;
-            if (ni < U.re) { n0[b] = A.s0[ni]; n1[b] = A.s1[ni]; n2[b] = A.s2[ni]; n3[b] = A.s3[ni]; }
-            const bool hit = i < U.re && box_hit(c3, bx0, bx1, by0, by1);
+            if (ni < b) { n0[q] = A.s0[ni]; n1[q] = A.s1[ni]; n2[q] = A.s2[ni]; n3[q] = A.s3[ni]; }
+            const bool hit = i < b && box_hit(c3, bx0, bx1, by0, by1);
             const unsigned mask = __ballot_sync(kFull, hit);
             if (hit) {
                 const int k = nh + __popc(mask & lt);
                 sr0[k] = c0; sr1[k] = c1; sr2[k] = c2;
-                spos[k] = i - U.rs;
+                spos[k] = i - trs;
             }
             nh += __popc(mask);
         }
         __syncwarp();
         for (int k = 0; k < nh && !lane_done; k++) {
-            const float4 a = sr0[k], b = sr1[k];
+            const float4 g0 = sr0[k], g1 = sr1[k];
             bool used = false;
             float wgt[D];
 #pragma unroll
@@ -160,20 +213,21 @@ __device__ __forceinline__ void fwd_unit(int u, const RasterArgs& A, const Raste
                 if (done[j]) continue;
                 float dx, dy, alpha;
                 bool capped;
-                if (!pair_eval(a, b, px, (float)(y0 + 4 * j), dx, dy, alpha, capped)) continue;
+                if (!pair_eval(g0, g1, px, py[j], dx, dy, alpha, capped)) continue;
                 const float tT = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
-                if (tT < kTransMin) { done[j] = true; continue; }
+                if (stop && __fmul_rn(Tin[j], tT) < kTransMin) { done[j] = true; continue; }
                 wgt[j] = alpha * T[j];
                 T[j] = tT;
                 last[j] = spos[k] + 1;
                 used = true;
+                if (!stop && tT == 0.0f) done[j] = true;
             }
             if (used) {
                 const float4 c = sr2[k];
 #pragma unroll
                 for (int j = 0; j < D; j++) {
                     C0[j] += c.x * wgt[j]; C1[j] += c.y * wgt[j]; C2[j] += c.z * wgt[j];
-                    Dd[j] += b.z * wgt[j]; Oo[j] += wgt[j];
+                    Dd[j] += g1.z * wgt[j]; Oo[j] += wgt[j];
                 }
             }
             lane_done = true;
@@ -182,16 +236,79 @@ __device__ __forceinline__ void fwd_unit(int u, const RasterArgs& A, const Raste
         }
         __syncwarp();
     }
+}
+
+// Per-lane pixel geometry of a unit.
+template <int D>
+struct LanePix {
+    int x;
+    float px, py[D];
+    bool inside[D];
+    int p[D];          // pixel index within the tile
+    float bx0, bx1, by0, by1;
+    __device__ __forceinline__ LanePix(const Unit& U, int TS, int lane)
+    {
+        x = U.x0 + (lane & 7);
+        px = (float)x;
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            const int y = U.y0 + (lane >> 3) + 4 * j;
+            py[j] = (float)y;
+            inside[j] = x < U.W && y < U.H;
+            p[j] = (U.ly0 + (lane >> 3) + 4 * j) * TS + U.lx0 + (lane & 7);
+        }
+        bx0 = (float)U.x0;
+        bx1 = (float)(U.x0 + 7);
+        by0 = (float)U.y0;
+        by1 = (float)(U.y0 + 4 * D - 1);
+    }
+    __device__ __forceinline__ size_t pix(const Unit& U, int j) const
+    {
+        return (size_t)U.pix_base + (size_t)(U.y0 + (threadIdx.x & 31) / 8 + 4 * j) * U.W + x;
+    }
+};
+
+template <int NB, int D>
+__device__ __forceinline__ void fwd_item(int u, const RasterArgs& A, const RasterOut& O, float4* sr0, float4* sr1,
+                                         float4* sr2, uint32_t* spos, int lane)
+{
+    Unit U;
+    unit_of<D>(u, A, U);
+    const LanePix<D> L(U, A.TS, lane);
+    float T[D], C0[D], C1[D], C2[D], Dd[D], Oo[D], one[D];
+    uint32_t last[D];
+    bool done[D];
 #pragma unroll
     for (int j = 0; j < D; j++) {
-        const int y = y0 + 4 * j;
-        if (!(x < U.W && y < U.H)) continue;
-        const size_t p = (size_t)U.pix_base + (size_t)y * U.W + x;
-        O.rgb[3 * p] = C0[j]; O.rgb[3 * p + 1] = C1[j]; O.rgb[3 * p + 2] = C2[j];
-        if (O.depth) O.depth[p] = Dd[j];
-        if (O.opac) O.opac[p] = Oo[j];
-        O.Tfin[p] = T[j];
-        O.ncon[p] = last[j];
+        T[j] = 1.0f; C0[j] = C1[j] = C2[j] = Dd[j] = Oo[j] = 0.0f;
+        one[j] = 1.0f;
+        last[j] = 0;
+        done[j] = !L.inside[j];
+    }
+    const bool whole = U.nseg == 1;
+    blend_range<NB, D>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, whole, one, done, T, C0, C1,
+                       C2, Dd, Oo, last, sr0, sr1, sr2, spos, lane);
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        if (!L.inside[j]) continue;
+        if (whole) {
+            const size_t p = L.pix(U, j);
+            O.rgb[3 * p] = C0[j]; O.rgb[3 * p + 1] = C1[j]; O.rgb[3 * p + 2] = C2[j];
+            if (O.depth) O.depth[p] = Dd[j];
+            if (O.opac) O.opac[p] = Oo[j];
+            O.Tfin[p] = T[j];
+            O.ncon[p] = last[j];
+        } else {
+            float* S = A.segstate;
+            const int q = L.p[j];
+            S[seg_at(U.w, 0, q, A.TS)] = T[j];
+            S[seg_at(U.w, 1, q, A.TS)] = C0[j];
+            S[seg_at(U.w, 2, q, A.TS)] = C1[j];
+            S[seg_at(U.w, 3, q, A.TS)] = C2[j];
+            S[seg_at(U.w, 4, q, A.TS)] = Dd[j];
+            S[seg_at(U.w, 5, q, A.TS)] = Oo[j];
+            S[seg_at(U.w, 6, q, A.TS)] = __uint_as_float(last[j]);
+        }
     }
 }
 
@@ -202,9 +319,144 @@ k_raster_fwd(RasterArgs A, RasterOut O)
     __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
     __shared__ uint32_t spos[kWarpsPerBlock][32 * NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, false);
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
-    while (u < A.nunits) {
-        fwd_unit<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
+    while (u < nunits) {
+        fwd_item<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
+        if (!A.work) break;
+        u = next_unit(A.work, lane);
+    }
+}
+
+// Combine the segments of a split tile for one pixel block (the unit of its
+// first segment): outputs, then the backward's starting state per segment.
+template <int NB, int D>
+__device__ __forceinline__ void combine_item(int u, const RasterArgs& A, const RasterOut& O, float4* sr0,
+                                             float4* sr1, float4* sr2, uint32_t* spos, int lane)
+{
+    Unit U;
+    unit_of<D>(u, A, U);
+    if (U.j != 0 || U.nseg < 2) return;
+    const LanePix<D> L(U, A.TS, lane);
+    const int w0 = U.w, ns = U.nseg, TS = A.TS;
+    float* S = A.segstate;
+    float Tb[D], C0[D], C1[D], C2[D], Dd[D], Oo[D];
+    uint32_t last[D];
+    int sstop[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        Tb[j] = 1.0f; C0[j] = C1[j] = C2[j] = Dd[j] = Oo[j] = 0.0f;
+        last[j] = 0;
+        sstop[j] = ns;
+    }
+    // pass 1: prefix of the segments' transmittance; find each pixel's stop segment
+    for (int s = 0; s < ns; s++) {
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            if (!L.inside[j] || sstop[j] < ns) continue;
+            const int q = L.p[j], ws = w0 + s;
+            const float Ts = S[seg_at(ws, 0, q, TS)];
+            S[seg_at(ws, 7, q, TS)] = Tb[j];
+            if (__fmul_rn(Tb[j], Ts) < kTransMin) { sstop[j] = s; continue; }
+            C0[j] += Tb[j] * S[seg_at(ws, 1, q, TS)];
+            C1[j] += Tb[j] * S[seg_at(ws, 2, q, TS)];
+            C2[j] += Tb[j] * S[seg_at(ws, 3, q, TS)];
+            Dd[j] += Tb[j] * S[seg_at(ws, 4, q, TS)];
+            Oo[j] += Tb[j] * S[seg_at(ws, 5, q, TS)];
+            const uint32_t ls = __float_as_uint(S[seg_at(ws, 6, q, TS)]);
+            if (ls) last[j] = ls;
+            Tb[j] = __fmul_rn(Tb[j], Ts);
+        }
+    }
+    // pass 2: replay each stop segment from its incoming transmittance
+    bool replayed[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) replayed[j] = false;
+    for (;;) {
+        int mine = 0x7fffffff;
+#pragma unroll
+        for (int j = 0; j < D; j++)
+            if (L.inside[j] && sstop[j] < ns && !replayed[j]) mine = min(mine, sstop[j]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mine = min(mine, __shfl_xor_sync(kFull, mine, off));
+        if (mine == 0x7fffffff) break;
+        const int s = mine;
+        float T2[D], c0[D], c1[D], c2[D], d2[D], o2[D];
+        uint32_t l2[D];
+        bool dn[D];
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            T2[j] = 1.0f; c0[j] = c1[j] = c2[j] = d2[j] = o2[j] = 0.0f;
+            l2[j] = 0;
+            dn[j] = !(L.inside[j] && sstop[j] == s && !replayed[j]);
+        }
+        const uint32_t a = U.trs + (uint32_t)s * (uint32_t)A.seg;
+        const uint32_t b = min(U.tre, a + (uint32_t)A.seg);
+        blend_range<NB, D>(A, a, b, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, true, Tb, dn, T2, c0, c1, c2,
+                           d2, o2, l2, sr0, sr1, sr2, spos, lane);
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            if (!(L.inside[j] && sstop[j] == s && !replayed[j])) continue;
+            replayed[j] = true;
+            C0[j] += Tb[j] * c0[j]; C1[j] += Tb[j] * c1[j]; C2[j] += Tb[j] * c2[j];
+            Dd[j] += Tb[j] * d2[j]; Oo[j] += Tb[j] * o2[j];
+            if (l2[j]) last[j] = l2[j];
+            Tb[j] = __fmul_rn(Tb[j], T2[j]);
+            const int q = L.p[j], ws = w0 + s;
+            S[seg_at(ws, 0, q, TS)] = T2[j];
+            S[seg_at(ws, 1, q, TS)] = c0[j];
+            S[seg_at(ws, 2, q, TS)] = c1[j];
+            S[seg_at(ws, 3, q, TS)] = c2[j];
+            S[seg_at(ws, 4, q, TS)] = d2[j];
+            S[seg_at(ws, 5, q, TS)] = o2[j];
+        }
+    }
+    // outputs, and the backward's starting state of every segment (back to front)
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        if (!L.inside[j]) continue;
+        const size_t p = L.pix(U, j);
+        O.rgb[3 * p] = C0[j]; O.rgb[3 * p + 1] = C1[j]; O.rgb[3 * p + 2] = C2[j];
+        if (O.depth) O.depth[p] = Dd[j];
+        if (O.opac) O.opac[p] = Oo[j];
+        O.Tfin[p] = Tb[j];
+        O.ncon[p] = last[j];
+        const int q = L.p[j];
+        const int jl = sstop[j] < ns ? sstop[j] : ns - 1;
+        float R0 = 0.f, R1 = 0.f, R2 = 0.f, RD = 0.f, RO = 0.f;
+        for (int s = ns - 1; s >= 0; s--) {
+            const int ws = w0 + s;
+            if (s > jl) {
+                for (int k = 0; k < 6; k++) S[seg_at(ws, k, q, TS)] = 0.0f;
+                continue;
+            }
+            const float Ts = S[seg_at(ws, 0, q, TS)];
+            const float cs0 = S[seg_at(ws, 1, q, TS)], cs1 = S[seg_at(ws, 2, q, TS)], cs2 = S[seg_at(ws, 3, q, TS)];
+            const float ds = S[seg_at(ws, 4, q, TS)], os = S[seg_at(ws, 5, q, TS)];
+            const float tin = S[seg_at(ws, 7, q, TS)];
+            S[seg_at(ws, 0, q, TS)] = __fmul_rn(tin, Ts);
+            S[seg_at(ws, 1, q, TS)] = R0;
+            S[seg_at(ws, 2, q, TS)] = R1;
+            S[seg_at(ws, 3, q, TS)] = R2;
+            S[seg_at(ws, 4, q, TS)] = RD;
+            S[seg_at(ws, 5, q, TS)] = RO;
+            R0 = cs0 + Ts * R0; R1 = cs1 + Ts * R1; R2 = cs2 + Ts * R2;
+            RD = ds + Ts * RD; RO = os + Ts * RO;
+        }
+    }
+}
+
+template <int NB, int D>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k_raster_combine(RasterArgs A, RasterOut O)
+{
+    __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
+    __shared__ uint32_t spos[kWarpsPerBlock][32 * NB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, true);
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    while (u < nunits) {
+        combine_item<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
     }
@@ -252,14 +504,12 @@ __device__ __forceinline__ float warp_transpose_reduce16(float (&v)[16])
 }
 
 template <bool EXTRA, int NB, int D, bool DET>
-__device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const RasterGrad& G, float4* sr0,
+__device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const RasterGrad& G, float4* sr0,
                                          float4* sr1, float4* sr2, uint32_t* spos, uint32_t* sg, int lane)
 {
     Unit U;
     unit_of<D>(u, A, U);
-    const int x = U.x0 + (lane & 7), y0 = U.y0 + (lane >> 3);
-    const float px = (float)x;
-    const float bx0 = (float)U.x0, bx1 = (float)(U.x0 + 7), by0 = (float)U.y0, by1 = (float)(U.y0 + 4 * D - 1);
+    const LanePix<D> L(U, A.TS, lane);
     const unsigned lt = (1u << lane) - 1u;
     float T[D], R0[D], R1[D], R2[D], RD[D], RO[D], g0[D], g1[D], g2[D], gD[D], gO[D];
     uint32_t last[D];
@@ -269,11 +519,21 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
         T[j] = 1.0f; R0[j] = R1[j] = R2[j] = RD[j] = RO[j] = 0.0f;
         g0[j] = g1[j] = g2[j] = gD[j] = gO[j] = 0.0f;
         last[j] = 0;
-        const int y = y0 + 4 * j;
-        if (x < U.W && y < U.H) {
-            const size_t p = (size_t)U.pix_base + (size_t)y * U.W + x;
-            T[j] = G.Tfin[p];
+        if (L.inside[j]) {
+            const size_t p = L.pix(U, j);
             last[j] = G.ncon[p];
+            if (U.nseg == 1) {
+                T[j] = G.Tfin[p];
+            } else {
+                const float* S = A.segstate;
+                const int q = L.p[j];
+                T[j] = S[seg_at(U.w, 0, q, A.TS)];
+                R0[j] = S[seg_at(U.w, 1, q, A.TS)];
+                R1[j] = S[seg_at(U.w, 2, q, A.TS)];
+                R2[j] = S[seg_at(U.w, 3, q, A.TS)];
+                RD[j] = S[seg_at(U.w, 4, q, A.TS)];
+                RO[j] = S[seg_at(U.w, 5, q, A.TS)];
+            }
             g0[j] = G.dL_drgb[3 * p]; g1[j] = G.dL_drgb[3 * p + 1]; g2[j] = G.dL_drgb[3 * p + 2];
             if (EXTRA) {
                 gD[j] = G.dL_ddepth ? G.dL_ddepth[p] : 0.0f;
@@ -284,8 +544,9 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, off));
-    const uint32_t end = U.rs + wmax;   // positions at or beyond this reach no pixel of the block
-    if (end == U.rs) return;
+    // positions at or beyond the last contributor reach no pixel of the block
+    const uint32_t end = min(U.re, U.trs + wmax);
+    if (end <= U.rs) return;
     // batches from the back: [bstart, bstart + 32 NB) with bstart = end - 32 NB k, clipped at rs
     constexpr int BS = 32 * NB;
     int64_t bstart = (int64_t)end - BS;
@@ -312,12 +573,12 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
                 n0[b] = A.s0[ni]; n1[b] = A.s1[ni]; n2[b] = A.s2[ni]; n3[b] = A.s3[ni];
                 ng[b] = DET ? G.sinst[ni] : A.sgid[ni];
             }
-            const bool hit = i >= (int64_t)U.rs && box_hit(c3, bx0, bx1, by0, by1);
+            const bool hit = i >= (int64_t)U.rs && box_hit(c3, L.bx0, L.bx1, L.by0, L.by1);
             const unsigned mask = __ballot_sync(kFull, hit);
             if (hit) {
                 const int k = nh + __popc(mask & lt);
                 sr0[k] = c0; sr1[k] = c1; sr2[k] = c2;
-                spos[k] = (uint32_t)(i - U.rs);
+                spos[k] = (uint32_t)(i - U.trs);
                 sg[k] = cg;
             }
             nh += __popc(mask);
@@ -334,7 +595,7 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
             for (int j = 0; j < D; j++) {
                 float dx, dy, alpha;
                 bool capped;
-                if (pos < last[j] && pair_eval(a, b, px, (float)(y0 + 4 * j), dx, dy, alpha, capped)) {
+                if (pos < last[j] && pair_eval(a, b, L.px, L.py[j], dx, dy, alpha, capped)) {
                     const float om = 1.0f - alpha;
                     T[j] = __fdividef(T[j], om);
                     const float wgt = alpha * T[j];
@@ -361,7 +622,7 @@ __device__ __forceinline__ void bwd_unit(int u, const RasterArgs& A, const Raste
                 const float r = warp_transpose_reduce16(v);
                 const int q = lane >> 1;
                 if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1)) {
-                    if (DET) G.part[((size_t)sg[k] * G.nblk + U.wb) * kNG + q] = r;
+                    if (DET) G.part[((size_t)sg[k] * A.nblk + U.wb) * kNG + q] = r;
                     else atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, r);
                 }
             }
@@ -377,9 +638,10 @@ k_raster_bwd(RasterArgs A, RasterGrad G)
     __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
     __shared__ uint32_t spos[kWarpsPerBlock][32 * NB], sg[kWarpsPerBlock][32 * NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, false);
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
-    while (u < A.nunits) {
-        bwd_unit<EXTRA, NB, D, DET>(u, A, G, sr0[w], sr1[w], sr2[w], spos[w], sg[w], lane);
+    while (u < nunits) {
+        bwd_item<EXTRA, NB, D, DET>(u, A, G, sr0[w], sr1[w], sr2[w], spos[w], sg[w], lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
     }
@@ -427,12 +689,12 @@ __global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __
 }
 
 template <typename K>
-int grid_for(K kernel, int variant, int nunits, bool persistent)
+int grid_for(K kernel, int variant, int64_t units_bound, bool persistent)
 {
-    const int need = (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (!persistent) return need;
+    const int64_t need = std::max<int64_t>(1, (units_bound + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (!persistent) return (int)std::min<int64_t>(need, 0x7fffffff);
     // resident CTAs of this variant, looked up once per process
-    static int cache[64] = {};
+    static int cache[128] = {};
     if (!cache[variant]) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
@@ -440,16 +702,27 @@ int grid_for(K kernel, int variant, int nunits, bool persistent)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32 * kWarpsPerBlock, 0);
         cache[variant] = std::max(1, sms * std::max(1, per));
     }
-    return std::max(1, std::min(need, cache[variant]));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, cache[variant]));
+}
+
+int blocks_per_tile(const View& v) { return v.Ts * v.Ts / (32 * v.pd); }
+
+// Split-tile items are bounded by 1.5 x capacity / seg: a tile of L >= 2 seg
+// records has at most L / seg + 1 <= 1.5 L / seg segments.
+int64_t split_items_bound(const View& v)
+{
+    return v.seg > 0 ? (int64_t)(v.itile.bytes / 4) * 3 / (2 * v.seg) + 1 : 0;
 }
 
 RasterArgs make_args(View& v, int* work)
 {
     RasterArgs A;
-    A.nunits = v.ntiles * (v.Ts * v.Ts / (32 * v.pd));
     A.TS = v.Ts;
     A.V = v.V;
-    A.order = v.tile_order.as<uint32_t>();
+    A.nblk = blocks_per_tile(v);
+    A.seg = v.seg;
+    A.items = v.items.as<uint2>();
+    A.ctl = v.count.as<uint64_t>();
     A.ranges = v.ranges.as<uint32_t>();
     A.s0 = v.srec0.as<float4>();
     A.s1 = v.srec1.as<float4>();
@@ -457,6 +730,7 @@ RasterArgs make_args(View& v, int* work)
     A.s3 = v.srec3.as<float4>();
     A.sgid = v.sgid.as<uint32_t>();
     A.views = v.d_desc();
+    A.segstate = v.segstate.as<float>();
     A.work = work;
     return A;
 }
@@ -469,40 +743,53 @@ gl_status check_exec(const View& v)
         set_error("pixels per lane must be 1, 2 or 4, with 4 x pixels per lane <= tile size");
         return GL_ERR_INVALID;
     }
+    if (v.seg != 0 && (v.seg < 64 || v.seg > 65536 || (v.seg & (v.seg - 1)) != 0)) {
+        set_error("segment length must be 0 or a power of two in 64..65536");
+        return GL_ERR_INVALID;
+    }
     return GL_OK;
 }
 
 template <int NB, int D>
-void fwd_launch(const RasterArgs& A, const RasterOut& O, bool persistent, cudaStream_t s)
+void fwd_launch(const RasterArgs& A, const RasterOut& O, int64_t units, int64_t split_units, bool persistent,
+                int* work, cudaStream_t s)
 {
-    const int grid = grid_for(k_raster_fwd<NB, D>, (NB - 1) * 4 + D, A.nunits, persistent);
-    k_raster_fwd<NB, D><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, O);
+    RasterArgs a1 = A;
+    a1.work = work;
+    k_raster_fwd<NB, D><<<grid_for(k_raster_fwd<NB, D>, (NB - 1) * 4 + D, units, persistent), 32 * kWarpsPerBlock,
+                          0, s>>>(a1, O);
+    if (split_units > 0) {
+        RasterArgs a2 = A;
+        a2.work = work ? work + 2 : nullptr;
+        k_raster_combine<NB, D><<<grid_for(k_raster_combine<NB, D>, 8 + (NB - 1) * 4 + D, split_units, persistent),
+                                  32 * kWarpsPerBlock, 0, s>>>(a2, O);
+    }
 }
 
 template <bool EXTRA, int NB, int D, bool DET>
-void bwd_launch(const RasterArgs& A, const RasterGrad& G, bool persistent, cudaStream_t s)
+void bwd_launch(const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent, cudaStream_t s)
 {
     const int variant = 32 + (DET ? 16 : 0) + (EXTRA ? 8 : 0) + (NB - 1) * 4 + D;   // < 64
-    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D, DET>, variant, A.nunits, persistent);
+    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D, DET>, variant, units, persistent);
     k_raster_bwd<EXTRA, NB, D, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
 }
 
 template <bool EXTRA>
-void bwd_dispatch(int nb, int pd, bool det, const RasterArgs& A, const RasterGrad& G, bool persistent,
+void bwd_dispatch(int nb, int pd, bool det, const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent,
                   cudaStream_t s)
 {
     if (det) {   // batch depth 32 only
-        if (pd == 1) bwd_launch<EXTRA, 1, 1, true>(A, G, persistent, s);
-        else if (pd == 2) bwd_launch<EXTRA, 1, 2, true>(A, G, persistent, s);
-        else bwd_launch<EXTRA, 1, 4, true>(A, G, persistent, s);
+        if (pd == 1) bwd_launch<EXTRA, 1, 1, true>(A, G, units, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 1, 2, true>(A, G, units, persistent, s);
+        else bwd_launch<EXTRA, 1, 4, true>(A, G, units, persistent, s);
     } else if (nb == 1) {
-        if (pd == 1) bwd_launch<EXTRA, 1, 1, false>(A, G, persistent, s);
-        else if (pd == 2) bwd_launch<EXTRA, 1, 2, false>(A, G, persistent, s);
-        else bwd_launch<EXTRA, 1, 4, false>(A, G, persistent, s);
+        if (pd == 1) bwd_launch<EXTRA, 1, 1, false>(A, G, units, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 1, 2, false>(A, G, units, persistent, s);
+        else bwd_launch<EXTRA, 1, 4, false>(A, G, units, persistent, s);
     } else {
-        if (pd == 1) bwd_launch<EXTRA, 2, 1, false>(A, G, persistent, s);
-        else if (pd == 2) bwd_launch<EXTRA, 2, 2, false>(A, G, persistent, s);
-        else bwd_launch<EXTRA, 2, 4, false>(A, G, persistent, s);
+        if (pd == 1) bwd_launch<EXTRA, 2, 1, false>(A, G, units, persistent, s);
+        else if (pd == 2) bwd_launch<EXTRA, 2, 2, false>(A, G, units, persistent, s);
+        else bwd_launch<EXTRA, 2, 4, false>(A, G, units, persistent, s);
     }
 }
 
@@ -535,24 +822,28 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     if (v.ntiles == 0) return GL_OK;
     GL_TRY(check_exec(v));
     GL_TRY(v.work.reserve(16));
+    const int64_t split = split_items_bound(v);
+    if (split > 0) GL_TRY(v.segstate.reserve(sizeof(float) * kSegFields * (size_t)(v.Ts * v.Ts) * (size_t)split));
     PhaseScope ps(v.prof, PH_RASTER_FWD, s);
     int* work = nullptr;
     if (v.persistent) {
         work = v.work.as<int>();
-        GL_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int), s));
+        GL_CUDA_TRY(cudaMemsetAsync(work, 0, 4 * sizeof(int), s));
     }
-    const RasterArgs A = make_args(v, work);
+    const RasterArgs A = make_args(v, nullptr);
     RasterOut O{rgb, depth, opac, v.Tfin.as<float>(), v.ncon.as<uint32_t>()};
+    const int nblk = blocks_per_tile(v);
+    const int64_t units = work_items_bound(v) * nblk, split_units = split * nblk;
     if (v.nb == 1) {
-        if (v.pd == 1) fwd_launch<1, 1>(A, O, v.persistent, s);
-        else if (v.pd == 2) fwd_launch<1, 2>(A, O, v.persistent, s);
-        else fwd_launch<1, 4>(A, O, v.persistent, s);
+        if (v.pd == 1) fwd_launch<1, 1>(A, O, units, split_units, v.persistent, work, s);
+        else if (v.pd == 2) fwd_launch<1, 2>(A, O, units, split_units, v.persistent, work, s);
+        else fwd_launch<1, 4>(A, O, units, split_units, v.persistent, work, s);
     } else {
-        if (v.pd == 1) fwd_launch<2, 1>(A, O, v.persistent, s);
-        else if (v.pd == 2) fwd_launch<2, 2>(A, O, v.persistent, s);
-        else fwd_launch<2, 4>(A, O, v.persistent, s);
+        if (v.pd == 1) fwd_launch<2, 1>(A, O, units, split_units, v.persistent, work, s);
+        else if (v.pd == 2) fwd_launch<2, 2>(A, O, units, split_units, v.persistent, work, s);
+        else fwd_launch<2, 4>(A, O, units, split_units, v.persistent, work, s);
     }
-    count_launches(1);
+    count_launches(split_units > 0 ? 2 : 1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -566,7 +857,7 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     GL_TRY(v.work.reserve(16));
     PhaseScope ps(v.prof, PH_RASTER_BWD, s);
     const bool det = v.det && v.ntiles > 0 && v.I != 0;
-    const int nblk = v.Ts * v.Ts / (32 * v.pd);
+    const int nblk = blocks_per_tile(v);
     if (!det) GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * pairs, s));
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     int* work = nullptr;
@@ -576,7 +867,7 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     }
     const RasterArgs A = make_args(v, work);
     RasterGrad G{v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>(),
-                 nullptr, v.sorted_inst, nblk};
+                 nullptr, v.sorted_inst};
     const size_t cap = v.itile.bytes / 4;
     if (det) {
         // every instance's block sums, zero where a block has no hit; the
@@ -587,8 +878,9 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
         GL_CUDA_TRY(cudaMemsetAsync(v.gpart.p, 0, sizeof(float) * kNG * (size_t)nblk * inst, s));
         G.part = v.gpart.as<float>();
     }
-    if (dL_ddepth != nullptr || dL_dopac != nullptr) bwd_dispatch<true>(v.nb, v.pd, det, A, G, v.persistent, s);
-    else bwd_dispatch<false>(v.nb, v.pd, det, A, G, v.persistent, s);
+    const int64_t units = work_items_bound(v) * nblk;
+    if (dL_ddepth != nullptr || dL_dopac != nullptr) bwd_dispatch<true>(v.nb, v.pd, det, A, G, units, v.persistent, s);
+    else bwd_dispatch<false>(v.nb, v.pd, det, A, G, units, v.persistent, s);
     count_launches(1);
     if (det) {
         const int blocks = (int)std::min<size_t>(8 * 152, (pairs + 255) / 256);

@@ -95,8 +95,10 @@ struct gl_server {
     int latest = -1;
     int64_t version = 0;
     std::vector<std::vector<uint8_t>> versions;
-    // in-flight work, for memory admission
-    int mut_busy = 0, ren_busy = 0;
+    // admitted work in flight, for memory admission (a worker still waiting
+    // for admission does not count: two waiting workers would otherwise wait
+    // for each other)
+    int mut_running = 0, ren_running = 0;
     double mut_scratch_hw = 0.0, ren_scratch_hw = 0.0;   // largest scratch estimates admitted
     double inst_per_px = 2.0;                              // instances per pixel, from the last render
     // statistics
@@ -161,15 +163,21 @@ void finish(gl_server* s, Req* q, const gl_result& res)
 }
 
 // Admission: wait until the device has `need` bytes beyond the reserve free.
-// Returns false when it cannot fit with nothing else in flight.
+// Returns false when it cannot fit while the other worker has no admitted
+// work in flight (nothing will be freed), or after 30 s.  On true the
+// caller's worker counts as running.
 bool admit_memory(gl_server* s, double need, bool render_side)
 {
+    const double deadline = s->now() + 30.0;
     for (;;) {
         const double f = (double)free_bytes();
-        if (f >= need + (double)s->cfg.reserve_bytes) return true;
         std::unique_lock<std::mutex> lk(s->mu);
-        const bool others = render_side ? s->mut_busy > 0 : s->ren_busy > 0;
-        if (!others) return false;
+        if (f >= need + (double)s->cfg.reserve_bytes) {
+            (render_side ? s->ren_running : s->mut_running)++;
+            return true;
+        }
+        const bool others = render_side ? s->mut_running > 0 : s->ren_running > 0;
+        if (!others || s->now() > deadline) return false;
         s->memory_waits++;
         s->cv.wait_for(lk, std::chrono::milliseconds(2));
     }
@@ -295,7 +303,6 @@ void mutation_worker(gl_server* s)
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->mut_q.pop_front();
-            s->mut_busy++;
         }
         const bool fits = admit_memory(s, need, false);
         res.t_admit = s->now();
@@ -316,9 +323,10 @@ void mutation_worker(gl_server* s)
                 if (st == GL_OK) st = record_version(s);
             }
         }
-        {
+        if (fits) {
             std::lock_guard<std::mutex> lk(s->mu);
-            s->mut_busy--;
+            s->mut_running--;
+            s->cv.notify_all();
         }
         res.status = st;
         res.t_done = s->now();
@@ -344,7 +352,6 @@ void render_worker(gl_server* s)
                 batch.push_back(s->ren_q.front());
                 s->ren_q.pop_front();
             }
-            s->ren_busy++;
         }
         double P = 0.0;
         for (Req* q : batch) P += (double)q->r.keyframe.K.width * q->r.keyframe.K.height;
@@ -371,6 +378,7 @@ void render_worker(gl_server* s)
             const GParams p = snapshot_params(s->map, s->snap[slot].arr, s->snap[slot].n);
             st = cudaStreamWaitEvent(s->rstream, s->snap[slot].ready, 0) == cudaSuccess ? GL_OK : GL_ERR_CUDA;
             if (st == GL_OK) st = s->rgb.reserve(12 * (size_t)P);
+            map_exec_knobs(s->map, s->rview, Ts);
             if (st == GL_OK) st = bin_views(s->rview, p, cams.data(), nullptr, V, Ts, s->rstream);
             if (st == GL_OK) st = raster_forward(s->rview, s->rgb.as<float>(), nullptr, nullptr, s->rstream);
             size_t off = 0;
@@ -393,9 +401,10 @@ void render_worker(gl_server* s)
             s->render_batches++;
             s->cv.notify_all();
         }
-        {
+        if (fits) {
             std::lock_guard<std::mutex> lk(s->mu);
-            s->ren_busy--;
+            s->ren_running--;
+            s->cv.notify_all();
         }
         const double t_done = s->now();
         for (Req* q : batch) {

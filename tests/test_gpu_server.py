@@ -62,7 +62,7 @@ def test_results_are_the_same_alone_and_in_the_mix(det):
         if i % 3 == 2:
             spec = dict(n_steps=5, window=2, seed=7 + i)
             reqs.append(("optimize", srv.optimize(**spec), spec))
-    out = [(kind, srv.wait(t), spec) for kind, t, spec in reqs]
+    out = [(kind, srv.wait(t, 120), spec) for kind, t, spec in reqs]
     st = srv.stats()
     n_mut = sum(1 for k, _, _ in reqs if k != "render")
     assert st["version"] == n_mut and st["render"]["completed"] == sum(1 for k, _, _ in reqs if k == "render")
@@ -94,7 +94,7 @@ def test_results_are_the_same_alone_and_in_the_mix(det):
         a.load(ckpt[v - 1])
         s2 = binding.Server(a)
         t = s2.keyframe_update(**spec) if kind == "update" else s2.optimize(**spec)
-        r2, _ = s2.wait(t)
+        r2, _ = s2.wait(t, 120)
         s2.close()
         assert r2["status"] == 0 and r2["n_added"] == res["n_added"], (r2, res)
         b = _map(det)
@@ -128,8 +128,8 @@ def test_requests_that_cannot_fit_fail_cleanly():
     cam, img, pts, col = frames[0]
     t1 = srv.keyframe_update(0, cam, img, pts, col, n_steps=2)
     t2 = srv.render(novel[0])
-    r1, _ = srv.wait(t1)
-    r2, _ = srv.wait(t2)
+    r1, _ = srv.wait(t1, 120)
+    r2, _ = srv.wait(t2, 120)
     assert r1["status"] == 2 and r2["status"] == 2   # GL_ERR_OOM
     st = srv.stats()
     assert st["keyframe_update"]["failed"] == 1 and st["render"]["failed"] == 1 and st["version"] == 0
@@ -150,8 +150,8 @@ def test_queue_limit_and_bad_requests():
     with pytest.raises(binding.GLError) as e:
         srv.render(novel[1])
     assert e.value.status == 6   # GL_ERR_BUSY
-    srv.wait(t1)
-    srv.wait(t2)
+    srv.wait(t1, 120)
+    srv.wait(t2, 120)
     with pytest.raises(binding.GLError):
         srv.optimize(3, window=0)
     bad = dict(novel[0], fx=-1.0)
@@ -170,7 +170,7 @@ def test_map_size_cap():
     cap = len(m) + 500
     srv = binding.Server(m, max_gaussians=cap)
     for i, (cam, img, pts, col) in enumerate(frames[:3]):
-        r, _ = srv.wait(srv.keyframe_update(i, cam, img, pts, col, n_steps=1))
+        r, _ = srv.wait(srv.keyframe_update(i, cam, img, pts, col, n_steps=1), 120)
         assert r["status"] == 0
     st = srv.stats()
     assert st["map_size"] <= cap and st["points_capped"] > 0
