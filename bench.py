@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--window", type=int, default=8, help="views per window in the equal-PSNR comparison")
     ap.add_argument("--exec", default="auto", choices=["auto", "eager", "graphs"],
                     help="auto: CUDA-graph steps with autotuned raster knobs (plain keeps tile 16)")
+    ap.add_argument("--knobs", default="",
+                    help="explicit execution knobs after --exec, e.g. segment=1024,persistent=1 (no autotuning)")
     ap.add_argument("--batched-views", type=int, default=12,
                     help="mixed-resolution window of the batched workload, 2M Gaussians (0: skip)")
     ap.add_argument("--batched-windows", type=int, default=30)
@@ -217,16 +219,22 @@ def mean_psnr(m, views, torch):
     return float(np.mean(out))
 
 
-def set_exec(m, mode, views, keep_tile):
+KNOBS = {}
+
+
+def set_exec(m, mode, views, keep_tile, window=None):
     """Execution of the map's steps: eager defaults, graphs with default
-    knobs, or graphs with the autotuner's pick for the window `views`."""
+    knobs, or graphs with the autotuner's pick for the window `views`;
+    explicit --knobs replace the autotuner."""
     if mode == "eager":
-        m.set_exec(use_graphs=0, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0)
+        m.set_exec(use_graphs=0, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0, segment=0)
+        m.set_exec(**KNOBS)
         return m.get_exec(), None
-    if mode == "graphs":
-        m.set_exec(use_graphs=1, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0)
+    if mode == "graphs" or KNOBS:
+        m.set_exec(use_graphs=1, persistent=0, batch_depth=32, pixels_per_lane=1, tile_size=0, segment=0)
+        m.set_exec(**KNOBS)
         return m.get_exec(), None
-    best, ms = m.autotune(views, reps=3, keep_tile_size=keep_tile)
+    best, ms = m.autotune(views, reps=3, keep_tile_size=keep_tile, window=window)
     return best, ms
 
 
@@ -397,7 +405,7 @@ def run_batched(args, binding, torch, dist, ws):
     w_ms = max_over_ranks(timed(torch, lambda: [m.optimize_step(win) for _ in range(nw)]), dist)
     st = m.stats()
     # the same views as plain single-view steps on the same map (tile 16, autotuned knobs)
-    plain_exec, _ = set_exec(m, args.exec, [win[0]], keep_tile=True)
+    plain_exec, _ = set_exec(m, args.exec, [win[k] for k in (0, 4, 8)], keep_tile=True, window=1)
     for k in range(n):
         m.optimize_step([win[k]])
     reps = max(1, nw // 2)
@@ -460,6 +468,7 @@ def run_serving(args, binding, torch):
         ev.append((t, "render"))
     ev.sort()
     n_start = len(m)
+    m.set_exec(use_graphs=1, persistent=1, segment=1024)
     cap = 750_000 if small else 3_000_000   # the stream's map target; extra points are capped and counted
     srv = binding.Server(m, render_batch=8, max_gaussians=cap)
     tickets, rejects, kid, ri = [], 0, 100, 0
@@ -502,7 +511,7 @@ def run_serving(args, binding, torch):
            "steps": st["steps"], "steps_per_s": st["steps_per_s"], "renders_per_s": st["renders_per_s"],
            "mean_render_batch": st["mean_render_batch"], "memory_waits": st["memory_waits"],
            "busy_rejects": rejects, "failed": int(sum(1 for x in statuses if x != 0)),
-           "map_cap": cap, "points_capped": st["points_capped"]}
+           "map_cap": cap, "points_capped": st["points_capped"], "exec": m.get_exec()}
     for k in ("keyframe_update", "render"):
         out[k] = {kk: st[k][kk] for kk in ("completed", "p50_ms", "p99_ms", "mean_ms")}
     m.close()
@@ -573,12 +582,11 @@ def run_ours(args):
     def step(k, img=None, want=False):
         return m.optimize_step([(int(k), cams[int(k)], img)], want_loss=want)
 
-    for i in range(args.warmup):
-        step(order[i])
     # execution of the plain step: the autotuner times the raster knobs with
-    # graph replay on one keyframe, keeping the 16-pixel tiles
-    k0 = int(order[0])
-    exec_cfg, tune_ms = set_exec(m, args.exec, [(k0, cams[k0], None)], keep_tile=True)
+    # graph replay on single-view steps of four keyframes along the
+    # trajectory, keeping the 16-pixel tiles
+    ks = sorted(set(int(k) for k in np.linspace(0, n_kf - 1, 4)))
+    exec_cfg, tune_ms = set_exec(m, args.exec, [(k, cams[k], None) for k in ks], keep_tile=True, window=1)
     for i in range(max(3, args.warmup)):
         step(order[i])
     torch.cuda.synchronize()
@@ -725,6 +733,7 @@ def run_ours(args):
         "equal_psnr": psnr,
         "serving": serving,
         "gpu_launches": int(launches),
+        "launches_before_timed": int(launches0),
         "clocks": clk,
         "keyframe_update": ({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                              "updates": len(lat), "steps_per_update": args.update_steps,
@@ -735,6 +744,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    for kv in filter(None, args.knobs.split(",")):
+        k, v = kv.split("=")
+        KNOBS[k.strip()] = int(v)
     if args.impl == "reference":
         run_reference(args)
     else:

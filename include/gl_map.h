@@ -233,17 +233,21 @@ typedef struct {
 GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
 GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
 
-/* Autotuner for one window shape: for each candidate execution (tile size
- * 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4 x persistent or not x
- * segment 0/1024, graphs on, deterministic as set) time `reps` optimisation steps of `views` (as gl_optimize_step)
- * with CUDA events, putting the Gaussians, their Adam moments, the views'
- * exposures and the step counters back after each trial.  With
- * keep_tile_size != 0 only gl_config's tile size is tried.  The fastest
- * candidate is installed with gl_map_set_exec and returned in *best, its
- * device time per step in *best_ms (nullable).  The map ends as it started.
- * Errors: as gl_optimize_step, GL_ERR_OOM for the state snapshot. */
-GL_API gl_status gl_map_autotune(gl_map* map, const gl_keyframe* views, int32_t n_views, int32_t reps,
-                                 int32_t keep_tile_size, gl_exec_config* best, float* best_ms);
+/* Autotuner: `views` holds n_views / window windows of `window` views each
+ * (as gl_optimize_step takes them; several windows make the timing
+ * representative of steps over different views).  For each candidate
+ * execution (tile size 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4
+ * x persistent or not x segment 0/1024, graphs on, deterministic as set) it
+ * times `reps` rounds of one step per window with CUDA events, putting the
+ * Gaussians, their Adam moments, the views' exposures and the step
+ * counters back after each trial.  With keep_tile_size != 0 only
+ * gl_config's tile size is tried.  The fastest candidate is installed with
+ * gl_map_set_exec and returned in *best, its device time per step in
+ * *best_ms (nullable).  The map ends as it started.  Errors: as
+ * gl_optimize_step; GL_ERR_INVALID if n_views is not 1..64 whole windows;
+ * GL_ERR_OOM for the state snapshot. */
+GL_API gl_status gl_map_autotune(gl_map* map, const gl_keyframe* views, int32_t n_views, int32_t window,
+                                 int32_t reps, int32_t keep_tile_size, gl_exec_config* best, float* best_ms);
 
 /* Change the configuration of an existing map: learning rates, Adam
  * constants, lambda_dssim, tau, opacity_fg, sparse_adam, tile_size and

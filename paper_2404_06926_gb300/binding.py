@@ -117,7 +117,7 @@ def lib():
             "gl_map_set_exec": ([P, P], i32),
             "gl_ctx_set_exec": ([P, P], i32),
             "gl_map_get_exec": ([P, P], i32),
-            "gl_map_autotune": ([P, P, i32, i32, i32, P, P], i32),
+            "gl_map_autotune": ([P, P, i32, i32, i32, i32, P, P], i32),
             "gl_map_checkpoint_size": ([P, i32, P], i32),
             "gl_map_set_config": ([P, P], i32),
             "gl_server_config_default": ([P], i32),
@@ -451,16 +451,18 @@ class Map:
         check(lib().gl_map_get_exec(self._h, C.byref(e)))
         return e.as_dict()
 
-    def autotune(self, views, reps: int = 3, keep_tile_size: bool = False):
-        """Time every execution candidate on the window `views` (list of
-        (id, cam, image-or-None)), install the fastest; returns (config, ms)."""
+    def autotune(self, views, reps: int = 3, keep_tile_size: bool = False, window: int | None = None):
+        """Time every execution candidate on `views` (list of (id, cam,
+        image-or-None)) taken as consecutive windows of `window` views (default:
+        one window of all), install the fastest; returns (config, ms per step)."""
+        window = len(views) if window is None else int(window)
         arr = (Keyframe * len(views))()
         for i, (kid, cam, img) in enumerate(views):
             arr[i] = keyframe(kid, cam, img)
         e = ExecConfig()
         ms = C.c_float()
-        check(lib().gl_map_autotune(self._h, arr, len(views), int(reps), int(bool(keep_tile_size)), C.byref(e),
-                                    C.byref(ms)))
+        check(lib().gl_map_autotune(self._h, arr, len(views), window, int(reps), int(bool(keep_tile_size)),
+                                    C.byref(e), C.byref(ms)))
         return e.as_dict(), ms.value
 
     def stats(self) -> dict:

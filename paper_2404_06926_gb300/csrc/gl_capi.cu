@@ -1218,15 +1218,15 @@ struct Snapshot {
     std::vector<int64_t> kf_steps;
 };
 
-gl_status snap_take(gl_map* m, const StepPlan& sp, Snapshot& S)
+gl_status snap_take(gl_map* m, const std::vector<Keyframe*>& kfs, Snapshot& S)
 {
     S.step = m->step;
     S.n = m->n;
-    S.kf_steps.resize(sp.V);
-    GL_TRY(S.expo.reserve(36 * 4 * (size_t)sp.V));
-    for (int i = 0; i < sp.V; i++) {
-        S.kf_steps[i] = sp.kfs[i]->steps;
-        GL_CUDA_TRY(cudaMemcpyAsync(S.expo.as<float>() + 36 * i, sp.kfs[i]->expo.p, 36 * 4, cudaMemcpyDeviceToDevice,
+    S.kf_steps.resize(kfs.size());
+    GL_TRY(S.expo.reserve(36 * 4 * std::max<size_t>(kfs.size(), 1)));
+    for (size_t i = 0; i < kfs.size(); i++) {
+        S.kf_steps[i] = kfs[i]->steps;
+        GL_CUDA_TRY(cudaMemcpyAsync(S.expo.as<float>() + 36 * i, kfs[i]->expo.p, 36 * 4, cudaMemcpyDeviceToDevice,
                                     m->stream));
     }
     for (int set = 0; set < 3; set++) {
@@ -1240,12 +1240,12 @@ gl_status snap_take(gl_map* m, const StepPlan& sp, Snapshot& S)
     return GL_OK;
 }
 
-gl_status snap_restore(gl_map* m, const StepPlan& sp, const Snapshot& S)
+gl_status snap_restore(gl_map* m, const std::vector<Keyframe*>& kfs, const Snapshot& S)
 {
     m->step = S.step;
-    for (int i = 0; i < sp.V; i++) {
-        sp.kfs[i]->steps = S.kf_steps[i];
-        GL_CUDA_TRY(cudaMemcpyAsync(sp.kfs[i]->expo.p, S.expo.as<float>() + 36 * i, 36 * 4, cudaMemcpyDeviceToDevice,
+    for (size_t i = 0; i < kfs.size(); i++) {
+        kfs[i]->steps = S.kf_steps[i];
+        GL_CUDA_TRY(cudaMemcpyAsync(kfs[i]->expo.p, S.expo.as<float>() + 36 * i, 36 * 4, cudaMemcpyDeviceToDevice,
                                     m->stream));
     }
     for (int set = 0; set < 3; set++) {
@@ -1282,18 +1282,28 @@ extern "C" gl_status gl_map_get_exec(gl_map* m, gl_exec_config* e)
     return GL_OK;
 }
 
-extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_t n_views, int32_t reps,
-                                     int32_t keep_tile_size, gl_exec_config* best, float* best_ms)
+extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_t n_views, int32_t window,
+                                     int32_t reps, int32_t keep_tile_size, gl_exec_config* best, float* best_ms)
 {
-    if (!m || !best) { set_error("null argument"); return GL_ERR_INVALID; }
+    if (!m || !best || !views) { set_error("null argument"); return GL_ERR_INVALID; }
     if (reps < 1) { set_error("reps must be >= 1"); return GL_ERR_INVALID; }
-    StepPlan sp;
-    GL_TRY(plan_step(m, views, n_views, sp));
+    if (window < 1 || n_views < window || n_views % window != 0 || n_views / window > 64) {
+        set_error("n_views must be 1..64 windows of `window` views");
+        return GL_ERR_INVALID;
+    }
+    const int nw = n_views / window;
+    std::vector<StepPlan> plans(nw);
+    for (int w = 0; w < nw; w++) GL_TRY(plan_step(m, views + (size_t)w * window, window, plans[w]));
     const gl_exec_config saved = m->exec;
     const bool timing = m->prof.on;
     m->prof.on = false;
+    std::vector<Keyframe*> kfs;   // every keyframe the windows touch, once
+    for (const StepPlan& sp : plans)
+        for (int i = 0; i < sp.V; i++)
+            if (std::find(kfs.begin(), kfs.end(), sp.kfs[i]) == kfs.end()) kfs.push_back(sp.kfs[i]);
     Snapshot S;
-    gl_status st = snap_take(m, sp, S);
+    gl_status st = snap_take(m, kfs, S);
+    auto restore = [&]() { return snap_restore(m, kfs, S); };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == GL_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
         set_error("event creation failed");
@@ -1312,25 +1322,28 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
                     if (4 * ppl > ts) continue;
                     gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic, sg, 0};
                     m->exec = cand;
-                    // one eager step (sizes buffers, captures the graph), one replay, then reps timed replays
-                    for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, sp, nullptr);
+                    // per window: one eager step (sizes buffers, captures the graph) and one
+                    // replay; then reps timed replays of every window in turn
+                    for (int w = 0; w < nw && st == GL_OK; w++)
+                        for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, plans[w], nullptr);
                     if (st != GL_OK) break;
                     cudaEventRecord(e0, m->stream);
-                    for (int r = 0; r < reps && st == GL_OK; r++) st = run_step(m, sp, nullptr);
+                    for (int r = 0; r < reps && st == GL_OK; r++)
+                        for (int w = 0; w < nw && st == GL_OK; w++) st = run_step(m, plans[w], nullptr);
                     cudaEventRecord(e1, m->stream);
                     if (st != GL_OK) break;
                     if (cudaEventSynchronize(e1) != cudaSuccess) { st = GL_ERR_CUDA; break; }
                     float ms = 0.0f;
                     cudaEventElapsedTime(&ms, e0, e1);
-                    ms /= (float)reps;
+                    ms /= (float)(reps * nw);
                     if (best_t < 0.0f || ms < best_t) {
                         best_t = ms;
                         best_e = cand;
                     }
-                    st = snap_restore(m, sp, S);
+                    st = restore();
                 }
     }
-    if (st == GL_OK) st = snap_restore(m, sp, S);
+    if (st == GL_OK) st = restore();
     cudaStreamSynchronize(m->stream);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

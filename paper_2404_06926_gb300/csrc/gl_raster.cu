@@ -24,18 +24,20 @@
 // tile's list) of the last blended Gaussian, so the backward recomputes T by
 // division.
 //
-// Forward of a split tile, in two launches.  (1) Each segment item blends
+// Forward of a split tile, in four launches.  (1) Each segment item blends
 // its records per pixel from T = 1 without the stop rule and stores the
 // segment's transmittance product T_s, colour, depth and opacity sums and
-// last blended position.  (2) A combine pass walks each pixel's segments in
+// last blended position.  (2) A prefix pass walks each pixel's segments in
 // order with the incoming transmittance T_in (the product of the earlier
 // T_s): the stop rule fires inside segment s exactly when T_in * T_s falls
 // below 1e-4 (the running value inside s is T_in times the segment's own
-// running product, and that product only decreases), and that one segment
-// is replayed from T_in to find the stop and its truncated sums.  The pass
-// writes the pixel's outputs and, per segment, the backward's starting
-// state: the transmittance after the segment and the normalised colour
-// blended behind it (R = C_next + T_next * R_next over the later segments).
+// running product, and that product only decreases).  (3) Each segment
+// item replays its records from T_in for the pixels that stop in it (one
+// replay per warp, all segments in parallel) to find the stop and the
+// truncated sums.  (4) A finish pass writes the pixel's outputs and, per
+// segment, the backward's starting state: the transmittance after the
+// segment and the normalised colour blended behind it (R = C_next + T_next
+// * R_next over the later segments).
 // The transmittance is the product of the per-segment products, so it can
 // differ from a single running product by float rounding.
 //
@@ -57,12 +59,17 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kNG = 10;   // screen-space gradient slots per Gaussian
-constexpr int kSegFields = 8;   // per (segment item, pixel): see below
+constexpr int kSegFields = 16;  // per (segment item, pixel): see below
 
-// segstate fields.  After the segment pass: 0 T_s, 1-3 colour, 4 depth,
-// 5 opacity, 6 last position (as bits), 7 the incoming transmittance (set by
-// the combine pass).  After the combine pass: 0 transmittance after the
-// segment, 1-3 R (colour behind it, normalised), 4 R depth, 5 R opacity.
+// segstate fields of a segment item.  After the segment pass: 0 T_s, 1-3
+// colour, 4 depth, 5 opacity, 6 last position (as bits); 7 the incoming
+// transmittance (prefix pass); fields 0-6 replaced by the truncated sums in
+// the segment where the pixel stops (replay pass).  After the finish pass:
+// 0 transmittance after the segment, 1-3 R (colour behind it, normalised),
+// 4 R depth, 5 R opacity.  Fields 8-15 of a split tile's first item hold the
+// tile-level state of the pixel: 8 stop segment (bits; segments = none),
+// 9 transmittance entering it (or the final one), 10-12 colour, 13 depth,
+// 14 opacity summed over the segments before it, 15 last position there.
 __device__ __forceinline__ size_t seg_at(int w, int k, int p, int TS)
 {
     return ((size_t)w * kSegFields + k) * (size_t)(TS * TS) + p;
@@ -328,11 +335,11 @@ k_raster_fwd(RasterArgs A, RasterOut O)
     }
 }
 
-// Combine the segments of a split tile for one pixel block (the unit of its
-// first segment): outputs, then the backward's starting state per segment.
-template <int NB, int D>
-__device__ __forceinline__ void combine_item(int u, const RasterArgs& A, const RasterOut& O, float4* sr0,
-                                             float4* sr1, float4* sr2, uint32_t* spos, int lane)
+// Split tiles, pass 2 of 4 (after the segment pass): per pixel of a split
+// tile, the prefix of its segments' transmittance, the segment where the
+// stop rule fires (T_in * T_s < 1e-4) and the sums before it.
+template <int D>
+__device__ __forceinline__ void prefix_item(int u, const RasterArgs& A, int lane)
 {
     Unit U;
     unit_of<D>(u, A, U);
@@ -340,89 +347,125 @@ __device__ __forceinline__ void combine_item(int u, const RasterArgs& A, const R
     const LanePix<D> L(U, A.TS, lane);
     const int w0 = U.w, ns = U.nseg, TS = A.TS;
     float* S = A.segstate;
-    float Tb[D], C0[D], C1[D], C2[D], Dd[D], Oo[D];
-    uint32_t last[D];
-    int sstop[D];
-#pragma unroll
-    for (int j = 0; j < D; j++) {
-        Tb[j] = 1.0f; C0[j] = C1[j] = C2[j] = Dd[j] = Oo[j] = 0.0f;
-        last[j] = 0;
-        sstop[j] = ns;
-    }
-    // pass 1: prefix of the segments' transmittance; find each pixel's stop segment
-    for (int s = 0; s < ns; s++) {
-#pragma unroll
-        for (int j = 0; j < D; j++) {
-            if (!L.inside[j] || sstop[j] < ns) continue;
-            const int q = L.p[j], ws = w0 + s;
-            const float Ts = S[seg_at(ws, 0, q, TS)];
-            S[seg_at(ws, 7, q, TS)] = Tb[j];
-            if (__fmul_rn(Tb[j], Ts) < kTransMin) { sstop[j] = s; continue; }
-            C0[j] += Tb[j] * S[seg_at(ws, 1, q, TS)];
-            C1[j] += Tb[j] * S[seg_at(ws, 2, q, TS)];
-            C2[j] += Tb[j] * S[seg_at(ws, 3, q, TS)];
-            Dd[j] += Tb[j] * S[seg_at(ws, 4, q, TS)];
-            Oo[j] += Tb[j] * S[seg_at(ws, 5, q, TS)];
-            const uint32_t ls = __float_as_uint(S[seg_at(ws, 6, q, TS)]);
-            if (ls) last[j] = ls;
-            Tb[j] = __fmul_rn(Tb[j], Ts);
-        }
-    }
-    // pass 2: replay each stop segment from its incoming transmittance
-    bool replayed[D];
-#pragma unroll
-    for (int j = 0; j < D; j++) replayed[j] = false;
-    for (;;) {
-        int mine = 0x7fffffff;
-#pragma unroll
-        for (int j = 0; j < D; j++)
-            if (L.inside[j] && sstop[j] < ns && !replayed[j]) mine = min(mine, sstop[j]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mine = min(mine, __shfl_xor_sync(kFull, mine, off));
-        if (mine == 0x7fffffff) break;
-        const int s = mine;
-        float T2[D], c0[D], c1[D], c2[D], d2[D], o2[D];
-        uint32_t l2[D];
-        bool dn[D];
-#pragma unroll
-        for (int j = 0; j < D; j++) {
-            T2[j] = 1.0f; c0[j] = c1[j] = c2[j] = d2[j] = o2[j] = 0.0f;
-            l2[j] = 0;
-            dn[j] = !(L.inside[j] && sstop[j] == s && !replayed[j]);
-        }
-        const uint32_t a = U.trs + (uint32_t)s * (uint32_t)A.seg;
-        const uint32_t b = min(U.tre, a + (uint32_t)A.seg);
-        blend_range<NB, D>(A, a, b, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, true, Tb, dn, T2, c0, c1, c2,
-                           d2, o2, l2, sr0, sr1, sr2, spos, lane);
-#pragma unroll
-        for (int j = 0; j < D; j++) {
-            if (!(L.inside[j] && sstop[j] == s && !replayed[j])) continue;
-            replayed[j] = true;
-            C0[j] += Tb[j] * c0[j]; C1[j] += Tb[j] * c1[j]; C2[j] += Tb[j] * c2[j];
-            Dd[j] += Tb[j] * d2[j]; Oo[j] += Tb[j] * o2[j];
-            if (l2[j]) last[j] = l2[j];
-            Tb[j] = __fmul_rn(Tb[j], T2[j]);
-            const int q = L.p[j], ws = w0 + s;
-            S[seg_at(ws, 0, q, TS)] = T2[j];
-            S[seg_at(ws, 1, q, TS)] = c0[j];
-            S[seg_at(ws, 2, q, TS)] = c1[j];
-            S[seg_at(ws, 3, q, TS)] = c2[j];
-            S[seg_at(ws, 4, q, TS)] = d2[j];
-            S[seg_at(ws, 5, q, TS)] = o2[j];
-        }
-    }
-    // outputs, and the backward's starting state of every segment (back to front)
 #pragma unroll
     for (int j = 0; j < D; j++) {
         if (!L.inside[j]) continue;
-        const size_t p = L.pix(U, j);
-        O.rgb[3 * p] = C0[j]; O.rgb[3 * p + 1] = C1[j]; O.rgb[3 * p + 2] = C2[j];
-        if (O.depth) O.depth[p] = Dd[j];
-        if (O.opac) O.opac[p] = Oo[j];
-        O.Tfin[p] = Tb[j];
-        O.ncon[p] = last[j];
         const int q = L.p[j];
-        const int jl = sstop[j] < ns ? sstop[j] : ns - 1;
+        float Tb = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, oo = 0.f;
+        uint32_t last = 0;
+        int stop = ns;
+        for (int s = 0; s < ns; s++) {
+            const int ws = w0 + s;
+            const float Ts = S[seg_at(ws, 0, q, TS)];
+            S[seg_at(ws, 7, q, TS)] = Tb;
+            if (__fmul_rn(Tb, Ts) < kTransMin) { stop = s; break; }
+            c0 += Tb * S[seg_at(ws, 1, q, TS)];
+            c1 += Tb * S[seg_at(ws, 2, q, TS)];
+            c2 += Tb * S[seg_at(ws, 3, q, TS)];
+            dd += Tb * S[seg_at(ws, 4, q, TS)];
+            oo += Tb * S[seg_at(ws, 5, q, TS)];
+            const uint32_t ls = __float_as_uint(S[seg_at(ws, 6, q, TS)]);
+            if (ls) last = ls;
+            Tb = __fmul_rn(Tb, Ts);
+        }
+        S[seg_at(w0, 8, q, TS)] = __uint_as_float((uint32_t)stop);
+        S[seg_at(w0, 9, q, TS)] = Tb;
+        S[seg_at(w0, 10, q, TS)] = c0;
+        S[seg_at(w0, 11, q, TS)] = c1;
+        S[seg_at(w0, 12, q, TS)] = c2;
+        S[seg_at(w0, 13, q, TS)] = dd;
+        S[seg_at(w0, 14, q, TS)] = oo;
+        S[seg_at(w0, 15, q, TS)] = __uint_as_float(last);
+    }
+}
+
+// Split tiles, pass 3 of 4: each segment item replays its records from the
+// incoming transmittance for the pixels whose stop segment it is, and stores
+// their truncated sums in place of the segment pass's.
+template <int NB, int D>
+__device__ __forceinline__ void replay_item(int u, const RasterArgs& A, float4* sr0, float4* sr1, float4* sr2,
+                                            uint32_t* spos, int lane)
+{
+    Unit U;
+    unit_of<D>(u, A, U);
+    if (U.nseg < 2) return;
+    const LanePix<D> L(U, A.TS, lane);
+    const int w0 = U.w - U.j, TS = A.TS;
+    float* S = A.segstate;
+    float Tin[D], T[D], c0[D], c1[D], c2[D], dd[D], oo[D];
+    uint32_t last[D];
+    bool dn[D];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        T[j] = 1.0f; c0[j] = c1[j] = c2[j] = dd[j] = oo[j] = 0.0f;
+        last[j] = 0;
+        Tin[j] = 1.0f;
+        dn[j] = true;
+        if (!L.inside[j]) continue;
+        const int q = L.p[j];
+        if ((int)__float_as_uint(S[seg_at(w0, 8, q, TS)]) != U.j) continue;
+        Tin[j] = S[seg_at(w0, 9, q, TS)];
+        dn[j] = false;
+        any = true;
+    }
+    if (!__any_sync(kFull, any)) return;
+    blend_range<NB, D>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, true, Tin, dn, T, c0, c1, c2,
+                       dd, oo, last, sr0, sr1, sr2, spos, lane);
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        if (!L.inside[j]) continue;
+        const int q = L.p[j];
+        if ((int)__float_as_uint(S[seg_at(w0, 8, q, TS)]) != U.j) continue;
+        S[seg_at(U.w, 0, q, TS)] = T[j];
+        S[seg_at(U.w, 1, q, TS)] = c0[j];
+        S[seg_at(U.w, 2, q, TS)] = c1[j];
+        S[seg_at(U.w, 3, q, TS)] = c2[j];
+        S[seg_at(U.w, 4, q, TS)] = dd[j];
+        S[seg_at(U.w, 5, q, TS)] = oo[j];
+        S[seg_at(U.w, 6, q, TS)] = __uint_as_float(last[j]);
+    }
+}
+
+// Split tiles, pass 4 of 4: per pixel, the outputs (sums before the stop
+// segment plus its truncated sums) and, back to front over the segments up
+// to the stop, the backward's starting state of each.
+template <int D>
+__device__ __forceinline__ void finish_item(int u, const RasterArgs& A, const RasterOut& O, int lane)
+{
+    Unit U;
+    unit_of<D>(u, A, U);
+    if (U.j != 0 || U.nseg < 2) return;
+    const LanePix<D> L(U, A.TS, lane);
+    const int w0 = U.w, ns = U.nseg, TS = A.TS;
+    float* S = A.segstate;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        if (!L.inside[j]) continue;
+        const int q = L.p[j];
+        const int stop = (int)__float_as_uint(S[seg_at(w0, 8, q, TS)]);
+        float Tb = S[seg_at(w0, 9, q, TS)];
+        float c0 = S[seg_at(w0, 10, q, TS)], c1 = S[seg_at(w0, 11, q, TS)], c2 = S[seg_at(w0, 12, q, TS)];
+        float dd = S[seg_at(w0, 13, q, TS)], oo = S[seg_at(w0, 14, q, TS)];
+        uint32_t last = __float_as_uint(S[seg_at(w0, 15, q, TS)]);
+        if (stop < ns) {
+            const int ws = w0 + stop;
+            c0 += Tb * S[seg_at(ws, 1, q, TS)];
+            c1 += Tb * S[seg_at(ws, 2, q, TS)];
+            c2 += Tb * S[seg_at(ws, 3, q, TS)];
+            dd += Tb * S[seg_at(ws, 4, q, TS)];
+            oo += Tb * S[seg_at(ws, 5, q, TS)];
+            const uint32_t ls = __float_as_uint(S[seg_at(ws, 6, q, TS)]);
+            if (ls) last = ls;
+            Tb = __fmul_rn(Tb, S[seg_at(ws, 0, q, TS)]);
+        }
+        const size_t p = L.pix(U, j);
+        O.rgb[3 * p] = c0; O.rgb[3 * p + 1] = c1; O.rgb[3 * p + 2] = c2;
+        if (O.depth) O.depth[p] = dd;
+        if (O.opac) O.opac[p] = oo;
+        O.Tfin[p] = Tb;
+        O.ncon[p] = last;
+        const int jl = stop < ns ? stop : ns - 1;
         float R0 = 0.f, R1 = 0.f, R2 = 0.f, RD = 0.f, RO = 0.f;
         for (int s = ns - 1; s >= 0; s--) {
             const int ws = w0 + s;
@@ -446,9 +489,21 @@ __device__ __forceinline__ void combine_item(int u, const RasterArgs& A, const R
     }
 }
 
+template <int D>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_seg_prefix(RasterArgs A)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, true);
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    while (u < nunits) {
+        prefix_item<D>(u, A, lane);
+        if (!A.work) break;
+        u = next_unit(A.work, lane);
+    }
+}
+
 template <int NB, int D>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
-k_raster_combine(RasterArgs A, RasterOut O)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_seg_replay(RasterArgs A)
 {
     __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
     __shared__ uint32_t spos[kWarpsPerBlock][32 * NB];
@@ -456,7 +511,20 @@ k_raster_combine(RasterArgs A, RasterOut O)
     const int nunits = units_of(A, true);
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
     while (u < nunits) {
-        combine_item<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
+        replay_item<NB, D>(u, A, sr0[w], sr1[w], sr2[w], spos[w], lane);
+        if (!A.work) break;
+        u = next_unit(A.work, lane);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_seg_finish(RasterArgs A, RasterOut O)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, true);
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    while (u < nunits) {
+        finish_item<D>(u, A, O, lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
     }
@@ -759,10 +827,16 @@ void fwd_launch(const RasterArgs& A, const RasterOut& O, int64_t units, int64_t 
     k_raster_fwd<NB, D><<<grid_for(k_raster_fwd<NB, D>, (NB - 1) * 4 + D, units, persistent), 32 * kWarpsPerBlock,
                           0, s>>>(a1, O);
     if (split_units > 0) {
-        RasterArgs a2 = A;
+        // persistent grids take units from counters 2-4
+        RasterArgs a2 = A, a3 = A, a4 = A;
         a2.work = work ? work + 2 : nullptr;
-        k_raster_combine<NB, D><<<grid_for(k_raster_combine<NB, D>, 8 + (NB - 1) * 4 + D, split_units, persistent),
-                                  32 * kWarpsPerBlock, 0, s>>>(a2, O);
+        a3.work = work ? work + 3 : nullptr;
+        a4.work = work ? work + 4 : nullptr;
+        k_seg_prefix<D><<<grid_for(k_seg_prefix<D>, 80 + D, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a2);
+        k_seg_replay<NB, D><<<grid_for(k_seg_replay<NB, D>, 88 + (NB - 1) * 4 + D, split_units, persistent),
+                              32 * kWarpsPerBlock, 0, s>>>(a3);
+        k_seg_finish<D><<<grid_for(k_seg_finish<D>, 100 + D, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(
+            a4, O);
     }
 }
 
@@ -821,14 +895,14 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     GL_TRY(v.ncon.reserve(4 * P));
     if (v.ntiles == 0) return GL_OK;
     GL_TRY(check_exec(v));
-    GL_TRY(v.work.reserve(16));
+    GL_TRY(v.work.reserve(32));
     const int64_t split = split_items_bound(v);
     if (split > 0) GL_TRY(v.segstate.reserve(sizeof(float) * kSegFields * (size_t)(v.Ts * v.Ts) * (size_t)split));
     PhaseScope ps(v.prof, PH_RASTER_FWD, s);
     int* work = nullptr;
     if (v.persistent) {
         work = v.work.as<int>();
-        GL_CUDA_TRY(cudaMemsetAsync(work, 0, 4 * sizeof(int), s));
+        GL_CUDA_TRY(cudaMemsetAsync(work, 0, 8 * sizeof(int), s));
     }
     const RasterArgs A = make_args(v, nullptr);
     RasterOut O{rgb, depth, opac, v.Tfin.as<float>(), v.ncon.as<uint32_t>()};
@@ -843,7 +917,7 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
         else if (v.pd == 2) fwd_launch<2, 2>(A, O, units, split_units, v.persistent, work, s);
         else fwd_launch<2, 4>(A, O, units, split_units, v.persistent, work, s);
     }
-    count_launches(split_units > 0 ? 2 : 1);
+    count_launches(split_units > 0 ? 4 : 1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
 }
@@ -854,7 +928,7 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     const size_t pairs = (size_t)v.n * v.V;
     GL_TRY(v.g2d.reserve(sizeof(float) * kNG * std::max<size_t>(pairs, 1)));
     GL_TRY(check_exec(v));
-    GL_TRY(v.work.reserve(16));
+    GL_TRY(v.work.reserve(32));
     PhaseScope ps(v.prof, PH_RASTER_BWD, s);
     const bool det = v.det && v.ntiles > 0 && v.I != 0;
     const int nblk = blocks_per_tile(v);

@@ -55,7 +55,7 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     assert b"null" in L.gl_last_error()
     e = binding.ExecConfig(1, 0, 32, 1, 0, 0)
     assert L.gl_map_set_exec(None, ctypes.byref(e)) == 1
-    assert L.gl_map_autotune(None, None, 1, 1, 0, None, None) == 1
+    assert L.gl_map_autotune(None, None, 1, 1, 1, 0, None, None) == 1
     assert L.gl_map_load(None, None, 0) == 1
     sc = binding.ServerConfig()
     assert L.gl_server_config_default(ctypes.byref(sc)) == 0 and sc.queue_capacity == 256 and sc.render_batch == 8

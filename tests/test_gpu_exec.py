@@ -247,3 +247,20 @@ def test_set_config_rejects_bad_values_and_keeps_the_map():
     binding.lib().gl_map_get_config(m._h, binding.C.byref(m2))
     assert abs(m2.lr_pos - 1.6e-4) < 1e-10 and m2.tile_size == 16
     assert m.get_exec() == before
+
+
+def test_autotune_over_several_single_view_windows_restores_the_map():
+    params, cams, targets = _window_scene()
+    m = _map(params)
+    views = [(10 + i, cams[i], targets[i]) for i in range(3)]
+    for v in views:
+        m.optimize_step([v])
+    before = m.get_params()
+    E = [m.exposure(10 + i) for i in range(3)]
+    best, ms = m.autotune(views, reps=2, keep_tile_size=True, window=1)
+    assert ms > 0 and best["tile_size"] == 0
+    after = m.get_params()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    for i in range(3):
+        assert np.array_equal(m.exposure(10 + i), E[i])
