@@ -10,7 +10,9 @@
 // five moment maps separably over a 5-pixel halo, forms the SSIM map and its
 // partials w.r.t. (mu_x, E[x^2], E[xy]), blurs those back (the adjoint of a
 // zero-padded symmetric correlation is the same correlation) and writes
-// dL/dC = A^T dL/dE[C].  Per-CTA partial sums of |.|, SSIM and dL/dE are
+// dL/dC = A^T dL/dE[C].  In every pass a thread slides the 11 taps along a
+// run of 7-8 outputs held in registers, so each shared-memory value is read
+// once per run rather than once per tap and output.  Per-CTA partial sums of |.|, SSIM and dL/dE are
 // reduced afterwards in a fixed order, in double.
 #include "gl_internal.h"
 
@@ -26,6 +28,10 @@ constexpr int RA = LT + 4 * HW;       // 52
 constexpr int RB = LT + 2 * HW;       // 42
 constexpr int kThreads = 256;
 constexpr int kNP = 14;               // partials per CTA: 12 dL/dE, sum|d|, sum SSIM
+constexpr int HR = 7;                 // outputs per thread, horizontal moment pass (RB = 6 x 7)
+constexpr int VR = 7;                 // outputs per thread, vertical moment pass
+constexpr int AR = 8;                 // outputs per thread, adjoint passes (LT = 4 x 8)
+static_assert(RB % HR == 0 && RB % VR == 0 && LT % AR == 0, "run lengths must tile the maps");
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -105,76 +111,117 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
             ys[e] = y;
         }
         __syncthreads();
-        for (int e = tid; e < RA * RB; e += kThreads) {
-            const int r = e / RB, c = e % RB;
-            float s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+        // horizontal pass of the five moments: a thread slides the 11 taps
+        // along a run of HR outputs of one row, loading each input once
+        for (int e = tid; e < RA * (RB / HR); e += kThreads) {
+            const int r = e / (RB / HR), c0 = (e % (RB / HR)) * HR;
+            float xv[HR + 10], yv[HR + 10];
 #pragma unroll
-            for (int k = 0; k < 11; k++) {
-                const float xv = xs[r * RA + c + k], yv = ys[r * RA + c + k], wk = wt[k];
-                s0 += wk * xv; s1 += wk * yv; s2 += wk * xv * xv; s3 += wk * yv * yv; s4 += wk * xv * yv;
-            }
-            hm[e] = s0; hm[RA * RB + e] = s1; hm[2 * RA * RB + e] = s2;
-            hm[3 * RA * RB + e] = s3; hm[4 * RA * RB + e] = s4;
-        }
-        __syncthreads();
-        for (int e = tid; e < RB * RB; e += kThreads) {
-            const int r = e / RB, c = e % RB;
-            const int gx = ox - HW + c, gy = oy - HW + r;
-            float ga = 0.0f, gb = 0.0f, gc = 0.0f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+            for (int k = 0; k < HR + 10; k++) { xv[k] = xs[r * RA + c0 + k]; yv[k] = ys[r * RA + c0 + k]; }
+#pragma unroll
+            for (int o = 0; o < HR; o++) {
+                float s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
 #pragma unroll
                 for (int k = 0; k < 11; k++) {
-                    const int i = (r + k) * RB + c;
-                    const float wk = wt[k];
-                    mx += wk * hm[i]; my += wk * hm[RA * RB + i]; exx += wk * hm[2 * RA * RB + i];
-                    eyy += wk * hm[3 * RA * RB + i]; exy += wk * hm[4 * RA * RB + i];
+                    const float x = xv[o + k], y = yv[o + k], wk = wt[k];
+                    s0 += wk * x; s1 += wk * y; s2 += wk * x * x; s3 += wk * y * y; s4 += wk * x * y;
                 }
-                const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-                const float N1 = 2.f * mx * my + kC1, N2 = 2.f * sxy + kC2;
-                const float D1 = mx * mx + my * my + kC1, D2 = sxx + syy + kC2;
-                const float iD = 1.0f / (D1 * D2);
-                const float S = N1 * N2 * iD;
-                if (r >= HW && r < HW + LT && c >= HW && c < HW + LT) sacc += S;
-                const float dN1 = N2 * iD, dN2 = N1 * iD, dD1 = -S / D1, dD2 = -S / D2;
-                const float dmx = dN1 * 2.f * my - dN2 * 2.f * my + dD1 * 2.f * mx - dD2 * 2.f * mx;
-                ga = gS * dmx;
-                gb = gS * dD2;
-                gc = gS * 2.f * dN2;
+                const int i = r * RB + c0 + o;
+                hm[i] = s0; hm[RA * RB + i] = s1; hm[2 * RA * RB + i] = s2;
+                hm[3 * RA * RB + i] = s3; hm[4 * RA * RB + i] = s4;
             }
-            gmap[e] = ga; gmap[RB * RB + e] = gb; gmap[2 * RB * RB + e] = gc;
         }
         __syncthreads();
-        for (int e = tid; e < RB * LT; e += kThreads) {
-            const int r = e / LT, c = e % LT;
-            float a = 0, b = 0, cc = 0;
+        // vertical pass, SSIM and its partials: a thread takes a run of VR
+        // rows of one column, one moment map at a time
+        for (int e = tid; e < RB * (RB / VR); e += kThreads) {
+            const int c = e % RB, r0 = (e / RB) * VR;
+            float mom[5][VR];
 #pragma unroll
-            for (int k = 0; k < 11; k++) {
-                const int i = r * RB + c + k;
-                const float wk = wt[k];
-                a += wk * gmap[i]; b += wk * gmap[RB * RB + i]; cc += wk * gmap[2 * RB * RB + i];
+            for (int m = 0; m < 5; m++) {
+                float col[VR + 10];
+#pragma unroll
+                for (int k = 0; k < VR + 10; k++) col[k] = hm[m * RA * RB + (r0 + k) * RB + c];
+#pragma unroll
+                for (int o = 0; o < VR; o++) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 11; k++) a += wt[k] * col[o + k];
+                    mom[m][o] = a;
+                }
             }
-            hg[e] = a; hg[RB * LT + e] = b; hg[2 * RB * LT + e] = cc;
+#pragma unroll
+            for (int o = 0; o < VR; o++) {
+                const int r = r0 + o;
+                const int gx = ox - HW + c, gy = oy - HW + r;
+                float ga = 0.0f, gb = 0.0f, gc = 0.0f;
+                if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                    const float mx = mom[0][o], my = mom[1][o], exx = mom[2][o], eyy = mom[3][o], exy = mom[4][o];
+                    const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                    const float N1 = 2.f * mx * my + kC1, N2 = 2.f * sxy + kC2;
+                    const float D1 = mx * mx + my * my + kC1, D2 = sxx + syy + kC2;
+                    const float iD = 1.0f / (D1 * D2);
+                    const float S = N1 * N2 * iD;
+                    if (r >= HW && r < HW + LT && c >= HW && c < HW + LT) sacc += S;
+                    const float dN1 = N2 * iD, dN2 = N1 * iD, dD1 = -S / D1, dD2 = -S / D2;
+                    const float dmx = dN1 * 2.f * my - dN2 * 2.f * my + dD1 * 2.f * mx - dD2 * 2.f * mx;
+                    ga = gS * dmx;
+                    gb = gS * dD2;
+                    gc = gS * 2.f * dN2;
+                }
+                const int i = r * RB + c;
+                gmap[i] = ga; gmap[RB * RB + i] = gb; gmap[2 * RB * RB + i] = gc;
+            }
         }
         __syncthreads();
-        for (int e = tid; e < LT * LT; e += kThreads) {
-            const int r = e / LT, c = e % LT;
-            const int gx = ox + c, gy = oy + r;
-            float g = 0.0f;
-            if (gx < W && gy < H) {
-                float a = 0, b = 0, cc = 0;
+        // adjoint, horizontal: runs of AR outputs of a row
+        for (int e = tid; e < RB * (LT / AR); e += kThreads) {
+            const int r = e / (LT / AR), c0 = (e % (LT / AR)) * AR;
 #pragma unroll
-                for (int k = 0; k < 11; k++) {
-                    const int i = (r + k) * LT + c;
-                    const float wk = wt[k];
-                    a += wk * hg[i]; b += wk * hg[RB * LT + i]; cc += wk * hg[2 * RB * LT + i];
+            for (int m = 0; m < 3; m++) {
+                float row[AR + 10];
+#pragma unroll
+                for (int k = 0; k < AR + 10; k++) row[k] = gmap[m * RB * RB + r * RB + c0 + k];
+#pragma unroll
+                for (int o = 0; o < AR; o++) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 11; k++) a += wt[k] * row[o + k];
+                    hg[m * RB * LT + r * LT + c0 + o] = a;
                 }
-                const float x = xs[(r + 2 * HW) * RA + c + 2 * HW], y = ys[(r + 2 * HW) * RA + c + 2 * HW];
-                const float d = x - y;
-                l1acc += fabsf(d);
-                g = a + 2.f * x * b + y * cc + gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
             }
-            dch[ch * LT * LT + e] = g;
+        }
+        __syncthreads();
+        // adjoint, vertical, and dL/dE[C] of the tile's pixels: runs of AR rows of a column
+        for (int e = tid; e < LT * (LT / AR); e += kThreads) {
+            const int c = e % LT, r0 = (e / LT) * AR;
+            float acc[3][AR];
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                float col[AR + 10];
+#pragma unroll
+                for (int k = 0; k < AR + 10; k++) col[k] = hg[m * RB * LT + (r0 + k) * LT + c];
+#pragma unroll
+                for (int o = 0; o < AR; o++) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 11; k++) a += wt[k] * col[o + k];
+                    acc[m][o] = a;
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < AR; o++) {
+                const int r = r0 + o;
+                const int gx = ox + c, gy = oy + r;
+                float g = 0.0f;
+                if (gx < W && gy < H) {
+                    const float x = xs[(r + 2 * HW) * RA + c + 2 * HW], y = ys[(r + 2 * HW) * RA + c + 2 * HW];
+                    const float d = x - y;
+                    l1acc += fabsf(d);
+                    g = acc[0][o] + 2.f * x * acc[1][o] + y * acc[2][o] + gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
+                }
+                dch[ch * LT * LT + r * LT + c] = g;
+            }
         }
         __syncthreads();
     }
