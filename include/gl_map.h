@@ -210,6 +210,13 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *                    step's results are bit-identical from run to run (at
  *                    the cost of one more pass over 40 bytes per instance
  *                    and pixel block); batch_depth is then 32.
+ *   exact_cull       1 (default): a (Gaussian, tile) pair of the 3-sigma
+ *                    rectangle gets an instance only if the Gaussian can
+ *                    reach alpha >= 1/255 at a pixel centre of the tile
+ *                    (closed-form minimum of its quadratic form over the
+ *                    tile, with a 2^-7 slack); renders are bit-identical
+ *                    either way, the instance lists (and contributor
+ *                    positions) shorter.
  *   segment          0, or a power of two in 64..65536: a tile whose list
  *                    holds at least 2 x segment Gaussians is rendered and
  *                    back-propagated as segments of `segment` consecutive
@@ -218,7 +225,7 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *                    single running product up to float rounding.
  * Apart from deterministic = 1, results differ between runs only by the
  * order of the backward's float atomics.
- * gl_map_create starts with {0, 0, 32, 1, 0, 0, 0}.  Errors: GL_ERR_INVALID. */
+ * gl_map_create starts with {0, 0, 32, 1, 0, 0, 0, 1}.  Errors: GL_ERR_INVALID. */
 typedef struct {
     int32_t use_graphs;
     int32_t persistent;
@@ -227,7 +234,7 @@ typedef struct {
     int32_t tile_size;
     int32_t deterministic;
     int32_t segment;
-    int32_t reserved;
+    int32_t exact_cull;
 } gl_exec_config;
 
 GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
@@ -435,7 +442,8 @@ GL_API gl_status gl_ctx_create(void* cuda_stream, gl_ctx** out);
 GL_API gl_status gl_ctx_destroy(gl_ctx* ctx);
 
 /* Raster execution of this context's calls: batch_depth, pixels_per_lane,
- * persistent, deterministic and segment as in gl_exec_config (use_graphs
+ * persistent, deterministic, segment and exact_cull as in gl_exec_config
+ * (defaults 32, 1, 0, 0, 0, 1; use_graphs
  * and tile_size are ignored: the tile size is each call's argument).  A
  * pixels_per_lane above tile_size / 4 is lowered to it.  Errors:
  * GL_ERR_INVALID. */

@@ -76,10 +76,10 @@ def _load():
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int, C.c_double
         lib.orc_sh_basis.argtypes = [i32, dbl, dbl, dbl, P, P]
-        lib.orc_preprocess.argtypes = [i64, i32, P, P, P, P, P, P, i32] + [P] * 10
+        lib.orc_preprocess.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32] + [P] * 11
         lib.orc_num_instances.argtypes = [i64, P]
         lib.orc_num_instances.restype = i64
-        lib.orc_bin.argtypes = [i64, P, P, P, i32, i32, P, P, P]
+        lib.orc_bin.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P]
         lib.orc_render.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, dbl, dbl, P, P, P, P, P, P, P]
         lib.orc_render_bruteforce.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, i32,
                                               P, P, P, P, P]
@@ -90,6 +90,8 @@ def _load():
         lib.orc_adam.argtypes = [i64, i32, P, P, P, P, P, dbl, dbl, dbl, dbl, i64]
         lib.orc_expf_decision.argtypes = [C.c_float]
         lib.orc_expf_decision.restype = C.c_float
+        lib.orc_logf_decision.argtypes = [C.c_float]
+        lib.orc_logf_decision.restype = C.c_float
         lib.orc_uniform.argtypes = [C.c_uint64, C.c_uint64]
         lib.orc_uniform.restype = dbl
         lib.orc_sky.argtypes = [i64, dbl, C.c_uint64, P, P]
@@ -147,8 +149,10 @@ def tiles(cam: dict, Ts: int):
     return (int(cam["width"]) + Ts - 1) // Ts, (int(cam["height"]) + Ts - 1) // Ts
 
 
-def preprocess(params: dict, cam: dict, Ts: int = 16) -> dict:
-    """Eq. 1-3 and the SH colour for every Gaussian (Sec. III-A)."""
+def preprocess(params: dict, cam: dict, Ts: int = 16, cull: bool = True) -> dict:
+    """Eq. 1-3 and the SH colour for every Gaussian (Sec. III-A).  With cull,
+    a tile of the 3-sigma rectangle counts only if the Gaussian can reach
+    alpha >= 1/255 at one of its pixel centres (exact tile culling)."""
     lib = _load()
     m, ls, q, lg, sh = _prm(params)
     n = m.shape[0]
@@ -156,13 +160,15 @@ def preprocess(params: dict, cam: dict, Ts: int = 16) -> dict:
     out = dict(radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                touched=np.zeros(n, np.uint32), depth_bits=np.zeros(n, np.uint32),
                mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n),
-               rgb=np.zeros((n, 3)), depth=np.zeros(n), flags=np.zeros(n, np.uint8))
+               rgb=np.zeros((n, 3)), depth=np.zeros(n), flags=np.zeros(n, np.uint8),
+               cullp=np.zeros((n, 8), np.float32))
     c = make_cam(cam)
-    lib.orc_preprocess(n, deg, _p(m), _p(ls), _p(q), _p(lg), _p(sh), C.byref(c), Ts,
+    lib.orc_preprocess(n, deg, _p(m), _p(ls), _p(q), _p(lg), _p(sh), C.byref(c), Ts, int(bool(cull)),
                        _p(out["radius"]), _p(out["rect"]), _p(out["touched"]), _p(out["depth_bits"]),
                        _p(out["mean2d"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
-                       _p(out["depth"]), _p(out["flags"]))
+                       _p(out["depth"]), _p(out["flags"]), _p(out["cullp"]))
     out["Ts"] = Ts
+    out["cull"] = bool(cull)
     return out
 
 
@@ -175,7 +181,8 @@ def bin_instances(pre: dict, cam: dict) -> dict:
     keys = np.zeros(max(I, 1), np.uint64)
     vals = np.zeros(max(I, 1), np.uint32)
     ranges = np.zeros((TX * TY, 2), np.uint32)
-    lib.orc_bin(n, _p(pre["rect"]), _p(pre["touched"]), _p(pre["depth_bits"]), TX, TY,
+    lib.orc_bin(n, _p(pre["rect"]), _p(pre["touched"]), _p(pre["depth_bits"]),
+                _p(pre["cullp"]) if pre.get("cull", False) else None, pre["Ts"], TX, TY,
                 _p(keys), _p(vals), _p(ranges))
     return dict(keys=keys[:I], vals=vals[:I], ranges=ranges, I=I, TX=TX, TY=TY)
 
@@ -269,6 +276,11 @@ def expf_decision(x: float) -> float:
     return float(_load().orc_expf_decision(float(x)))
 
 
+def logf_decision(x: float) -> float:
+    """log as the float32 decision path evaluates it (see gl_oracle.c)."""
+    return float(_load().orc_logf_decision(float(x)))
+
+
 def uniform(seed: int, i: int) -> float:
     return _load().orc_uniform(C.c_uint64(seed), C.c_uint64(i))
 
@@ -311,9 +323,9 @@ def init_gaussians(xyz, rgb, depth, fx, opacity=OPACITY_FG, scale=None, sh_deg=3
                 quats=q.astype(np.float32), logits=lg.astype(np.float32), sh=sh.astype(np.float32))
 
 
-def forward(params: dict, cam: dict, Ts: int = 16):
+def forward(params: dict, cam: dict, Ts: int = 16, cull: bool = True):
     """Preprocess, bin and render: returns (pre, bins, image dict)."""
-    pre = preprocess(params, cam, Ts)
+    pre = preprocess(params, cam, Ts, cull)
     bins = bin_instances(pre, cam)
     img = render(pre, bins, cam)
     return pre, bins, img

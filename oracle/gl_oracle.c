@@ -149,12 +149,81 @@ float orc_expf_decision(float x)
 }
 
 /* ------------------------------------------------------------------------- */
+/* log in the float32 decision path: x = m 2^e with m in [sqrt(1/2),        */
+/* sqrt(2)) taken from the bits, ln m = 2 atanh(s) with s = (m-1)/(m+1) by   */
+/* its odd series to s^11 (|s| <= 0.1716, truncation 2 s^13/13 < 2e-11), then */
+/* e ln2 with ln2 split as in the exp above.  A fixed sequence of correctly   */
+/* rounded float32 operations.                                               */
+/* ------------------------------------------------------------------------- */
+float orc_logf_decision(float x)
+{
+    if (!(x > 0.0f)) return -INFINITY;
+    if (x == INFINITY) return INFINITY;
+    uint32_t bits;
+    int e0 = 0;
+    if (x < 1.17549435e-38f) { x = x * 16777216.0f; e0 = -24; }   /* subnormal: scale by 2^24 */
+    memcpy(&bits, &x, 4);
+    int e = (int)((bits >> 23) & 0xffu) - 126 + e0;
+    uint32_t mb = (bits & 0x7fffffu) | 0x3f000000u;                  /* m in [0.5, 1) */
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m < 0.70710678118654752f) { m = m * 2.0f; e -= 1; }
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.42860682030941723212e-6f;
+    const float sv = (m - 1.0f) / (m + 1.0f);
+    const float s2 = sv * sv;
+    float p = (float)(2.0 / 11.0);
+    p = p * s2 + (float)(2.0 / 9.0);
+    p = p * s2 + (float)(2.0 / 7.0);
+    p = p * s2 + (float)(2.0 / 5.0);
+    p = p * s2 + (float)(2.0 / 3.0);
+    p = p * s2 + 2.0f;
+    const float lm = p * sv;
+    const float fe = (float)e;
+    return fe * ln2_hi + (fe * ln2_lo + lm);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact tile culling, float32 decision path: can the Gaussian reach alpha   */
+/* >= 1/255 at a pixel centre of the tile whose centres span [X0, X0+T1] x    */
+/* [Y0, Y0+T1]?  q(d) = A dx^2 + 2B dx dy + C dy^2 (the conic) is convex, so  */
+/* off the centre its minimum over the rectangle lies on an edge; on an edge  */
+/* x = const the 1-D minimiser is dy = (-B/C) dx, on y = const dx = (-B/A) dy, */
+/* clamped to the edge.  Kept iff that minimum is <= ks, where ks = 2 ln(255  */
+/* o) with a slack of 2^-7 (relative and absolute) so that every dropped tile */
+/* stays below the alpha threshold by a margin far above the rounding of the  */
+/* per-pixel alpha.  cp = (u, v, A, B, C, ks, -B/C, -B/A).                    */
+/* ------------------------------------------------------------------------- */
+static int tile_keep(const float cp[8], float X0, float Y0, float T1)
+{
+    const float u = cp[0], v = cp[1], A = cp[2], B = cp[3], C = cp[4], ks = cp[5], bc = cp[6], ba = cp[7];
+    const float dx0 = X0 - u, dx1 = (X0 + T1) - u, dy0 = Y0 - v, dy1 = (Y0 + T1) - v;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return 1;
+    const float B2 = 2.0f * B;
+    float qmin = INFINITY;
+    const float dxs[2] = { dx0, dx1 }, dys[2] = { dy0, dy1 };
+    for (int i = 0; i < 2; i++) {
+        const float dx = dxs[i];
+        const float t = fminf(fmaxf(bc * dx, dy0), dy1);
+        const float q = ((A * dx) * dx + (B2 * dx) * t) + (C * t) * t;
+        qmin = fminf(qmin, q);
+    }
+    for (int i = 0; i < 2; i++) {
+        const float dy = dys[i];
+        const float t = fminf(fmaxf(ba * dy, dx0), dx1);
+        const float q = ((A * t) * t + (B2 * t) * dy) + (C * dy) * dy;
+        qmin = fminf(qmin, q);
+    }
+    return qmin <= ks;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Float32 decision path: cull, radius, rectangle, depth key (Eq. 2-3).      */
 /* Returns 1 if the Gaussian is kept.                                         */
 /* ------------------------------------------------------------------------- */
-static int project_f32(const double* mud, const double* lsd, const double* qd,
+static int project_f32(const double* mud, const double* lsd, const double* qd, double logit,
                        const orc_cam* cam, int Ts,
-                       int32_t* radius, int32_t rect[4], uint32_t* dbits)
+                       int32_t* radius, int32_t rect[4], uint32_t* dbits, float cp[8])
 {
     float R[9], t[3], mu[3], ls[3], q[4];
     for (int i = 0; i < 9; i++) R[i] = (float)cam->R[i];
@@ -236,7 +305,35 @@ static int project_f32(const double* mud, const double* lsd, const double* qd,
     if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) return 0;
     *radius = (r > 2.0e9f) ? 2000000000 : (int32_t)r;
     memcpy(dbits, &z, 4);
+    /* exact tile culling inputs: mu', conic, 2 ln(255 o) with slack */
+    const float og = 1.0f / (1.0f + orc_expf_decision(-(float)logit));
+    const float kap = 2.0f * orc_logf_decision(255.0f * og);
+    cp[0] = u;
+    cp[1] = v;
+    cp[2] = c / det;
+    cp[3] = -b / det;
+    cp[4] = a / det;
+    cp[5] = kap + (kap * 0.0078125f + 0.0078125f);
+    cp[6] = -cp[3] / cp[4];
+    cp[7] = -cp[3] / cp[2];
     return 1;
+}
+
+/* The exact culling applies to rectangles of at most 64 tiles (a larger    */
+/* one keeps all its tiles, which is always allowed: it only costs          */
+/* instances).                                                               */
+#define OR_CULL_MAX_TILES 64
+
+/* Tiles of the rectangle kept by the exact culling (all with cull = 0).    */
+static uint32_t kept_tiles(const int32_t rc[4], const float cp[8], int Ts, int cull)
+{
+    const int area = (rc[2] - rc[0]) * (rc[3] - rc[1]);
+    if (!cull || area > OR_CULL_MAX_TILES) return (uint32_t)area;
+    uint32_t k = 0;
+    const float T1 = (float)(Ts - 1);
+    for (int ty = rc[1]; ty < rc[3]; ty++)
+        for (int tx = rc[0]; tx < rc[2]; tx++) k += (uint32_t)tile_keep(cp, (float)(tx * Ts), (float)(ty * Ts), T1);
+    return k;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -343,21 +440,25 @@ static void project_f64(const double* mu, const double* ls, const double* q, dou
 /* ------------------------------------------------------------------------- */
 /* Preprocess every Gaussian.                                                */
 /* ------------------------------------------------------------------------- */
+/* cull = 1: exact tile culling (touched counts only the kept tiles; cullp, */
+/* 8 floats per Gaussian, holds the test's inputs for orc_bin).              */
 void orc_preprocess(int64_t n, int deg, const double* means, const double* lscale,
                     const double* quat, const double* logit, const double* sh,
-                    const orc_cam* cam, int Ts,
+                    const orc_cam* cam, int Ts, int cull,
                     int32_t* radius, int32_t* rect, uint32_t* touched, uint32_t* dbits,
                     double* mean2d, double* conic, double* opac, double* rgb, double* depth,
-                    uint8_t* flags)
+                    uint8_t* flags, float* cullp)
 {
     int nb = (deg + 1) * (deg + 1);
     for (int64_t g = 0; g < n; g++) {
         int32_t r = 0, rc[4] = { 0, 0, 0, 0 };
         uint32_t db = 0;
-        int keep = project_f32(means + 3 * g, lscale + 3 * g, quat + 4 * g, cam, Ts, &r, rc, &db);
+        float cp[8] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+        int keep = project_f32(means + 3 * g, lscale + 3 * g, quat + 4 * g, logit[g], cam, Ts, &r, rc, &db, cp);
         radius[g] = keep ? r : 0;
         for (int i = 0; i < 4; i++) rect[4 * g + i] = keep ? rc[i] : 0;
-        touched[g] = keep ? (uint32_t)((rc[2] - rc[0]) * (rc[3] - rc[1])) : 0;
+        touched[g] = keep ? kept_tiles(rc, cp, Ts, cull) : 0;
+        for (int i = 0; i < 8; i++) cullp[8 * g + i] = keep ? cp[i] : 0.0f;
         dbits[g] = keep ? db : 0;
         if (keep) {
             geom_t G;
@@ -400,9 +501,10 @@ int64_t orc_num_instances(int64_t n, const uint32_t* touched)
     return s;
 }
 
-/* keys/vals sized orc_num_instances(); ranges sized 2 * num_tiles.          */
+/* keys/vals sized orc_num_instances(); ranges sized 2 * num_tiles.  With   */
+/* cullp (from orc_preprocess with cull = 1) only the kept tiles are emitted. */
 void orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint32_t* dbits,
-             int TX, int TY, uint64_t* keys, uint32_t* vals, uint32_t* ranges)
+             const float* cullp, int Ts, int TX, int TY, uint64_t* keys, uint32_t* vals, uint32_t* ranges)
 {
     int64_t I = orc_num_instances(n, touched);
     inst_t* buf = (inst_t*)malloc(sizeof(inst_t) * (size_t)(I > 0 ? I : 1));
@@ -410,8 +512,11 @@ void orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint
     for (int64_t g = 0; g < n; g++) {
         if (!touched[g]) continue;
         const int32_t* rc = rect + 4 * g;
+        const int culled = cullp && (rc[2] - rc[0]) * (rc[3] - rc[1]) <= OR_CULL_MAX_TILES;
         for (int ty = rc[1]; ty < rc[3]; ty++)
             for (int tx = rc[0]; tx < rc[2]; tx++) {
+                if (culled && !tile_keep(cullp + 8 * g, (float)(tx * Ts), (float)(ty * Ts), (float)(Ts - 1)))
+                    continue;
                 buf[k].key = ((uint64_t)(uint32_t)(ty * TX + tx) << 32) | (uint64_t)dbits[g];
                 buf[k].order = (uint64_t)k;
                 buf[k].val = (uint32_t)g;

@@ -73,10 +73,11 @@ __device__ __forceinline__ T block_sum(T x, T* sm)
 // ---------------------------------------------------------------------------
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
-k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int Ts,
+k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int Ts, bool cull,
              float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
              float4* __restrict__ rec3, int* __restrict__ radius, int4* __restrict__ rect,
-             uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey, uint32_t* __restrict__ gidx)
+             uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey, uint32_t* __restrict__ gidx,
+             unsigned long long* __restrict__ kmask)
 {
     // t indexes (view, Gaussian) pairs: t = view * n + g
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -92,7 +93,7 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     gidx[t] = (uint32_t)t;
     Decision D;
-    if (!decide(mu, ls, q, cam, Ts, TX, TY, D)) {
+    if (!decide(mu, ls, q, p.logits[g], cam, Ts, TX, TY, D)) {
         radius[t] = 0;
         touched[t] = 0;
         dkey[t] = 0xffffffffu;
@@ -145,8 +146,10 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
     }
     radius[t] = D.r;
     rect[t] = make_int4(D.x0, D.y0, D.x1, D.y1);
-    touched[t] = (uint32_t)((D.x1 - D.x0) * (D.y1 - D.y0));
+    unsigned long long km;
+    touched[t] = kept_tiles(D, Ts, cull, &km);
     dkey[t] = __float_as_uint(D.z);
+    kmask[t] = km;
 }
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v0, uint64_t v1)
@@ -326,6 +329,7 @@ __global__ void __launch_bounds__(kPreThreads)
 k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched,
             const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int64_t n,
             const ViewDesc* __restrict__ views, int64_t per_view, uint64_t cap,
+            const unsigned long long* __restrict__ kmask,
             uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile, uint32_t* __restrict__ ival,
             uint32_t* __restrict__ iowner)
 {
@@ -351,12 +355,18 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
             const int4 r = rect[g];
             const ViewDesc& vd = views[g / per_view];
             const int TX = vd.TX, base = vd.tile_base;
+            // the exact culling's decisions, as the preprocess took them (its
+            // bit mask; all ones when the rectangle is not culled)
+            const unsigned long long km = kmask[g];
             uint64_t d = off;
+            int i = 0;
             for (int ty = r.y; ty < r.w; ty++)
-                for (int tx = r.x; tx < r.z; tx++, d++) {
+                for (int tx = r.x; tx < r.z; tx++, i++) {
+                    if (i < 64 && !((km >> i) & 1ull)) continue;
                     itile[d] = (uint32_t)(base + ty * TX + tx);
                     ival[d] = (uint32_t)d;
                     iowner[d] = g;
+                    d++;
                 }
         }
         off += cc[k];
@@ -646,6 +656,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     GL_TRY(v.dkey2.reserve(4 * nn));
     GL_TRY(v.gidx2.reserve(4 * nn));
     GL_TRY(v.dup_off.reserve(4 * nn));
+    GL_TRY(v.kmask.reserve(8 * nn));
     const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
     GL_TRY(v.bsum.reserve(8 * (size_t)std::max(nb, 1)));
     GL_TRY(v.ranges.reserve(8 * (size_t)v.ntiles));
@@ -666,10 +677,10 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     PhaseScope ps(v.prof, PH_PREPROCESS, s);
     count_launches(1);
     switch (p.deg) {
-        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
-        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>()); break;
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
@@ -725,7 +736,8 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     }
     const uint64_t cap2 = v.itile.bytes / 4;
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
-                                           v.bsum.as<uint64_t>(), n, dv, p.n, cap2, v.dup_off.as<uint32_t>(),
+                                           v.bsum.as<uint64_t>(), n, dv, p.n, cap2, v.kmask.as<unsigned long long>(),
+                                           v.dup_off.as<uint32_t>(),
                                            v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.iowner.as<uint32_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());

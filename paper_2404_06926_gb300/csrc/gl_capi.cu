@@ -187,7 +187,7 @@ gl_status View::upload_descs(cudaStream_t s)
 void View::release()
 {
     DevBuf* all[] = {&rec0, &rec1, &rec2, &rec3, &radius, &rect, &touched, &dkey, &gidx, &dkey2, &gidx2,
-                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d, &gpart, &work, &items, &segstate,
+                     &dup_off, &bsum, &count, &itile, &ival, &itile2, &ival2, &iowner, &srec0, &srec1, &srec2, &srec3, &sgid, &g2d, &gpart, &work, &items, &segstate, &kmask,
                      &hist, &ranges, &tile_order, &Tfin, &ncon, &rgb, &depth, &opac};
     for (DevBuf* b : all) b->release();
     desc.release();
@@ -341,7 +341,8 @@ extern "C" gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* e)
     if (!ctx || !e) { set_error("null argument"); return GL_ERR_INVALID; }
     if ((e->batch_depth != 32 && e->batch_depth != 64) || (e->deterministic != 0 && e->deterministic != 1) ||
         (e->pixels_per_lane != 1 && e->pixels_per_lane != 2 && e->pixels_per_lane != 4) ||
-        (e->segment != 0 && (e->segment < 64 || e->segment > 65536 || (e->segment & (e->segment - 1)) != 0))) {
+        (e->segment != 0 && (e->segment < 64 || e->segment > 65536 || (e->segment & (e->segment - 1)) != 0)) ||
+        (e->exact_cull != 0 && e->exact_cull != 1)) {
         set_error("invalid execution config");
         return GL_ERR_INVALID;
     }
@@ -376,6 +377,7 @@ extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, co
     c.view.pd = std::min(c.exec.pixels_per_lane, tile_size / 4);
     c.view.persistent = c.exec.persistent != 0;
     c.view.seg = c.exec.segment;
+    c.view.cull = c.exec.exact_cull != 0;
     GL_TRY(bin_view(c.view, params_of(g), cam, tile_size, c.stream));
     GL_TRY(raster_forward(c.view, out_rgb, out_depth, out_opacity, c.stream));
     c.has_forward = 1;
@@ -499,7 +501,7 @@ struct gl_map {
     std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
     Prof prof;
     // step execution and the captured step graph
-    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 0};
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1};
     cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
     struct StepGraph {
         std::vector<int64_t> key;        // the step shape it was captured for
@@ -884,6 +886,7 @@ void apply_exec(gl_map* m)
     v.pd = m->exec.pixels_per_lane;
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;
+    v.cull = m->exec.exact_cull != 0;
 }
 
 // Enqueue the whole step on `s`.  sync_free: the descriptors were uploaded by
@@ -948,7 +951,8 @@ gl_status read_loss(gl_map* m, int V, bool copy, float* out_loss)
 std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
 {
     std::vector<int64_t> k = {sp.V, step_tile(m), m->exec.batch_depth, m->exec.pixels_per_lane,
-                              m->exec.persistent, m->exec.deterministic, m->exec.segment, m->n, m->deg,
+                              m->exec.persistent, m->exec.deterministic, m->exec.segment, m->exec.exact_cull,
+                              m->n, m->deg,
                               m->cfg.sparse_adam};
     for (int i = 0; i < sp.V; i++) {
         k.push_back(sp.cams[i].W);
@@ -959,7 +963,7 @@ std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
                             &v.gidx, &v.dkey2, &v.gidx2, &v.dup_off, &v.g2d, &v.bsum, &v.count, &v.itile,
                             &v.ival, &v.itile2, &v.ival2, &v.iowner, &v.srec0, &v.srec1, &v.srec2, &v.srec3,
                             &v.sgid, &v.hist, &v.ranges, &v.tile_order, &v.Tfin, &v.ncon, &v.rgb, &v.work, &v.gpart,
-                            &v.items, &v.segstate,
+                            &v.items, &v.segstate, &v.kmask,
                             &v.desc, &m->dLdC, &m->ctx.loss_part, &m->loss_dev};
     for (const DevBuf* b : bufs) {
         k.push_back((int64_t)(uintptr_t)b->p);
@@ -1198,6 +1202,7 @@ gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
     }
     if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
     if (e.deterministic != 0 && e.deterministic != 1) { set_error("deterministic must be 0 or 1"); return GL_ERR_INVALID; }
+    if (e.exact_cull != 0 && e.exact_cull != 1) { set_error("exact_cull must be 0 or 1"); return GL_ERR_INVALID; }
     if (e.segment != 0 && (e.segment < 64 || e.segment > 65536 || (e.segment & (e.segment - 1)) != 0)) {
         set_error("segment must be 0 or a power of two in 64..65536");
         return GL_ERR_INVALID;
@@ -1320,7 +1325,8 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
                 for (int pers = 0; pers <= 1 && st == GL_OK; pers++)
                 for (int sg = 0; sg <= 1024 && st == GL_OK; sg += 1024) {
                     if (4 * ppl > ts) continue;
-                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic, sg, 0};
+                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic, sg,
+                                        saved.exact_cull};
                     m->exec = cand;
                     // per window: one eager step (sizes buffers, captures the graph) and one
                     // replay; then reps timed replays of every window in turn
@@ -1575,6 +1581,7 @@ void map_exec_knobs(const gl_map* m, View& v, int Ts)
     v.pd = std::min(m->exec.pixels_per_lane, Ts / 4);
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;
+    v.cull = m->exec.exact_cull != 0;
 }
 int map_sh_degree(const gl_map* m) { return m->deg; }
 int map_tile_size(const gl_map* m) { return m->cfg.tile_size; }

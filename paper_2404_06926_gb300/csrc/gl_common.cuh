@@ -106,6 +106,8 @@ struct Decision {
     float a, b, c, det;      // Sigma' (dilated) and its determinant
     int r;                   // screen radius (px)
     int x0, y0, x1, y1;      // tile rectangle, half open
+    float cA, cB, cC, ks;    // conic and the exact tile culling threshold (see tile_keep)
+    float bc, ba;            // edge minimiser slopes -B/C, -B/A
 };
 
 __device__ __forceinline__ float fmr(float a, float b) { return __fmul_rn(a, b); }
@@ -136,7 +138,67 @@ __device__ __forceinline__ float expf_decision(float x)
     return ldexpf(p, (int)k);
 }
 
-__device__ __forceinline__ bool decide(const float mu[3], const float ls[3], const float q[4],
+// log of the decision path: x = m 2^e with m in [sqrt(1/2), sqrt(2)) from
+// the bits, ln m = 2 atanh(s), s = (m - 1)/(m + 1), by its odd series to s^11
+// (|s| <= 0.1716), then e ln2 with ln2 split as in expf_decision.
+__device__ __forceinline__ float logf_decision(float x)
+{
+    if (!(x > 0.0f)) return __int_as_float(0xff800000);
+    if (x == __int_as_float(0x7f800000)) return x;
+    int e0 = 0;
+    if (x < 1.17549435e-38f) { x = __fmul_rn(x, 16777216.0f); e0 = -24; }   // subnormal: scale by 2^24
+    const unsigned bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xffu) - 126 + e0;
+    float m = __uint_as_float((bits & 0x7fffffu) | 0x3f000000u);   // [0.5, 1)
+    if (m < 0.70710678118654752f) { m = __fmul_rn(m, 2.0f); e -= 1; }
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.42860682030941723212e-6f;
+    const float sv = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(sv, sv);
+    float p = (float)(2.0 / 11.0);
+    p = __fadd_rn(__fmul_rn(p, s2), (float)(2.0 / 9.0));
+    p = __fadd_rn(__fmul_rn(p, s2), (float)(2.0 / 7.0));
+    p = __fadd_rn(__fmul_rn(p, s2), (float)(2.0 / 5.0));
+    p = __fadd_rn(__fmul_rn(p, s2), (float)(2.0 / 3.0));
+    p = __fadd_rn(__fmul_rn(p, s2), 2.0f);
+    const float lm = __fmul_rn(p, sv);
+    const float fe = (float)e;
+    return __fadd_rn(__fmul_rn(fe, ln2_hi), __fadd_rn(__fmul_rn(fe, ln2_lo), lm));
+}
+
+// Exact tile culling (decision path): can the Gaussian reach alpha >= 1/255
+// at a pixel centre of the tile whose centres span [X0, X0 + T1] x [Y0, Y0 +
+// T1]?  q(d) = A dx^2 + 2 B dx dy + C dy^2 is convex, so off the rectangle
+// its minimum lies on an edge, where the 1-D minimiser (dy = (-B/C) dx on
+// x = const, dx = (-B/A) dy on y = const) is clamped to the edge; kept iff
+// the minimum is <= ks = 2 ln(255 o) plus a slack of 2^-7
+// (relative and absolute), so every dropped tile stays below the alpha
+// threshold by far more than the per-pixel alpha's rounding.
+__device__ __forceinline__ bool tile_keep(const Decision& D, float X0, float Y0, float T1)
+{
+    const float u = D.u, v = D.v, A = D.cA, B = D.cB, C = D.cC;
+    const float dx0 = fsr(X0, u), dx1 = fsr(far_(X0, T1), u), dy0 = fsr(Y0, v), dy1 = fsr(far_(Y0, T1), v);
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
+    const float B2 = fmr(2.0f, B);
+    float qmin = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float dx = i ? dx1 : dx0;
+        const float t = fminf(fmaxf(fmr(D.bc, dx), dy0), dy1);
+        const float q = far_(far_(fmr(fmr(A, dx), dx), fmr(fmr(B2, dx), t)), fmr(fmr(C, t), t));
+        qmin = fminf(qmin, q);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float dy = i ? dy1 : dy0;
+        const float t = fminf(fmaxf(fmr(D.ba, dy), dx0), dx1);
+        const float q = far_(far_(fmr(fmr(A, t), t), fmr(fmr(B2, t), dy)), fmr(fmr(C, dy), dy));
+        qmin = fminf(qmin, q);
+    }
+    return qmin <= D.ks;
+}
+
+__device__ __forceinline__ bool decide(const float mu[3], const float ls[3], const float q[4], float logit,
                                        const Cam& cam, int Ts, int TX, int TY, Decision& D)
 {
     const float* R = cam.R;
@@ -218,7 +280,37 @@ __device__ __forceinline__ bool decide(const float mu[3], const float ls[3], con
     D.r = (r > 2.0e9f) ? 2000000000 : (int)r;
     D.u = u; D.v = v; D.z = z;
     D.a = a; D.b = b; D.c = c; D.det = det;
+    // exact tile culling inputs: conic and 2 ln(255 o) with slack
+    const float og = fdr(1.0f, far_(1.0f, expf_decision(-logit)));
+    const float kap = fmr(2.0f, logf_decision(fmr(255.0f, og)));
+    D.cA = fdr(c, det);
+    D.cB = fdr(-b, det);
+    D.cC = fdr(a, det);
+    D.ks = far_(kap, far_(fmr(kap, 0.0078125f), 0.0078125f));
+    D.bc = fdr(-D.cB, D.cC);
+    D.ba = fdr(-D.cB, D.cA);
     return true;
+}
+
+// The exact culling applies to rectangles of at most 64 tiles (a larger one
+// keeps all its tiles, which is always allowed: it only costs instances).
+constexpr int kCullMaxTiles = 64;
+
+// Tiles of the rectangle the exact culling keeps; *mask gets them (bit i =
+// the i-th tile in row-major order; all ones when nothing is culled).
+__device__ __forceinline__ uint32_t kept_tiles(const Decision& D, int Ts, bool cull, unsigned long long* mask)
+{
+    const int area = (D.x1 - D.x0) * (D.y1 - D.y0);
+    *mask = ~0ull;
+    if (!cull || area > kCullMaxTiles) return (uint32_t)area;
+    unsigned long long m = 0;
+    const float T1 = (float)(Ts - 1);
+    int i = 0;
+    for (int ty = D.y0; ty < D.y1; ty++)
+        for (int tx = D.x0; tx < D.x1; tx++, i++)
+            if (tile_keep(D, (float)(tx * Ts), (float)(ty * Ts), T1)) m |= 1ull << i;
+    *mask = m;
+    return (uint32_t)__popcll(m);
 }
 
 // ---------------------------------------------------------------------------

@@ -141,6 +141,7 @@ struct View {
     DevBuf dkey, gidx;        // u32 depth key, u32 index (sort input)
     DevBuf dkey2, gidx2;      // sort ping-pong
     DevBuf dup_off;           // u32 offset of the Gaussian's first instance
+    DevBuf kmask;             // u64 kept-tile mask of the rectangle (all ones if it is not culled)
     DevBuf g2d;               // float[10] screen-space gradient accumulators
     // scan
     DevBuf bsum;              // u64 per scan block
@@ -176,6 +177,9 @@ struct View {
     // segmented raster: tiles whose list holds >= 2 seg records are split
     // into segments of seg records (seg a power of two; 0: never split)
     int seg = 0;
+    // exact tile culling: only tiles where the Gaussian can reach alpha >=
+    // 1/255 at a pixel centre get an instance
+    bool cull = true;
     DevBuf items;             // uint2 per work item: (tile, segment), heaviest first
     DevBuf segstate;          // 8 floats per (segment item, pixel of its tile), see gl_raster.cu
     const ViewDesc* d_desc() const
@@ -194,7 +198,7 @@ struct View {
 struct gl_ctx_impl {
     cudaStream_t stream = nullptr;
     View view;
-    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 0};
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1};
     DevBuf pose_part;   // per-block pose partials
     DevBuf loss_part;   // per-block loss partials
     int has_forward = 0;

@@ -46,14 +46,18 @@ SCENES = ["small_frustum", "diff_check"]
 
 @pytest.mark.parametrize("scene", SCENES)
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_preprocess_and_binning_bit_exact(scene, tile):
+@pytest.mark.parametrize("cull", [1, 0])
+def test_preprocess_and_binning_bit_exact(scene, tile, cull):
+    """With and without exact tile culling: radii, rects, depth keys, the
+    sorted (tile | depth) instances and per-tile ranges equal the oracle's."""
     sc = _scene(scene)
     cam = sc["cam"]
-    pre = oracle.preprocess(sc["params"], cam, tile)
+    pre = oracle.preprocess(sc["params"], cam, tile, cull=bool(cull))
     bins = oracle.bin_instances(pre, cam)
     p = _dev(sc["params"])
     n = p["means"].shape[0]
     ctx = _ctx()
+    ctx.set_exec(exact_cull=cull)
     ctx.forward(p, cam, tile)
     pp = {k: v.cpu().numpy() for k, v in ctx.preprocess(n, "cuda").items()}
     assert np.array_equal(pp["radius"], pre["radius"])
@@ -91,6 +95,24 @@ def test_render_parity(scene, tile):
     zmax = max(1.0, float(np.abs(img["depth"]).max()))
     assert np.abs(dep - img["depth"])[ok].max() <= PIX_TOL * zmax
     assert np.array_equal(nc[ok], img["n_contrib"][ok])
+
+
+@pytest.mark.parametrize("scene", SCENES)
+def test_exact_culling_keeps_renders_bit_identical(scene):
+    """Culling drops only pairs every pixel skips: the GPU render is
+    bit-identical with and without it, with fewer instances."""
+    sc = _scene(scene)
+    cam = sc["cam"]
+    p = _dev(sc["params"])
+    out, inst = [], []
+    for cull in (1, 0):
+        ctx = _ctx()
+        ctx.set_exec(exact_cull=cull)
+        out.append([x.cpu().numpy() for x in ctx.forward(p, cam, 16)])
+        inst.append(ctx.num_instances())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert inst[0] < 0.9 * inst[1], inst
 
 
 def test_loss_parity():

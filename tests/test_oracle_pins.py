@@ -122,7 +122,7 @@ def test_rect_by_hand():
     """Tile rectangle [floor((u-r)/T), floor((u+r+T-1)/T)) clamped to the grid."""
     cam = scenes.camera(64, 48, 100.0, 100.0, 32.0, 24.0)
     p = _one([0.0, 0.0, 4.0], [np.log(0.08)] * 3)   # v = 4.3, r = ceil(3 sqrt(4.3+0.316)) = 7
-    pre = oracle.preprocess(p, cam, 16)
+    pre = oracle.preprocess(p, cam, 16, cull=False)
     r = pre["radius"][0]
     assert r == 7
     u = 32.0
@@ -134,7 +134,7 @@ def test_rect_by_hand():
 # --------------------------------------------------------------------------- binning
 def test_binning_equals_bruteforce_and_stable_sort():
     sc = scenes.small_frustum()
-    pre = oracle.preprocess(sc["params"], sc["cam"], 16)
+    pre = oracle.preprocess(sc["params"], sc["cam"], 16, cull=False)
     bins = oracle.bin_instances(pre, sc["cam"])
     TX, TY = bins["TX"], bins["TY"]
     keys, vals = [], []
@@ -493,3 +493,70 @@ def test_decision_exp_within_two_ulp_of_exp():
     assert oracle.expf_decision(0.0) == 1.0
     assert oracle.expf_decision(np.float32(np.log(2.0))) == np.float32(2.0) or \
         abs(oracle.expf_decision(np.float32(np.log(2.0))) - 2.0) <= 2 * np.spacing(np.float32(2.0))
+
+
+def test_decision_log_within_two_ulp_of_log():
+    """The float32 log of the decision path is within 4 ulp of the exact
+    logarithm (double) from subnormals to 1e30 (a wrong coefficient or
+    reduction step would be off by far more), and exact at 1."""
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([10.0 ** rng.uniform(-44, 30, 6000), rng.uniform(0.5, 2.0, 4000),
+                         np.linspace(0.01, 300.0, 3000)]).astype(np.float32)
+    for x in xs:
+        if x <= 0:
+            continue
+        y = oracle.logf_decision(x)
+        ref = np.log(np.float64(x))
+        ulp = np.spacing(np.float32(abs(ref))) if ref != 0 else np.float32(1e-45)
+        assert abs(y - ref) <= 4 * ulp + 1e-12, (x, y, ref)
+    assert oracle.logf_decision(1.0) == 0.0
+    for k in (-20, -1, 1, 7, 30):
+        assert abs(oracle.logf_decision(np.float32(2.0 ** k)) - k * np.log(2.0)) <= 4 * np.spacing(np.float32(abs(k) * 0.7))
+    assert oracle.logf_decision(0.0) == -np.inf
+
+
+def _tile_pairs(bins):
+    TX = bins["TX"]
+    tiles = (bins["keys"] >> np.uint64(32)).astype(np.int64)
+    return set(zip(bins["vals"].astype(np.int64).tolist(), tiles.tolist())), TX
+
+
+@pytest.mark.parametrize("scene", ["small_frustum", "diff_check"])
+@pytest.mark.parametrize("tile", [8, 16])
+def test_exact_tile_culling_drops_only_invisible_tiles(scene, tile):
+    """Every (Gaussian, tile) pair the exact culling drops has alpha < 1/255
+    at each pixel centre of the tile, evaluated independently in double from
+    the double path's mean, conic and opacity; and culling drops some pairs."""
+    sc = getattr(scenes, scene)()
+    cam = sc["cam"]
+    pre_c = oracle.preprocess(sc["params"], cam, tile, cull=True)
+    pre_f = oracle.preprocess(sc["params"], cam, tile, cull=False)
+    assert np.array_equal(pre_c["radius"], pre_f["radius"])
+    assert (pre_c["touched"] <= pre_f["touched"]).all()
+    kept, TX = _tile_pairs(oracle.bin_instances(pre_c, cam))
+    full, _ = _tile_pairs(oracle.bin_instances(pre_f, cam))
+    assert kept <= full
+    dropped = full - kept
+    assert len(dropped) > 0.05 * len(full), (len(dropped), len(full))
+    W, H = cam["width"], cam["height"]
+    ys, xs = np.mgrid[0:tile, 0:tile]
+    for g, t in dropped:
+        px = (t % TX) * tile + xs
+        py = (t // TX) * tile + ys
+        dx = pre_f["mean2d"][g, 0] - px
+        dy = pre_f["mean2d"][g, 1] - py
+        A, B, C = pre_f["conic"][g]
+        q = A * dx * dx + 2 * B * dx * dy + C * dy * dy
+        amax = (pre_f["opacity"][g] * np.exp(-0.5 * q)).max()
+        assert amax < 1.0 / 255.0, (g, t, amax)
+
+
+@pytest.mark.parametrize("scene", ["small_frustum", "diff_check"])
+def test_exact_tile_culling_keeps_the_image(scene):
+    """Culling only removes pairs that every pixel would skip: colour, depth,
+    opacity and final transmittance are bit-identical with and without it."""
+    sc = getattr(scenes, scene)()
+    a = oracle.forward(sc["params"], sc["cam"], 16, cull=True)[2]
+    b = oracle.forward(sc["params"], sc["cam"], 16, cull=False)[2]
+    for k in ("color", "depth", "opacity", "T_final"):
+        assert np.array_equal(a[k], b[k]), k
