@@ -17,6 +17,7 @@ namespace gl {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kUnroll = 4;   // float4 loads per thread in flight in the Adam pass
 constexpr int kNG = 10;
 
 struct Geo {
@@ -117,7 +118,7 @@ __device__ __forceinline__ void coop_one(float* __restrict__ P, float* __restric
 // start at multiples of 128 Gaussians): MODE 0 writes the staged gradients,
 // MODE 1 applies Adam (the first three floats of a row take lr0, the SH DC
 // band; the rest lr).  Rows flagged off in upd are left untouched.  float4
-// accesses, two per thread in flight.
+// accesses, kUnroll per thread in flight.
 template <int MODE, int WIDTH, int NR>
 __device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
                                      int64_t g0, int cnt, const float* __restrict__ sR, int off,
@@ -128,11 +129,11 @@ __device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ 
     float4* P4 = reinterpret_cast<float4*>(P + base);
     float4* M4 = reinterpret_cast<float4*>(Mm + base);
     float4* V4 = reinterpret_cast<float4*>(Vv + base);
-    for (int f0 = threadIdx.x; f0 < nv; f0 += 2 * kThreads) {
-        float4 pp[2], mm[2], vv[2];
-        bool any[2];
+    for (int f0 = threadIdx.x; f0 < nv; f0 += kUnroll * kThreads) {
+        float4 pp[kUnroll], mm[kUnroll], vv[kUnroll];
+        bool any[kUnroll];
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
+        for (int u = 0; u < kUnroll; u++) {
             const int f = f0 + u * kThreads;
             any[u] = false;
             if (f < nv) {
@@ -142,7 +143,7 @@ __device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ 
             if (any[u] && MODE == 1) { pp[u] = P4[f]; mm[u] = M4[f]; vv[u] = V4[f]; }
         }
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
+        for (int u = 0; u < kUnroll; u++) {
             const int f = f0 + u * kThreads;
             if (!any[u]) continue;
             float* pa = &pp[u].x;
