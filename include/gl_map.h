@@ -242,12 +242,14 @@ GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
 
 /* Autotuner: `views` holds n_views / window windows of `window` views each
  * (as gl_optimize_step takes them; several windows make the timing
- * representative of steps over different views).  For each candidate
- * execution (tile size 8/16/32 x batch depth 32/64 x pixels per lane 1/2/4
- * x persistent or not x segment 0/1024, graphs on, deterministic as set) it
- * times `reps` rounds of one step per window with CUDA events, putting the
- * Gaussians, their Adam moments, the views' exposures and the step
- * counters back after each trial.  With keep_tile_size != 0 only
+ * representative of steps over different views).  Coordinate descent from
+ * {graphs, persistent, batch depth 32, 1 pixel per lane, segment 1024}: the
+ * tile size (8/16/32), the segment length (0/256/512/1024), persistence,
+ * the batch depth (32/64) and the pixels per lane (1/2/4) in turn take the
+ * value whose `reps` rounds of one step per window are fastest (CUDA
+ * events) with the other knobs fixed; deterministic and exact_cull stay as
+ * set.  The Gaussians, their Adam moments, the views' exposures and the
+ * step counters are put back after each trial.  With keep_tile_size != 0 only
  * gl_config's tile size is tried.  The fastest candidate is installed with
  * gl_map_set_exec and returned in *best, its device time per step in
  * *best_ms (nullable).  The map ends as it started.  Errors: as

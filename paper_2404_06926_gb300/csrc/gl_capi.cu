@@ -1314,40 +1314,53 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
         set_error("event creation failed");
         st = GL_ERR_CUDA;
     }
+    // time one candidate: per window one eager step (sizes buffers, captures
+    // the graph) and one replay, then reps timed rounds of every window
+    auto trial = [&](const gl_exec_config& cand, float* ms_out) -> gl_status {
+        m->exec = cand;
+        gl_status r = GL_OK;
+        for (int w = 0; w < nw && r == GL_OK; w++)
+            for (int k = 0; k < 2 && r == GL_OK; k++) r = run_step(m, plans[w], nullptr);
+        if (r != GL_OK) return r;
+        cudaEventRecord(e0, m->stream);
+        for (int k = 0; k < reps && r == GL_OK; k++)
+            for (int w = 0; w < nw && r == GL_OK; w++) r = run_step(m, plans[w], nullptr);
+        cudaEventRecord(e1, m->stream);
+        if (r != GL_OK) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return GL_ERR_CUDA;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *ms_out = ms / (float)(reps * nw);
+        return restore();
+    };
+    // coordinate descent from the defaults: each knob in turn takes the
+    // value that is fastest with the others fixed
     float best_t = -1.0f;
-    gl_exec_config best_e = saved;
-    const int tiles[3] = {8, 16, 32};
-    for (int ti = 0; ti < 3 && st == GL_OK; ti++) {
-        const int ts = tiles[ti];
-        if (keep_tile_size && ts != m->cfg.tile_size) continue;
-        for (int bd = 32; bd <= (saved.deterministic ? 32 : 64) && st == GL_OK; bd *= 2)
-            for (int ppl = 1; ppl <= 4 && st == GL_OK; ppl *= 2)
-                for (int pers = 0; pers <= 1 && st == GL_OK; pers++)
-                for (int sg = 0; sg <= 1024 && st == GL_OK; sg += 1024) {
-                    if (4 * ppl > ts) continue;
-                    gl_exec_config cand{1, pers, bd, ppl, keep_tile_size ? 0 : ts, saved.deterministic, sg,
-                                        saved.exact_cull};
-                    m->exec = cand;
-                    // per window: one eager step (sizes buffers, captures the graph) and one
-                    // replay; then reps timed replays of every window in turn
-                    for (int w = 0; w < nw && st == GL_OK; w++)
-                        for (int r = 0; r < 2 && st == GL_OK; r++) st = run_step(m, plans[w], nullptr);
-                    if (st != GL_OK) break;
-                    cudaEventRecord(e0, m->stream);
-                    for (int r = 0; r < reps && st == GL_OK; r++)
-                        for (int w = 0; w < nw && st == GL_OK; w++) st = run_step(m, plans[w], nullptr);
-                    cudaEventRecord(e1, m->stream);
-                    if (st != GL_OK) break;
-                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = GL_ERR_CUDA; break; }
-                    float ms = 0.0f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    ms /= (float)(reps * nw);
-                    if (best_t < 0.0f || ms < best_t) {
-                        best_t = ms;
-                        best_e = cand;
-                    }
-                    st = restore();
-                }
+    gl_exec_config best_e{1, 1, 32, 1, keep_tile_size ? 0 : m->cfg.tile_size, saved.deterministic, 1024,
+                          saved.exact_cull};
+    if (st == GL_OK) st = trial(best_e, &best_t);
+    const int tile_vals[3] = {8, 16, 32}, seg_vals[4] = {0, 256, 512, 1024}, pers_vals[2] = {0, 1},
+              bd_vals[2] = {32, 64}, ppl_vals[3] = {1, 2, 4};
+    struct Dim { int32_t gl_exec_config::*field; const int* vals; int n; };
+    const Dim dims[5] = {{&gl_exec_config::tile_size, tile_vals, keep_tile_size ? 0 : 3},
+                         {&gl_exec_config::segment, seg_vals, 4},
+                         {&gl_exec_config::persistent, pers_vals, 2},
+                         {&gl_exec_config::batch_depth, bd_vals, saved.deterministic ? 1 : 2},
+                         {&gl_exec_config::pixels_per_lane, ppl_vals, 3}};
+    for (const Dim& d : dims) {
+        for (int i = 0; i < d.n && st == GL_OK; i++) {
+            gl_exec_config cand = best_e;
+            cand.*(d.field) = d.vals[i];
+            if (cand.*(d.field) == best_e.*(d.field)) continue;
+            const int ts = cand.tile_size ? cand.tile_size : m->cfg.tile_size;
+            if (4 * cand.pixels_per_lane > ts) continue;
+            float ms = 0.0f;
+            st = trial(cand, &ms);
+            if (st == GL_OK && ms < best_t) {
+                best_t = ms;
+                best_e = cand;
+            }
+        }
     }
     if (st == GL_OK) st = restore();
     cudaStreamSynchronize(m->stream);
