@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--window", type=int, default=8, help="views per window in the equal-PSNR comparison")
     ap.add_argument("--exec", default="auto", choices=["auto", "eager", "graphs"],
                     help="auto: CUDA-graph steps with autotuned raster knobs (plain keeps tile 16)")
+    ap.add_argument("--fixed-view", type=int, default=-1,
+                    help="every plain step on this keyframe (profiling: counters of one known view)")
     ap.add_argument("--knobs", default="",
                     help="explicit execution knobs after --exec, e.g. segment=1024,persistent=1 (no autotuning)")
     ap.add_argument("--batched-views", type=int, default=12,
@@ -578,6 +580,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(100 + rank)
     order = rng.integers(0, n_kf, size=args.warmup + args.steps + 1)
+    if args.fixed_view >= 0:
+        order[:] = args.fixed_view % n_kf
 
     def step(k, img=None, want=False):
         return m.optimize_step([(int(k), cams[int(k)], img)], want_loss=want)

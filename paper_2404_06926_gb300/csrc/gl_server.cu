@@ -450,7 +450,11 @@ extern "C" gl_status gl_server_create(gl_map* map, const gl_server_config* cfg, 
     s->cfg = c;
     s->t0 = std::chrono::steady_clock::now();
     GL_CUDA_TRY(cudaGetDevice(&s->device));
-    GL_CUDA_TRY(cudaStreamCreateWithFlags(&s->rstream, cudaStreamNonBlocking));
+    // renders are latency-bound and small: their stream gets the highest
+    // priority, so their CTAs go first whenever SM slots free up
+    int prio_lo = 0, prio_hi = 0;
+    GL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    GL_CUDA_TRY(cudaStreamCreateWithPriority(&s->rstream, cudaStreamNonBlocking, prio_hi));
     for (Snap& sn : s->snap) GL_CUDA_TRY(cudaEventCreateWithFlags(&sn.ready, cudaEventDisableTiming));
     GL_TRY(s->rview.init());
     GL_TRY(publish(s.get()));
