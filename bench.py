@@ -366,13 +366,15 @@ def timed(torch, fn):
     return e0.elapsed_time(e1)
 
 
-def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist):
+def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist, ck0):
     """Wall (device) time for plain single-view steps to reach their PSNR on
     held-out views after `psnr_steps` steps, against windows of `window`
-    views from the same starting state (the map's checkpoint)."""
+    views, both from the freshly initialised map (checkpoint ck0)."""
     n_kf = len(cams)
     views = held_out(sc, 20, wsz["W"], wsz["H"], wsz["f"], torch)
-    ck = m.save(with_images=True)
+    ck_now = m.save(with_images=True)
+    m.load(ck0)
+    ck = ck0
     plain_exec = m.get_exec()
     p0 = mean_psnr(m, views, torch)
     # plain: a random keyframe per step
@@ -408,7 +410,7 @@ def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist):
                      "time_ratio_plain_over_batched": (ms_plain / ms_win) if reached else None}
         m.load(ck)
     m.set_config(lr_window_exp=0.0)
-    m.load(ck)
+    m.load(ck_now)
     m.set_exec(**plain_exec)
     return {"held_out_views": len(views), "psnr_start": p0, "target_psnr": target,
             "plain": {"steps": args.psnr_steps, "ms": ms_plain, "views": args.psnr_steps,
@@ -620,6 +622,7 @@ def run_ours(args):
     wsz = workload_sizes(args.small)
     sc, m, cams, imgs = build_map(binding, torch, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"], wsz["f"],
                                   [(wsz["W"], wsz["H"])] * n_kf)
+    ck0 = m.save(with_images=True) if args.psnr_steps > 0 else None   # the freshly initialised map
     n_total = len(m)
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(100 + rank)
@@ -674,7 +677,7 @@ def run_ours(args):
     # starting state
     psnr = None
     if args.psnr_steps > 0:
-        psnr = psnr_compare(args, m, cams, sc, wsz, rng, torch, dist)
+        psnr = psnr_compare(args, m, cams, sc, wsz, rng, torch, dist, ck0)
 
     # end to end through the C ABI with host buffers: pinned host target in,
     # loss out, every step
