@@ -387,13 +387,12 @@ def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist, ck0):
         curve.append((c0 + len(ks), mean_psnr(m, views, torch)))
     target = curve[-1][1]
     # batched: windows of distinct random keyframes, autotuned execution
-    m.load(ck)
-    wv = min(args.window, n_kf)
-    win = [(k, cams[k], None) for k in range(wv)]
-    w_exec, _ = set_exec(m, args.exec, win, keep_tile=False)
-    m.load(ck)
     runs = {}
-    for exp in (0.0, 0.5):
+    for wv, exp in ((min(args.window, n_kf), 0.0), (min(args.window, n_kf), 0.5), (min(4, n_kf), 0.5)):
+        m.load(ck)
+        win = [(k, cams[k], None) for k in range(wv)]
+        w_exec, _ = set_exec(m, args.exec, win, keep_tile=False)
+        m.load(ck)
         m.set_config(lr_window_exp=exp)
         ms_win, nwin, reached, wcurve = 0.0, 0, False, []
         every = 10
@@ -404,7 +403,7 @@ def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist, ck0):
             q = mean_psnr(m, views, torch)
             wcurve.append((nwin, q))
             reached = q >= target
-        runs[exp] = {"views_per_window": wv, "lr_window_exp": exp, "windows": nwin, "views": nwin * wv,
+        runs[(wv, exp)] = {"views_per_window": wv, "lr_window_exp": exp, "windows": nwin, "views": nwin * wv,
                      "ms": ms_win, "reached": reached, "exec": w_exec,
                      "curve": [(int(a), round(b, 3)) for a, b in wcurve],
                      "time_ratio_plain_over_batched": (ms_plain / ms_win) if reached else None}
@@ -415,7 +414,9 @@ def psnr_compare(args, m, cams, sc, wsz, rng, torch, dist, ck0):
     return {"held_out_views": len(views), "psnr_start": p0, "target_psnr": target,
             "plain": {"steps": args.psnr_steps, "ms": ms_plain, "views": args.psnr_steps,
                       "curve": [(int(a), round(b, 3)) for a, b in curve]},
-            "batched_paper_lr": runs[0.0], "batched_sqrt_lr": runs[0.5]}
+            "batched_paper_lr": runs[(min(args.window, n_kf), 0.0)],
+            "batched_sqrt_lr": runs[(min(args.window, n_kf), 0.5)],
+            "batched4_sqrt_lr": runs[(min(4, n_kf), 0.5)]}
 
 
 def run_batched(args, binding, torch, dist, ws):
