@@ -20,9 +20,6 @@ namespace gl {
 namespace {
 
 constexpr int kPreThreads = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
 constexpr int kSortMaxBlocks = 4 * 152;                // 4 CTAs per SM on 152 SMs
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kPreThreads * kScanItems;   // 1024 Gaussians per scan block
@@ -160,123 +157,242 @@ __global__ void k_set_u64(uint64_t* p, uint64_t v0, uint64_t v1)
 
 // ---------------------------------------------------------------------------
 // LSD radix sort of (u32 key, u32 value), 8-bit digits, stable.
-// Each pass: per-block digit histograms over contiguous chunks, one
-// digit-major exclusive scan, then a stable scatter.  n is read on device.
+//
+// One histogram kernel counts the digits of every pass in a single read of
+// the keys; then each pass is ONE scatter kernel over tiles of kOsTile keys.
+// A CTA takes the next tile from a counter, ranks its keys by digit in
+// shared memory, publishes the tile's per-digit counts and finds the counts
+// of all earlier tiles by a chained scan with decoupled look-back (Merrill
+// and Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
+// 2016; the one-histogram-then-one-kernel-per-digit layout is the "Onesweep"
+// sort of Adinets and Merrill, 2022).  Keys then leave the tile in digit
+// order, so consecutive threads write consecutive addresses.
+//
+// Scratch (u32 words): global digit counts [pass][256] | tile counters
+// [pass] | look-back words [pass][tiles][256], each (flag << 30 | count):
+// flag 1 = this tile's count, flag 2 = inclusive count of tiles 0..t.
+// A CTA only waits for tiles taken before its own, by CTAs already running,
+// so the waits end; they are still bounded (kOsSpin polls), after which the
+// CTA raises ctl[8] and goes on with the counts it has (its writes stay in
+// bounds, the order is then wrong and the host reports GL_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void sort_chunk(uint64_t n, int nblocks, uint64_t& begin, uint64_t& end)
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 15;
+constexpr int kOsTile = kOsThreads * kOsItems;   // 3840 keys per tile
+constexpr int kOsMaxPasses = 4;
+constexpr int kOsTicketOff = kOsMaxPasses * 256;
+constexpr int kOsStatusOff = kOsTicketOff + 64;
+constexpr uint32_t kOsAgg = 1u << 30, kOsIncl = 2u << 30, kOsValMask = kOsAgg - 1u;
+constexpr int kOsSpin = 1 << 20;   // polls of a tile not yet published before giving up
+constexpr int kOsWindow = 16;      // earlier tiles read per look-back round trip
+
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p)
 {
-    uint64_t chunk = ((n + nblocks - 1) / nblocks + kSortTile - 1) / kSortTile * kSortTile;
-    begin = min(n, (uint64_t)blockIdx.x * chunk);
-    end = min(n, begin + chunk);
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int shift, int nblocks,
-            uint32_t* __restrict__ hist)
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v)
 {
-    __shared__ uint32_t h[256];
-    const int tid = threadIdx.x, lane = tid & 31;
-    h[tid] = 0;
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Digit counts of all passes (scratch counts and counters zeroed before) and
+// clearing of the look-back words of the tiles (tile_keys keys each) this
+// sort visits.  A thread loads kOsHistKeys keys before counting any of them.
+constexpr int kOsHistKeys = 16;
+__global__ void __launch_bounds__(kOsThreads)
+k_os_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int passes, int tile_keys,
+          int64_t tiles_max, uint32_t* __restrict__ scratch)
+{
+    __shared__ uint32_t h[kOsMaxPasses * 256];
+    const uint64_t n = *n_dev;
+    for (int i = threadIdx.x; i < kOsMaxPasses * 256; i += kOsThreads) h[i] = 0;
+    const uint64_t nt = (n + tile_keys - 1) / tile_keys;
+    const uint64_t gsz = (uint64_t)gridDim.x * kOsThreads;
+    const uint64_t gid = (uint64_t)blockIdx.x * kOsThreads + threadIdx.x;
+    uint32_t* status = scratch + kOsStatusOff;
+    for (int p = 0; p < passes; p++)
+        for (uint64_t i = gid; i < nt * 256; i += gsz) status[(uint64_t)p * tiles_max * 256 + i] = 0u;
     __syncthreads();
-    uint64_t begin, end;
-    sort_chunk(*n_dev, nblocks, begin, end);
-    const unsigned lt = (1u << lane) - 1u;
-    for (uint64_t base = begin; base < end; base += kSortThreads) {
-        uint64_t idx = base + tid;
-        int d = idx < end ? (int)((kin[idx] >> shift) & 255u) : 256;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (d < 256 && (peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    // key j of a thread: b + (j / 4 * kOsThreads + threadIdx.x) * 4 + j % 4 (16-byte loads)
+    for (uint64_t b = (uint64_t)blockIdx.x * kOsThreads * kOsHistKeys; b < n; b += gsz * kOsHistKeys) {
+        uint32_t k[kOsHistKeys];
+#pragma unroll
+        for (int q = 0; q < kOsHistKeys / 4; q++) {
+            const uint64_t i0 = b + ((uint64_t)q * kOsThreads + threadIdx.x) * 4;
+            if (i0 + 3 < n) {
+                const uint4 v = *reinterpret_cast<const uint4*>(kin + i0);
+                k[4 * q] = v.x; k[4 * q + 1] = v.y; k[4 * q + 2] = v.z; k[4 * q + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) k[4 * q + e] = i0 + e < n ? kin[i0 + e] : 0u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kOsHistKeys; j++) {
+            const bool ok = b + ((uint64_t)(j / 4) * kOsThreads + threadIdx.x) * 4 + (j % 4) < n;
+            if (ok)
+                for (int p = 0; p < passes; p++) atomicAdd(&h[p * 256 + ((k[j] >> (8 * p)) & 255u)], 1u);
+        }
     }
     __syncthreads();
-    hist[tid * nblocks + blockIdx.x] = h[tid];
+    for (int i = threadIdx.x; i < passes * 256; i += kOsThreads)
+        if (h[i]) atomicAdd(&scratch[i], h[i]);
 }
 
-// Exclusive scan of one digit's row of per-block counts (one CTA per digit);
-// the row total goes to totals[digit].
-__global__ void __launch_bounds__(256) k_sort_rowscan(uint32_t* __restrict__ hist, int nblocks,
-                                                     uint32_t* __restrict__ totals)
+// One pass over tiles of NT x ITEMS keys; threads 0..255 own one digit each
+// in the per-digit phases (count, look-back, offsets).  Keys are ranked
+// within a warp item by item: the lanes holding digit d set their bits in a
+// shared mask word of d, read it back (the lanes below them with the same
+// digit come first), and the lowest of them advances the warp's count of d
+// and clears the mask.
+template <int NT, int ITEMS, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+          uint32_t* __restrict__ vout, const uint64_t* n_dev, int pass, int64_t tiles_max,
+          uint32_t* __restrict__ scratch, unsigned long long* __restrict__ err)
 {
-    __shared__ uint32_t sm[256 / 32 + 1];
-    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
-    uint32_t carry = 0;
-    for (int base = 0; base < nblocks; base += 256) {
-        const int i = base + threadIdx.x;
-        const uint32_t x = i < nblocks ? row[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<uint32_t, 256>(x, sm, &tot);
-        if (i < nblocks) row[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
-}
-
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint64_t* n_dev,
-               int shift, int nblocks, const uint32_t* __restrict__ hist,
-               const uint32_t* __restrict__ totals)
-{
-    __shared__ uint32_t wcnt[kSortThreads / 32][256];
-    __shared__ uint32_t doff[256];
-    __shared__ uint32_t tcnt[256];
-    __shared__ uint32_t sm[kSortThreads / 32 + 1];
+    static_assert(NT >= 256 && NT % 32 == 0, "a thread per digit");
+    constexpr int TILE = NT * ITEMS;
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t skey[TILE];
+    __shared__ uint32_t sval[TILE];
+    __shared__ uint32_t wcnt[NW][256];
+    __shared__ uint32_t wmask[NW][256];
+    __shared__ uint32_t dexcl[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t sm[NW + 1];
+    __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    uint64_t begin, end;
-    sort_chunk(*n_dev, nblocks, begin, end);
-    {
-        // digit base = exclusive scan of the digit totals; plus this block's row prefix
-        uint32_t tot;
-        const uint32_t base = block_exclusive_scan<uint32_t, kSortThreads>(totals[tid], sm, &tot);
-        doff[tid] = base + hist[tid * nblocks + blockIdx.x];
+    const bool owner = tid < 256;
+    const int shift = 8 * pass;
+    const uint64_t n = *n_dev;
+    const uint64_t nt = (n + TILE - 1) / TILE;
+    if (tid == 0) s_tile = atomicAdd(&scratch[kOsTicketOff + pass], 1u);
+    for (int d = lane; d < 256; d += 32) {
+        wcnt[w][d] = 0u;
+        wmask[w][d] = 0u;
+    }
+    // global digit offsets (while the tile counter answers)
+    uint32_t tot;
+    const uint32_t gex = block_exclusive_scan<uint32_t, NT>(owner ? scratch[pass * 256 + tid] : 0u, sm, &tot);
+    const uint32_t t = s_tile;
+    if (t >= nt) return;
+    const uint64_t base = (uint64_t)t * TILE;
+    const unsigned lt = (1u << lane) - 1u;
+
+    // load (warp w holds the contiguous run [w * 32 * ITEMS, ...)) and rank
+    // within the warp: earlier items, then lower lanes, come first;
+    // rd[j] = rank within the warp's digit << 9 | digit (256: past the end)
+    uint32_t kk[ITEMS], vv[ITEMS], rd[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const uint64_t idx = base + (uint64_t)w * (32 * ITEMS) + j * 32 + lane;
+        const bool ok = idx < n;
+        kk[j] = ok ? kin[idx] : 0u;
+        vv[j] = ok ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const uint64_t idx = base + (uint64_t)w * (32 * ITEMS) + j * 32 + lane;
+        const int d = idx < n ? (int)((kk[j] >> shift) & 255u) : 256;
+        if (d < 256) atomicOr(&wmask[w][d], 1u << lane);
+        __syncwarp();
+        const unsigned peers = d < 256 ? wmask[w][d] : 0u;
+        const uint32_t prev = d < 256 ? wcnt[w][d] : 0u;
+        rd[j] = ((prev + __popc(peers & lt)) << 9) | (uint32_t)d;
+        __syncwarp();
+        if (d < 256 && (peers & lt) == 0) {
+            wcnt[w][d] = prev + __popc(peers);
+            wmask[w][d] = 0u;
+        }
+        __syncwarp();
     }
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    for (uint64_t base = begin; base < end; base += kSortTile) {
-        for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
-        __syncwarp();
-        uint32_t kk[kSortItems], vv[kSortItems], rk[kSortItems];
-        int dg[kSortItems];
-#pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            uint64_t idx = base + (uint64_t)w * (32 * kSortItems) + j * 32 + lane;
-            bool ok = idx < end;
-            kk[j] = ok ? kin[idx] : 0u;
-            vv[j] = ok ? vin[idx] : 0u;
-            dg[j] = ok ? (int)((kk[j] >> shift) & 255u) : 256;
+
+    // per digit: offsets of the warps, the tile's count, published at once
+    uint32_t cnt = 0;
+    uint32_t* status = scratch + kOsStatusOff + (uint64_t)pass * tiles_max * 256;
+    uint32_t* mine = status + (uint64_t)t * 256 + tid;
+    if (owner) {
+#pragma unroll 8
+        for (int ww = 0; ww < NW; ww++) {
+            const uint32_t c = wcnt[ww][tid];
+            wcnt[ww][tid] = cnt;
+            cnt += c;
         }
+        st_relaxed_gpu(mine, (t == 0 ? kOsIncl : kOsAgg) | cnt);
+    }
+    const uint32_t ex = block_exclusive_scan<uint32_t, NT>(owner ? cnt : 0u, sm, &tot);
+    if (owner) dexcl[tid] = ex;
+    __syncthreads();
+    // the tile in digit order, in shared memory
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            const int d = dg[j];
-            const unsigned peers = __match_any_sync(kFull, d);
-            const uint32_t prev = (d < 256) ? wcnt[w][d] : 0u;
-            rk[j] = prev + __popc(peers & lt);
-            __syncwarp();
-            if (d < 256 && (peers & lt) == 0) wcnt[w][d] = prev + __popc(peers);
-            __syncwarp();
+    for (int j = 0; j < ITEMS; j++) {
+        const uint32_t d = rd[j] & 511u;
+        if (d < 256) {
+            const uint32_t pos = dexcl[d] + wcnt[w][d] + (rd[j] >> 9);
+            skey[pos] = kk[j];
+            sval[pos] = vv[j];
         }
-        __syncthreads();
-        {
-            uint32_t run = 0;
+    }
+
+    // look back over the earlier tiles for this digit, kOsWindow of them per
+    // round trip: add their counts in order up to the first inclusive one;
+    // a tile not yet published ends the round (retried from there)
+    uint32_t prefix = 0;
+    if (owner && t > 0) {
+        int64_t tt = (int64_t)t - 1;
+        int spins = 0;
+        while (true) {
+            uint32_t sw[kOsWindow];
 #pragma unroll
-            for (int ww = 0; ww < kSortThreads / 32; ww++) {
-                uint32_t c = wcnt[ww][tid];
-                wcnt[ww][tid] = run;
-                run += c;
+            for (int q = 0; q < kOsWindow; q++)
+                sw[q] = tt - q >= 0 ? ld_relaxed_gpu(status + (uint64_t)(tt - q) * 256 + tid) : kOsIncl;
+            uint32_t acc = 0;
+            int used = 0, state = 0;   // 0: keep going, 1: inclusive count reached, 2: not yet published
+#pragma unroll
+            for (int q = 0; q < kOsWindow; q++) {
+                if (state == 0) {
+                    const uint32_t fl = sw[q] >> 30;
+                    if (fl == 0) {
+                        state = 2;
+                    } else {
+                        acc += sw[q] & kOsValMask;
+                        used++;
+                        if (fl == 2) state = 1;
+                    }
+                }
             }
-            tcnt[tid] = run;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            if (dg[j] < 256) {
-                uint32_t pos = doff[dg[j]] + wcnt[w][dg[j]] + rk[j];
-                kout[pos] = kk[j];
-                vout[pos] = vv[j];
+            prefix += acc;
+            tt -= used;
+            if (state == 1) break;
+            if (state == 2) {
+                if (++spins >= kOsSpin) {
+                    atomicOr(err, 1ull);
+                    break;
+                }
+                __nanosleep(32);
             }
         }
-        __syncthreads();
-        doff[tid] += tcnt[tid];
-        __syncthreads();
+        st_relaxed_gpu(mine, kOsIncl | (prefix + cnt));
+    }
+    if (owner) gbase[tid] = gex + prefix - ex;   // output index = gbase[d] + position in the digit-sorted tile
+    __syncthreads();
+    const int tn = (int)min((uint64_t)TILE, n - base);
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int i = tid + j * NT;
+        if (i < tn) {
+            const uint32_t k = skey[i];
+            const uint64_t o = (uint64_t)(uint32_t)(gbase[(k >> shift) & 255u] + (uint32_t)i);
+            if (o < n) {
+                kout[o] = k;
+                vout[o] = sval[i];
+            }
+        }
     }
 }
 
@@ -521,28 +637,48 @@ gl_status build_items(View& v, cudaStream_t s)
 }
 
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                         const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
-                         uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
+                         const uint64_t* n_dev, int64_t n_max, int64_t n_reserve, int bits, DevBuf& scratch,
+                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
 {
-    int nblocks = (int)std::min<int64_t>(kSortMaxBlocks, std::max<int64_t>(1, (n_max + kSortTile - 1) / kSortTile));
-    // sized for the largest grid, so that no later sort (graph steps
-    // included) has to grow it
-    GL_TRY(hist.reserve(sizeof(uint32_t) * 256 * ((size_t)kSortMaxBlocks + 1)));
-    uint32_t* totals = hist.as<uint32_t>() + 256 * (size_t)nblocks;
+    const int passes = std::max(1, std::min(kOsMaxPasses, (bits + 7) / 8));
+    // look-back words sized for the larger of this sort and its reserve, so
+    // that graph steps (whose bound is the capacity) never grow the buffer
+    const int64_t nbig = std::max<int64_t>(std::max<int64_t>(n_max, n_reserve), 1);
+    if (nbig >= (int64_t)kOsValMask) {
+        set_error("radix sort: 2^30 keys or more");
+        return GL_ERR_CAPACITY;
+    }
+    const int64_t tiles_max = (nbig + kOsTile - 1) / kOsTile;
+    GL_TRY(scratch.reserve(sizeof(uint32_t) * ((size_t)kOsStatusOff + (size_t)kOsMaxPasses * tiles_max * 256)));
+    uint32_t* sc = scratch.as<uint32_t>();
+    GL_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(uint32_t) * kOsStatusOff, s));
+    const int tile_keys = kOsTile;
+    const int64_t tiles = std::max<int64_t>(1, (n_max + tile_keys - 1) / tile_keys);
+    const int hblocks = (int)std::min<int64_t>(
+        kSortMaxBlocks, std::max<int64_t>(1, (n_max + kOsThreads * kOsHistKeys - 1) / (kOsThreads * kOsHistKeys)));
+    k_os_hist<<<hblocks, kOsThreads, 0, s>>>(k0, n_dev, passes, tile_keys, tiles_max, sc);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_sort_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_dev, shift, nblocks, hist.as<uint32_t>());
-        k_sort_rowscan<<<256, 256, 0, s>>>(hist.as<uint32_t>(), nblocks, totals);
-        k_sort_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, nblocks,
-                                                        hist.as<uint32_t>(), totals);
-        count_launches(3);
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(ctl + 8);
+    for (int p = 0; p < passes; p++) {
+        k_os_pass<kOsThreads, kOsItems, 3><<<(unsigned)tiles, kOsThreads, 0, s>>>(ki, vi, ko, vo, n_dev, p, tiles_max,
+                                                                                  sc, err);
         std::swap(ki, ko);
         std::swap(vi, vo);
     }
+    count_launches(1 + passes);
     GL_CUDA_TRY(cudaGetLastError());
     *out_k = ki;
     *out_v = vi;
     return GL_OK;
+}
+
+gl_status sort_wait_status(View& v, cudaStream_t s)
+{
+    if (!v.h_count || v.h_count[8] == 0) return GL_OK;
+    v.h_count[8] = 0;
+    GL_CUDA_TRY(cudaMemsetAsync(v.count.as<uint64_t>() + 8, 0, sizeof(uint64_t), s));
+    set_error("radix sort: a look-back wait gave up (result order invalid)");
+    return GL_ERR_TIMEOUT;
 }
 
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s)
@@ -693,7 +829,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         k_set_u64<<<1, 1, 0, s>>>(count + 2, (uint64_t)n, 0);
         count_launches(1);
         GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
-                              v.gidx2.as<uint32_t>(), count + 2, n, 32, v.hist, &sk, &sv, s));
+                              v.gidx2.as<uint32_t>(), count + 2, n, n, 32, v.hist, count, &sk, &sv, s));
     }
     v.sorted_g = sv;
 
@@ -713,8 +849,9 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         v.I = -1;   // known on the device only
         nmax = (int64_t)cap;
     } else {
-        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, 32, cudaMemcpyDeviceToHost, s));
+        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, kCountCopy, cudaMemcpyDeviceToHost, s));
         GL_CUDA_TRY(cudaStreamSynchronize(s));
+        GL_TRY(sort_wait_status(v, s));
         const uint64_t I = v.h_count[3];
         if (I > 0xffffffffull) {
             set_error("more than 2^32-1 (Gaussian, tile) instances in one step");
@@ -756,7 +893,8 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     {
         PhaseScope ps(v.prof, PH_TILE_SORT, s);
         GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
-                              v.ival2.as<uint32_t>(), count, nmax, tbits, v.hist, &sk, &sv, s));
+                              v.ival2.as<uint32_t>(), count, nmax, (int64_t)cap2, tbits, v.hist, count, &sk, &sv,
+                              s));
     }
     v.sorted_tile = sk;
     v.sorted_inst = sv;
@@ -772,6 +910,9 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         // steps (which size nothing) find room for any count that fits
         GL_TRY(permute_records(v, (int64_t)(v.itile.bytes / 4), s));
     }
+    // the counters reach the host at the caller's next synchronisation
+    // (sort_wait_status); graph steps copy them at the end of the step
+    if (!sync_free) GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, count, kCountCopy, cudaMemcpyDeviceToHost, s));
     return GL_OK;
 }
 

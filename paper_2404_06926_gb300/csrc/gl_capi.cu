@@ -158,8 +158,14 @@ void DevBuf::release()
 
 gl_status View::init()
 {
-    GL_TRY(count.reserve(64));
-    if (!h_count) GL_CUDA_TRY(cudaMallocHost(&h_count, 64));
+    if (!count.p) {
+        GL_TRY(count.reserve(128));
+        GL_CUDA_TRY(cudaMemset(count.p, 0, 128));
+    }
+    if (!h_count) {
+        GL_CUDA_TRY(cudaMallocHost(&h_count, 128));
+        std::memset(h_count, 0, 128);
+    }
     if (!hpin) GL_CUDA_TRY(cudaMallocHost(&hpin, kDescBlock * kDescRing));
     for (int i = 0; i < kDescRing; i++)
         if (!pin_ev[i]) GL_CUDA_TRY(cudaEventCreateWithFlags(&pin_ev[i], cudaEventDisableTiming));
@@ -791,7 +797,7 @@ extern "C" gl_status gl_render(gl_map* m, const gl_pose* pose, const gl_intrinsi
     if (out_depth) GL_TRY(from_device(out_depth, v.depth.as<float>(), P, m->stream));
     if (out_opacity) GL_TRY(from_device(out_opacity, v.opac.as<float>(), P, m->stream));
     GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
-    return GL_OK;
+    return sort_wait_status(v, m->stream);
 }
 
 namespace {
@@ -929,7 +935,7 @@ gl_status enqueue_step(gl_map* m, const StepPlan& sp, cudaStream_t s, bool sync_
     GL_TRY(params_adam(v, m->params(), gl_map::mut(m->prm), a, s));
     if (sync_free) {
         GL_CUDA_TRY(cudaMemcpyAsync(m->h_loss, m->loss_dev.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, s));
-        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, v.count.p, 32, cudaMemcpyDeviceToHost, s));
+        GL_CUDA_TRY(cudaMemcpyAsync(v.h_count, v.count.p, kCountCopy, cudaMemcpyDeviceToHost, s));
     }
     return GL_OK;
 }
@@ -1063,6 +1069,7 @@ gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
         count_launches(g->nodes);
         m->graph_replays++;
         GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        GL_TRY(sort_wait_status(v, m->stream));
         if (v.h_count[1] == 0) {
             if (out_loss) GL_TRY(read_loss(m, sp.V, false, out_loss));
             return GL_OK;
@@ -1073,6 +1080,8 @@ gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
     }
     GL_TRY(enqueue_step(m, sp, m->stream, false));
     GL_TRY(read_loss(m, sp.V, true, out_loss));
+    GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    GL_TRY(sort_wait_status(v, m->stream));
     if (graphs) capture_step(m, sp);
     return GL_OK;
 }

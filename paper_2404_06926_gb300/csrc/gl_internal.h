@@ -145,9 +145,10 @@ struct View {
     DevBuf g2d;               // float[10] screen-space gradient accumulators
     // scan
     DevBuf bsum;              // u64 per scan block
-    DevBuf count;             // u64[8]: I (0 after an overflow), overflow flag, N (depth
+    DevBuf count;             // u64[16]: I (0 after an overflow), overflow flag, N (depth
                               // sort), instances needed, view-count scratch [4..5],
-                              // work items [6], segment items [7]
+                              // work items [6], segment items [7], radix-sort wait
+                              // gave up [8] (sticky until sort_wait_status reads it)
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
@@ -163,7 +164,7 @@ struct View {
     const uint32_t* sorted_g = nullptr;
     const uint32_t* sorted_tile = nullptr;
     const uint32_t* sorted_inst = nullptr;
-    uint64_t* h_count = nullptr;          // pinned: I, overflow
+    uint64_t* h_count = nullptr;          // pinned copy of count[0..8]
     Prof* prof = nullptr;                 // optional phase timers
     // raster execution: records per lane per batch (1: 32, 2: 64), pixels per
     // lane (1, 2, 4), persistent grid with a unit counter in `work`
@@ -277,11 +278,19 @@ gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, 
 gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P,
                          cudaStream_t s);
 
-// Radix sort of (u32 key, u32 value) pairs over bits [0, bits); n on device.
-// Returns in *out_k/*out_v the buffers holding the result.
+// Stable radix sort of (u32 key, u32 value) pairs over bits [0, bits); n on
+// the device, at most n_max; scratch sized for max(n_max, n_reserve) keys;
+// ctl[8] is raised if a look-back wait gave up.  Returns in *out_k/*out_v the
+// buffers holding the result.
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                         const uint64_t* n_dev, int64_t n_max, int bits, DevBuf& hist,
-                         uint32_t** out_k, uint32_t** out_v, cudaStream_t s);
+                         const uint64_t* n_dev, int64_t n_max, int64_t n_reserve, int bits, DevBuf& scratch,
+                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s);
+// Bytes of the counters copied to View::h_count (count[0..8]).
+constexpr size_t kCountCopy = 9 * sizeof(uint64_t);
+// GL_ERR_TIMEOUT (once) if a radix-sort pass gave up a look-back wait, as
+// seen in the host copy of the counters taken before the caller's last
+// synchronisation; GL_OK otherwise.
+gl_status sort_wait_status(View& v, cudaStream_t s);
 
 // Visible Gaussians and the summed contributor count of the last view.
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s);

@@ -390,6 +390,7 @@ void render_worker(gl_server* s)
                 off += b;
             }
             if (cudaStreamSynchronize(s->rstream) != cudaSuccess && st == GL_OK) st = GL_ERR_CUDA;
+            if (st == GL_OK) st = sort_wait_status(s->rview, s->rstream);
             if (st == GL_ERR_CUDA) {
                 set_error(cudaGetErrorString(cudaGetLastError()));
             } else if (P > 0 && s->rview.I > 0) {
