@@ -87,6 +87,44 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     G.dir[0] = d0 * idn; G.dir[1] = d1 * idn; G.dir[2] = d2 * idn;
 }
 
+// Hint the L2 to fetch [p, p + bytes) (the 16-byte aligned part of it) with
+// one bulk prefetch; nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
+{
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
+// Shared-memory row stride of an array of WIDTH floats per Gaussian: rows of
+// an even number of float4 get one float4 of padding, so that the float4
+// reads of a quarter warp (8 rows) fall in distinct banks.
+template <int WIDTH>
+constexpr int staged_stride() { return (WIDTH % 4 == 0 && (WIDTH / 4) % 2 == 0) ? WIDTH + 4 : WIDTH; }
+
+// Copy the block's rows [g0, g0 + cnt) of one parameter array into shared
+// memory at the staged stride; float4 loads where rows allow them.
+template <int WIDTH>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ P, int64_t g0, int cnt, float* __restrict__ dst)
+{
+    constexpr int S = staged_stride<WIDTH>();
+    const float* src = P + (size_t)g0 * WIDTH;
+    const int ne = cnt * WIDTH;
+    if constexpr (WIDTH % 4 == 0) {
+        constexpr int R4 = WIDTH / 4;
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int f = threadIdx.x; f < ne / 4; f += kThreads) d4[(f / R4) * (S / 4) + f % R4] = s4[f];
+    } else {
+        // S == WIDTH: the span is copied as is
+        const int nv = ne / 4;
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int f = threadIdx.x; f < nv; f += kThreads) d4[f] = s4[f];
+        for (int e = 4 * nv + threadIdx.x; e < ne; e += kThreads) dst[e] = src[e];
+    }
+}
+
 // p -= lr (m / bc1) / (sqrt(v / bc2) + eps), with 1/bc1 and 1/sqrt(bc2)
 // precomputed for the step: the same update with one square root and one
 // fast division per element.
@@ -98,95 +136,171 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
 }
 
 // Block-cooperative pass over one parameter array of the block's Gaussians
-// (a contiguous span of cnt * WIDTH floats): MODE 0 writes the staged
-// gradients, MODE 1 applies Adam (the first three floats of a row take lr0,
-// the SH DC band; the rest lr).  Rows flagged off in upd are left untouched.
-template <int MODE, int WIDTH, int NR>
-__device__ __forceinline__ void coop_one(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
-                                         size_t base, int e, const float* __restrict__ sR, int off,
-                                         const uint8_t* __restrict__ upd, float lr, float lr0, const AdamArgs& ad)
-{
-    const int loc = e / WIDTH, w = e - loc * WIDTH;
-    if (!upd[loc]) return;
-    const float gr = sR[loc * NR + off + w];
-    if (MODE == 0) P[base + e] = gr;
-    else adam1(P[base + e], Mm[base + e], Vv[base + e], gr, w < 3 ? lr0 : lr, ad);
-}
-
-// Block-cooperative pass over one parameter array of the block's Gaussians
 // (a contiguous span of cnt * WIDTH floats, 16-byte aligned because blocks
-// start at multiples of 128 Gaussians): MODE 0 writes the staged gradients,
-// MODE 1 applies Adam (the first three floats of a row take lr0, the SH DC
-// band; the rest lr).  Rows flagged off in upd are left untouched.  float4
-// accesses, kUnroll per thread in flight.
+// start at multiples of 128 Gaussians): MODE 0 writes the gradient rows
+// (sR, stride NR, this array's columns from off), MODE 1 applies Adam to the
+// parameters staged in shared memory (sP, rows at the staged stride) and
+// writes them back with the moments (the first three floats of a row take
+// lr0, the SH DC band; the rest lr).  Rows flagged off in upd are left
+// untouched (MODE 1).  Rows of a multiple of 4 floats go by float4, a row
+// quarter per thread; other widths element by element.  kUnroll accesses per
+// thread are in flight.
 template <int MODE, int WIDTH, int NR>
 __device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
                                      int64_t g0, int cnt, const float* __restrict__ sR, int off,
-                                     const uint8_t* __restrict__ upd, float lr, float lr0, const AdamArgs& ad)
+                                     const float* __restrict__ sP, const uint8_t* __restrict__ upd, float lr,
+                                     float lr0, const AdamArgs& ad)
 {
+    constexpr int S = staged_stride<WIDTH>();
     const size_t base = (size_t)g0 * WIDTH;
-    const int ne = cnt * WIDTH, nv = ne / 4;
-    float4* P4 = reinterpret_cast<float4*>(P + base);
-    float4* M4 = reinterpret_cast<float4*>(Mm + base);
-    float4* V4 = reinterpret_cast<float4*>(Vv + base);
-    for (int f0 = threadIdx.x; f0 < nv; f0 += kUnroll * kThreads) {
-        float4 pp[kUnroll], mm[kUnroll], vv[kUnroll];
-        bool any[kUnroll];
+    if constexpr (WIDTH % 4 == 0) {
+        constexpr int R4 = WIDTH / 4;
+        const int nv = cnt * R4;
+        float4* P4 = reinterpret_cast<float4*>(P + base);
+        float4* M4 = reinterpret_cast<float4*>(Mm + base);
+        float4* V4 = reinterpret_cast<float4*>(Vv + base);
+        const float4* S4 = reinterpret_cast<const float4*>(sP);
+        for (int f0 = threadIdx.x; f0 < nv; f0 += kUnroll * kThreads) {
+            float4 pp[kUnroll], mm[kUnroll], vv[kUnroll];
+            int row[kUnroll], c4[kUnroll];
+            bool ok[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const int f = f0 + u * kThreads;
-            any[u] = false;
-            if (f < nv) {
-#pragma unroll
-                for (int e = 0; e < 4; e++) any[u] = any[u] || upd[(4 * f + e) / WIDTH];
+            for (int u = 0; u < kUnroll; u++) {
+                const int f = f0 + u * kThreads;
+                row[u] = f / R4;
+                c4[u] = f - row[u] * R4;
+                ok[u] = f < nv && (MODE == 0 || upd[row[u]]);
+                if (ok[u] && MODE == 1) {
+                    mm[u] = M4[f];
+                    vv[u] = V4[f];
+                    pp[u] = S4[row[u] * (S / 4) + c4[u]];
+                }
             }
-            if (any[u] && MODE == 1) { pp[u] = P4[f]; mm[u] = M4[f]; vv[u] = V4[f]; }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (!ok[u]) continue;
+                const int f = f0 + u * kThreads;
+                const float* gr = sR + row[u] * NR + off + 4 * c4[u];
+                if (MODE == 0) {
+                    P4[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+                } else {
+                    float* pa = &pp[u].x;
+                    float* ma = &mm[u].x;
+                    float* va = &vv[u].x;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) adam1(pa[e], ma[e], va[e], gr[e], 4 * c4[u] + e < 3 ? lr0 : lr, ad);
+                    P4[f] = pp[u];
+                    M4[f] = mm[u];
+                    V4[f] = vv[u];
+                }
+            }
         }
+    } else {
+        const int ne = cnt * WIDTH;
+        for (int e0 = threadIdx.x; e0 < ne; e0 += kUnroll * kThreads) {
+            float pv[kUnroll], mv[kUnroll], vv[kUnroll];
+            int row[kUnroll], w[kUnroll];
+            bool ok[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const int f = f0 + u * kThreads;
-            if (!any[u]) continue;
-            float* pa = &pp[u].x;
-            float* ma = &mm[u].x;
-            float* va = &vv[u].x;
-            float gr[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int el = 4 * f + e, loc = el / WIDTH, w = el - loc * WIDTH;
-                gr[e] = sR[loc * NR + off + w];
-                if (MODE == 1 && upd[loc]) adam1(pa[e], ma[e], va[e], gr[e], w < 3 ? lr0 : lr, ad);
+            for (int u = 0; u < kUnroll; u++) {
+                const int e = e0 + u * kThreads;
+                row[u] = e / WIDTH;
+                w[u] = e - row[u] * WIDTH;
+                ok[u] = e < ne && (MODE == 0 || upd[row[u]]);
+                if (ok[u] && MODE == 1) {
+                    mv[u] = Mm[base + e];
+                    vv[u] = Vv[base + e];
+                    pv[u] = sP[row[u] * S + w[u]];
+                }
             }
-            if (MODE == 0) {
-                // rows not updated still receive their (zero) gradient
-                P4[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
-            } else {
-                P4[f] = pp[u]; M4[f] = mm[u]; V4[f] = vv[u];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (!ok[u]) continue;
+                const int e = e0 + u * kThreads;
+                const float gr = sR[row[u] * NR + off + w[u]];
+                if (MODE == 0) {
+                    P[base + e] = gr;
+                } else {
+                    adam1(pv[u], mv[u], vv[u], gr, w[u] < 3 ? lr0 : lr, ad);
+                    P[base + e] = pv[u];
+                    Mm[base + e] = mv[u];
+                    Vv[base + e] = vv[u];
+                }
             }
         }
     }
-    for (int e = 4 * nv + threadIdx.x; e < ne; e += kThreads) coop_one<MODE, WIDTH, NR>(P, Mm, Vv, base, e, sR, off, upd, lr, lr0, ad);
 }
+
+// Shared memory of k_params_bwd (floats): the gradient rows (odd stride NR),
+// then the block's staged parameter rows (means, log-scales, quaternions,
+// logits, SH at their staged strides), each part 16-byte aligned.
+template <int DEG>
+struct ParamsSmem {
+    static constexpr int KF = (DEG + 1) * (DEG + 1) * 3;   // SH floats per Gaussian
+    static constexpr int NR = 11 + KF + ((11 + KF) % 2 == 0 ? 1 : 0);
+    static constexpr int SHS = staged_stride<KF>();
+    static constexpr int R = (kThreads * NR + 3) / 4 * 4;
+    static constexpr int MU = R, LS = MU + kThreads * 3, Q = LS + kThreads * 3, LG = Q + kThreads * 4,
+                         SH = LG + kThreads, END = SH + kThreads * SHS;
+    static constexpr size_t bytes = sizeof(float) * (size_t)END;
+};
 
 template <int DEG, int MODE>
 __global__ void __launch_bounds__(kThreads, 3)
 k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __restrict__ radius,
              const float* __restrict__ g2d, GMut out, AdamArgs ad, float* __restrict__ pose_part)
 {
+    using SM = ParamsSmem<DEG>;
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int KF = K * 3;   // SH floats per Gaussian
+    constexpr int KF = SM::KF;
     // one row of gradients per Gaussian of the block: means 3, log-scales 3,
     // quaternion 4, logit 1, SH KF (odd stride against bank conflicts); the
     // Adam update then streams every parameter array with coalesced accesses
-    constexpr int NR = 11 + KF + ((11 + KF) % 2 == 0 ? 1 : 0);
+    constexpr int NR = SM::NR;
     if (MODE == 1) {
         // a step whose binning overflowed its buffers updates nothing (it is re-run)
         if (ad.abort && ad.abort[1]) return;
         if (ad.bc) { ad.ibc1 = ad.bc[0]; ad.isbc2 = ad.bc[1]; }
     }
-    __shared__ float sR[kThreads * NR];
+    extern __shared__ float4 smem4[];
+    float* smf = reinterpret_cast<float*>(smem4);
+    float* sR = smf;
+    float* sMu = smf + SM::MU;
+    float* sLs = smf + SM::LS;
+    float* sQ = smf + SM::Q;
+    float* sLg = smf + SM::LG;
+    float* sSH = smf + SM::SH;
     __shared__ uint8_t sUpd[kThreads];
     const int64_t g0 = blockIdx.x * (int64_t)kThreads;
     const int64_t g = g0 + threadIdx.x;
+    const int cnt = (int)min((int64_t)kThreads, p.n - g0);
+    // the moments and screen-space gradients of the block head for the L2
+    // while its parameters are staged and its geometry is recomputed
+    if (threadIdx.x == 0) {
+        if (MODE == 1) {
+            const size_t c4 = sizeof(float) * (size_t)cnt;
+            prefetch_l2(ad.m.means + 3 * g0, 3 * c4);
+            prefetch_l2(ad.v.means + 3 * g0, 3 * c4);
+            prefetch_l2(ad.m.log_scales + 3 * g0, 3 * c4);
+            prefetch_l2(ad.v.log_scales + 3 * g0, 3 * c4);
+            prefetch_l2(ad.m.quats + 4 * g0, 4 * c4);
+            prefetch_l2(ad.v.quats + 4 * g0, 4 * c4);
+            prefetch_l2(ad.m.logits + g0, c4);
+            prefetch_l2(ad.v.logits + g0, c4);
+            prefetch_l2(ad.m.sh + (size_t)KF * g0, KF * c4);
+            prefetch_l2(ad.v.sh + (size_t)KF * g0, KF * c4);
+        }
+        for (int vw = 0; vw < V; vw++) {
+            prefetch_l2(g2d + ((size_t)vw * p.n + g0) * kNG, sizeof(float) * kNG * (size_t)cnt);
+            prefetch_l2(radius + (size_t)vw * p.n + g0, sizeof(int) * (size_t)cnt);
+        }
+    }
+    stage_rows<3>(p.means, g0, cnt, sMu);
+    stage_rows<3>(p.log_scales, g0, cnt, sLs);
+    stage_rows<4>(p.quats, g0, cnt, sQ);
+    stage_rows<1>(p.logits, g0, cnt, sLg);
+    stage_rows<KF>(p.sh, g0, cnt, sSH);
+    __syncthreads();
     float pose[6] = {0, 0, 0, 0, 0, 0};
     const bool valid = g < p.n;
     bool vis = false;
@@ -204,12 +318,13 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
     float grgb[3] = {0, 0, 0};
     float Y[16];
     {
-        float mu[3] = {p.means[3 * g], p.means[3 * g + 1], p.means[3 * g + 2]};
-        float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
-        const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
+        const int r = threadIdx.x;
+        float mu[3] = {sMu[3 * r], sMu[3 * r + 1], sMu[3 * r + 2]};
+        float ls[3] = {sLs[3 * r], sLs[3 * r + 1], sLs[3 * r + 2]};
+        const float4 q4 = reinterpret_cast<const float4*>(sQ)[r];
         float q[4] = {q4.x, q4.y, q4.z, q4.w};
         Geo G;
-        geometry(mu, ls, q, p.logits[g], cam, G);
+        geometry(mu, ls, q, sLg[r], cam, G);
 
         // screen-space gradients of this Gaussian, accumulated by the raster backward
         float s[kNG];
@@ -225,7 +340,7 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
 
         // colour -> SH and view direction (clamped channels pass no gradient)
         sh_eval<DEG>(G.dir[0], G.dir[1], G.dir[2], Y);
-        const float* sh = p.sh + (size_t)g * K * 3;
+        const float* sh = sSH + threadIdx.x * SM::SHS;
         float raw[3] = {0.5f, 0.5f, 0.5f};
         for (int k = 0; k < K; k++)
             for (int c = 0; c < 3; c++) raw[c] += Y[k] * sh[3 * k + c];
@@ -340,14 +455,14 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         row[10] = glg;
     }
     __syncthreads();
-    const int cnt = (int)min((int64_t)kThreads, p.n - g0);
     if (cnt > 0) {
-        coop<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sR, 0, sUpd, ad.lr_pos, ad.lr_pos, ad);
-        coop<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sR, 3, sUpd, ad.lr_scale,
+        coop<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sR, 0, sMu, sUpd, ad.lr_pos, ad.lr_pos, ad);
+        coop<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sR, 3, sLs, sUpd, ad.lr_scale,
                           ad.lr_scale, ad);
-        coop<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sR, 6, sUpd, ad.lr_rot, ad.lr_rot, ad);
-        coop<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sR, 10, sUpd, ad.lr_op, ad.lr_op, ad);
-        coop<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sR, 11, sUpd, ad.lr_rest, ad.lr_dc, ad);
+        coop<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sR, 6, sQ, sUpd, ad.lr_rot, ad.lr_rot, ad);
+        coop<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sR, 10, sLg, sUpd, ad.lr_op, ad.lr_op,
+                          ad);
+        coop<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sR, 11, sSH, sUpd, ad.lr_rest, ad.lr_dc, ad);
     }
 
     if (MODE == 0 && pose_part) {
@@ -385,9 +500,14 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
     const unsigned grid = (unsigned)((p.n + kThreads - 1) / kThreads);
     PhaseScope ps(v.prof, PH_PARAMS, s);
     count_launches(1);
-#define GL_PB(D_)                                                                            \
-    k_params_bwd<D_, MODE><<<grid, kThreads, 0, s>>>(p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), \
-                                                     o, a, pose_part)
+#define GL_PB(D_)                                                                                         \
+    {                                                                                                     \
+        static const cudaError_t attr = cudaFuncSetAttribute(                                             \
+            k_params_bwd<D_, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ParamsSmem<D_>::bytes); \
+        GL_CUDA_TRY(attr);                                                                                \
+        k_params_bwd<D_, MODE><<<grid, kThreads, ParamsSmem<D_>::bytes, s>>>(                             \
+            p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), o, a, pose_part);                  \
+    }
     switch (p.deg) {
         case 0: GL_PB(0); break;
         case 1: GL_PB(1); break;
