@@ -132,7 +132,10 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
 {
     m = a.b1 * m + (1.0f - a.b1) * g;
     v = a.b2 * v + (1.0f - a.b2) * g * g;
-    p -= __fdividef(lr * a.ibc1 * m, sqrtf(v) * a.isbc2 + a.eps);
+    // sqrt(v) as v * rsqrt(v) (the hardware reciprocal square root, a few
+    // ulp), 0 at v = 0
+    const float sv = v > 0.0f ? v * rsqrtf(v) : 0.0f;
+    p -= __fdividef(lr * a.ibc1 * m, sv * a.isbc2 + a.eps);
 }
 
 // Block-cooperative pass over one parameter array of the block's Gaussians
@@ -303,11 +306,10 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
     __syncthreads();
     float pose[6] = {0, 0, 0, 0, 0, 0};
     const bool valid = g < p.n;
-    bool vis = false;
+    bool vis = false, first = true;
 
     float gm[3] = {0, 0, 0}, gl3[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glg = 0.0f;
-    float* dsh = sR + threadIdx.x * NR + 11;   // this Gaussian's SH gradient, accumulated in place
-    for (int k = 0; k < KF; k++) dsh[k] = 0.0f;
+    float* dsh = sR + threadIdx.x * NR + 11;   // this Gaussian's SH gradient, summed over its views in place
 
     // every view the Gaussian is visible in contributes (window steps sum them)
     for (int vw = 0; vw < V && valid; vw++) {
@@ -316,8 +318,8 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
     vis = true;
     const Cam cam = views[vw].cam;
     float grgb[3] = {0, 0, 0};
-    float Y[16];
     {
+        float Y[16];
         const int r = threadIdx.x;
         float mu[3] = {sMu[3 * r], sMu[3 * r + 1], sMu[3 * r + 2]};
         float ls[3] = {sLs[3 * r], sLs[3 * r + 1], sLs[3 * r + 2]};
@@ -345,6 +347,12 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         for (int k = 0; k < K; k++)
             for (int c = 0; c < 3; c++) raw[c] += Y[k] * sh[3 * k + c];
         for (int c = 0; c < 3; c++) grgb[c] = raw[c] < 0.0f ? 0.0f : s[c];
+        // dL/dsh_k = Y_k dL/drgb (the first view writes the row)
+#pragma unroll
+        for (int k = 0; k < K; k++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) dsh[3 * k + c] = (first ? 0.0f : dsh[3 * k + c]) + Y[k] * grgb[c];
+        first = false;
         float gdir[3] = {0, 0, 0};
         if (DEG > 0) sh_grad_acc<DEG>(G.dir[0], G.dir[1], G.dir[2], sh, grgb, gdir);
         const float dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
@@ -438,12 +446,9 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         pose[4] += P[6] - P[2];
         pose[5] += P[1] - P[3];
     }
-
-#pragma unroll
-    for (int k = 0; k < K; k++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) dsh[3 * k + c] += Y[k] * grgb[c];
     }
+    if (!vis)
+        for (int k = 0; k < KF; k++) dsh[k] = 0.0f;
 
     const bool upd = valid && (MODE == 0 || !ad.sparse || vis);
     sUpd[threadIdx.x] = upd ? 1 : 0;
