@@ -74,10 +74,14 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
              float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
              float4* __restrict__ rec3, int* __restrict__ radius, int4* __restrict__ rect,
              uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey, uint32_t* __restrict__ gidx,
-             unsigned long long* __restrict__ kmask)
+             unsigned long long* __restrict__ kmask, uint64_t* __restrict__ ctl)
 {
     // t indexes (view, Gaussian) pairs: t = view * n + g
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t == 0) {
+        ctl[2] = (uint64_t)total;   // keys of the depth sort
+        ctl[3] = 0;
+    }
     if (t >= total) return;
     const int vw = (int)(t / p.n);
     const int64_t g = t - (int64_t)vw * p.n;
@@ -493,8 +497,8 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
 // longest-processing-time first), so long tiles start early instead of
 // forming the tail.  Order within a bucket is arbitrary; tiles are
 // independent, so results do not depend on it.
-__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
-                                                     uint32_t* __restrict__ order)
+__device__ __forceinline__ void tile_order_block(const uint32_t* __restrict__ ranges, int ntiles,
+                                                 uint32_t* __restrict__ order)
 {
     __shared__ uint32_t cnt[33], off[33];
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
@@ -521,11 +525,14 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
 // for a tile whose list holds at least 2 seg records, one per segment of
 // seg records (seg a power of two, so such tiles sit in the log2 buckets
 // ahead of all others and their items come first).  item = (tile,
-// segment); count[6] = items, count[7] = items of split tiles.
-__global__ void __launch_bounds__(1024) k_seg_items(const uint32_t* __restrict__ order,
-                                                    const uint32_t* __restrict__ ranges, int ntiles, int seg,
-                                                    uint2* __restrict__ items, uint64_t* __restrict__ count)
+// segment); count[6] = items, count[7] = items of split tiles.  One CTA of
+// 1024 threads computes the tile launch order first, then the items.
+__global__ void __launch_bounds__(1024) k_order_items(const uint32_t* __restrict__ ranges, int ntiles, int seg,
+                                                      uint32_t* __restrict__ order, uint2* __restrict__ items,
+                                                      uint64_t* __restrict__ count)
 {
+    tile_order_block(ranges, ntiles, order);
+    __syncthreads();   // the block's writes of order are visible to all its threads
     __shared__ uint32_t sm[1024 / 32 + 1];
     __shared__ uint32_t seg_end;
     if (threadIdx.x == 0) seg_end = 0;
@@ -629,8 +636,9 @@ int64_t work_items_bound(const View& v)
 gl_status build_items(View& v, cudaStream_t s)
 {
     GL_TRY(v.items.reserve(sizeof(uint2) * (size_t)std::max<int64_t>(work_items_bound(v), 1)));
-    k_seg_items<<<1, 1024, 0, s>>>(v.tile_order.as<uint32_t>(), v.ranges.as<uint32_t>(), v.ntiles, v.seg,
-                                   v.items.as<uint2>(), v.count.as<uint64_t>());
+    GL_TRY(v.tile_order.reserve(4 * (size_t)std::max(v.ntiles, 1)));
+    k_order_items<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.seg, v.tile_order.as<uint32_t>(),
+                                     v.items.as<uint2>(), v.count.as<uint64_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
@@ -802,9 +810,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     if (n == 0) {
         v.I = 0;
         k_set_u64<<<1, 1, 0, s>>>(count, 0, 0);
-        GL_TRY(v.tile_order.reserve(4 * (size_t)v.ntiles));
-        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
-        count_launches(2);
+        count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());
         return build_items(v, s);
     }
@@ -813,10 +819,10 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     PhaseScope ps(v.prof, PH_PREPROCESS, s);
     count_launches(1);
     switch (p.deg) {
-        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
-        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
-        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
-        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>()); break;
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
@@ -826,8 +832,6 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     uint32_t *sk, *sv;
     {
         PhaseScope ps(v.prof, PH_DEPTH_SORT, s);
-        k_set_u64<<<1, 1, 0, s>>>(count + 2, (uint64_t)n, 0);
-        count_launches(1);
         GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
                               v.gidx2.as<uint32_t>(), count + 2, n, n, 32, v.hist, count, &sk, &sv, s));
     }
@@ -883,9 +887,6 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     if (nmax == 0) {
         v.sorted_tile = v.itile.as<uint32_t>();
         v.sorted_inst = v.ival.as<uint32_t>();
-        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
-        count_launches(1);
-        GL_CUDA_TRY(cudaGetLastError());
         return build_items(v, s);
     }
     // stable sort of the instances by tile id
@@ -902,8 +903,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         PhaseScope ps(v.prof, PH_RANGES, s);
         int rb = (int)std::min<int64_t>(4 * 152, (nmax + 255) / 256);
         k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
-        k_tile_order<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.tile_order.as<uint32_t>());
-        count_launches(2);
+        count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());
         GL_TRY(build_items(v, s));
         // the sorted records always get the full capacity, so that graph
