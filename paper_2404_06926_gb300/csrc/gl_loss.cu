@@ -9,11 +9,14 @@
 // exposed colour and the target over the tile plus a 10-pixel halo, blurs the
 // five moment maps separably over a 5-pixel halo, forms the SSIM map and its
 // partials w.r.t. (mu_x, E[x^2], E[xy]), blurs those back (the adjoint of a
-// zero-padded symmetric correlation is the same correlation) and writes
-// dL/dC = A^T dL/dE[C].  In every pass a thread slides the 11 taps along a
+// zero-padded symmetric correlation is the same correlation) and adds the
+// channel's part of dL/dC = A^T dL/dE[C] (the thread owning a pixel is the
+// same in every channel).  In every pass a thread slides the 11 taps along a
 // run of 7-8 outputs held in registers, so each shared-memory value is read
-// once per run rather than once per tap and output.  Per-CTA partial sums of |.|, SSIM and dL/dE are
-// reduced afterwards in a fixed order, in double.
+// once per run rather than once per tap and output.  The maps of later passes
+// reuse the space of those consumed (65 KB, three CTAs per SM).  Per-CTA
+// partial sums of |.|, SSIM and dL/dE are reduced afterwards in a fixed
+// order, in double.
 #include "gl_internal.h"
 
 #include <algorithm>
@@ -35,7 +38,10 @@ static_assert(RB % HR == 0 && RB % VR == 0 && LT % AR == 0, "run lengths must ti
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
-constexpr size_t kSmemFloats = 2 * RA * RA + 5 * RA * RB + 3 * RB * RB + 3 * LT * LT;
+// x and y over the tile and halo (later the three SSIM partial maps), then
+// the five moment maps (later the horizontally blurred partials)
+constexpr size_t kSmemFloats = 2 * RA * RA + 5 * RA * RB;
+static_assert(3 * RB * RB <= 2 * RA * RA && 3 * RB * LT <= 5 * RA * RB, "aliased maps must fit");
 
 // One view passed by value (the stateless and allocation-free entry points).
 struct LossOne {
@@ -49,7 +55,7 @@ struct LossOne {
 // Grid: one CTA per 32x32 loss tile over all views.  With `views` null the
 // single view `one` is used; otherwise view, images, exposure and weight
 // come from the descriptors and images are the concatenated ones.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __restrict__ rgb_all,
        float* __restrict__ dL_all, float lambda, float* __restrict__ part)
 {
@@ -76,8 +82,7 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
     float* xs = sm;
     float* ys = xs + RA * RA;
     float* hm = ys + RA * RA;          // 5 maps, RA rows x RB cols
-    float* gmap = hm + 5 * RA * RB;    // 3 maps, RB x RB
-    float* dch = gmap + 3 * RB * RB;   // 3 channels, LT x LT
+    float* gmap = xs;                  // 3 maps, RB x RB (reuses x, y after the horizontal pass)
     float* hg = hm;                    // 3 maps, RB rows x LT cols (reuses hm)
     __shared__ float wt[11];
     __shared__ float Es[12];
@@ -96,8 +101,11 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
     const float gS = -lambda * invN * weight;
     const float gL1 = (1.0f - lambda) * invN * weight;
     float l1acc = 0.0f, sacc = 0.0f;
+    const int lane = tid & 31, wid = tid >> 5;
 
     for (int ch = 0; ch < 3; ch++) {
+        // exposure gradient partials of this channel: sum g C_j (j < 3), sum g
+        float pe[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         const float e0 = Es[4 * ch], e1 = Es[4 * ch + 1], e2 = Es[4 * ch + 2], e3 = Es[4 * ch + 3];
         for (int e = tid; e < RA * RA; e += kThreads) {
             const int gx = ox - 2 * HW + e % RA, gy = oy - 2 * HW + e / RA;
@@ -209,53 +217,51 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
                     acc[m][o] = a;
                 }
             }
+            // dL/dE[C]_ch of the pixels (x, y read again: their shared copy
+            // now holds the partial maps); dL/dC += A_ch^T dL/dE[C]_ch, by
+            // the thread that owns the pixel in every channel
 #pragma unroll
             for (int o = 0; o < AR; o++) {
                 const int r = r0 + o;
                 const int gx = ox + c, gy = oy + r;
-                float g = 0.0f;
                 if (gx < W && gy < H) {
-                    const float x = xs[(r + 2 * HW) * RA + c + 2 * HW], y = ys[(r + 2 * HW) * RA + c + 2 * HW];
+                    const size_t p = (size_t)gy * W + gx;
+                    const float c0 = rgb[3 * p], c1 = rgb[3 * p + 1], c2 = rgb[3 * p + 2];
+                    const float x = e0 * c0 + e1 * c1 + e2 * c2 + e3, y = target[3 * p + ch];
                     const float d = x - y;
                     l1acc += fabsf(d);
-                    g = acc[0][o] + 2.f * x * acc[1][o] + y * acc[2][o] + gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
+                    const float g = acc[0][o] + 2.f * x * acc[1][o] + y * acc[2][o] +
+                                    gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
+                    pe[0] += g * c0; pe[1] += g * c1; pe[2] += g * c2; pe[3] += g;
+                    if (ch == 0) {
+                        dL_drgb[3 * p] = e0 * g;
+                        dL_drgb[3 * p + 1] = e1 * g;
+                        dL_drgb[3 * p + 2] = e2 * g;
+                    } else {
+                        dL_drgb[3 * p] += e0 * g;
+                        dL_drgb[3 * p + 1] += e1 * g;
+                        dL_drgb[3 * p + 2] += e2 * g;
+                    }
                 }
-                dch[ch * LT * LT + r * LT + c] = g;
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float v = pe[i];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+            if (lane == 0) red[4 * ch + i][wid] = v;
         }
         __syncthreads();
     }
 
-    float pe[12];
+    {
+        const float vals[2] = {l1acc, sacc};
 #pragma unroll
-    for (int i = 0; i < 12; i++) pe[i] = 0.0f;
-    for (int e = tid; e < LT * LT; e += kThreads) {
-        const int gx = ox + e % LT, gy = oy + e / LT;
-        if (gx >= W || gy >= H) continue;
-        const size_t p = (size_t)gy * W + gx;
-        const float c0 = rgb[3 * p], c1 = rgb[3 * p + 1], c2 = rgb[3 * p + 2];
-        const float g0 = dch[e], g1 = dch[LT * LT + e], g2 = dch[2 * LT * LT + e];
-        dL_drgb[3 * p] = Es[0] * g0 + Es[4] * g1 + Es[8] * g2;
-        dL_drgb[3 * p + 1] = Es[1] * g0 + Es[5] * g1 + Es[9] * g2;
-        dL_drgb[3 * p + 2] = Es[2] * g0 + Es[6] * g1 + Es[10] * g2;
-        const float gg[3] = {g0, g1, g2};
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            pe[4 * i] += gg[i] * c0; pe[4 * i + 1] += gg[i] * c1; pe[4 * i + 2] += gg[i] * c2;
-            pe[4 * i + 3] += gg[i];
+        for (int i = 0; i < 2; i++) {
+            float v = vals[i];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+            if (lane == 0) red[12 + i][wid] = v;
         }
-    }
-    float vals[kNP];
-#pragma unroll
-    for (int i = 0; i < 12; i++) vals[i] = pe[i];
-    vals[12] = l1acc;
-    vals[13] = sacc;
-    const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-    for (int i = 0; i < kNP; i++) {
-        float v = vals[i];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (lane == 0) red[i][w] = v;
     }
     __syncthreads();
     if (tid < kNP) {
