@@ -359,19 +359,30 @@ __device__ __forceinline__ void prefix_item(int u, const RasterArgs& A, int lane
         float Tb = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, oo = 0.f;
         uint32_t last = 0;
         int stop = ns;
+        // segment s's seven fields are loaded during segment s - 1, so that
+        // the serial walk waits for memory once rather than once per segment
+        float f[7], nf[7];
+#pragma unroll
+        for (int k = 0; k < 7; k++) f[k] = S[seg_at(w0, k, q, TS)];
         for (int s = 0; s < ns; s++) {
             const int ws = w0 + s;
-            const float Ts = S[seg_at(ws, 0, q, TS)];
+            if (s + 1 < ns) {
+#pragma unroll
+                for (int k = 0; k < 7; k++) nf[k] = S[seg_at(ws + 1, k, q, TS)];
+            }
+            const float Ts = f[0];
             S[seg_at(ws, 7, q, TS)] = Tb;
             if (__fmul_rn(Tb, Ts) < kTransMin) { stop = s; break; }
-            c0 += Tb * S[seg_at(ws, 1, q, TS)];
-            c1 += Tb * S[seg_at(ws, 2, q, TS)];
-            c2 += Tb * S[seg_at(ws, 3, q, TS)];
-            dd += Tb * S[seg_at(ws, 4, q, TS)];
-            oo += Tb * S[seg_at(ws, 5, q, TS)];
-            const uint32_t ls = __float_as_uint(S[seg_at(ws, 6, q, TS)]);
+            c0 += Tb * f[1];
+            c1 += Tb * f[2];
+            c2 += Tb * f[3];
+            dd += Tb * f[4];
+            oo += Tb * f[5];
+            const uint32_t ls = __float_as_uint(f[6]);
             if (ls) last = ls;
             Tb = __fmul_rn(Tb, Ts);
+#pragma unroll
+            for (int k = 0; k < 7; k++) f[k] = nf[k];
         }
         S[seg_at(w0, 8, q, TS)] = __uint_as_float((uint32_t)stop);
         S[seg_at(w0, 9, q, TS)] = Tb;
@@ -471,17 +482,23 @@ __device__ __forceinline__ void finish_item(int u, const RasterArgs& A, const Ra
         O.Tfin[p] = Tb;
         O.ncon[p] = last;
         const int jl = stop < ns ? stop : ns - 1;
+        for (int s = ns - 1; s > jl; s--)
+            for (int k = 0; k < 6; k++) S[seg_at(w0 + s, k, q, TS)] = 0.0f;
+        // back to front from the stop segment; segment s - 1's fields
+        // (0-5 and the incoming transmittance, 7) are loaded during segment s
         float R0 = 0.f, R1 = 0.f, R2 = 0.f, RD = 0.f, RO = 0.f;
-        for (int s = ns - 1; s >= 0; s--) {
+        float f[7], nf[7];
+#pragma unroll
+        for (int k = 0; k < 6; k++) f[k] = S[seg_at(w0 + jl, k, q, TS)];
+        f[6] = S[seg_at(w0 + jl, 7, q, TS)];
+        for (int s = jl; s >= 0; s--) {
             const int ws = w0 + s;
-            if (s > jl) {
-                for (int k = 0; k < 6; k++) S[seg_at(ws, k, q, TS)] = 0.0f;
-                continue;
+            if (s > 0) {
+#pragma unroll
+                for (int k = 0; k < 6; k++) nf[k] = S[seg_at(ws - 1, k, q, TS)];
+                nf[6] = S[seg_at(ws - 1, 7, q, TS)];
             }
-            const float Ts = S[seg_at(ws, 0, q, TS)];
-            const float cs0 = S[seg_at(ws, 1, q, TS)], cs1 = S[seg_at(ws, 2, q, TS)], cs2 = S[seg_at(ws, 3, q, TS)];
-            const float ds = S[seg_at(ws, 4, q, TS)], os = S[seg_at(ws, 5, q, TS)];
-            const float tin = S[seg_at(ws, 7, q, TS)];
+            const float Ts = f[0], cs0 = f[1], cs1 = f[2], cs2 = f[3], ds = f[4], os = f[5], tin = f[6];
             S[seg_at(ws, 0, q, TS)] = __fmul_rn(tin, Ts);
             S[seg_at(ws, 1, q, TS)] = R0;
             S[seg_at(ws, 2, q, TS)] = R1;
@@ -490,6 +507,8 @@ __device__ __forceinline__ void finish_item(int u, const RasterArgs& A, const Ra
             S[seg_at(ws, 5, q, TS)] = RO;
             R0 = cs0 + Ts * R0; R1 = cs1 + Ts * R1; R2 = cs2 + Ts * R2;
             RD = ds + Ts * RD; RO = os + Ts * RO;
+#pragma unroll
+            for (int k = 0; k < 7; k++) f[k] = nf[k];
         }
     }
 }
