@@ -332,6 +332,16 @@ GL_API const char* gl_phase_name(int32_t i);
 /* Number of kernels this library has launched in this process so far. */
 GL_API int64_t gl_kernel_launch_count(void);
 
+/* Self-test of the bounded device waits (no GPU fault, no hang): runs one
+ * radix-sort scatter pass as the CTA of tile 1 of a two-tile sort whose tile
+ * 0 is never published, so its look-back wait has nothing to find and must
+ * give up after its poll limit (about a second).  *expired (host) receives
+ * 1 if the pass gave up and raised its flag, 0 otherwise; the pass writes
+ * only its own scratch buffers, which are freed before returning.
+ * Synchronous; uses device 0's current context.  Errors: GL_ERR_INVALID
+ * (null expired), GL_ERR_OOM, GL_ERR_CUDA. */
+GL_API gl_status gl_selftest_bounded_wait(int32_t* expired);
+
 /* ---------------------------------------------------------------------- */
 /* Serving loop (not in the paper, which runs the mapping thread of        */
 /* Sec. III-C beside tracking): a request loop over one map that keeps    */

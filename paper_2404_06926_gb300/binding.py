@@ -131,6 +131,7 @@ def lib():
             "gl_map_get_config": ([P, P], i32),
             "gl_map_save": ([P, i32, P, i64], i32),
             "gl_map_load": ([P, P, i64], i32),
+            "gl_selftest_bounded_wait": ([P], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -313,6 +314,15 @@ def photometric_loss_noalloc(rgb, target, E, lam: float = 0.2, stream=None):
 def kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(lib().gl_kernel_launch_count())
+
+
+def selftest_bounded_wait() -> bool:
+    """Run the device self-test of the bounded waits (a radix-sort pass whose
+    look-back can never complete); True if the wait gave up and raised its
+    flag.  Takes about a second."""
+    expired = C.c_int32(0)
+    check(lib().gl_selftest_bounded_wait(C.byref(expired)))
+    return bool(expired.value)
 
 
 def keyframe(kid: int, cam: dict, image=None) -> Keyframe:

@@ -680,6 +680,47 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
     return GL_OK;
 }
 
+gl_status sort_wait_selftest(int32_t* expired)
+{
+    // two tiles of keys; the tile counter starts at 1, so the only CTA takes
+    // tile 1 and looks back at tile 0, whose look-back words stay zero
+    const uint64_t n = 2 * (uint64_t)kOsTile;
+    const int64_t tiles_max = 2;
+    const size_t words = (size_t)kOsStatusOff + (size_t)tiles_max * 256;
+    struct Bufs {
+        DevBuf keys, vals, kout, vout, scratch, ctl;
+        ~Bufs()
+        {
+            for (DevBuf* b : {&keys, &vals, &kout, &vout, &scratch, &ctl}) b->release();
+        }
+    } B;
+    DevBuf &keys = B.keys, &vals = B.vals, &kout = B.kout, &vout = B.vout, &scratch = B.scratch, &ctl = B.ctl;
+    GL_TRY(keys.reserve(4 * n));
+    GL_TRY(vals.reserve(4 * n));
+    GL_TRY(kout.reserve(4 * n));
+    GL_TRY(vout.reserve(4 * n));
+    GL_TRY(scratch.reserve(4 * words));
+    GL_TRY(ctl.reserve(16 * sizeof(uint64_t)));
+    GL_CUDA_TRY(cudaMemset(keys.p, 0, 4 * n));
+    GL_CUDA_TRY(cudaMemset(vals.p, 0, 4 * n));
+    GL_CUDA_TRY(cudaMemset(scratch.p, 0, 4 * words));
+    GL_CUDA_TRY(cudaMemset(ctl.p, 0, 16 * sizeof(uint64_t)));
+    uint64_t* c = ctl.as<uint64_t>();
+    GL_CUDA_TRY(cudaMemcpy(c, &n, sizeof(n), cudaMemcpyHostToDevice));   // ctl[0] = n
+    const uint32_t one = 1;
+    GL_CUDA_TRY(cudaMemcpy(scratch.as<uint32_t>() + kOsTicketOff, &one, sizeof(one), cudaMemcpyHostToDevice));
+    k_os_pass<kOsThreads, kOsItems, 3><<<1, kOsThreads>>>(keys.as<uint32_t>(), vals.as<uint32_t>(), kout.as<uint32_t>(),
+                                                         vout.as<uint32_t>(), c, 0, tiles_max, scratch.as<uint32_t>(),
+                                                         reinterpret_cast<unsigned long long*>(c + 8));
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    GL_CUDA_TRY(cudaDeviceSynchronize());
+    uint64_t flag = 0;
+    GL_CUDA_TRY(cudaMemcpy(&flag, c + 8, sizeof(flag), cudaMemcpyDeviceToHost));
+    *expired = flag ? 1 : 0;
+    return GL_OK;
+}
+
 gl_status sort_wait_status(View& v, cudaStream_t s)
 {
     if (!v.h_count || v.h_count[8] == 0) return GL_OK;

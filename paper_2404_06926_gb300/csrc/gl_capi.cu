@@ -1197,6 +1197,13 @@ extern "C" const char* gl_phase_name(int32_t i)
 
 extern "C" int64_t gl_kernel_launch_count(void) { return g_launches.load(); }
 
+extern "C" gl_status gl_selftest_bounded_wait(int32_t* expired)
+{
+    if (!expired) { set_error("null expired"); return GL_ERR_INVALID; }
+    *expired = 0;
+    return sort_wait_selftest(expired);
+}
+
 // ---------------------------------------------------------------------------
 // Step execution and the autotuner
 // ---------------------------------------------------------------------------

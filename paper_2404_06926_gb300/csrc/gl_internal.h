@@ -291,6 +291,9 @@ constexpr size_t kCountCopy = 9 * sizeof(uint64_t);
 // seen in the host copy of the counters taken before the caller's last
 // synchronisation; GL_OK otherwise.
 gl_status sort_wait_status(View& v, cudaStream_t s);
+// Runs one sort pass whose look-back can never complete (see
+// gl_selftest_bounded_wait); *expired = 1 if it gave up and raised its flag.
+gl_status sort_wait_selftest(int32_t* expired);
 
 // Visible Gaussians and the summed contributor count of the last view.
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s);

@@ -62,6 +62,7 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     assert L.gl_server_create(None, None, None) == 1
     assert L.gl_server_submit(None, None, None) == 1
     assert L.gl_map_save(None, 0, None, 0) == 1
+    assert L.gl_selftest_bounded_wait(None) == 1
 
 
 def test_struct_layouts_match_c(libpath, tmp_path):
