@@ -134,9 +134,13 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
     }
     // log2-domain conic and opacity for the raster kernels
     const float A = D.c * id, B = -D.b * id, C = D.a * id;
-    rec0[t] = make_float4(D.u, D.v, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
-    rec1[t] = make_float4(-kLog2e * B, log2f(o), D.z, o);
-    rec2[t] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
+    // the mean for rendering in double-float (hi in rec0, lo in rec2.w and
+    // rec1.w); the permute makes it tile-relative
+    float uh, ul, vh, vl;
+    mean2d_df(mu, cam, uh, ul, vh, vl);
+    rec0[t] = make_float4(uh, vh, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
+    rec1[t] = make_float4(-kLog2e * B, log2f(o), D.z, vl);
+    rec2[t] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), ul);
     // conservative box of {alpha >= 1/255}: the ellipse d^T Sigma'^-1 d <= 2 ln(255 o)
     const float kappa = 2.0f * logf(255.0f * o);
     if (kappa > 0.0f) {
@@ -595,7 +599,7 @@ __global__ void k_export_pre(const float4* __restrict__ rec0, const float4* __re
             conic[3 * g + 1] = b.x / -kLog2e;
             conic[3 * g + 2] = a.w / (-0.5f * kLog2e);
         }
-        if (opacity) opacity[g] = b.w;
+        if (opacity) opacity[g] = exp2f(b.y);
         if (depth) depth[g] = b.z;
         if (rgb) { rgb[3 * g] = c.x; rgb[3 * g + 1] = c.y; rgb[3 * g + 2] = c.z; }
     }

@@ -388,6 +388,83 @@ __device__ __forceinline__ void sh_grad_acc(float x, float y, float z, const flo
 }
 
 // ---------------------------------------------------------------------------
+// The screen-space mean mu' = pi(R mu + t) (Eq. 2) for rendering, in
+// double-float arithmetic: a value is an unevaluated sum hi + lo of two
+// floats, built from the error-free transformations TwoSum (Knuth) and
+// TwoProd by fused multiply-add (the method of Dekker, 1971).  World
+// coordinates of tens to hundreds of metres cancel in R mu + t, and a float
+// product loses up to ~1e-4 px of the mean at 1280 px; the double-float
+// result is exact to ~1e-12 px, so a pixel's offset from the mean can be
+// formed to float precision relative to its tile (see the record permute).
+// The decision path (decide) keeps its own rounded float mean.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (ah + al) + (bh + bl)
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    two_sum(s, __fadd_rn(e, __fadd_rn(al, bl)), sh, sl);
+}
+
+// (ah + al) * b
+__device__ __forceinline__ void df_mul_f(float ah, float al, float b, float& ph, float& pl)
+{
+    float p, e;
+    two_prod(ah, b, p, e);
+    two_sum(p, __fmaf_rn(al, b, e), ph, pl);
+}
+
+// (ah + al) / (bh + bl): the float quotient plus one correction from the
+// remainder a - q b, formed with TwoProd
+__device__ __forceinline__ void df_div(float ah, float al, float bh, float bl, float& qh, float& ql)
+{
+    const float q1 = __fdiv_rn(ah, bh);
+    float p, e;
+    two_prod(q1, bh, p, e);
+    float rh, re;
+    two_sum(ah, -p, rh, re);
+    const float r = __fadd_rn(__fsub_rn(__fadd_rn(rh, __fadd_rn(re, al)), e), -__fmul_rn(q1, bl));
+    two_sum(q1, __fdiv_rn(r, bh), qh, ql);
+}
+
+// mu' as (u_hi + u_lo, v_hi + v_lo); z > 0 is known (the decision passed)
+__device__ __forceinline__ void mean2d_df(const float mu[3], const Cam& cam, float& uh, float& ul, float& vh,
+                                          float& vl)
+{
+    float c[3][2];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float h, l, ph, pl;
+        two_prod(cam.R[3 * i], mu[0], h, l);
+        two_prod(cam.R[3 * i + 1], mu[1], ph, pl);
+        df_add(h, l, ph, pl, h, l);
+        two_prod(cam.R[3 * i + 2], mu[2], ph, pl);
+        df_add(h, l, ph, pl, h, l);
+        df_add(h, l, cam.t[i], 0.0f, c[i][0], c[i][1]);
+    }
+    float qh, ql;
+    df_div(c[0][0], c[0][1], c[2][0], c[2][1], qh, ql);
+    df_mul_f(qh, ql, cam.fx, qh, ql);
+    df_add(qh, ql, cam.cx, 0.0f, uh, ul);
+    df_div(c[1][0], c[1][1], c[2][0], c[2][1], qh, ql);
+    df_mul_f(qh, ql, cam.fy, qh, ql);
+    df_add(qh, ql, cam.cy, 0.0f, vh, vl);
+}
+
+// ---------------------------------------------------------------------------
 // Per-pair blending weight (Eq. 4) shared by the forward and the backward
 // raster kernels, evaluated in the log2 domain:
 //   e = log2(o exp(power)) = A' dx^2 + C' dy^2 + B' dx dy + log2(o),
@@ -395,7 +472,9 @@ __device__ __forceinline__ void sh_grad_acc(float x, float y, float z, const flo
 // Gaussian.  The pair is skipped when e < log2(1/255) (alpha below 1/255) or
 // when e > log2(o) (power > 0, possible only through rounding).  Explicitly
 // rounded operations keep the decisions of the two kernels identical.
-// Record layout: r0 = (u, v, A', C'), r1 = (B', log2 o, depth, o).
+// Records as the raster kernels read them (sorted-instance order): r0 =
+// (u, v, A', C') with (u, v) relative to the origin of the instance's tile,
+// r1 = (B', log2 o, depth, -); (px, py) are tile-relative pixel coordinates.
 // ---------------------------------------------------------------------------
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2AlphaMin = -7.994353436858858f;   // log2(1/255)

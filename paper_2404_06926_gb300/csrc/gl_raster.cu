@@ -254,18 +254,18 @@ __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uin
 template <int D>
 struct LanePix {
     int x;
-    float px, py[D];
+    float px, py[D];   // relative to the tile's origin, as the records' means
     bool inside[D];
     int p[D];          // pixel index within the tile
     float bx0, bx1, by0, by1;
     __device__ __forceinline__ LanePix(const Unit& U, int TS, int lane)
     {
         x = U.x0 + (lane & 7);
-        px = (float)x;
+        px = (float)(U.lx0 + (lane & 7));
 #pragma unroll
         for (int j = 0; j < D; j++) {
             const int y = U.y0 + (lane >> 3) + 4 * j;
-            py[j] = (float)y;
+            py[j] = (float)(U.ly0 + (lane >> 3) + 4 * j);
             inside[j] = x < U.W && y < U.H;
             p[j] = (U.ly0 + (lane >> 3) + 4 * j) * TS + U.lx0 + (lane & 7);
         }
@@ -765,8 +765,12 @@ __global__ void k_part_reduce(const float* __restrict__ part, const uint32_t* __
     }
 }
 
-// Records in sorted-instance order (and the owning Gaussian of each).
+// Records in sorted-instance order (and the owning Gaussian of each), the
+// mean made relative to the origin of the instance's tile: (u_hi - x0) is
+// exact near the tile (Sterbenz), and adding u_lo leaves an offset accurate
+// to float precision of a number of pixels, not of the image coordinate.
 __global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __restrict__ sinst,
+                          const uint32_t* __restrict__ stile, const ViewDesc* __restrict__ views, int V, int TS,
                           const uint32_t* __restrict__ owner, const float4* __restrict__ r0,
                           const float4* __restrict__ r1, const float4* __restrict__ r2,
                           const float4* __restrict__ r3, float4* __restrict__ s0, float4* __restrict__ s1,
@@ -775,7 +779,15 @@ __global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __
     const uint64_t I = *n_dev;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < I; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t g = owner[sinst[i]];
-        s0[i] = r0[g]; s1[i] = r1[g]; s2[i] = r2[g]; s3[i] = r3[g];
+        const int tile = (int)stile[i];
+        const ViewDesc& d = views[view_of_tile(views, V, tile)];
+        const int lt = tile - d.tile_base;
+        const float x0 = (float)((lt % d.TX) * TS), y0 = (float)((lt / d.TX) * TS);
+        float4 a = r0[g];
+        const float4 b = r1[g], c = r2[g];
+        a.x = __fadd_rn(__fsub_rn(a.x, x0), c.w);
+        a.y = __fadd_rn(__fsub_rn(a.y, y0), b.w);
+        s0[i] = a; s1[i] = b; s2[i] = c; s3[i] = r3[g];
         sg[i] = g;
     }
 }
@@ -903,7 +915,8 @@ gl_status permute_records(View& v, int64_t nmax, cudaStream_t s)
     GL_TRY(v.srec3.reserve(16 * I));
     GL_TRY(v.sgid.reserve(4 * I));
     const int blocks = (int)std::min<size_t>(8 * 152, (I + 255) / 256);
-    k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.sorted_inst, v.iowner.as<uint32_t>(),
+    k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.sorted_inst, v.sorted_tile, v.d_desc(), v.V, v.Ts,
+                                     v.iowner.as<uint32_t>(),
                                      v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(),
                                      v.rec3.as<float4>(), v.srec0.as<float4>(), v.srec1.as<float4>(),
                                      v.srec2.as<float4>(), v.srec3.as<float4>(), v.sgid.as<uint32_t>());
