@@ -437,6 +437,127 @@ def test_adam_matches_torch_optim():
     assert np.allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
 
 
+# --------------------------------------------------------------------------- step composition
+_GAUSS_KEYS = ("means", "log_scales", "quats", "logits", "sh")
+
+
+def _two_sided_scene():
+    """Gaussians in front of a camera A (identity pose, looking down +z), a
+    mirrored copy in front of a camera B turned 180 degrees about y (looking
+    down -z), and a few far off to the side that neither camera sees."""
+    sc = scenes.small_frustum(seed=11, n=300, width=64, height=48, f=50.0)
+    p = sc["params"]
+    back = {k: v.copy() for k, v in p.items()}
+    back["means"] = back["means"] * np.array([-1, 1, -1], np.float32)
+    side = {k: v[:20].copy() for k, v in p.items()}
+    side["means"] = side["means"] + np.array([500.0, 0, 0], np.float32)
+    params = {k: np.ascontiguousarray(np.concatenate([p[k], back[k], side[k]])) for k in p}
+    camA = sc["cam"]
+    camB = scenes.camera(64, 48, 50.0, R=np.diag([-1.0, 1.0, -1.0]))
+    return params, camA, camB, sc["target"], sc["E"].astype(np.float64)
+
+
+def _as_params(state):
+    return {k: state["p"][k].astype(np.float32) for k in _GAUSS_KEYS}
+
+
+def test_window_of_one_view_is_the_plain_step():
+    """Sec. III-C 3 optimises one keyframe per iteration; a window of one view
+    must reduce to exactly that step (mean over one view, union of one mask)."""
+    params, camA, _, tgt, E = _two_sided_scene()
+    st = oracle.new_state(params, E)
+    r = oracle.optimize_step(params, st, camA, tgt, E, 1)
+    sw = oracle.new_window_state(params, 1)
+    sw["p"]["E"][0] = E.copy()
+    rw = oracle.optimize_window(params, sw, [camA], [tgt], 1)
+    assert rw["loss"] == r["loss"]["loss"]
+    for k in _GAUSS_KEYS:
+        for d in ("p", "m", "v"):
+            assert np.array_equal(st[d][k], sw[d][k]), (k, d)
+    for d in ("p", "m", "v"):
+        assert np.array_equal(st[d]["E"], sw[d]["E"][0]), d
+
+
+def test_window_of_a_repeated_view_moves_the_map_like_one_view():
+    """Two copies of one view: the mean gradient is the view's own (g/2 + g/2
+    = g exactly), so the Gaussians take the plain step bit for bit; each copy's
+    exposure takes a first Adam step on half the gradient, which is the same
+    -lr sign(g) move up to eps."""
+    params, camA, _, tgt, E = _two_sided_scene()
+    st = oracle.new_state(params, E)
+    r = oracle.optimize_step(params, st, camA, tgt, E, 1)
+    sw = oracle.new_window_state(params, 2)
+    sw["p"]["E"] = [E.copy(), E.copy()]
+    rw = oracle.optimize_window(params, sw, [camA, camA], [tgt, tgt], 1)
+    assert rw["loss"] == r["loss"]["loss"]
+    for k in _GAUSS_KEYS:
+        assert np.array_equal(st["p"][k], sw["p"][k]), k
+    for v in range(2):
+        assert np.allclose(sw["p"]["E"][v], st["p"]["E"], rtol=0, atol=1e-15)
+
+
+def test_sparse_adam_mask_is_the_union_of_the_window_views():
+    """Sparse Adam (Sec. III-D 2) updates exactly the Gaussians with a non-zero
+    radius in some view of the step: those seen only by B move in an A+B
+    window and stay bitwise put (moments too) in a step on A alone; those that
+    no camera sees never change."""
+    params, camA, camB, tgt, E = _two_sided_scene()
+    n = params["means"].shape[0]
+    visA = oracle.preprocess(params, camA)["radius"] > 0
+    visB = oracle.preprocess(params, camB)["radius"] > 0
+    onlyB = visB & ~visA
+    assert onlyB.sum() > 50 and not (visA | visB)[-20:].any()
+    sw = oracle.new_window_state(params, 2)
+    rw = oracle.optimize_window(params, sw, [camA, camB], [tgt, tgt], 1)
+    assert np.array_equal(rw["visible"], visA | visB)
+    moved = np.zeros(n, bool)
+    for k in _GAUSS_KEYS:
+        d = (sw["p"][k] != params[k].astype(np.float64)).reshape(n, -1).any(1)
+        moved |= d
+        assert np.all(sw["m"][k].reshape(n, -1)[~(visA | visB)] == 0), k
+    assert moved[onlyB].all() and not moved[~(visA | visB)].any()
+    st = oracle.new_state(params, E)
+    oracle.optimize_step(params, st, camA, tgt, E, 1)
+    for k in _GAUSS_KEYS:
+        rows = st["p"][k].reshape(n, -1)[~visA]
+        assert np.array_equal(rows, params[k].astype(np.float64).reshape(n, -1)[~visA]), k
+        assert np.all(st["v"][k].reshape(n, -1)[~visA] == 0), k
+
+
+def test_dense_adam_keeps_moving_gaussians_out_of_view():
+    """The dense mode (the "w/o acc" row of Table II) applies Adam to every Gaussian:
+    one seen by A in step 1 but not by B in step 2 keeps moving on its first
+    moment in step 2, while sparse Adam leaves it exactly where step 1 put it."""
+    params, camA, camB, tgt, E = _two_sided_scene()
+    n = params["means"].shape[0]
+    visA = oracle.preprocess(params, camA)["radius"] > 0
+    visB = oracle.preprocess(params, camB)["radius"] > 0
+    onlyA = visA & ~visB
+    assert onlyA.sum() > 50
+    out = {}
+    for sparse in (True, False):
+        st = oracle.new_state(params, E)
+        oracle.optimize_step(params, st, camA, tgt, E, 1, sparse=sparse)
+        after1 = {(d, k): st[d][k].copy() for d in ("p", "m", "v") for k in _GAUSS_KEYS}
+        oracle.optimize_step(_as_params(st), st, camB, tgt, st["p"]["E"].copy(), 2, sparse=sparse)
+        out[sparse] = (after1, st)
+    after1, st = out[True]
+    for k in _GAUSS_KEYS:
+        for d in ("p", "m", "v"):
+            assert np.array_equal(st[d][k].reshape(n, -1)[onlyA], after1[d, k].reshape(n, -1)[onlyA]), (d, k)
+    after1, st = out[False]
+    m1 = after1["m", "means"].reshape(n, -1)[onlyA]
+    v1 = after1["v", "means"].reshape(n, -1)[onlyA]
+    assert (m1 != 0).any(1).mean() > 0.9
+    # no gradient in step 2: m2 = b1 m1, v2 = b2 v1, and the bias-corrected move
+    # of Adam (Kingma and Ba 2015, Algorithm 1) is lr m2/(1-b1^2) / (sqrt(v2/(1-b2^2)) + eps)
+    assert np.array_equal(st["m"]["means"].reshape(n, -1)[onlyA], 0.9 * m1)
+    expect = 1.6e-4 * (0.9 * m1 / (1 - 0.9 ** 2)) / (np.sqrt(0.999 * v1 / (1 - 0.999 ** 2)) + 1e-15)
+    moved = after1["p", "means"].reshape(n, -1)[onlyA] - st["p"]["means"].reshape(n, -1)[onlyA]
+    assert np.allclose(moved, expect, rtol=1e-9, atol=1e-18)
+    assert (np.abs(moved).max(1)[(m1 != 0).any(1)] > 0).all()
+
+
 # --------------------------------------------------------------------------- sky / expansion
 def test_sky_points_hemisphere_and_nearest_neighbour():
     from scipy.spatial import cKDTree
