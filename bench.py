@@ -609,8 +609,10 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "outdoor LiDAR street, 1M Gaussians, SH3, 1280x1024, plain single-view step",
-                      "parallelism": "replicas"},
+           "config": {"workload": ("outdoor LiDAR street, %d Gaussians (%d LiDAR+visual, %d sky), SH3, %dx%d, "
+                                   "plain single-view step" % (n, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"])),
+                      "n_gaussians": n, "width": wsz["W"], "height": wsz["H"], "tile": 16,
+                      "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                             "wall_s": wall},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
