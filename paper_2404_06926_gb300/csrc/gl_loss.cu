@@ -12,8 +12,11 @@
 // zero-padded symmetric correlation is the same correlation) and adds the
 // channel's part of dL/dC = A^T dL/dE[C] (the thread owning a pixel is the
 // same in every channel).  In every pass a thread slides the 11 taps along a
-// run of 7-8 outputs held in registers, so each shared-memory value is read
-// once per run rather than once per tap and output.  The maps of later passes
+// run of 3-7 outputs held in registers, so each shared-memory value is read
+// once per run rather than once per tap and output; the run lengths (and the
+// split of the horizontal adjoint by map) are chosen so that each pass gives
+// the CTA's 256 threads close to a whole number of rounds of equal items
+// (728 = 2.8 x 256, 252, 504 = 2 x 252, 256).  The maps of later passes
 // reuse the space of those consumed (65 KB, three CTAs per SM).  Per-CTA
 // partial sums of |.|, SSIM and dL/dE are reduced afterwards in a fixed
 // order, in double.
@@ -31,10 +34,11 @@ constexpr int RA = LT + 4 * HW;       // 52
 constexpr int RB = LT + 2 * HW;       // 42
 constexpr int kThreads = 256;
 constexpr int kNP = 14;               // partials per CTA: 12 dL/dE, sum|d|, sum SSIM
-constexpr int HR = 7;                 // outputs per thread, horizontal moment pass (RB = 6 x 7)
-constexpr int VR = 7;                 // outputs per thread, vertical moment pass
-constexpr int AR = 8;                 // outputs per thread, adjoint passes (LT = 4 x 8)
-static_assert(RB % HR == 0 && RB % VR == 0 && LT % AR == 0, "run lengths must tile the maps");
+constexpr int HR = 3;                 // outputs per thread, horizontal moment pass (RB = 14 x 3)
+constexpr int VR = 7;                 // outputs per thread, vertical moment pass (RB = 6 x 7)
+constexpr int AHR = 8;                // outputs per item, horizontal adjoint pass (LT = 4 x 8)
+constexpr int AVR = 4;                // outputs per thread, vertical adjoint pass (LT = 8 x 4)
+static_assert(RB % HR == 0 && RB % VR == 0 && LT % AHR == 0 && LT % AVR == 0, "run lengths must tile the maps");
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -182,35 +186,33 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
             }
         }
         __syncthreads();
-        // adjoint, horizontal: runs of AR outputs of a row
-        for (int e = tid; e < RB * (LT / AR); e += kThreads) {
-            const int r = e / (LT / AR), c0 = (e % (LT / AR)) * AR;
+        // adjoint, horizontal: one item per (map, row, run of AHR outputs)
+        for (int e = tid; e < 3 * RB * (LT / AHR); e += kThreads) {
+            const int m = e / (RB * (LT / AHR)), rr = e % (RB * (LT / AHR));
+            const int r = rr / (LT / AHR), c0 = (rr % (LT / AHR)) * AHR;
+            float row[AHR + 10];
 #pragma unroll
-            for (int m = 0; m < 3; m++) {
-                float row[AR + 10];
+            for (int k = 0; k < AHR + 10; k++) row[k] = gmap[m * RB * RB + r * RB + c0 + k];
 #pragma unroll
-                for (int k = 0; k < AR + 10; k++) row[k] = gmap[m * RB * RB + r * RB + c0 + k];
+            for (int o = 0; o < AHR; o++) {
+                float a = 0.0f;
 #pragma unroll
-                for (int o = 0; o < AR; o++) {
-                    float a = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < 11; k++) a += wt[k] * row[o + k];
-                    hg[m * RB * LT + r * LT + c0 + o] = a;
-                }
+                for (int k = 0; k < 11; k++) a += wt[k] * row[o + k];
+                hg[m * RB * LT + r * LT + c0 + o] = a;
             }
         }
         __syncthreads();
-        // adjoint, vertical, and dL/dE[C] of the tile's pixels: runs of AR rows of a column
-        for (int e = tid; e < LT * (LT / AR); e += kThreads) {
-            const int c = e % LT, r0 = (e / LT) * AR;
-            float acc[3][AR];
+        // adjoint, vertical, and dL/dE[C] of the tile's pixels: runs of AVR rows of a column
+        for (int e = tid; e < LT * (LT / AVR); e += kThreads) {
+            const int c = e % LT, r0 = (e / LT) * AVR;
+            float acc[3][AVR];
 #pragma unroll
             for (int m = 0; m < 3; m++) {
-                float col[AR + 10];
+                float col[AVR + 10];
 #pragma unroll
-                for (int k = 0; k < AR + 10; k++) col[k] = hg[m * RB * LT + (r0 + k) * LT + c];
+                for (int k = 0; k < AVR + 10; k++) col[k] = hg[m * RB * LT + (r0 + k) * LT + c];
 #pragma unroll
-                for (int o = 0; o < AR; o++) {
+                for (int o = 0; o < AVR; o++) {
                     float a = 0.0f;
 #pragma unroll
                     for (int k = 0; k < 11; k++) a += wt[k] * col[o + k];
@@ -221,7 +223,7 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
             // now holds the partial maps); dL/dC += A_ch^T dL/dE[C]_ch, by
             // the thread that owns the pixel in every channel
 #pragma unroll
-            for (int o = 0; o < AR; o++) {
+            for (int o = 0; o < AVR; o++) {
                 const int r = r0 + o;
                 const int gx = ox + c, gy = oy + r;
                 if (gx < W && gy < H) {
