@@ -12,7 +12,7 @@
 // zero-padded symmetric correlation is the same correlation) and adds the
 // channel's part of dL/dC = A^T dL/dE[C] (the thread owning a pixel is the
 // same in every channel).  In every pass a thread slides the 11 taps along a
-// run of 3-7 outputs held in registers, so each shared-memory value is read
+// run of 3-8 outputs held in registers, so each shared-memory value is read
 // once per run rather than once per tap and output; the run lengths (and the
 // split of the horizontal adjoint by map) are chosen so that each pass gives
 // the CTA's 256 threads close to a whole number of rounds of equal items
