@@ -58,6 +58,8 @@ def parse():
                     help="Poisson request stream of the serving loop (0: skip)")
     ap.add_argument("--psnr-steps", type=int, default=500,
                     help="plain steps of the equal-PSNR comparison on held-out views (0: skip)")
+    ap.add_argument("--tile-stats", default="",
+                    help="only print the per-tile load of these plain-workload keyframes, e.g. 0,5,10,15")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -243,9 +245,19 @@ def set_exec(m, mode, views, keep_tile, window=None):
     return best, ms
 
 
-def algorithmic_bytes(st, n_total):
-    """Algorithmic bytes per launch of each phase (fp32, SH degree 3)."""
-    N, Nv, I, P = n_total, st["n_visible"], st["n_instances"], st["pixels"]
+def timed_counts(st):
+    """Per-step means of the counts the library summed over the steps the
+    phase timers timed (the same steps, so numerators and denominators match)."""
+    k = max(1, st["timed_steps"])
+    return {"visible": st["timed_visible"] / k, "instances": st["timed_instances"] / k,
+            "pairs": st["timed_contrib"] / k, "pixels": st["timed_pixels"] / k, "steps": st["timed_steps"],
+            "views_per_step": st["timed_views"] / k}
+
+
+def algorithmic_bytes(cnt, n_total):
+    """Algorithmic bytes per launch of each phase (fp32, SH degree 3), from
+    per-step counts (timed_counts)."""
+    N, Nv, I, P = n_total, cnt["visible"], cnt["instances"], cnt["pixels"]
     return {
         "preprocess": N * 16 + Nv * (220 + 52),
         "depth_sort": N * 16,
@@ -267,9 +279,9 @@ def load_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, sms):
+    # SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_source_hash():
@@ -277,6 +289,30 @@ def kernel_source_hash():
     for f in ("gl_raster.cu", "gl_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2404_06926_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def cycle_order(n):
+    """The keyframes 0..n-1 in bit-reversed order of their index (0, n/2,
+    n/4, 3n/4, ... for n a power of two): any prefix of the cycle is spread
+    along the trajectory, so a short run times about the same view mix as a
+    long one."""
+    bits = max(1, (n - 1).bit_length())
+    keys = [int(format(i, f"0{bits}b")[::-1], 2) for i in range(1 << bits)]
+    return [k for k in keys if k < n]
+
+
+def ncu_flops(kernel):
+    """Executed FP32 flops per (pixel, Gaussian) pair of `kernel`, from the
+    committed ncu instruction counters of one launch; None unless they were
+    taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "flops_raster_backward.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e
 
 
 def ncu_traffic(kernel, alg_full):
@@ -294,68 +330,109 @@ def ncu_traffic(kernel, alg_full):
 
 
 # ----------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded crop of the same view
+# CPU baseline: the oracle's float32 / OpenMP build on the same workload
 # ----------------------------------------------------------------------------
-def crop_camera(cam, crop):
-    cw, ch = crop
-    x0, y0 = cam["width"] // 2 - cw // 2, cam["height"] // 2 - ch // 2
-    return dict(cam, width=cw, height=ch, cx=cam["cx"] - x0, cy=cam["cy"] - y0), x0, y0
+def cpu_info():
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
 
 
-def oracle_step_on_crop(params, cam, target, E, crop):
-    """One oracle step on a centre crop with all Gaussians preprocessed;
-    returns (extrapolated full-view seconds, wall, t_preprocess, t_rest)."""
+_ORACLE_WL = {}
+
+
+def oracle_workload(wsz, n_kf):
+    """The plain workload as the oracle builds it (Sec. III-C 1): the street's
+    LiDAR + visual points as new Gaussians (scale d / f in the capture pose),
+    the sky hemisphere with its nearest-neighbour scales, SH degree 3; and the
+    keyframe cameras of the GPU run with their ray-cast targets (built on
+    first use).  Nothing here comes from the CUDA path."""
+    key = (wsz["n_points"], wsz["n_sky"], wsz["W"], n_kf)
+    if key in _ORACLE_WL:
+        return _ORACLE_WL[key]
     import oracle
-    c2, x0, y0 = crop_camera(cam, crop)
-    cw, ch = crop
-    tgt = np.ascontiguousarray(target[y0:y0 + ch, x0:x0 + cw])
-    t0 = time.perf_counter()
-    pre = oracle.preprocess(params, c2, 16)
-    t1 = time.perf_counter()
-    bins = oracle.bin_instances(pre, c2)
-    img = oracle.render(pre, bins, c2)
-    L = oracle.loss(img["color"], tgt, E)
-    oracle.backward(params, c2, pre, bins, L["dL_dC"])
-    t2 = time.perf_counter()
-    scale = (cam["width"] * cam["height"]) / float(cw * ch)
-    full = (t1 - t0) + scale * (t2 - t1)
-    return full, t2 - t0, t1 - t0, t2 - t1
-
-
-def oracle_step_sample(params, sub, local, cam, target, E, crop, stride):
-    """A bounded sample of one oracle step: the full-view preprocess of every
-    stride-th Gaussian (time x stride) plus preprocess, binning, render, loss
-    and backward of a centre crop over the Gaussians that reach it (time x
-    full pixels / crop pixels); returns (extrapolated seconds, wall)."""
-    import oracle
-    c2, x0, y0 = crop_camera(cam, crop)
-    cw, ch = crop
-    tgt = np.ascontiguousarray(target[y0:y0 + ch, x0:x0 + cw])
-    t0 = time.perf_counter()
-    oracle.preprocess(sub, cam, 16)
-    t1 = time.perf_counter()
-    pre = oracle.preprocess(local, c2, 16)
-    bins = oracle.bin_instances(pre, c2)
-    img = oracle.render(pre, bins, c2)
-    L = oracle.loss(img["color"], tgt, E)
-    oracle.backward(local, c2, pre, bins, L["dL_dC"])
-    t2 = time.perf_counter()
-    scale = (cam["width"] * cam["height"]) / float(cw * ch)
-    return stride * (t1 - t0) + scale * (t2 - t1), t2 - t0
-
-
-def cpu_baseline(m, cams, imgs, crop, reps=1):
-    import oracle
+    from paper_2404_06926_gb300 import scenes
     oracle.build()
-    params = {k: v.astype(np.float64) for k, v in m.get_params().items()}
-    E = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
-    fulls, walls = [], []
-    for r in range(reps):
-        k = r % len(cams)
-        full, wall = oracle_step_on_crop(params, cams[k], imgs[k].cpu().numpy(), E, crop)[:2]
-        fulls.append(full)
-        walls.append(wall)
-    return 1.0 / float(np.mean(fulls)), float(np.sum(walls))
+    oracle.build_timing()
+    sc = scenes.Outdoor(seed=2, width=wsz["W"], img_height=wsz["H"], f=wsz["f"])
+    xyz, rgb, idx = sc.point_cloud(wsz["n_points"])
+    deps = np.zeros(len(xyz), np.float32)
+    for i, s in enumerate(sc.traj_x):
+        sel = idx == i
+        _, d, _ = oracle.expand_mask(xyz[sel], sc.camera_at(s), None)
+        deps[sel] = d
+    p = oracle.init_gaussians(xyz, rgb, deps, wsz["f"])
+    sxyz, nn = oracle.sky_points_parallel(wsz["n_sky"], 1e4, seed=0x5eed)
+    ps = oracle.init_gaussians(sxyz, np.ones_like(sxyz), None, wsz["f"], opacity=0.7, scale=nn)
+    params = {k: np.ascontiguousarray(np.concatenate([p[k], ps[k]]).astype(np.float32)) for k in p}
+    pos = np.linspace(sc.traj_x[2], sc.traj_x[-12], n_kf)
+    cams = [sc.camera_at(float(s)) for s in pos]
+    wl = {"sc": sc, "params": params, "cams": cams, "steps": {}}
+    _ORACLE_WL[key] = wl
+    return wl
+
+
+def oracle_step(wl, k, tile_step):
+    """One timed oracle step on keyframe k (TimedStep.sample: every
+    tile_step-th tile / Gaussian for the sampled phases, extrapolated)."""
+    import oracle
+    if k not in wl["steps"]:
+        cam = wl["cams"][k]
+        tgt = wl["sc"].target_image(cam)[0]
+        wl["steps"][k] = oracle.TimedStep(wl["params"], cam, tgt, np.hstack([np.eye(3), np.zeros((3, 1))]))
+    return wl["steps"][k].sample(tile_step)
+
+
+def sample_factor(t_full, phases, n_steps, budget_s):
+    """Smallest power-of-two sample factor whose steps fit the budget."""
+    t_loss = phases["loss"]
+    rest = max(t_full - t_loss, 1e-9)
+    k = 1
+    while k < 256 and n_steps * (t_loss + rest / k) > budget_s:
+        k *= 2
+    return k
+
+
+SAMPLE_RULE = ("TimedStep.sample(k): preprocess, parameter backward and Adam over every k-th Gaussian, "
+               "binning, compositing and the 2-D backward over every k-th tile, each timed and multiplied by "
+               "k, plus the full-image loss; k = 1 is the whole step")
+
+
+def cpu_baseline(wsz, n_kf, order, budget_s=30.0):
+    """The oracle's float32 OpenMP build on all host cores: whole steps on
+    the first keyframes of the timed cycle while they fit the budget (at
+    least one), then a single-thread figure on a sample of one step."""
+    import oracle
+    wl = oracle_workload(wsz, n_kf)
+    threads = oracle.timing_threads()
+    t0 = time.perf_counter()
+    steps = []
+    for k in order:
+        steps.append(oracle_step(wl, int(k), 1))
+        if len(steps) >= 3 or time.perf_counter() - t0 + steps[-1]["step_s"] > budget_s:
+            break
+    full = float(np.mean([r["step_s"] for r in steps]))
+    oracle.timing_threads(1)
+    st = oracle_step(wl, int(order[0]), 16)
+    oracle.timing_threads(threads)
+    out = {"value": 1.0 / full, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"{len(steps)} whole oracle steps (float32 OpenMP build, {threads} threads) on keyframes "
+                      f"{[int(k) for k in order[:len(steps)]]} of the timed cycle, {wsz['W']}x{wsz['H']}, "
+                      f"{len(wl['params']['logits'])} Gaussians; no extrapolation"),
+           "s_per_step": full, "phases_s": {a: float(np.mean([r["phases"][a] for r in steps])) for a in
+                                            steps[0]["phases"]},
+           "wall_s": time.perf_counter() - t0,
+           "single_thread": {"value": 1.0 / st["step_s"], "s_per_step": st["step_s"], "sample": SAMPLE_RULE
+                             + f"; k = 16, keyframe {int(order[0])}, 1 thread"}}
+    out.update(cpu_info())
+    return out
 
 
 def timed(torch, fn):
@@ -555,66 +632,79 @@ def run_serving(args, binding, torch):
     return out
 
 
+def tile_load(ctx, params: dict, cam: dict, tile: int = 16) -> dict:
+    """Per-tile load of one forward render (params: device tensors): how long
+    each tile's (Gaussian, tile) list is and how far each 8x4 pixel block walks
+    it (the last contributor of its pixels), the serial work of one raster
+    warp when a tile is not split."""
+    ctx.forward(params, cam, tile)
+    H, W = int(cam["height"]), int(cam["width"])
+    TX, TY = (W + tile - 1) // tile, (H + tile - 1) // tile
+    _, _, ranges = ctx.instances(TX * TY, params["means"].device)
+    L = (ranges[:, 1] - ranges[:, 0]).cpu().numpy().astype(np.int64)
+    _, ncon = ctx.pixel_state(H, W, params["means"].device)
+    nc = ncon.cpu().numpy().astype(np.int64)
+    Hp, Wp = (H + 3) // 4 * 4, (W + 7) // 8 * 8
+    pad = np.zeros((Hp, Wp), np.int64)
+    pad[:H, :W] = nc
+    block = pad.reshape(Hp // 4, 4, Wp // 8, 8).max(axis=(1, 3))
+    top = np.argsort(-L)[:5]
+    return dict(instances=int(L.sum()), tiles=int(L.size), list_mean=float(L.mean()),
+                list_p99=float(np.percentile(L, 99)), list_max=int(L.max()),
+                heaviest_tiles=[dict(tile=int(t), x=int(t % TX) * tile, y=int(t // TX) * tile, length=int(L[t]))
+                                for t in top],
+                block_walk_mean=float(block.mean()), block_walk_p99=float(np.percentile(block, 99)),
+                block_walk_max=int(block.max()), blocks=int(block.size))
+
+
+def run_tile_stats(args):
+    import torch
+    from paper_2404_06926_gb300 import binding
+    wsz = workload_sizes(args.small)
+    sc, m, cams, imgs = build_map(binding, torch, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"], wsz["f"],
+                                  [(wsz["W"], wsz["H"])] * args.keyframes)
+    p = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in m.get_params().items()}
+    ctx = binding.Ctx()
+    out = {int(k): tile_load(ctx, p, cams[int(k)]) for k in args.tile_stats.split(",")}
+    print(json.dumps(out, indent=1), flush=True)
+    m.close()
+
+
 # ----------------------------------------------------------------------------
 def run_reference(args):
-    """The oracle as it stands, on host cores, on a bounded crop per step."""
+    """The oracle as it stands (its float32 OpenMP build) on the host cores,
+    the same workload and keyframe cycle as the GPU arm; each step a
+    TimedStep sample sized so that warm-up plus timed steps take ~150 s."""
     rank, ws, local, dist = dist_setup(args.gpus)
     if rank != 0:
         return
     import oracle
-    from paper_2404_06926_gb300 import scenes
-    oracle.build()
     wsz = workload_sizes(args.small)
-    sc = scenes.Outdoor(seed=2, width=wsz["W"], img_height=wsz["H"], f=wsz["f"])
-    xyz, rgb, idx = sc.point_cloud(wsz["n_points"])
-    deps = np.zeros(len(xyz), np.float32)
-    for i, s in enumerate(sc.traj_x):
-        sel = idx == i
-        _, d, _ = oracle.expand_mask(xyz[sel], sc.camera_at(s), None)
-        deps[sel] = d
-    p = oracle.init_gaussians(xyz, rgb, deps, wsz["f"])
-    sxyz, nn = oracle.sky_points(wsz["n_sky"], 1e4, seed=0x5eed)
-    ps = oracle.init_gaussians(sxyz, np.ones_like(sxyz), None, wsz["f"], opacity=0.7, scale=nn)
-    params = {k: np.concatenate([p[k], ps[k]]).astype(np.float64) for k in p}
-    cam = sc.camera_at(float(sc.traj_x[30]))
-    target = sc.target_image(cam)[0]
-    E = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
-    # each step is a bounded sample (oracle_step_sample), sized so that
-    # warm-up plus timed steps take about 150 s: a calibration step gives the
-    # preprocess time per Gaussian and the crop's time per pixel
-    n = len(params["logits"])
-    _, _, t_pre, t_rest = oracle_step_on_crop(params, cam, target, E, (160, 128))
-    per_step = 150.0 / max(1, args.steps + args.warmup)
-    stride = int(np.clip(np.ceil(t_pre / (0.5 * per_step)), 1, n))
-    px = float(np.clip(0.5 * per_step / max(t_rest / (160 * 128), 1e-9), 64, 160 * 128))
-    cw = max(8, int(np.sqrt(px * 1.25)) // 4 * 4)
-    ch = max(8, int(cw / 1.25) // 4 * 4)
-    crop = (cw, ch)
-    c2, _, _ = crop_camera(cam, crop)
-    reach = oracle.preprocess(params, c2, 16)["radius"] > 0
-    local = {k: np.ascontiguousarray(v[reach]) for k, v in params.items()}
-    sub = {k: np.ascontiguousarray(v[::stride]) for k, v in params.items()}
-    for _ in range(args.warmup):
-        oracle_step_sample(params, sub, local, cam, target, E, crop, stride)
+    n_kf = args.keyframes
+    wl = oracle_workload(wsz, n_kf)
+    threads = oracle.timing_threads()
+    cyc = cycle_order(n_kf)
+    cal = oracle_step(wl, cyc[0], 1)   # calibration: one whole step
+    k = sample_factor(cal["step_s"], cal["phases"], args.steps + args.warmup, 150.0)
+    for i in range(args.warmup):
+        oracle_step(wl, cyc[i % n_kf], k)
     t0 = time.perf_counter()
-    fulls = []
-    for _ in range(args.steps):
-        fulls.append(oracle_step_sample(params, sub, local, cam, target, E, crop, stride)[0])
+    steps = [oracle_step(wl, cyc[i % n_kf], k) for i in range(args.steps)]
     wall = time.perf_counter() - t0
-    v = 1.0 / float(np.mean(fulls))
-    sample = (f"oracle (C, 1 thread): per step, the full-view preprocess of every {stride}-th of the {n} "
-              f"Gaussians (time x {stride}) plus preprocess, binning, render, loss and backward of a "
-              f"{crop[0]}x{crop[1]} centre crop over the {int(reach.sum())} Gaussians reaching it (time x "
-              f"full pixels / crop pixels); sized for ~150 s over {args.steps + args.warmup} steps")
+    v = 1.0 / float(np.mean([r["step_s"] for r in steps]))
+    n = len(wl["params"]["logits"])
+    sample = (SAMPLE_RULE + f"; k = {k} (whole-step calibration {cal['step_s']:.2f} s), keyframes in the "
+              f"GPU arm's cycle, {threads} threads")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": ("outdoor LiDAR street, %d Gaussians (%d LiDAR+visual, %d sky), SH3, %dx%d, "
                                    "plain single-view step" % (n, wsz["n_points"], wsz["n_sky"], wsz["W"], wsz["H"])),
                       "n_gaussians": n, "width": wsz["W"], "height": wsz["H"], "tile": 16,
+                      "keyframes": n_kf, "keyframe_order": "bit-reversed cycle %s" % cyc,
                       "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                            "wall_s": wall},
+           "cpu_baseline": dict({"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                                 "wall_s": wall, "tile_step": k}, **cpu_info()),
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -632,7 +722,9 @@ def run_ours(args):
     n_total = len(m)
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(100 + rank)
-    order = rng.integers(0, n_kf, size=args.warmup + args.steps + 1)
+    # warm-up steps, then the timed steps from the start of a fixed cycle
+    cyc = cycle_order(n_kf)
+    order = np.array([cyc[i % n_kf] for i in range(args.warmup)] + [cyc[i % n_kf] for i in range(args.steps + 1)])
     if args.fixed_view >= 0:
         order[:] = args.fixed_view % n_kf
 
@@ -730,21 +822,32 @@ def run_ours(args):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: launch time and counts from the same
+    # (timed) steps
     hbm_peak, sm_max, peak_src = load_peaks()
     phases = st["phases"]
-    byts = algorithmic_bytes(st, n_total)
+    cnt = timed_counts(st)
+    byts = algorithmic_bytes(cnt, n_total)
     per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in phases.items()}
     dom = max((k for k in per_launch if k in byts), key=lambda k: phases[k][0])
     t_launch = per_launch[dom] / 1e3
-    kp = st["sum_contrib"]
-    flops_per_pair = {"raster_forward": 20.0, "raster_backward": 70.0}
-    if dom in flops_per_pair:
-        peak = fp32_peak_tflops(sm_max)
-        ach = flops_per_pair[dom] * kp / t_launch / 1e12
+    kp = cnt["pairs"]
+    nominal = {"raster_forward": 20.0, "raster_backward": 70.0}
+    if dom in nominal:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = fp32_peak_tflops(sm_max, sms)
+        ex = ncu_flops(dom)
+        per_pair = ex["flops_per_pair"] if ex else nominal[dom]
+        ach = per_pair * kp / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": ncu_traffic(dom, byts[dom]), "kernel": dom,
-                "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "flops": ("executed FP32 flops per pair from ncu instruction counters (%s), x pairs walked"
+                          % ex["source"]) if ex else "nominal %g flop per pair walked (no counters of this source)"
+                          % nominal[dom],
+                "flops_per_pair": per_pair, "pairs_per_launch": kp,
+                "nominal_frac": nominal[dom] * kp / t_launch / 1e12 / peak,
+                "peak_source": f"{sms} SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "counts": cnt,
                 "hbm": {"achieved": byts[dom] / t_launch / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": byts[dom] / t_launch / 1e9 / hbm_peak, "peak_source": peak_src}}
     else:
@@ -756,16 +859,8 @@ def run_ours(args):
                for k in phases if phases[k][1]}
 
     cpu = None
-    if not args.no_cpu_baseline and args.gpus == 1 and not args.small:
-        # the central quarter of the view (it holds the street's vanishing
-        # point, the deepest tile lists), on two keyframes: 10-30 s of host work
-        crop, reps = (wsz["W"] // 2, wsz["H"] // 2), 2
-        v, wall = cpu_baseline(m, cams, imgs, crop, reps=reps)
-        scale = (wsz["W"] * wsz["H"]) // (crop[0] * crop[1])
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{reps} oracle steps (keyframes 0-{reps - 1}) on the {crop[0]}x{crop[1]} centre crop of "
-                         f"the {wsz['W']}x{wsz['H']} view, each with all {n_total} Gaussians preprocessed; "
-                         f"steps/s extrapolated as 1/mean(t_preprocess + {scale} * t_rest); wall {wall:.1f} s"}
+    if not args.no_cpu_baseline and args.gpus == 1:
+        cpu = cpu_baseline(wsz, n_kf, order[args.warmup:args.warmup + n_kf])
     map_after = len(m)
     m.close()
     serving = None
@@ -782,8 +877,9 @@ def run_ours(args):
                    "keyframes": n_kf, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "exec": exec_cfg, "autotune_ms_per_step": tune_ms,
                    "l2": "inputs larger than L2 (params + Adam moments %.2f GB)" % (n_total * 708 / 1e9),
-                   "visible": st["n_visible"], "instances": st["n_instances"],
-                   "pairs_backward": st["sum_contrib"]},
+                   "keyframe_order": "bit-reversed cycle %s" % cycle_order(n_kf),
+                   "visible": cnt["visible"], "instances": cnt["instances"],
+                   "pairs_backward": cnt["pairs"]},
         "roofline": roof,
         "kernels": kernels,
         "kernels_pass_ms_per_step": ms_timed / args.steps,
@@ -807,7 +903,9 @@ def main():
     for kv in filter(None, args.knobs.split(",")):
         k, v = kv.split("=")
         KNOBS[k.strip()] = int(v)
-    if args.impl == "reference":
+    if args.tile_stats:
+        run_tile_stats(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

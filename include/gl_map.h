@@ -315,6 +315,14 @@ typedef struct {
     int64_t graph_captures;  /* step graphs captured                             */
     int64_t graph_replays;   /* steps run by replaying a graph                   */
     int64_t graph_reruns;    /* replays whose instances overflowed (re-run eagerly) */
+    /* Summed over the steps taken since the timers were last switched on (the
+     * steps whose phases phase_ms times), over all their views:            */
+    int64_t timed_steps;     /* steps                                             */
+    int64_t timed_views;     /* views                                             */
+    int64_t timed_visible;   /* (view, Gaussian) pairs with a non-zero radius     */
+    int64_t timed_instances; /* (Gaussian, tile) instances                        */
+    int64_t timed_contrib;   /* (pixel, Gaussian) pairs the backward walks        */
+    int64_t timed_pixels;    /* pixels                                            */
 } gl_stats;
 
 /* Turn the per-phase timers on (1) or off (0); either way they restart from
@@ -322,8 +330,8 @@ typedef struct {
  * the map's stream (no extra synchronisation). */
 GL_API gl_status gl_map_set_timing(gl_map* map, int32_t enable);
 
-/* Counts of the last rendered view and the accumulated phase times.
- * Synchronises the map's stream. */
+/* Counts of the last rendered view, the accumulated phase times and the
+ * counts summed over the timed steps.  Synchronises the map's stream. */
 GL_API gl_status gl_map_get_stats(gl_map* map, gl_stats* out);
 
 /* Name of phase i (0 <= i < GL_NUM_PHASES), e.g. "raster_backward". */
@@ -461,16 +469,19 @@ GL_API gl_status gl_ctx_destroy(gl_ctx* ctx);
  * GL_ERR_INVALID. */
 GL_API gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* exec);
 
-/* Forward (Eq. 1-7) of the Gaussians `g` (device arrays) seen from
- * (pose, K) with square tiles of side tile_size (8, 16 or 32).  Writes the
- * device images out_rgb (H*W*3), out_depth (H*W, nullable) and
+/* Forward (Eq. 1-7) of the Gaussians `g` (device arrays) seen from the pose
+ * exp(xi^) T_cw with T_cw = `pose` and xi = twist6 (host, 6 floats: a
+ * twist (rho, phi), translation part first; NULL means xi = 0, i.e. `pose`
+ * itself), with square tiles of side tile_size (8, 16 or 32).  exp is the
+ * SE(3) exponential, evaluated in double precision inside the library.
+ * Writes the device images out_rgb (H*W*3), out_depth (H*W, nullable) and
  * out_opacity (H*W, nullable), and keeps the per-view state (records,
  * sorted instances, per-pixel final transmittance and contributor count)
- * in `ctx` for gl_rasterize_backward.  Errors: GL_ERR_INVALID,
- * GL_ERR_CAPACITY, GL_ERR_OOM. */
+ * in `ctx` for gl_rasterize_backward.  Errors: GL_ERR_INVALID (also for a
+ * non-finite twist), GL_ERR_CAPACITY, GL_ERR_OOM. */
 GL_API gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, const gl_pose* pose,
-                               const gl_intrinsics* K, int32_t tile_size,
-                               float* out_rgb, float* out_depth, float* out_opacity);
+                                      const float* twist6, const gl_intrinsics* K, int32_t tile_size,
+                                      float* out_rgb, float* out_depth, float* out_opacity);
 
 /* Backward of the last gl_rasterize_forward on `ctx` (same `g`, unchanged).
  * dL_drgb (H*W*3, device) is required; dL_ddepth and dL_dopacity (H*W,
@@ -478,18 +489,20 @@ GL_API gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, const 
  * stored final value, not stored per pair.  Writes gradients for every
  * attribute into `grad` (device arrays shaped like `g`; Gaussians outside
  * the view get 0) and, if grad_pose6 (device, 6 floats) is not NULL, the
- * gradient w.r.t. a left twist xi = (rho, phi) of the pose,
- * T_cw <- exp(xi^) T_cw, at xi = 0. */
+ * gradient dL/dxi w.r.t. the forward's twist: J_l(xi)^T g, where g is the
+ * gradient w.r.t. a left perturbation d of the rendered pose,
+ * exp(d^) exp(xi^) T_cw, at d = 0, and J_l the SE(3) left Jacobian (so at
+ * xi = 0 it is g itself). */
 GL_API gl_status gl_rasterize_backward(gl_ctx* ctx, const gl_gaussians* g, const float* dL_drgb,
-                                const float* dL_ddepth, const float* dL_dopacity,
-                                gl_gaussians* grad, float* grad_pose6);
+                                       const float* dL_ddepth, const float* dL_dopacity,
+                                       gl_gaussians* grad, float* grad_pose6);
 
 /* Photometric loss, Eq. 9: L = (1-lambda) mean|E[C] - C_bar| + lambda
  * (1 - mean SSIM(E[C], C_bar)), SSIM with an 11x11 Gaussian window of
  * sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels
  * and channels.  rgb, target (H*W*3), E34 (12) are device.  Writes the
- * device scalars loss_out (1 float), the device gradients dL_drgb (H*W*3)
- * and dL_dE (12). */
+ * device scalar loss_out (1 float; may be NULL), the device gradients
+ * dL_drgb (H*W*3; required) and dL_dE (12; may be NULL). */
 GL_API gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const float* target, const float* E34,
                               int32_t width, int32_t height, float lambda_dssim,
                               float* loss_out, float* dL_drgb, float* dL_dE);
@@ -500,19 +513,24 @@ GL_API gl_status gl_photometric_loss(gl_ctx* ctx, const float* rgb, const float*
  * thread for which cudaMalloc's implicit device-wide synchronisation would
  * stall the other work on the GPU, or a process whose device memory is all
  * owned by another allocator (a framework's caching allocator, a fixed
- * memory budget).  Arguments and results are those of gl_photometric_loss,
- * with the stream passed directly (cudaStream_t, NULL for the legacy
- * default stream) instead of through a gl_ctx.
+ * memory budget).  Arguments and results are those of gl_photometric_loss
+ * (loss_out and dL_dE may be NULL, dL_drgb is required), with the stream
+ * passed directly (cudaStream_t, NULL for the legacy default stream)
+ * instead of through a gl_ctx.
  * Scratch: the per-tile partial sums live in one fixed array inside the
  * library (917,504 bytes), which every GPU that loads the library holds
  * until the process exits.  Limit: at most 16,384 tiles of 32x32 pixels
  * (e.g. 4096 x 4096); larger images are rejected with GL_ERR_INVALID before
- * any work is enqueued.  The first call on each device looks up the array's
- * device address once; make that first call before any stream capture.
+ * any work is enqueued.  First call on each device: it looks up the array's
+ * device address and raises the loss kernel's shared-memory limit, and the
+ * CUDA runtime loads the library's device code (with the array) on that
+ * device if nothing has loaded it yet -- a one-time allocation made by the
+ * runtime, not by this call.  Make that first call at set-up, before any
+ * real-time section and before any stream capture; later calls allocate
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  * All calls share the array, which keeps the last call's contents; calls
  * that overlap on the GPU (on different streams, or from different threads)
- * race on it, so serialise them.  Allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library routine. */
+ * race on it, so serialise them. */
 GL_API gl_status gl_photometric_loss_noalloc(const float* rgb, const float* target, const float* E34,
                                              int32_t width, int32_t height, float lambda_dssim,
                                              float* loss_out, float* dL_drgb, float* dL_dE,

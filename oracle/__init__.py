@@ -56,7 +56,7 @@ def build(force: bool = False) -> str:
             return _LIB_PATH
         os.makedirs(_OUT_DIR, exist_ok=True)
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-Wno-unknown-pragmas",
                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
@@ -79,13 +79,14 @@ def _load():
         lib.orc_preprocess.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32] + [P] * 11
         lib.orc_num_instances.argtypes = [i64, P]
         lib.orc_num_instances.restype = i64
-        lib.orc_bin.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P]
-        lib.orc_render.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, dbl, dbl, P, P, P, P, P, P, P]
+        lib.orc_bin.argtypes = [i64, P, P, P, P, i32, i32, i32, i32, P, P, P]
+        lib.orc_bin.restype = i64
+        lib.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, dbl, dbl, P, P, P, P, P, P, P]
         lib.orc_render_bruteforce.argtypes = [i32, i32, i32, i64, P, P, P, P, P, P, P, P, i32,
                                               P, P, P, P, P]
         lib.orc_loss.argtypes = [i32, i32, P, P, P, dbl, P, P, P, P]
         lib.orc_loss.restype = dbl
-        lib.orc_backward_2d.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, P, P, i64, P]
+        lib.orc_backward_2d.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, i64, P]
         lib.orc_backward_params.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_adam.argtypes = [i64, i32, P, P, P, P, P, dbl, dbl, dbl, dbl, i64]
         lib.orc_expf_decision.argtypes = [C.c_float]
@@ -182,7 +183,7 @@ def bin_instances(pre: dict, cam: dict) -> dict:
     vals = np.zeros(max(I, 1), np.uint32)
     ranges = np.zeros((TX * TY, 2), np.uint32)
     lib.orc_bin(n, _p(pre["rect"]), _p(pre["touched"]), _p(pre["depth_bits"]),
-                _p(pre["cullp"]) if pre.get("cull", False) else None, pre["Ts"], TX, TY,
+                _p(pre["cullp"]) if pre.get("cull", False) else None, pre["Ts"], TX, TY, 1,
                 _p(keys), _p(vals), _p(ranges))
     return dict(keys=keys[:I], vals=vals[:I], ranges=ranges, I=I, TX=TX, TY=TY)
 
@@ -197,7 +198,7 @@ def render(pre: dict, bins: dict, cam: dict, amb_alpha_rel: float = 2e-5,
                T_final=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
                ambiguous=np.zeros((H, W), np.uint8), signature=np.zeros((H, W), np.uint64))
     vals = bins["vals"] if bins["I"] > 0 else np.zeros(1, np.uint32)
-    lib.orc_render(W, H, pre["Ts"], _p(vals), _p(bins["ranges"]), _p(pre["mean2d"]),
+    lib.orc_render(W, H, pre["Ts"], 1, _p(vals), _p(bins["ranges"]), _p(pre["mean2d"]),
                    _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]),
                    amb_alpha_rel, amb_T_rel, _p(out["color"]), _p(out["depth"]),
                    _p(out["opacity"]), _p(out["T_final"]), _p(out["n_contrib"]),
@@ -249,7 +250,7 @@ def backward(params: dict, cam: dict, pre: dict, bins: dict, dL_dC, dL_dD=None, 
     dC = _c(dL_dC, np.float64)
     dD = None if dL_dD is None else _c(dL_dD, np.float64)
     dO = None if dL_dO is None else _c(dL_dO, np.float64)
-    lib.orc_backward_2d(W, H, pre["Ts"], _p(vals), _p(bins["ranges"]), _p(pre["mean2d"]),
+    lib.orc_backward_2d(W, H, pre["Ts"], 1, _p(vals), _p(bins["ranges"]), _p(pre["mean2d"]),
                         _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]),
                         _p(dC), _p(dD), _p(dO), n, _p(g2d))
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
@@ -269,6 +270,176 @@ def adam_update(p, m, v, g, lr, step, mask=None, b1=0.9, b2=0.999, eps=1e-15):
     stride = int(np.prod(p.shape[1:])) if p.ndim > 1 else 1
     mk = None if mask is None else _c(mask, np.uint8)
     lib.orc_adam(p.size, stride, _p(mk), _p(p), _p(m), _p(v), _p(g), lr, b1, b2, eps, int(step))
+
+
+# ---------------------------------------------------------------------------
+# Timing build: the float instantiation of gl_oracle.c with OpenMP, timed as
+# the CPU baseline of the benchmark (never used as a checker).
+# ---------------------------------------------------------------------------
+_TIMING_PATH = os.path.join(_OUT_DIR, "liboracle_f32_omp.so")
+_tlib = None
+
+
+def build_timing(force: bool = False) -> str:
+    """Compile gl_oracle.c with -DORC_REAL=float -O3 -fopenmp (no FP contraction)."""
+    with _lock:
+        if (not force and os.path.exists(_TIMING_PATH)
+                and os.path.getmtime(_TIMING_PATH) >= os.path.getmtime(_SRC)):
+            return _TIMING_PATH
+        os.makedirs(_OUT_DIR, exist_ok=True)
+        tmp = _TIMING_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-DORC_REAL=float",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _TIMING_PATH)
+        return _TIMING_PATH
+
+
+def _load_timing():
+    global _tlib
+    if _tlib is None:
+        lib = C.CDLL(build_timing())
+        P = C.c_void_p
+        i64, i32, f32 = C.c_int64, C.c_int, C.c_float
+        lib.orc_num_threads.restype = i32
+        lib.orc_set_num_threads.argtypes = [i32]
+        lib.orc_sky.argtypes = [i64, C.c_double, C.c_uint64, P, P]
+        lib.orc_preprocess.argtypes = [i64, i32, P, P, P, P, P, P, i32, i32] + [P] * 11
+        lib.orc_num_instances.argtypes = [i64, P]
+        lib.orc_num_instances.restype = i64
+        lib.orc_bin.argtypes = [i64, P, P, P, P, i32, i32, i32, i32, P, P, P]
+        lib.orc_bin.restype = i64
+        lib.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, f32, f32, P, P, P, P, P, P, P]
+        lib.orc_loss.argtypes = [i32, i32, P, P, P, f32, P, P, P, P]
+        lib.orc_loss.restype = f32
+        lib.orc_backward_2d.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, i64, P]
+        lib.orc_backward_params.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_adam.argtypes = [i64, i32, P, P, P, P, P, f32, f32, f32, f32, i64]
+        _tlib = lib
+    return _tlib
+
+
+def sky_points_parallel(n: int, radius: float = SKY_RADIUS, seed: int = 0):
+    """sky_points by the timing build: the same double arithmetic per point
+    (identical results), its brute-force nearest-neighbour loop parallel."""
+    lib = _load_timing()
+    xyz = np.zeros((n, 3), np.float32)
+    nn = np.zeros(n)
+    lib.orc_sky(n, radius, C.c_uint64(seed), _p(xyz), _p(nn))
+    return xyz, nn
+
+
+def timing_threads(n: int | None = None) -> int:
+    """Threads the timing build uses (OMP_NUM_THREADS, else every host core);
+    with n, set them first."""
+    lib = _load_timing()
+    if n is not None:
+        lib.orc_set_num_threads(int(n))
+    return int(lib.orc_num_threads())
+
+
+class TimedStep:
+    """One optimisation step of the float32 oracle (timing build): preprocess,
+    binning, compositing, loss (Eq. 9), backward to the parameters and sparse
+    Adam, on the parameters given (held fixed: the step is re-timed, not
+    applied).  `sample(k)` times a bounded sample of the step -- every k-th
+    tile for binning, compositing and the 2-D backward, every k-th Gaussian
+    for the preprocess, the parameter backward and Adam, the loss in full --
+    and extrapolates each sampled phase by k; k = 1 is the whole step."""
+
+    def __init__(self, params: dict, cam: dict, target, E, Ts: int = 16):
+        self.lib = _load_timing()
+        self.cam, self.Ts = cam, Ts
+        self.p = {k: np.ascontiguousarray(v, np.float32) for k, v in params.items()}
+        self.n = self.p["means"].shape[0]
+        self.deg = sh_degree(self.p)
+        self.target = np.ascontiguousarray(target, np.float32)
+        self.E = np.ascontiguousarray(np.asarray(E, np.float32).reshape(12))
+        self.c = make_cam(cam)
+        self.full = None
+
+    def _pre(self, p, n):
+        out = dict(radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
+                   touched=np.zeros(n, np.uint32), depth_bits=np.zeros(n, np.uint32),
+                   mean2d=np.zeros((n, 2), np.float32), conic=np.zeros((n, 3), np.float32),
+                   opacity=np.zeros(n, np.float32), rgb=np.zeros((n, 3), np.float32),
+                   depth=np.zeros(n, np.float32), flags=np.zeros(n, np.uint8), cullp=np.zeros((n, 8), np.float32))
+        self.lib.orc_preprocess(n, self.deg, _p(p["means"]), _p(p["log_scales"]), _p(p["quats"]), _p(p["logits"]),
+                                _p(p["sh"]), C.byref(self.c), self.Ts, 1, _p(out["radius"]), _p(out["rect"]),
+                                _p(out["touched"]), _p(out["depth_bits"]), _p(out["mean2d"]), _p(out["conic"]),
+                                _p(out["opacity"]), _p(out["rgb"]), _p(out["depth"]), _p(out["flags"]),
+                                _p(out["cullp"]))
+        return out
+
+    def sample(self, k: int = 1) -> dict:
+        """Phase times (s) of one (sampled) step and the extrapolated step time."""
+        import time
+        lib, n, Ts = self.lib, self.n, self.Ts
+        W, H = int(self.cam["width"]), int(self.cam["height"])
+        TX, TY = tiles(self.cam, Ts)
+        k = max(1, int(k))
+        sub = self.p if k == 1 else {key: np.ascontiguousarray(v[::k]) for key, v in self.p.items()}
+        ns = sub["means"].shape[0]
+        t = {}
+        t0 = time.perf_counter()
+        pre_s = self._pre(sub, ns)
+        t["preprocess"] = time.perf_counter() - t0
+        if k == 1:
+            pre = pre_s
+        else:
+            if self.full is None:
+                self.full = self._pre(self.p, n)
+            pre = self.full
+        I = int(lib.orc_num_instances(n, _p(pre["touched"])))
+        keys = np.zeros(max(I, 1), np.uint64)
+        vals = np.zeros(max(I, 1), np.uint32)
+        ranges = np.zeros((TX * TY, 2), np.uint32)
+        t0 = time.perf_counter()
+        lib.orc_bin(n, _p(pre["rect"]), _p(pre["touched"]), _p(pre["depth_bits"]), _p(pre["cullp"]), Ts, TX, TY,
+                    k, _p(keys), _p(vals), _p(ranges))
+        t["bin"] = time.perf_counter() - t0
+        img = {key: np.zeros(sh, dt) for key, sh, dt in
+               (("C", (H, W, 3), np.float32), ("D", (H, W), np.float32), ("O", (H, W), np.float32),
+                ("T", (H, W), np.float32), ("nc", (H, W), np.int32), ("amb", (H, W), np.uint8))}
+        t0 = time.perf_counter()
+        lib.orc_render(W, H, Ts, k, _p(vals), _p(ranges), _p(pre["mean2d"]), _p(pre["conic"]), _p(pre["opacity"]),
+                       _p(pre["rgb"]), _p(pre["depth"]), 0.0, 0.0, _p(img["C"]), _p(img["D"]), _p(img["O"]),
+                       _p(img["T"]), _p(img["nc"]), _p(img["amb"]), None)
+        t["render"] = time.perf_counter() - t0
+        dC = np.zeros((H, W, 3), np.float32)
+        dE = np.zeros(12, np.float32)
+        ss, l1 = C.c_float(), C.c_float()
+        t0 = time.perf_counter()
+        lib.orc_loss(W, H, _p(img["C"]), _p(self.target), _p(self.E), 0.2, _p(dC), _p(dE), C.byref(ss),
+                     C.byref(l1))
+        t["loss"] = time.perf_counter() - t0
+        g2d = np.zeros((n, 10), np.float32)
+        t0 = time.perf_counter()
+        lib.orc_backward_2d(W, H, Ts, k, _p(vals), _p(ranges), _p(pre["mean2d"]), _p(pre["conic"]),
+                            _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]), _p(dC), None, None, n, _p(g2d))
+        t["backward_2d"] = time.perf_counter() - t0
+        g2s = g2d if k == 1 else np.ascontiguousarray(g2d[::k])
+        grads = {key: np.zeros_like(v) for key, v in sub.items()}
+        pose = np.zeros(6, np.float32)
+        t0 = time.perf_counter()
+        lib.orc_backward_params(ns, self.deg, _p(sub["means"]), _p(sub["log_scales"]), _p(sub["quats"]),
+                                _p(sub["logits"]), _p(sub["sh"]), C.byref(self.c), _p(pre_s["radius"]), _p(g2s),
+                                _p(grads["means"]), _p(grads["log_scales"]), _p(grads["quats"]),
+                                _p(grads["logits"]), _p(grads["sh"]), _p(pose))
+        t["backward_params"] = time.perf_counter() - t0
+        mask = (pre_s["radius"] > 0).astype(np.uint8)
+        work = {key: v.copy() for key, v in sub.items()}
+        mom = {key: (np.zeros_like(v), np.zeros_like(v)) for key, v in sub.items()}
+        t0 = time.perf_counter()
+        for key, lr in (("means", 1.6e-4), ("log_scales", 5e-3), ("quats", 1e-3), ("logits", 0.05),
+                        ("sh", 2.5e-3)):
+            v = work[key]
+            stride = int(np.prod(v.shape[1:])) if v.ndim > 1 else 1
+            lib.orc_adam(v.size, stride, _p(mask), _p(v), _p(mom[key][0]), _p(mom[key][1]), _p(grads[key]), lr,
+                         0.9, 0.999, 1e-15, 1)
+        t["adam"] = time.perf_counter() - t0
+        step = t["loss"] + k * sum(v for key, v in t.items() if key != "loss")
+        return dict(phases=t, k=k, step_s=step, wall_s=sum(t.values()), instances=I)
 
 
 def expf_decision(x: float) -> float:

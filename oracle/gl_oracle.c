@@ -20,10 +20,56 @@
  *
  * Readings of points the paper leaves open are listed beside each constant.
  */
-#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Scalar of the continuous arithmetic.  The checker is this file as it is
+ * (double, single-threaded: the OpenMP pragmas below are inert without
+ * -fopenmp, so every loop runs in its written order).  The CPU baseline the
+ * benchmark times is the same source built with -DORC_REAL=float -fopenmp:
+ * the float instantiation, parallel over Gaussians, pixel rows and map
+ * entries, with per-thread gradient buffers summed in thread order.  The
+ * float32 decision path is float in both. */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
+static int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Threads the parallel loops use (1 in the checker build), and a way to set
+ * them (no effect in the checker build). */
+int orc_num_threads(void) { return orc_threads(); }
+
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+static int orc_thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* Constants (the paper cites 3DGS for all of them and prints none).         */
@@ -59,7 +105,7 @@ typedef struct {
 /* Normalisation K_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2  */
 /* for m != 0), written as the per-polynomial factors below.                 */
 /* ------------------------------------------------------------------------- */
-static void sh_consts(double* k)
+static void sh_consts(real* k)
 {
     k[0] = 0.5 * sqrt(1.0 / OR_PI);              /* Y00                  */
     k[1] = sqrt(3.0 / (4.0 * OR_PI));            /* l=1                  */
@@ -74,12 +120,12 @@ static void sh_consts(double* k)
 }
 
 /* Y[16] at unit direction (x,y,z); dY[16][3] its gradient (may be NULL).    */
-void orc_sh_basis(int deg, double x, double y, double z, double* Y, double* dY)
+void orc_sh_basis(int deg, real x, real y, real z, real* Y, real* dY)
 {
-    double k[10];
+    real k[10];
     sh_consts(k);
     int nb = (deg + 1) * (deg + 1);
-    double d[16][3];
+    real d[16][3];
     memset(d, 0, sizeof(d));
     Y[0] = k[0];
     if (deg >= 1) {
@@ -221,7 +267,7 @@ static int tile_keep(const float cp[8], float X0, float Y0, float T1)
 /* Float32 decision path: cull, radius, rectangle, depth key (Eq. 2-3).      */
 /* Returns 1 if the Gaussian is kept.                                         */
 /* ------------------------------------------------------------------------- */
-static int project_f32(const double* mud, const double* lsd, const double* qd, double logit,
+static int project_f32(const real* mud, const real* lsd, const real* qd, real logit,
                        const orc_cam* cam, int Ts,
                        int32_t* radius, int32_t rect[4], uint32_t* dbits, float cp[8])
 {
@@ -339,75 +385,75 @@ static uint32_t kept_tiles(const int32_t rc[4], const float cp[8], int Ts, int c
 /* ------------------------------------------------------------------------- */
 /* Double path: rotation, covariance, EWA, conic, opacity, SH colour.        */
 /* ------------------------------------------------------------------------- */
-static void quat_to_rot(const double* qn, double* Rm)
+static void quat_to_rot(const real* qn, real* Rm)
 {
-    double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    real w = qn[0], x = qn[1], y = qn[2], z = qn[3];
     Rm[0] = 1 - 2 * (y * y + z * z); Rm[1] = 2 * (x * y - w * z);     Rm[2] = 2 * (x * z + w * y);
     Rm[3] = 2 * (x * y + w * z);     Rm[4] = 1 - 2 * (x * x + z * z); Rm[5] = 2 * (y * z - w * x);
     Rm[6] = 2 * (x * z - w * y);     Rm[7] = 2 * (y * z + w * x);     Rm[8] = 1 - 2 * (x * x + y * y);
 }
 
 typedef struct {
-    double mc[3];        /* camera-space mean mu-hat                        */
-    double u, v;         /* mu'                                             */
-    double s[3];         /* scales                                          */
-    double qn[4];        /* unit quaternion                                 */
-    double qnorm;
-    double Rq[9];        /* rotation from the quaternion                    */
-    double Sig[9];       /* 3-D covariance                                  */
-    double J[6];         /* 2x3 EWA Jacobian (row-major), clamp applied     */
+    real mc[3];        /* camera-space mean mu-hat                        */
+    real u, v;         /* mu'                                             */
+    real s[3];         /* scales                                          */
+    real qn[4];        /* unit quaternion                                 */
+    real qnorm;
+    real Rq[9];        /* rotation from the quaternion                    */
+    real Sig[9];       /* 3-D covariance                                  */
+    real J[6];         /* 2x3 EWA Jacobian (row-major), clamp applied     */
     int clx, cly;        /* 1 if the x/z (y/z) clamp is active              */
-    double T[6];         /* J W                                             */
-    double cov[3];       /* a, b, c of Sigma' (with dilation)               */
-    double det;
-    double conic[3];     /* A, B, C                                         */
-    double o;            /* opacity                                         */
-    double dir[3];       /* unit view direction                             */
-    double dnorm;
-    double rgb[3];
+    real T[6];         /* J W                                             */
+    real cov[3];       /* a, b, c of Sigma' (with dilation)               */
+    real det;
+    real conic[3];     /* A, B, C                                         */
+    real o;            /* opacity                                         */
+    real dir[3];       /* unit view direction                             */
+    real dnorm;
+    real rgb[3];
     int clamp[3];        /* 1 where rgb was clamped at 0                    */
-    double Y[16];
+    real Y[16];
 } geom_t;
 
-static void project_f64(const double* mu, const double* ls, const double* q, double logit,
-                        const double* sh, int deg, const orc_cam* cam, geom_t* G)
+static void project_f64(const real* mu, const real* ls, const real* q, real logit,
+                        const real* sh, int deg, const orc_cam* cam, geom_t* G)
 {
-    double R[9], t[3];
+    real R[9], t[3];
     for (int i = 0; i < 9; i++) R[i] = cam->R[i];
     for (int i = 0; i < 3; i++) t[i] = cam->t[i];
-    double m[3] = { mu[0], mu[1], mu[2] };
+    real m[3] = { mu[0], mu[1], mu[2] };
     for (int i = 0; i < 3; i++)
         G->mc[i] = R[i * 3 + 0] * m[0] + R[i * 3 + 1] * m[1] + R[i * 3 + 2] * m[2] + t[i];
-    double x = G->mc[0], y = G->mc[1], z = G->mc[2];
-    double fx = cam->fx, fy = cam->fy;
+    real x = G->mc[0], y = G->mc[1], z = G->mc[2];
+    real fx = cam->fx, fy = cam->fy;
     G->u = fx * x / z + cam->cx;
     G->v = fy * y / z + cam->cy;
     for (int i = 0; i < 3; i++) G->s[i] = exp(ls[i]);
-    double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    real qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     G->qnorm = sqrt(qq);
     for (int i = 0; i < 4; i++) G->qn[i] = q[i] / G->qnorm;
     quat_to_rot(G->qn, G->Rq);
-    double M[9];
+    real M[9];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) M[i * 3 + j] = G->Rq[i * 3 + j] * G->s[j];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++)
             G->Sig[i * 3 + j] = M[i * 3 + 0] * M[j * 3 + 0] + M[i * 3 + 1] * M[j * 3 + 1]
                                 + M[i * 3 + 2] * M[j * 3 + 2];
-    double limx = OR_JCLAMP * (0.5 * cam->width / fx);
-    double limy = OR_JCLAMP * (0.5 * cam->height / fy);
-    double xz = x / z, yz = y / z;
+    real limx = OR_JCLAMP * (0.5 * cam->width / fx);
+    real limy = OR_JCLAMP * (0.5 * cam->height / fy);
+    real xz = x / z, yz = y / z;
     G->clx = (xz < -limx || xz > limx);
     G->cly = (yz < -limy || yz > limy);
-    double cxz = xz < -limx ? -limx : (xz > limx ? limx : xz);
-    double cyz = yz < -limy ? -limy : (yz > limy ? limy : yz);
+    real cxz = xz < -limx ? -limx : (xz > limx ? limx : xz);
+    real cyz = yz < -limy ? -limy : (yz > limy ? limy : yz);
     G->J[0] = fx / z; G->J[1] = 0; G->J[2] = -fx * cxz / z;
     G->J[3] = 0; G->J[4] = fy / z; G->J[5] = -fy * cyz / z;
     for (int i = 0; i < 2; i++)
         for (int k = 0; k < 3; k++)
             G->T[i * 3 + k] = G->J[i * 3 + 0] * R[k] + G->J[i * 3 + 1] * R[3 + k]
                               + G->J[i * 3 + 2] * R[6 + k];
-    double U[6];
+    real U[6];
     for (int i = 0; i < 2; i++)
         for (int k = 0; k < 3; k++)
             U[i * 3 + k] = G->T[i * 3 + 0] * G->Sig[k] + G->T[i * 3 + 1] * G->Sig[3 + k]
@@ -422,15 +468,15 @@ static void project_f64(const double* mu, const double* ls, const double* q, dou
     G->o = 1.0 / (1.0 + exp(-logit));
 
     /* SH colour: direction from the camera centre c_w = -R^T t to the mean.  */
-    double cw[3];
+    real cw[3];
     for (int i = 0; i < 3; i++) cw[i] = -(R[0 * 3 + i] * t[0] + R[1 * 3 + i] * t[1] + R[2 * 3 + i] * t[2]);
-    double d[3] = { m[0] - cw[0], m[1] - cw[1], m[2] - cw[2] };
+    real d[3] = { m[0] - cw[0], m[1] - cw[1], m[2] - cw[2] };
     G->dnorm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     for (int i = 0; i < 3; i++) G->dir[i] = d[i] / G->dnorm;
     orc_sh_basis(deg, G->dir[0], G->dir[1], G->dir[2], G->Y, NULL);
     int nb = (deg + 1) * (deg + 1);
     for (int c = 0; c < 3; c++) {
-        double acc = 0.5;
+        real acc = 0.5;
         for (int k = 0; k < nb; k++) acc += G->Y[k] * sh[k * 3 + c];
         G->clamp[c] = acc < 0.0;
         G->rgb[c] = acc < 0.0 ? 0.0 : acc;
@@ -442,14 +488,15 @@ static void project_f64(const double* mu, const double* ls, const double* q, dou
 /* ------------------------------------------------------------------------- */
 /* cull = 1: exact tile culling (touched counts only the kept tiles; cullp, */
 /* 8 floats per Gaussian, holds the test's inputs for orc_bin).              */
-void orc_preprocess(int64_t n, int deg, const double* means, const double* lscale,
-                    const double* quat, const double* logit, const double* sh,
+void orc_preprocess(int64_t n, int deg, const real* means, const real* lscale,
+                    const real* quat, const real* logit, const real* sh,
                     const orc_cam* cam, int Ts, int cull,
                     int32_t* radius, int32_t* rect, uint32_t* touched, uint32_t* dbits,
-                    double* mean2d, double* conic, double* opac, double* rgb, double* depth,
+                    real* mean2d, real* conic, real* opac, real* rgb, real* depth,
                     uint8_t* flags, float* cullp)
 {
     int nb = (deg + 1) * (deg + 1);
+#pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < n; g++) {
         int32_t r = 0, rc[4] = { 0, 0, 0, 0 };
         uint32_t db = 0;
@@ -503,11 +550,15 @@ int64_t orc_num_instances(int64_t n, const uint32_t* touched)
 
 /* keys/vals sized orc_num_instances(); ranges sized 2 * num_tiles.  With   */
 /* cullp (from orc_preprocess with cull = 1) only the kept tiles are emitted. */
-void orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint32_t* dbits,
-             const float* cullp, int Ts, int TX, int TY, uint64_t* keys, uint32_t* vals, uint32_t* ranges)
+/* Only tiles t with t % tile_step == 0 get instances (1: all of them; a     */
+/* larger step is the benchmark's sample of the work); returns the number   */
+/* emitted.                                                                  */
+int64_t orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint32_t* dbits,
+                const float* cullp, int Ts, int TX, int TY, int tile_step, uint64_t* keys, uint32_t* vals,
+                uint32_t* ranges)
 {
-    int64_t I = orc_num_instances(n, touched);
-    inst_t* buf = (inst_t*)malloc(sizeof(inst_t) * (size_t)(I > 0 ? I : 1));
+    int64_t ninst = orc_num_instances(n, touched);
+    inst_t* buf = (inst_t*)malloc(sizeof(inst_t) * (size_t)(ninst > 0 ? ninst : 1));
     int64_t k = 0;
     for (int64_t g = 0; g < n; g++) {
         if (!touched[g]) continue;
@@ -517,23 +568,26 @@ void orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint
             for (int tx = rc[0]; tx < rc[2]; tx++) {
                 if (culled && !tile_keep(cullp + 8 * g, (float)(tx * Ts), (float)(ty * Ts), (float)(Ts - 1)))
                     continue;
+                if ((ty * TX + tx) % tile_step) continue;
                 buf[k].key = ((uint64_t)(uint32_t)(ty * TX + tx) << 32) | (uint64_t)dbits[g];
                 buf[k].order = (uint64_t)k;
                 buf[k].val = (uint32_t)g;
                 k++;
             }
     }
-    qsort(buf, (size_t)I, sizeof(inst_t), inst_cmp);
+    ninst = k;
+    qsort(buf, (size_t)ninst, sizeof(inst_t), inst_cmp);
     int nt = TX * TY;
     for (int i = 0; i < 2 * nt; i++) ranges[i] = 0;
-    for (int64_t i = 0; i < I; i++) {
+    for (int64_t i = 0; i < ninst; i++) {
         keys[i] = buf[i].key;
         vals[i] = buf[i].val;
         uint32_t tile = (uint32_t)(buf[i].key >> 32);
         if (i == 0 || (uint32_t)(buf[i - 1].key >> 32) != tile) ranges[2 * tile] = (uint32_t)i;
-        if (i == I - 1 || (uint32_t)(buf[i + 1].key >> 32) != tile) ranges[2 * tile + 1] = (uint32_t)(i + 1);
+        if (i == ninst - 1 || (uint32_t)(buf[i + 1].key >> 32) != tile) ranges[2 * tile + 1] = (uint32_t)(i + 1);
     }
     free(buf);
+    return ninst;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -541,40 +595,40 @@ void orc_bin(int64_t n, const int32_t* rect, const uint32_t* touched, const uint
 /* the backward.  Returns the number of contributors written to `list`.      */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-    double amb_alpha_rel;   /* relative window around the alpha threshold  */
-    double amb_T_rel;       /* relative window around the T threshold      */
+    real amb_alpha_rel;   /* relative window around the alpha threshold  */
+    real amb_T_rel;       /* relative window around the T threshold      */
 } orc_amb;
 
-static int composite_pixel(double px, double py, const uint32_t* idx, int64_t cnt,
-                           const double* mean2d, const double* conic, const double* opac,
-                           const double* rgb, const double* depth,
-                           double* C, double* D, double* O, double* Tfin, int32_t* ncontrib,
+static int composite_pixel(real px, real py, const uint32_t* idx, int64_t cnt,
+                           const real* mean2d, const real* conic, const real* opac,
+                           const real* rgb, const real* depth,
+                           real* C, real* D, real* O, real* Tfin, int32_t* ncontrib,
                            uint8_t* amb, const orc_amb* ab,
-                           int64_t* list_pos, double* list_alpha, double* list_T, int* list_capped,
-                           double* list_G, uint64_t* sig)
+                           int64_t* list_pos, real* list_alpha, real* list_T, int* list_capped,
+                           real* list_G, uint64_t* sig)
 {
-    double T = 1.0, c0 = 0, c1 = 0, c2 = 0, dd = 0, oo = 0;
+    real T = 1.0, c0 = 0, c1 = 0, c2 = 0, dd = 0, oo = 0;
     int32_t last = 0;
     int nl = 0;
     uint8_t a = 0;
     uint64_t h = 1469598103934665603ULL;   /* FNV-1a over (position, capped) */
     for (int64_t i = 0; i < cnt; i++) {
         uint32_t g = idx[i];
-        double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
-        double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
-        double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
-        double scale = 0.5 * (fabs(A * dx * dx) + fabs(Cc * dy * dy)) + fabs(B * dx * dy);
+        real dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+        real A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
+        real power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+        real scale = 0.5 * (fabs(A * dx * dx) + fabs(Cc * dy * dy)) + fabs(B * dx * dy);
         if (fabs(power) <= 1e-6 * scale + 1e-30 && power <= 0.0 && scale > 0) a = 1;
         if (power > 0.0) { if (power <= 1e-6 * scale) a = 1; continue; }
-        double G = exp(power);
-        double araw = opac[g] * G;
+        real G = exp(power);
+        real araw = opac[g] * G;
         if (fabs(araw - OR_ALPHA_MIN) <= ab->amb_alpha_rel * OR_ALPHA_MIN) a = 1;
-        double alpha = araw < OR_ALPHA_MAX ? araw : OR_ALPHA_MAX;
+        real alpha = araw < OR_ALPHA_MAX ? araw : OR_ALPHA_MAX;
         if (alpha < OR_ALPHA_MIN) continue;
-        double test_T = T * (1.0 - alpha);
+        real test_T = T * (1.0 - alpha);
         if (fabs(test_T - OR_T_MIN) <= ab->amb_T_rel * OR_T_MIN) a = 1;
         if (test_T < OR_T_MIN) break;
-        double w = alpha * T;
+        real w = alpha * T;
         c0 += rgb[3 * g] * w; c1 += rgb[3 * g + 1] * w; c2 += rgb[3 * g + 2] * w;
         dd += depth[g] * w; oo += w;
         if (list_pos) {
@@ -593,21 +647,24 @@ static int composite_pixel(double px, double py, const uint32_t* idx, int64_t cn
     return nl;
 }
 
-void orc_render(int W, int H, int Ts, const uint32_t* vals, const uint32_t* ranges,
-                const double* mean2d, const double* conic, const double* opac,
-                const double* rgb, const double* depth,
-                double amb_alpha_rel, double amb_T_rel,
-                double* C, double* D, double* O, double* Tfin, int32_t* ncontrib, uint8_t* amb,
+/* Pixels of tiles t with t % tile_step != 0 are left untouched.           */
+void orc_render(int W, int H, int Ts, int tile_step, const uint32_t* vals, const uint32_t* ranges,
+                const real* mean2d, const real* conic, const real* opac,
+                const real* rgb, const real* depth,
+                real amb_alpha_rel, real amb_T_rel,
+                real* C, real* D, real* O, real* Tfin, int32_t* ncontrib, uint8_t* amb,
                 uint64_t* sig)
 {
     int TX = (W + Ts - 1) / Ts;
     orc_amb ab = { amb_alpha_rel, amb_T_rel };
+#pragma omp parallel for schedule(dynamic, 1)
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             int tile = (py / Ts) * TX + (px / Ts);
+            if (tile % tile_step) continue;
             uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
             size_t p = (size_t)py * W + px;
-            composite_pixel((double)px, (double)py, vals + s, (int64_t)e - s, mean2d, conic, opac,
+            composite_pixel((real)px, (real)py, vals + s, (int64_t)e - s, mean2d, conic, opac,
                             rgb, depth, C + 3 * p, D + p, O + p, Tfin + p, ncontrib + p, amb + p, &ab,
                             NULL, NULL, NULL, NULL, NULL, sig ? sig + p : NULL);
         }
@@ -626,9 +683,9 @@ static int dg_cmp(const void* a, const void* b)
 
 void orc_render_bruteforce(int W, int H, int Ts, int64_t n, const int32_t* rect,
                            const uint32_t* touched, const uint32_t* dbits,
-                           const double* mean2d, const double* conic, const double* opac,
-                           const double* rgb, const double* depth, int use_rect,
-                           double* C, double* D, double* O, double* Tfin, int32_t* ncontrib)
+                           const real* mean2d, const real* conic, const real* opac,
+                           const real* rgb, const real* depth, int use_rect,
+                           real* C, real* D, real* O, real* Tfin, int32_t* ncontrib)
 {
     dg_t* lst = (dg_t*)malloc(sizeof(dg_t) * (size_t)(n > 0 ? n : 1));
     uint32_t* ids = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
@@ -647,7 +704,7 @@ void orc_render_bruteforce(int W, int H, int Ts, int64_t n, const int32_t* rect,
             for (int64_t i = 0; i < m; i++) ids[i] = lst[i].g;
             size_t p = (size_t)py * W + px;
             uint8_t a;
-            composite_pixel((double)px, (double)py, ids, m, mean2d, conic, opac, rgb, depth,
+            composite_pixel((real)px, (real)py, ids, m, mean2d, conic, opac, rgb, depth,
                             C + 3 * p, D + p, O + p, Tfin + p, ncontrib + p, &a, &ab,
                             NULL, NULL, NULL, NULL, NULL, NULL);
         }
@@ -659,11 +716,11 @@ void orc_render_bruteforce(int W, int H, int Ts, int64_t n, const int32_t* rect,
 /* Exposure + L1 + D-SSIM loss (Eq. 9) and its exact adjoint.                */
 /* E is 3x4 row-major [A | b]; C_hat = A C + b.                               */
 /* ------------------------------------------------------------------------- */
-static void ssim_window(double* w)
+static void ssim_window(real* w)
 {
-    double s = 0;
+    real s = 0;
     for (int i = 0; i < OR_SSIM_WIN; i++) {
-        double d = i - OR_SSIM_WIN / 2;
+        real d = i - OR_SSIM_WIN / 2;
         w[i] = exp(-d * d / (2.0 * OR_SSIM_SIGMA * OR_SSIM_SIGMA));
         s += w[i];
     }
@@ -671,21 +728,23 @@ static void ssim_window(double* w)
 }
 
 /* Zero-padded "same" 2-D correlation with the separable window (one map). */
-static void blur(int W, int H, const double* in, double* out, const double* w, double* tmp)
+static void blur(int W, int H, const real* in, real* out, const real* w, real* tmp)
 {
     int h = OR_SSIM_WIN / 2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
-            double s = 0;
+            real s = 0;
             for (int k = -h; k <= h; k++) {
                 int xx = x + k;
                 if (xx >= 0 && xx < W) s += w[k + h] * in[(size_t)y * W + xx];
             }
             tmp[(size_t)y * W + x] = s;
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
-            double s = 0;
+            real s = 0;
             for (int k = -h; k <= h; k++) {
                 int yy = y + k;
                 if (yy >= 0 && yy < H) s += w[k + h] * tmp[(size_t)yy * W + x];
@@ -694,79 +753,89 @@ static void blur(int W, int H, const double* in, double* out, const double* w, d
         }
 }
 
-double orc_loss(int W, int H, const double* C, const float* target, const float* E, double lambda,
-                double* dL_dC, double* dL_dE, double* ssim_mean_out, double* l1_out)
+real orc_loss(int W, int H, const real* C, const float* target, const float* E, real lambda,
+                real* dL_dC, real* dL_dE, real* ssim_mean_out, real* l1_out)
 {
     size_t P = (size_t)W * H;
-    double w[OR_SSIM_WIN];
+    real w[OR_SSIM_WIN];
     ssim_window(w);
-    double* Ch = (double*)malloc(sizeof(double) * P * 3);
-    double* gCh = (double*)calloc(P * 3, sizeof(double));
+    real* Ch = (real*)malloc(sizeof(real) * P * 3);
+    real* gCh = (real*)calloc(P * 3, sizeof(real));
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < P; p++)
         for (int i = 0; i < 3; i++)
             Ch[3 * p + i] = E[4 * i + 0] * C[3 * p + 0] + E[4 * i + 1] * C[3 * p + 1]
                             + E[4 * i + 2] * C[3 * p + 2] + E[4 * i + 3];
-    double l1 = 0;
-    double inv = 1.0 / (3.0 * (double)P);
+    real l1 = 0;
+    real inv = 1.0 / (3.0 * (real)P);
+#pragma omp parallel for schedule(static) reduction(+ : l1)
     for (size_t p = 0; p < 3 * P; p++) {
-        double d = Ch[p] - (double)target[p];
+        real d = Ch[p] - (real)target[p];
         l1 += fabs(d);
         gCh[p] += (1.0 - lambda) * inv * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0));
     }
     l1 *= inv;
 
-    double *x = malloc(sizeof(double) * P), *y = malloc(sizeof(double) * P), *tmp = malloc(sizeof(double) * P);
-    double *mx = malloc(sizeof(double) * P), *my = malloc(sizeof(double) * P);
-    double *exx = malloc(sizeof(double) * P), *eyy = malloc(sizeof(double) * P), *exy = malloc(sizeof(double) * P);
-    double *buf = malloc(sizeof(double) * P);
-    double *ga = malloc(sizeof(double) * P), *gb = malloc(sizeof(double) * P), *gc = malloc(sizeof(double) * P);
-    double *ba = malloc(sizeof(double) * P), *bb = malloc(sizeof(double) * P), *bc = malloc(sizeof(double) * P);
-    double ssim_sum = 0;
-    double gS = -lambda * inv;     /* dL / dS(p, channel) */
+    real *x = malloc(sizeof(real) * P), *y = malloc(sizeof(real) * P), *tmp = malloc(sizeof(real) * P);
+    real *mx = malloc(sizeof(real) * P), *my = malloc(sizeof(real) * P);
+    real *exx = malloc(sizeof(real) * P), *eyy = malloc(sizeof(real) * P), *exy = malloc(sizeof(real) * P);
+    real *buf = malloc(sizeof(real) * P);
+    real *ga = malloc(sizeof(real) * P), *gb = malloc(sizeof(real) * P), *gc = malloc(sizeof(real) * P);
+    real *ba = malloc(sizeof(real) * P), *bb = malloc(sizeof(real) * P), *bc = malloc(sizeof(real) * P);
+    real ssim_sum = 0;
+    real gS = -lambda * inv;     /* dL / dS(p, channel) */
     for (int ch = 0; ch < 3; ch++) {
+#pragma omp parallel for schedule(static)
         for (size_t p = 0; p < P; p++) { x[p] = Ch[3 * p + ch]; y[p] = target[3 * p + ch]; }
         blur(W, H, x, mx, w, tmp);
         blur(W, H, y, my, w, tmp);
+#pragma omp parallel for schedule(static)
         for (size_t p = 0; p < P; p++) buf[p] = x[p] * x[p];
         blur(W, H, buf, exx, w, tmp);
+#pragma omp parallel for schedule(static)
         for (size_t p = 0; p < P; p++) buf[p] = y[p] * y[p];
         blur(W, H, buf, eyy, w, tmp);
+#pragma omp parallel for schedule(static)
         for (size_t p = 0; p < P; p++) buf[p] = x[p] * y[p];
         blur(W, H, buf, exy, w, tmp);
+#pragma omp parallel for schedule(static) reduction(+ : ssim_sum)
         for (size_t p = 0; p < P; p++) {
-            double sxx = exx[p] - mx[p] * mx[p];
-            double syy = eyy[p] - my[p] * my[p];
-            double sxy = exy[p] - mx[p] * my[p];
-            double N1 = 2 * mx[p] * my[p] + OR_SSIM_C1, N2 = 2 * sxy + OR_SSIM_C2;
-            double D1 = mx[p] * mx[p] + my[p] * my[p] + OR_SSIM_C1, D2 = sxx + syy + OR_SSIM_C2;
-            double S = N1 * N2 / (D1 * D2);
+            real sxx = exx[p] - mx[p] * mx[p];
+            real syy = eyy[p] - my[p] * my[p];
+            real sxy = exy[p] - mx[p] * my[p];
+            real N1 = 2 * mx[p] * my[p] + OR_SSIM_C1, N2 = 2 * sxy + OR_SSIM_C2;
+            real D1 = mx[p] * mx[p] + my[p] * my[p] + OR_SSIM_C1, D2 = sxx + syy + OR_SSIM_C2;
+            real S = N1 * N2 / (D1 * D2);
             ssim_sum += S;
             /* partials w.r.t. mu_x, E[x^2], E[xy] (mu_y, E[y^2] are constants) */
-            double dS_dN1 = N2 / (D1 * D2), dS_dN2 = N1 / (D1 * D2);
-            double dS_dD1 = -S / D1, dS_dD2 = -S / D2;
-            double dmx = dS_dN1 * 2 * my[p] + dS_dN2 * (-2 * my[p]) + dS_dD1 * 2 * mx[p]
+            real dS_dN1 = N2 / (D1 * D2), dS_dN2 = N1 / (D1 * D2);
+            real dS_dD1 = -S / D1, dS_dD2 = -S / D2;
+            real dmx = dS_dN1 * 2 * my[p] + dS_dN2 * (-2 * my[p]) + dS_dD1 * 2 * mx[p]
                          + dS_dD2 * (-2 * mx[p]);
-            double dexx = dS_dD2;
-            double dexy = dS_dN2 * 2;
+            real dexx = dS_dD2;
+            real dexy = dS_dN2 * 2;
             ga[p] = gS * dmx; gb[p] = gS * dexx; gc[p] = gS * dexy;
         }
         blur(W, H, ga, ba, w, tmp);
         blur(W, H, gb, bb, w, tmp);
         blur(W, H, gc, bc, w, tmp);
+#pragma omp parallel for schedule(static)
         for (size_t p = 0; p < P; p++) gCh[3 * p + ch] += ba[p] + 2 * x[p] * bb[p] + y[p] * bc[p];
     }
-    double ssim_mean = ssim_sum * inv;
-    double loss = (1.0 - lambda) * l1 + lambda * (1.0 - ssim_mean);
+    real ssim_mean = ssim_sum * inv;
+    real loss = (1.0 - lambda) * l1 + lambda * (1.0 - ssim_mean);
 
     for (int i = 0; i < 12; i++) dL_dE[i] = 0;
+#pragma omp parallel for schedule(static) reduction(+ : dL_dE[:12])
     for (size_t p = 0; p < P; p++)
         for (int i = 0; i < 3; i++) {
-            double g = gCh[3 * p + i];
+            real g = gCh[3 * p + i];
             dL_dE[4 * i + 0] += g * C[3 * p + 0];
             dL_dE[4 * i + 1] += g * C[3 * p + 1];
             dL_dE[4 * i + 2] += g * C[3 * p + 2];
             dL_dE[4 * i + 3] += g;
         }
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < P; p++)
         for (int j = 0; j < 3; j++)
             dL_dC[3 * p + j] = E[0 * 4 + j] * gCh[3 * p + 0] + E[1 * 4 + j] * gCh[3 * p + 1]
@@ -779,89 +848,115 @@ double orc_loss(int W, int H, const double* C, const float* target, const float*
 }
 
 /* ------------------------------------------------------------------------- */
-/* Backward.  Per pixel, the contributor list is replayed in double; each    */
+/* Backward.  Per pixel, the contributor list is replayed in real; each    */
 /* contributor receives dL/d(mu'), dL/d(conic), dL/d(o), dL/d(rgb),          */
 /* dL/d(depth); the chain rule then reaches the parameters and the pose.     */
 /* g2d layout per Gaussian: [du, dv, dA, dB, dC, do, dr, dg, db, dz].         */
 /* ------------------------------------------------------------------------- */
-void orc_backward_2d(int W, int H, int Ts, const uint32_t* vals, const uint32_t* ranges,
-                     const double* mean2d, const double* conic, const double* opac,
-                     const double* rgb, const double* depth,
-                     const double* dL_dC, const double* dL_dD, const double* dL_dO,
-                     int64_t n, double* g2d)
+/* Pixels of tiles t with t % tile_step != 0 contribute nothing.  Built   */
+/* with OpenMP, each thread sums into its own buffer and the buffers are    */
+/* added in thread order; the checker build sums in pixel order directly.   */
+void orc_backward_2d(int W, int H, int Ts, int tile_step, const uint32_t* vals, const uint32_t* ranges,
+                     const real* mean2d, const real* conic, const real* opac,
+                     const real* rgb, const real* depth,
+                     const real* dL_dC, const real* dL_dD, const real* dL_dO,
+                     int64_t n, real* g2d)
 {
     int TX = (W + Ts - 1) / Ts;
-    memset(g2d, 0, sizeof(double) * 10 * (size_t)n);
+    memset(g2d, 0, sizeof(real) * 10 * (size_t)n);
     int64_t maxc = 0;
     int nt = TX * ((H + Ts - 1) / Ts);
     for (int t = 0; t < nt; t++) {
         int64_t c = (int64_t)ranges[2 * t + 1] - ranges[2 * t];
         if (c > maxc) maxc = c;
     }
-    int64_t* lp = malloc(sizeof(int64_t) * (size_t)(maxc + 1));
-    double* la = malloc(sizeof(double) * (size_t)(maxc + 1));
-    double* lT = malloc(sizeof(double) * (size_t)(maxc + 1));
-    double* lG = malloc(sizeof(double) * (size_t)(maxc + 1));
-    int* lc = malloc(sizeof(int) * (size_t)(maxc + 1));
-    orc_amb ab = { 0, 0 };
-    for (int py = 0; py < H; py++)
-        for (int px = 0; px < W; px++) {
-            int tile = (py / Ts) * TX + (px / Ts);
-            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
-            size_t p = (size_t)py * W + px;
-            double Cp[3], Dp, Op, Tf; int32_t nc; uint8_t a;
-            int nl = composite_pixel((double)px, (double)py, vals + s, (int64_t)e - s, mean2d, conic,
-                                     opac, rgb, depth, Cp, &Dp, &Op, &Tf, &nc, &a, &ab,
-                                     lp, la, lT, lc, lG, NULL);
-            double gC[3] = { dL_dC[3 * p], dL_dC[3 * p + 1], dL_dC[3 * p + 2] };
-            double gD = dL_dD ? dL_dD[p] : 0.0, gO = dL_dO ? dL_dO[p] : 0.0;
-            /* suffix sums: S_after = sum_{j>i} x_j alpha_j T_j (background 0) */
-            double sc[3] = { 0, 0, 0 }, sd = 0, so = 0;
-            for (int k = nl - 1; k >= 0; k--) {
-                uint32_t g = vals[s + lp[k]];
-                double al = la[k], T = lT[k], w = al * T;
-                double dalpha = 0;
-                for (int c = 0; c < 3; c++) {
-                    dalpha += gC[c] * (T * rgb[3 * g + c] - sc[c] / (1.0 - al));
-                    g2d[10 * g + 6 + c] += w * gC[c];
+    const int nth = orc_threads();
+    real* acc = nth > 1 ? (real*)calloc((size_t)nth * 10 * (size_t)n, sizeof(real)) : g2d;
+#pragma omp parallel num_threads(nth)
+    {
+        real* gg = nth > 1 ? acc + (size_t)orc_thread_id() * 10 * (size_t)n : g2d;
+        int64_t* lp = malloc(sizeof(int64_t) * (size_t)(maxc + 1));
+        real* la = malloc(sizeof(real) * (size_t)(maxc + 1));
+        real* lT = malloc(sizeof(real) * (size_t)(maxc + 1));
+        real* lG = malloc(sizeof(real) * (size_t)(maxc + 1));
+        int* lc = malloc(sizeof(int) * (size_t)(maxc + 1));
+        orc_amb ab = { 0, 0 };
+#pragma omp for schedule(dynamic, 1)
+        for (int py = 0; py < H; py++)
+            for (int px = 0; px < W; px++) {
+                int tile = (py / Ts) * TX + (px / Ts);
+                if (tile % tile_step) continue;
+                uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+                size_t p = (size_t)py * W + px;
+                real Cp[3], Dp, Op, Tf; int32_t nc; uint8_t a;
+                int nl = composite_pixel((real)px, (real)py, vals + s, (int64_t)e - s, mean2d, conic,
+                                         opac, rgb, depth, Cp, &Dp, &Op, &Tf, &nc, &a, &ab,
+                                         lp, la, lT, lc, lG, NULL);
+                real gC[3] = { dL_dC[3 * p], dL_dC[3 * p + 1], dL_dC[3 * p + 2] };
+                real gD = dL_dD ? dL_dD[p] : 0.0, gO = dL_dO ? dL_dO[p] : 0.0;
+                /* suffix sums: S_after = sum_{j>i} x_j alpha_j T_j (background 0) */
+                real sc[3] = { 0, 0, 0 }, sd = 0, so = 0;
+                for (int k = nl - 1; k >= 0; k--) {
+                    uint32_t g = vals[s + lp[k]];
+                    real al = la[k], T = lT[k], w = al * T;
+                    real dalpha = 0;
+                    for (int c = 0; c < 3; c++) {
+                        dalpha += gC[c] * (T * rgb[3 * g + c] - sc[c] / (1.0 - al));
+                        gg[10 * g + 6 + c] += w * gC[c];
+                    }
+                    dalpha += gD * (T * depth[g] - sd / (1.0 - al));
+                    dalpha += gO * (T - so / (1.0 - al));
+                    gg[10 * g + 9] += w * gD;
+                    for (int c = 0; c < 3; c++) sc[c] += rgb[3 * g + c] * w;
+                    sd += depth[g] * w; so += w;
+                    if (lc[k]) continue;      /* cap active: alpha is constant */
+                    real dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                    real A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
+                    real dpow = dalpha * al;       /* d alpha / d power = alpha */
+                    gg[10 * g + 5] += dalpha * lG[k];
+                    gg[10 * g + 0] += dpow * (-A * dx - B * dy);
+                    gg[10 * g + 1] += dpow * (-Cc * dy - B * dx);
+                    gg[10 * g + 2] += dpow * (-0.5 * dx * dx);
+                    gg[10 * g + 3] += dpow * (-dx * dy);
+                    gg[10 * g + 4] += dpow * (-0.5 * dy * dy);
                 }
-                dalpha += gD * (T * depth[g] - sd / (1.0 - al));
-                dalpha += gO * (T - so / (1.0 - al));
-                g2d[10 * g + 9] += w * gD;
-                for (int c = 0; c < 3; c++) sc[c] += rgb[3 * g + c] * w;
-                sd += depth[g] * w; so += w;
-                if (lc[k]) continue;      /* cap active: alpha is constant */
-                double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
-                double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
-                double dpow = dalpha * al;       /* d alpha / d power = alpha */
-                g2d[10 * g + 5] += dalpha * lG[k];
-                g2d[10 * g + 0] += dpow * (-A * dx - B * dy);
-                g2d[10 * g + 1] += dpow * (-Cc * dy - B * dx);
-                g2d[10 * g + 2] += dpow * (-0.5 * dx * dx);
-                g2d[10 * g + 3] += dpow * (-dx * dy);
-                g2d[10 * g + 4] += dpow * (-0.5 * dy * dy);
             }
+        free(lp); free(la); free(lT); free(lG); free(lc);
+    }
+    if (nth > 1) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < 10 * n; i++) {
+            real t = 0;
+            for (int th = 0; th < nth; th++) t += acc[(size_t)th * 10 * (size_t)n + (size_t)i];
+            g2d[i] = t;
         }
-    free(lp); free(la); free(lT); free(lG); free(lc);
+        free(acc);
+    }
 }
 
 /* From the 2-D gradients to the parameters (Eq. 1-3, SH) and the pose.      */
 /* Pose: left perturbation T_cw <- exp(xi^) T_cw, xi = (rho, phi), at xi = 0. */
-void orc_backward_params(int64_t n, int deg, const double* means, const double* lscale,
-                         const double* quat, const double* logit, const double* sh,
-                         const orc_cam* cam, const int32_t* radius, const double* g2d,
-                         double* g_means, double* g_lscale, double* g_quat, double* g_logit,
-                         double* g_sh, double* g_pose)
+void orc_backward_params(int64_t n, int deg, const real* means, const real* lscale,
+                         const real* quat, const real* logit, const real* sh,
+                         const orc_cam* cam, const int32_t* radius, const real* g2d,
+                         real* g_means, real* g_lscale, real* g_quat, real* g_logit,
+                         real* g_sh, real* g_pose)
 {
     int nb = (deg + 1) * (deg + 1);
-    double R[9];
+    real R[9];
     for (int i = 0; i < 9; i++) R[i] = cam->R[i];
     for (int i = 0; i < 6; i++) g_pose[i] = 0;
+    const int nth = orc_threads();
+    real* pose_part = (real*)calloc((size_t)nth * 6, sizeof(real));
+#pragma omp parallel num_threads(nth)
+    {
+    real* gp = pose_part + 6 * orc_thread_id();
+#pragma omp for schedule(static)
     for (int64_t g = 0; g < n; g++) {
-        double* gm = g_means + 3 * g;
-        double* gl = g_lscale + 3 * g;
-        double* gq = g_quat + 4 * g;
-        double* gs = g_sh + (size_t)nb * 3 * g;
+        real* gm = g_means + 3 * g;
+        real* gl = g_lscale + 3 * g;
+        real* gq = g_quat + 4 * g;
+        real* gs = g_sh + (size_t)nb * 3 * g;
         for (int i = 0; i < 3; i++) { gm[i] = 0; gl[i] = 0; }
         for (int i = 0; i < 4; i++) gq[i] = 0;
         for (int i = 0; i < nb * 3; i++) gs[i] = 0;
@@ -870,76 +965,76 @@ void orc_backward_params(int64_t n, int deg, const double* means, const double* 
         geom_t G;
         project_f64(means + 3 * g, lscale + 3 * g, quat + 4 * g, logit[g], sh + (size_t)nb * 3 * g,
                     deg, cam, &G);
-        const double* d2 = g2d + 10 * g;
-        double x = G.mc[0], y = G.mc[1], z = G.mc[2];
-        double fx = cam->fx, fy = cam->fy;
+        const real* d2 = g2d + 10 * g;
+        real x = G.mc[0], y = G.mc[1], z = G.mc[2];
+        real fx = cam->fx, fy = cam->fy;
 
         /* opacity */
         g_logit[g] = d2[5] * G.o * (1.0 - G.o);
 
         /* colour -> SH and view direction */
-        double grgb[3];
+        real grgb[3];
         for (int c = 0; c < 3; c++) grgb[c] = G.clamp[c] ? 0.0 : d2[6 + c];
-        double dY[48], Y[16];
+        real dY[48], Y[16];
         orc_sh_basis(deg, G.dir[0], G.dir[1], G.dir[2], Y, dY);
-        double gdir[3] = { 0, 0, 0 };
+        real gdir[3] = { 0, 0, 0 };
         for (int k = 0; k < nb; k++)
             for (int c = 0; c < 3; c++) {
                 gs[k * 3 + c] = Y[k] * grgb[c];
-                double coef = sh[(size_t)nb * 3 * g + k * 3 + c] * grgb[c];
+                real coef = sh[(size_t)nb * 3 * g + k * 3 + c] * grgb[c];
                 for (int j = 0; j < 3; j++) gdir[j] += coef * dY[k * 3 + j];
             }
         /* d = dir_unnormalised / |.|: dL/d(unnormalised) = (I - d d^T) gdir / |.| */
-        double dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
-        double gdu[3];
+        real dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
+        real gdu[3];
         for (int j = 0; j < 3; j++) gdu[j] = (gdir[j] - G.dir[j] * dd) / G.dnorm;
         /* dir_unnormalised = mu - c_w; c_w moves by -R^T rho under the pose twist */
         for (int j = 0; j < 3; j++) gm[j] += gdu[j];
         for (int i = 0; i < 3; i++)
-            g_pose[i] += R[i * 3 + 0] * gdu[0] + R[i * 3 + 1] * gdu[1] + R[i * 3 + 2] * gdu[2];
+            gp[i] += R[i * 3 + 0] * gdu[0] + R[i * 3 + 1] * gdu[1] + R[i * 3 + 2] * gdu[2];
 
         /* conic (A,B,C) -> Sigma' (a,b,c) */
-        double a = G.cov[0], b = G.cov[1], c = G.cov[2], det = G.det, d2i = 1.0 / (det * det);
-        double gA = d2[2], gB = d2[3], gC = d2[4];
-        double ga = gA * (-c * c * d2i) + gB * (b * c * d2i) + gC * (-b * b * d2i);
-        double gb = gA * (2 * b * c * d2i) + gB * (-(a * c + b * b) * d2i) + gC * (2 * a * b * d2i);
-        double gc = gA * (-b * b * d2i) + gB * (a * b * d2i) + gC * (-a * a * d2i);
+        real a = G.cov[0], b = G.cov[1], c = G.cov[2], det = G.det, d2i = 1.0 / (det * det);
+        real gA = d2[2], gB = d2[3], gC = d2[4];
+        real ga = gA * (-c * c * d2i) + gB * (b * c * d2i) + gC * (-b * b * d2i);
+        real gb = gA * (2 * b * c * d2i) + gB * (-(a * c + b * b) * d2i) + gC * (2 * a * b * d2i);
+        real gc = gA * (-b * b * d2i) + gB * (a * b * d2i) + gC * (-a * a * d2i);
         /* symmetric gradient matrix of the 2x2 Sigma' */
-        double Gm[4] = { ga, 0.5 * gb, 0.5 * gb, gc };
+        real Gm[4] = { ga, 0.5 * gb, 0.5 * gb, gc };
         /* Sigma' = T Sigma T^T: dL/dSigma = T^T G T; dL/dT = 2 G T Sigma      */
-        double gSig[9];
+        real gSig[9];
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) {
-                double s = 0;
+                real s = 0;
                 for (int p = 0; p < 2; p++)
                     for (int q = 0; q < 2; q++) s += G.T[p * 3 + i] * Gm[p * 2 + q] * G.T[q * 3 + j];
                 gSig[i * 3 + j] = s;
             }
-        double TS[6];
+        real TS[6];
         for (int p = 0; p < 2; p++)
             for (int j = 0; j < 3; j++) {
-                double s = 0;
+                real s = 0;
                 for (int k = 0; k < 3; k++) s += G.T[p * 3 + k] * G.Sig[k * 3 + j];
                 TS[p * 3 + j] = s;
             }
-        double gT[6];
+        real gT[6];
         for (int p = 0; p < 2; p++)
             for (int j = 0; j < 3; j++)
                 gT[p * 3 + j] = 2.0 * (Gm[p * 2 + 0] * TS[0 * 3 + j] + Gm[p * 2 + 1] * TS[1 * 3 + j]);
         /* Sigma = M M^T, M = Rq diag(s): dL/dM = 2 gSig M                      */
-        double M[9];
+        real M[9];
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) M[i * 3 + j] = G.Rq[i * 3 + j] * G.s[j];
-        double gM[9];
+        real gM[9];
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) {
-                double s = 0;
+                real s = 0;
                 for (int k = 0; k < 3; k++) s += gSig[i * 3 + k] * M[k * 3 + j];
                 gM[i * 3 + j] = 2.0 * s;
             }
-        double gRq[9];
+        real gRq[9];
         for (int j = 0; j < 3; j++) {
-            double s = 0;
+            real s = 0;
             for (int i = 0; i < 3; i++) {
                 s += gM[i * 3 + j] * G.Rq[i * 3 + j];
                 gRq[i * 3 + j] = gM[i * 3 + j] * G.s[j];
@@ -947,8 +1042,8 @@ void orc_backward_params(int64_t n, int deg, const double* means, const double* 
             gl[j] = s * G.s[j];    /* s = exp(log-scale) */
         }
         /* rotation matrix -> unit quaternion -> raw quaternion */
-        double w = G.qn[0], qx = G.qn[1], qy = G.qn[2], qz = G.qn[3];
-        double gn[4];
+        real w = G.qn[0], qx = G.qn[1], qy = G.qn[2], qz = G.qn[3];
+        real gn[4];
         gn[0] = 2 * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
         gn[1] = 2 * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2 * qx * gRq[4] - w * gRq[5]
                      + qz * gRq[6] + w * gRq[7] - 2 * qx * gRq[8]);
@@ -956,68 +1051,73 @@ void orc_backward_params(int64_t n, int deg, const double* means, const double* 
                      - w * gRq[6] + qz * gRq[7] - 2 * qy * gRq[8]);
         gn[3] = 2 * (-2 * qz * gRq[0] - w * gRq[1] + qx * gRq[2] + w * gRq[3] - 2 * qz * gRq[4]
                      + qy * gRq[5] + qx * gRq[6] + qy * gRq[7]);
-        double qdot = G.qn[0] * gn[0] + G.qn[1] * gn[1] + G.qn[2] * gn[2] + G.qn[3] * gn[3];
+        real qdot = G.qn[0] * gn[0] + G.qn[1] * gn[1] + G.qn[2] * gn[2] + G.qn[3] * gn[3];
         for (int i = 0; i < 4; i++) gq[i] = (gn[i] - G.qn[i] * qdot) / G.qnorm;
 
         /* T = J W: dL/dJ = gT W^T (only the 4 non-zero entries), dL/dW = J^T gT */
-        double gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+        real gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
         for (int k = 0; k < 3; k++) {
             gJ00 += gT[k] * R[k];
             gJ02 += gT[k] * R[6 + k];
             gJ11 += gT[3 + k] * R[3 + k];
             gJ12 += gT[3 + k] * R[6 + k];
         }
-        double gW[9];
+        real gW[9];
         for (int r = 0; r < 3; r++)
             for (int k = 0; k < 3; k++)
                 gW[r * 3 + k] = G.J[0 * 3 + r] * gT[0 * 3 + k] + G.J[1 * 3 + r] * gT[1 * 3 + k];
 
         /* camera-space mean: through mu', J and the depth output */
-        double gmc[3] = { 0, 0, 0 };
+        real gmc[3] = { 0, 0, 0 };
         gmc[0] += d2[0] * fx / z;
         gmc[1] += d2[1] * fy / z;
         gmc[2] += -d2[0] * fx * x / (z * z) - d2[1] * fy * y / (z * z);
         gmc[2] += d2[9];
         gmc[2] += gJ00 * (-fx / (z * z)) + gJ11 * (-fy / (z * z));
         if (!G.clx) { gmc[0] += gJ02 * (-fx / (z * z)); gmc[2] += gJ02 * (2 * fx * x / (z * z * z)); }
-        else { double lim = G.J[2] * z / -fx; gmc[2] += gJ02 * (fx * lim / (z * z)); }
+        else { real lim = G.J[2] * z / -fx; gmc[2] += gJ02 * (fx * lim / (z * z)); }
         if (!G.cly) { gmc[1] += gJ12 * (-fy / (z * z)); gmc[2] += gJ12 * (2 * fy * y / (z * z * z)); }
-        else { double lim = G.J[5] * z / -fy; gmc[2] += gJ12 * (fy * lim / (z * z)); }
+        else { real lim = G.J[5] * z / -fy; gmc[2] += gJ12 * (fy * lim / (z * z)); }
 
         /* world mean: mu-hat = W mu + t */
         for (int j = 0; j < 3; j++) gm[j] += R[0 * 3 + j] * gmc[0] + R[1 * 3 + j] * gmc[1] + R[2 * 3 + j] * gmc[2];
 
         /* pose: d mu-hat = rho + phi x mu-hat ; dW = phi^ W                    */
-        g_pose[0] += gmc[0]; g_pose[1] += gmc[1]; g_pose[2] += gmc[2];
-        g_pose[3] += y * gmc[2] - z * gmc[1];
-        g_pose[4] += z * gmc[0] - x * gmc[2];
-        g_pose[5] += x * gmc[1] - y * gmc[0];
-        double Pm[9];   /* W gW^T */
+        gp[0] += gmc[0]; gp[1] += gmc[1]; gp[2] += gmc[2];
+        gp[3] += y * gmc[2] - z * gmc[1];
+        gp[4] += z * gmc[0] - x * gmc[2];
+        gp[5] += x * gmc[1] - y * gmc[0];
+        real Pm[9];   /* W gW^T */
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) {
-                double s = 0;
+                real s = 0;
                 for (int k = 0; k < 3; k++) s += R[i * 3 + k] * gW[j * 3 + k];
                 Pm[i * 3 + j] = s;
             }
-        g_pose[3] += Pm[1 * 3 + 2] - Pm[2 * 3 + 1];
-        g_pose[4] += Pm[2 * 3 + 0] - Pm[0 * 3 + 2];
-        g_pose[5] += Pm[0 * 3 + 1] - Pm[1 * 3 + 0];
+        gp[3] += Pm[1 * 3 + 2] - Pm[2 * 3 + 1];
+        gp[4] += Pm[2 * 3 + 0] - Pm[0 * 3 + 2];
+        gp[5] += Pm[0 * 3 + 1] - Pm[1 * 3 + 0];
     }
+    }
+    for (int th = 0; th < nth; th++)
+        for (int i = 0; i < 6; i++) g_pose[i] += pose_part[6 * th + i];
+    free(pose_part);
 }
 
 /* ------------------------------------------------------------------------- */
 /* Adam (bias-corrected), one parameter array.  Only entries with mask != 0  */
 /* (or all, if mask is NULL) are updated; the rest keep p, m and v.          */
 /* ------------------------------------------------------------------------- */
-void orc_adam(int64_t count, int stride, const uint8_t* mask, double* p, double* m, double* v,
-              const double* g, double lr, double b1, double b2, double eps, int64_t step)
+void orc_adam(int64_t count, int stride, const uint8_t* mask, real* p, real* m, real* v,
+              const real* g, real lr, real b1, real b2, real eps, int64_t step)
 {
-    double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
+    real bc1 = 1.0 - pow(b1, (real)step), bc2 = 1.0 - pow(b2, (real)step);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < count; i++) {
         if (mask && !mask[i / stride]) continue;
         m[i] = b1 * m[i] + (1.0 - b1) * g[i];
         v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
-        double mh = m[i] / bc1, vh = v[i] / bc2;
+        real mh = m[i] / bc1, vh = v[i] / bc2;
         p[i] -= lr * mh / (sqrt(vh) + eps);
     }
 }
@@ -1052,6 +1152,7 @@ void orc_sky(int64_t ns, double radius, uint64_t seed, float* xyz, double* nn_di
         xyz[3 * i + 1] = (float)(radius * rr * sin(ph));
         xyz[3 * i + 2] = (float)(radius * zc);
     }
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < ns; i++) {
         double best = INFINITY;
         for (int64_t j = 0; j < ns; j++) {

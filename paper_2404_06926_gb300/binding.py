@@ -59,7 +59,9 @@ class Stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("sum_contrib", C.c_int64), ("pixels", C.c_int64), ("steps", C.c_int64),
                 ("phase_ms", C.c_double * NUM_PHASES), ("phase_calls", C.c_int64 * NUM_PHASES),
-                ("graph_captures", C.c_int64), ("graph_replays", C.c_int64), ("graph_reruns", C.c_int64)]
+                ("graph_captures", C.c_int64), ("graph_replays", C.c_int64), ("graph_reruns", C.c_int64),
+                ("timed_steps", C.c_int64), ("timed_views", C.c_int64), ("timed_visible", C.c_int64),
+                ("timed_instances", C.c_int64), ("timed_contrib", C.c_int64), ("timed_pixels", C.c_int64)]
 
 
 class ExecConfig(C.Structure):
@@ -102,7 +104,7 @@ def lib():
             "gl_map_get_exposure": ([P, i64, P], i32),
             "gl_ctx_create": ([P, P], i32),
             "gl_ctx_destroy": ([P], i32),
-            "gl_rasterize_forward": ([P, P, P, P, i32, P, P, P], i32),
+            "gl_rasterize_forward": ([P, P, P, P, P, i32, P, P, P], i32),
             "gl_rasterize_backward": ([P, P, P, P, P, P, P], i32),
             "gl_photometric_loss": ([P, P, P, P, i32, i32, f32, P, P, P], i32),
             "gl_ctx_get_preprocess": ([P, P, P, P, P, P, P, P], i32),
@@ -224,7 +226,10 @@ class Ctx:
         except Exception:
             pass
 
-    def forward(self, params: dict, cam: dict, tile: int = 16, depth: bool = True, opacity: bool = True):
+    def forward(self, params: dict, cam: dict, tile: int = 16, depth: bool = True, opacity: bool = True,
+                twist=None):
+        """Render from the pose exp(twist^) T_cw (twist: 6 numbers (rho, phi)
+        or None for T_cw itself)."""
         import torch
         H, W = int(cam["height"]), int(cam["width"])
         dev = params["means"].device
@@ -233,7 +238,10 @@ class Ctx:
         opa = torch.empty((H, W), dtype=torch.float32, device=dev) if opacity else None
         g = gaussians(params)
         K, P = intrinsics(cam), pose(cam)
-        check(lib().gl_rasterize_forward(self._h, C.byref(g), C.byref(P), C.byref(K), int(tile),
+        tw = None
+        if twist is not None:
+            tw = (C.c_float * 6)(*[float(x) for x in twist])
+        check(lib().gl_rasterize_forward(self._h, C.byref(g), C.byref(P), tw, C.byref(K), int(tile),
                                          _ptr(rgb), _ptr(dep), _ptr(opa)))
         return rgb, dep, opa
 
@@ -480,7 +488,8 @@ class Map:
         check(lib().gl_map_get_stats(self._h, C.byref(st)))
         out = {k: getattr(st, k) for k in ("n_gaussians", "n_visible", "n_instances", "sum_contrib",
                                            "pixels", "steps", "graph_captures", "graph_replays",
-                                           "graph_reruns")}
+                                           "graph_reruns", "timed_steps", "timed_views", "timed_visible",
+                                           "timed_instances", "timed_contrib", "timed_pixels")}
         out["phases"] = {lib().gl_phase_name(i).decode(): (st.phase_ms[i], st.phase_calls[i])
                          for i in range(NUM_PHASES)}
         return out

@@ -20,7 +20,6 @@ namespace gl {
 namespace {
 
 constexpr int kPreThreads = 256;
-constexpr int kSortMaxBlocks = 4 * 152;                // 4 CTAs per SM on 152 SMs
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kPreThreads * kScanItems;   // 1024 Gaussians per scan block
 
@@ -622,6 +621,27 @@ __global__ void k_view_counts(const int* __restrict__ radius, int64_t n, const u
     }
 }
 
+__global__ void k_accumulate_counts(const int* __restrict__ radius, int64_t n, const uint32_t* __restrict__ ncon,
+                                    int64_t P, const uint64_t* __restrict__ ctl, unsigned long long* acc)
+{
+    unsigned long long vis = 0, sc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) vis += radius[i] > 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += stride) sc += ncon[i];
+    for (int off = 16; off > 0; off >>= 1) {
+        vis += __shfl_xor_sync(kFull, vis, off);
+        sc += __shfl_xor_sync(kFull, sc, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, vis);
+        atomicAdd(acc + 2, sc);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(acc + 1, (unsigned long long)ctl[0]);
+        atomicAdd(acc + 3, (unsigned long long)P);
+    }
+}
+
 int ceil_log2(int64_t x)
 {
     int b = 0;
@@ -667,7 +687,7 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
     const int tile_keys = kOsTile;
     const int64_t tiles = std::max<int64_t>(1, (n_max + tile_keys - 1) / tile_keys);
     const int hblocks = (int)std::min<int64_t>(
-        kSortMaxBlocks, std::max<int64_t>(1, (n_max + kOsThreads * kOsHistKeys - 1) / (kOsThreads * kOsHistKeys)));
+        4 * (int64_t)sm_count(), std::max<int64_t>(1, (n_max + kOsThreads * kOsHistKeys - 1) / (kOsThreads * kOsHistKeys)));
     k_os_hist<<<hblocks, kOsThreads, 0, s>>>(k0, n_dev, passes, tile_keys, tiles_max, sc);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     unsigned long long* err = reinterpret_cast<unsigned long long*>(ctl + 8);
@@ -734,6 +754,17 @@ gl_status sort_wait_status(View& v, cudaStream_t s)
     return GL_ERR_TIMEOUT;
 }
 
+gl_status accumulate_view_counts(const View& v, uint64_t* acc, cudaStream_t s)
+{
+    if (v.n * v.V == 0 && v.P == 0) return GL_OK;
+    k_accumulate_counts<<<4 * sm_count(), 256, 0, s>>>(v.radius.as<int>(), v.n * v.V, v.ncon.as<uint32_t>(),
+                                                      v.ncon.p ? v.P : 0, v.count.as<uint64_t>(),
+                                                      reinterpret_cast<unsigned long long*>(acc));
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    return GL_OK;
+}
+
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s)
 {
     *n_visible = 0;
@@ -742,7 +773,7 @@ gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, c
     if (v.n == 0 && P == 0) return GL_OK;
     unsigned long long* d = reinterpret_cast<unsigned long long*>(v.count.as<uint64_t>() + 4);
     GL_CUDA_TRY(cudaMemsetAsync(d, 0, 16, s));
-    k_view_counts<<<4 * 152, 256, 0, s>>>(v.radius.as<int>(), v.n * v.V, v.ncon.as<uint32_t>(), v.ncon.p ? P : 0, d);
+    k_view_counts<<<4 * sm_count(), 256, 0, s>>>(v.radius.as<int>(), v.n * v.V, v.ncon.as<uint32_t>(), v.ncon.p ? P : 0, d);
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     unsigned long long h[2];
@@ -757,7 +788,7 @@ gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* o
                             float* depth, cudaStream_t s)
 {
     if (v.n == 0) return GL_OK;
-    int blocks = (int)std::min<int64_t>(4 * 152, (v.n + 255) / 256);
+    int blocks = (int)std::min<int64_t>(4 * (int64_t)sm_count(), (v.n + 255) / 256);
     k_export_pre<<<blocks, 256, 0, s>>>(v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.n,
                                         mean2d, conic, opacity, rgb, depth);
     count_launches(1);
@@ -768,7 +799,7 @@ gl_status export_preprocess(const View& v, float* mean2d, float* conic, float* o
 gl_status export_instances(const View& v, uint64_t* keys, uint32_t* vals, cudaStream_t s)
 {
     if (v.I == 0) return GL_OK;
-    int blocks = (int)std::min<int64_t>(4 * 152, (v.I + 255) / 256);
+    int blocks = (int)std::min<int64_t>(4 * (int64_t)sm_count(), (v.I + 255) / 256);
     k_export<<<blocks, 256, 0, s>>>(v.sorted_tile, v.sorted_inst, v.iowner.as<uint32_t>(),
                                     v.rec1.as<float4>(), v.I, keys, vals);
     count_launches(1);
@@ -946,7 +977,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     v.sorted_inst = sv;
     {
         PhaseScope ps(v.prof, PH_RANGES, s);
-        int rb = (int)std::min<int64_t>(4 * 152, (nmax + 255) / 256);
+        int rb = (int)std::min<int64_t>(4 * (int64_t)sm_count(), (nmax + 255) / 256);
         k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
         count_launches(1);
         GL_CUDA_TRY(cudaGetLastError());

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -35,6 +36,45 @@ const char* kPhaseNames[PH_COUNT] = {"preprocess", "depth_sort", "scan_duplicate
 }
 
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_dev_mu;
+int g_sms[kMaxDev] = {};
+struct SmemLimit { const void* fn; int dev; int bytes; };
+std::vector<SmemLimit> g_smem;
+}
+
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 152;
+    }
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        g_sms[dev] = n;
+    }
+    return g_sms[dev];
+}
+
+gl_status ensure_smem_limit(const void* fn, int bytes)
+{
+    int dev = 0;
+    GL_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    for (const SmemLimit& e : g_smem)
+        if (e.fn == fn && e.dev == dev && e.bytes >= bytes) return GL_OK;
+    GL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    g_smem.push_back({fn, dev, bytes});
+    return GL_OK;
+}
 
 cudaEvent_t Prof::begin(cudaStream_t s)
 {
@@ -240,6 +280,103 @@ gl_status make_cam(const gl_pose* pose, const gl_intrinsics* K, Cam& cam)
     return GL_OK;
 }
 
+// Twists xi = (rho, phi) in R^6, translation part first.  se3_exp maps a
+// twist to a rigid motion (R, t); the left Jacobian J_l(xi) relates a change
+// of the twist to a left perturbation of the motion it gives:
+// exp((xi + d)^) = exp((J_l(xi) d)^) exp(xi^) to first order.  Closed forms
+// of SO(3)/SE(3) (Barfoot, "State Estimation for Robotics", 2017, Sec. 7.1),
+// with Taylor series of the coefficients below 0.1 rad, in double.
+void so3_hat(const double w[3], double W[9])
+{
+    W[0] = 0.0;   W[1] = -w[2]; W[2] = w[1];
+    W[3] = w[2];  W[4] = 0.0;   W[5] = -w[0];
+    W[6] = -w[1]; W[7] = w[0];  W[8] = 0.0;
+}
+
+void mat3_mul(const double A[9], const double B[9], double C[9])
+{
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            C[i * 3 + j] = A[i * 3] * B[j] + A[i * 3 + 1] * B[3 + j] + A[i * 3 + 2] * B[6 + j];
+}
+
+// Coefficients of the rotation angle th: sin(th)/th, (1 - cos th)/th^2,
+// (th - sin th)/th^3, (th^2 + 2 cos th - 2)/(2 th^4), (2 th - 3 sin th + th cos th)/(2 th^5).
+void so3_coefs(double th, double c[5])
+{
+    const double t2 = th * th;
+    if (th < 0.1) {
+        c[0] = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+        c[1] = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        c[2] = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+        c[3] = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
+        c[4] = 1.0 / 120.0 - t2 / 2520.0 + t2 * t2 / 120960.0;
+        return;
+    }
+    const double s = std::sin(th), co = std::cos(th);
+    c[0] = s / th;
+    c[1] = (1.0 - co) / t2;
+    c[2] = (th - s) / (t2 * th);
+    c[3] = (t2 + 2.0 * co - 2.0) / (2.0 * t2 * t2);
+    c[4] = (2.0 * th - 3.0 * s + th * co) / (2.0 * t2 * t2 * th);
+}
+
+// SO(3) left Jacobian J(phi) = I + c1 phi^ + c2 phi^2.
+void so3_left_jacobian(const double phi[3], const double c[5], double J[9])
+{
+    double P[9], P2[9];
+    so3_hat(phi, P);
+    mat3_mul(P, P, P2);
+    for (int i = 0; i < 9; i++) J[i] = (i % 4 == 0 ? 1.0 : 0.0) + c[1] * P[i] + c[2] * P2[i];
+}
+
+void se3_exp(const double xi[6], double R[9], double t[3])
+{
+    const double* phi = xi + 3;
+    const double th = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    double c[5], P[9], P2[9], J[9];
+    so3_coefs(th, c);
+    so3_hat(phi, P);
+    mat3_mul(P, P, P2);
+    for (int i = 0; i < 9; i++) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + c[0] * P[i] + c[1] * P2[i];
+    so3_left_jacobian(phi, c, J);
+    for (int i = 0; i < 3; i++) t[i] = J[i * 3] * xi[0] + J[i * 3 + 1] * xi[1] + J[i * 3 + 2] * xi[2];
+}
+
+// J_l(xi) (6 x 6, row-major) = [[J, Q], [0, J]], Q(rho, phi) from Barfoot's
+// series summed in closed form.
+void se3_left_jacobian(const double xi[6], double Jl[36])
+{
+    const double* rho = xi;
+    const double* phi = xi + 3;
+    const double th = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    double c[5], J[9], P[9], Rh[9];
+    so3_coefs(th, c);
+    so3_left_jacobian(phi, c, J);
+    so3_hat(phi, P);
+    so3_hat(rho, Rh);
+    double PR[9], RP[9], PRP[9], PP[9], PPR[9], RPP[9], PRPP[9], PPRP[9];
+    mat3_mul(P, Rh, PR);
+    mat3_mul(Rh, P, RP);
+    mat3_mul(PR, P, PRP);
+    mat3_mul(P, P, PP);
+    mat3_mul(PP, Rh, PPR);
+    mat3_mul(RP, P, RPP);
+    mat3_mul(PRP, P, PRPP);
+    mat3_mul(P, PRP, PPRP);
+    double Q[9];
+    for (int i = 0; i < 9; i++)
+        Q[i] = 0.5 * Rh[i] + c[2] * (PR[i] + RP[i] + PRP[i]) + c[3] * (PPR[i] + RPP[i] - 3.0 * PRP[i]) +
+               c[4] * (PRPP[i] + PPRP[i]);
+    for (int i = 0; i < 36; i++) Jl[i] = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            Jl[i * 6 + j] = J[i * 3 + j];
+            Jl[i * 6 + 3 + j] = Q[i * 3 + j];
+            Jl[(3 + i) * 6 + 3 + j] = J[i * 3 + j];
+        }
+}
+
 bool is_device_ptr(const void* p)
 {
     if (!p) return false;
@@ -299,7 +436,7 @@ using namespace gl;
 // ===========================================================================
 extern "C" const char* gl_last_error(void) { return g_err.c_str(); }
 
-extern "C" int32_t gl_version(void) { return 101; }
+extern "C" int32_t gl_version(void) { return 102; }
 
 extern "C" gl_status gl_config_default(gl_config* c)
 {
@@ -368,8 +505,8 @@ extern "C" gl_status gl_ctx_destroy(gl_ctx* ctx)
 }
 
 extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, const gl_pose* pose,
-                                          const gl_intrinsics* K, int32_t tile_size, float* out_rgb,
-                                          float* out_depth, float* out_opacity)
+                                          const float* twist6, const gl_intrinsics* K, int32_t tile_size,
+                                          float* out_rgb, float* out_depth, float* out_opacity)
 {
     if (!ctx || !out_rgb) { set_error("null ctx or out_rgb"); return GL_ERR_INVALID; }
     GL_TRY(check_gauss(g, true));
@@ -378,6 +515,25 @@ extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, co
     GL_TRY(make_cam(pose, K, cam));
     gl_ctx_impl& c = ctx->impl;
     c.has_forward = 0;
+    // the pose rendered: exp(xi^) T_cw (T_cw itself when twist6 is null)
+    double xi[6] = {0, 0, 0, 0, 0, 0};
+    if (twist6) {
+        if (!finite_all(twist6, 6)) { set_error("twist contains NaN or Inf"); return GL_ERR_INVALID; }
+        for (int i = 0; i < 6; i++) xi[i] = twist6[i];
+    }
+    double Rd[9], td[3], Jl[36];
+    se3_exp(xi, Rd, td);
+    se3_left_jacobian(xi, Jl);
+    double R0[9], R1[9];
+    for (int i = 0; i < 9; i++) R0[i] = pose->R_cw[i];
+    mat3_mul(Rd, R0, R1);
+    for (int i = 0; i < 3; i++) {
+        cam.t[i] = (float)(Rd[i * 3] * pose->t_cw[0] + Rd[i * 3 + 1] * pose->t_cw[1] + Rd[i * 3 + 2] * pose->t_cw[2] +
+                           td[i]);
+        for (int j = 0; j < 3; j++) cam.R[i * 3 + j] = (float)R1[i * 3 + j];
+    }
+    if (!finite_all(cam.R, 9) || !finite_all(cam.t, 3)) { set_error("twisted pose is not finite"); return GL_ERR_INVALID; }
+    for (int i = 0; i < 36; i++) c.pose_jac[i] = (float)Jl[i];
     c.view.det = c.exec.deterministic != 0;
     c.view.nb = (c.exec.batch_depth == 64 && !c.view.det) ? 2 : 1;
     c.view.pd = std::min(c.exec.pixels_per_lane, tile_size / 4);
@@ -414,7 +570,7 @@ extern "C" gl_status gl_rasterize_backward(gl_ctx* ctx, const gl_gaussians* g, c
     GL_TRY(params_backward(c.view, params_of(g), mut_of(grad), pp, npart, c.stream));
     if (grad_pose6) {
         if (g->n == 0) GL_CUDA_TRY(cudaMemsetAsync(grad_pose6, 0, 24, c.stream));
-        else GL_TRY(pose_reduce(pp, npart, grad_pose6, c.stream));
+        else GL_TRY(pose_reduce(pp, npart, c.pose_jac, grad_pose6, c.stream));
     }
     return GL_OK;
 }
@@ -517,6 +673,10 @@ struct gl_map {
     std::vector<StepGraph> graphs;       // most recently used last, at most kMaxGraphs
     static constexpr size_t kMaxGraphs = 8;
     int64_t graph_captures = 0, graph_replays = 0, graph_reruns = 0;
+    // counts of the steps taken while the phase timers are on (device u64:
+    // visible pairs, instances, contributor sum, pixels), and their views
+    DevBuf timed_counts;
+    int64_t timed_steps = 0, timed_views = 0;
 
     size_t row_floats(int which) const
     {
@@ -1079,6 +1239,12 @@ gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
         m->graph_reruns++;
     }
     GL_TRY(enqueue_step(m, sp, m->stream, false));
+    if (m->prof.on) {
+        GL_TRY(m->timed_counts.reserve(4 * sizeof(uint64_t)));
+        GL_TRY(accumulate_view_counts(v, m->timed_counts.as<uint64_t>(), m->stream));
+        m->timed_steps++;
+        m->timed_views += sp.V;
+    }
     GL_TRY(read_loss(m, sp.V, true, out_loss));
     GL_CUDA_TRY(cudaStreamSynchronize(m->stream));
     GL_TRY(sort_wait_status(v, m->stream));
@@ -1159,6 +1325,8 @@ extern "C" gl_status gl_map_set_timing(gl_map* m, int32_t enable)
     m->prof.reset();
     m->prof.on = enable != 0;
     if (m->prof.on) m->prof.prefill(8192);
+    m->timed_steps = m->timed_views = 0;
+    if (m->timed_counts.p) GL_CUDA_TRY(cudaMemset(m->timed_counts.p, 0, 4 * sizeof(uint64_t)));
     return GL_OK;
 }
 
@@ -1182,6 +1350,16 @@ extern "C" gl_status gl_map_get_stats(gl_map* m, gl_stats* out)
     out->graph_reruns = m->graph_reruns;
     out->pixels = (int64_t)v.W * v.H;
     GL_TRY(view_counts(v, &out->n_visible, &out->sum_contrib, m->stream));
+    out->timed_steps = m->timed_steps;
+    out->timed_views = m->timed_views;
+    if (m->timed_counts.p && m->timed_steps) {
+        uint64_t h[4];
+        GL_CUDA_TRY(cudaMemcpy(h, m->timed_counts.p, sizeof(h), cudaMemcpyDeviceToHost));
+        out->timed_visible = (int64_t)h[0];
+        out->timed_instances = (int64_t)h[1];
+        out->timed_contrib = (int64_t)h[2];
+        out->timed_pixels = (int64_t)h[3];
+    }
     for (int i = 0; i < PH_COUNT && i < GL_NUM_PHASES; i++) {
         out->phase_ms[i] = m->prof.ms[i];
         out->phase_calls[i] = m->prof.calls[i];

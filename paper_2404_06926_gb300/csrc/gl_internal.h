@@ -34,6 +34,13 @@ void set_error(const std::string& msg);
 // Kernel launch accounting (process-wide).
 void count_launches(int64_t n);
 
+// Streaming multiprocessors of the current device (looked up once per device).
+int sm_count();
+
+// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device, once per (kernel, device); safe from several host threads.
+gl_status ensure_smem_limit(const void* fn, int bytes);
+
 // Phases timed by the optional CUDA-event profiler.
 enum Phase {
     PH_PREPROCESS = 0, PH_DEPTH_SORT, PH_SCAN_DUP, PH_TILE_SORT, PH_RANGES, PH_RASTER_FWD, PH_LOSS,
@@ -202,6 +209,7 @@ struct gl_ctx_impl {
     gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1};
     DevBuf pose_part;   // per-block pose partials
     DevBuf loss_part;   // per-block loss partials
+    float pose_jac[36] = {};   // J_l of the last forward's twist (row-major 6 x 6)
     int has_forward = 0;
     int deg = 0;
 };
@@ -257,7 +265,10 @@ gl_status params_backward(View& v, const GParams& p, GMut grad, float* pose_part
 // mode 1: fused Adam update of `upd` (same storage as p) with moments.
 gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cudaStream_t s);
 int pose_partials_needed(int64_t n);
-gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s);
+// Sum the per-block pose partials (the gradient g of a left perturbation of
+// the rendered pose) and write J^T g, J the 6 x 6 row-major left Jacobian of
+// the forward's twist (the identity for a zero twist).
+gl_status pose_reduce(const float* part, int npart, const float jac[36], float* out6, cudaStream_t s);
 
 // Photometric loss (Eq. 9) of one view given by value (no descriptor upload):
 // writes dL/drgb and per-tile partials; then the final reduction writes loss
@@ -294,6 +305,11 @@ gl_status sort_wait_status(View& v, cudaStream_t s);
 // Runs one sort pass whose look-back can never complete (see
 // gl_selftest_bounded_wait); *expired = 1 if it gave up and raised its flag.
 gl_status sort_wait_selftest(int32_t* expired);
+
+// Add the counts of the step just enqueued on `v` to acc[0..4) on the device
+// (no synchronisation): visible (view, Gaussian) pairs, instances,
+// contributor sum over the pixels, pixels.
+gl_status accumulate_view_counts(const View& v, uint64_t* acc, cudaStream_t s);
 
 // Visible Gaussians and the summed contributor count of the last view.
 gl_status view_counts(const View& v, int64_t* n_visible, int64_t* sum_contrib, cudaStream_t s);

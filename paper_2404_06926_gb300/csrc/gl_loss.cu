@@ -349,13 +349,7 @@ int loss_partials_needed(int W, int H)
 namespace {
 gl_status loss_attr()
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        GL_CUDA_TRY(cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kSmemFloats * sizeof(float))));
-        attr_set = true;
-    }
-    return GL_OK;
+    return ensure_smem_limit(reinterpret_cast<const void*>(&k_loss), (int)(kSmemFloats * sizeof(float)));
 }
 }  // namespace
 
@@ -391,7 +385,7 @@ gl_status photometric_loss_views(const View& v, const float* rgb, float lambda, 
 
 gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_t P, cudaStream_t s)
 {
-    int blocks = (int)std::min<int64_t>(8 * 152, (P + 255) / 256);
+    int blocks = (int)std::min<int64_t>(8 * (int64_t)sm_count(), (P + 255) / 256);
     if (blocks < 1) blocks = 1;
     k_apply_exposure<<<blocks, 256, 0, s>>>(src, dst, P, E[0], E[1], E[2], E[3], E[4], E[5], E[6], E[7],
                                             E[8], E[9], E[10], E[11]);

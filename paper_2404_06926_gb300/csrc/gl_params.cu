@@ -487,15 +487,27 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
     }
 }
 
-__global__ void k_pose_reduce(const float* __restrict__ part, int npart, float* __restrict__ out6)
+struct Jac6 {
+    float m[36];
+};
+
+__global__ void k_pose_reduce(const float* __restrict__ part, int npart, Jac6 J, float* __restrict__ out6)
 {
-    // one warp per component, fixed summation order
+    // one warp per component, fixed summation order; then J^T g
+    __shared__ double gsum[6];
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= 6) return;
-    double acc = 0.0;
-    for (int i = lane; i < npart; i += 32) acc += part[i * 6 + k];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-    if (lane == 0) out6[k] = (float)acc;
+    if (k < 6) {
+        double acc = 0.0;
+        for (int i = lane; i < npart; i += 32) acc += part[i * 6 + k];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+        if (lane == 0) gsum[k] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double o = 0.0;
+        for (int i = 0; i < 6; i++) o += (double)J.m[i * 6 + threadIdx.x] * gsum[i];
+        out6[threadIdx.x] = (float)o;
+    }
 }
 
 template <int MODE>
@@ -507,9 +519,8 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
     count_launches(1);
 #define GL_PB(D_)                                                                                         \
     {                                                                                                     \
-        static const cudaError_t attr = cudaFuncSetAttribute(                                             \
-            k_params_bwd<D_, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ParamsSmem<D_>::bytes); \
-        GL_CUDA_TRY(attr);                                                                                \
+        GL_TRY(ensure_smem_limit(reinterpret_cast<const void*>(&k_params_bwd<D_, MODE>),                 \
+                                 (int)ParamsSmem<D_>::bytes));                                            \
         k_params_bwd<D_, MODE><<<grid, kThreads, ParamsSmem<D_>::bytes, s>>>(                             \
             p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), o, a, pose_part);                  \
     }
@@ -541,9 +552,11 @@ gl_status params_adam(View& v, const GParams& p, GMut upd, const AdamArgs& a, cu
     return launch<1>(v, p, upd, a, nullptr, s);
 }
 
-gl_status pose_reduce(const float* part, int npart, float* out6, cudaStream_t s)
+gl_status pose_reduce(const float* part, int npart, const float jac[36], float* out6, cudaStream_t s)
 {
-    k_pose_reduce<<<1, 192, 0, s>>>(part, npart, out6);
+    Jac6 J;
+    for (int i = 0; i < 36; i++) J.m[i] = jac[i];
+    k_pose_reduce<<<1, 192, 0, s>>>(part, npart, J, out6);
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;

@@ -914,7 +914,7 @@ gl_status permute_records(View& v, int64_t nmax, cudaStream_t s)
     GL_TRY(v.srec2.reserve(16 * I));
     GL_TRY(v.srec3.reserve(16 * I));
     GL_TRY(v.sgid.reserve(4 * I));
-    const int blocks = (int)std::min<size_t>(8 * 152, (I + 255) / 256);
+    const int blocks = (int)std::min<size_t>(8 * (size_t)sm_count(), (I + 255) / 256);
     k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.sorted_inst, v.sorted_tile, v.d_desc(), v.V, v.Ts,
                                      v.iowner.as<uint32_t>(),
                                      v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(),
@@ -994,7 +994,7 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     else bwd_dispatch<false>(v.nb, v.pd, det, A, G, units, v.persistent, s);
     count_launches(1);
     if (det) {
-        const int blocks = (int)std::min<size_t>(8 * 152, (pairs + 255) / 256);
+        const int blocks = (int)std::min<size_t>(8 * (size_t)sm_count(), (pairs + 255) / 256);
         k_part_reduce<<<std::max(blocks, 1), 256, 0, s>>>(v.gpart.as<float>(), v.touched.as<uint32_t>(),
                                                           v.dup_off.as<uint32_t>(), nblk, (int64_t)pairs,
                                                           v.count.as<uint64_t>(), (uint64_t)cap, v.g2d.as<float>());

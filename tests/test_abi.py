@@ -47,7 +47,7 @@ def test_calls_without_gpu_fail_cleanly(libpath):
     """No compute call: only calls that validate arguments before touching CUDA."""
     from paper_2404_06926_gb300 import binding
     L = binding.lib()
-    assert L.gl_version() == 101
+    assert L.gl_version() == 102
     cfg = binding.default_config()
     assert cfg.sh_degree == 3 and cfg.tile_size == 16 and abs(cfg.lambda_dssim - 0.2) < 1e-7
     assert abs(cfg.tau - 0.99) < 1e-7 and cfg.n_sky == 100000

@@ -8,11 +8,17 @@ within a relative 2e-5 (alpha) / 1e-4 (transmittance) of its threshold in the
 oracle are "ambiguous": float32 may legitimately decide them the other way, so
 they are excluded from the element-wise comparison and must stay rare.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2404_06926_gb300 import scenes
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import _parity as PT  # noqa: E402
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -157,8 +163,17 @@ def test_gradient_parity(scene, extra):
         assert np.all(a[~vis] == 0), name
         med, p99 = rel_stats(a[vis], ref[vis])
         assert med < 1e-3 and p99 < 1e-2, (name, med, p99)
-    pose = pose.cpu().numpy()
-    assert np.linalg.norm(pose - g["pose"]) <= 1e-3 * np.linalg.norm(g["pose"])
+    assert_pose_matches(pose.cpu().numpy(), g["pose"])
+
+
+def assert_pose_matches(gpu, ref):
+    """The six pose components one by one: relative error with the gradient
+    bars' floor of 1e-4 of the largest component; median 1e-3, each 1e-2."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    floor = 1e-4 * max(np.abs(ref).max(), 1e-30)
+    rel = np.abs(gpu - ref) / np.maximum(np.abs(ref), floor)
+    assert np.median(rel) < 1e-3 and rel.max() < 1e-2, (gpu, ref, rel)
 
 
 def test_optimize_step_parity():
@@ -180,29 +195,20 @@ def test_optimize_step_parity():
     assert abs(loss - r["loss"]["loss"]) <= 2e-5 * r["loss"]["loss"]
     got = m.get_params()
     vis = r["pre"]["radius"] > 0
-    lr = oracle.DEFAULT_LR
-    for name, key in (("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"),
-                      ("logits", "logits")):
-        d_gpu = got[name].astype(np.float64) - sc["params"][name]
-        d_or = st["p"][name] - sc["params"][name]
-        assert np.all(d_gpu[~vis] == 0), name
-        # first Adam step moves each entry by ~lr * sign(g): compare where the
-        # oracle gradient is clearly non-zero
-        gref = r["grads"][name][vis]
-        clear = np.abs(gref) > 1e-3 * np.sqrt(np.mean(gref ** 2))
-        agree = np.abs(d_gpu[vis] - d_or[vis])[clear] <= 1e-3 * lr[key] + 1e-7
-        assert agree.mean() > 0.99, (name, agree.mean())
+    PT.assert_step_matches(got, sc["params"], st["p"], r["grads"], vis, PT.learning_rates(oracle.DEFAULT_LR))
     E = m.exposure(7)
     assert np.allclose(E, st["p"]["E"], atol=1e-6)
     del E0
 
 
 def _edge_params(n, deg=0, seed=0):
+    """Anisotropic, randomly rotated Gaussians (so that no gradient class is
+    identically zero) in front of the camera."""
     rng = np.random.default_rng(seed)
     K = (deg + 1) ** 2
     return dict(means=rng.normal(0, 1, (n, 3)).astype(np.float32) + np.float32([0, 0, 4]),
-                log_scales=np.full((n, 3), -2.5, np.float32),
-                quats=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+                log_scales=(-2.5 + rng.normal(0, 0.3, (n, 3))).astype(np.float32),
+                quats=rng.normal(0, 1, (n, 4)).astype(np.float32),
                 logits=np.zeros(n, np.float32), sh=rng.normal(0, 0.3, (n, K, 3)).astype(np.float32))
 
 
@@ -216,7 +222,7 @@ def test_edge_cases(case):
         params["means"][:, 2] = -1.0
     if case == "single_big":
         params["means"][:] = [0.0, 0.0, 1.0]
-        params["log_scales"][:] = 0.5
+        params["log_scales"][:] = [0.5, 0.2, -0.1]
     pre, bins, img = oracle.forward(params, cam, 16)
     p = _dev(params) if n else {k: torch.zeros((0,) + v.shape[1:], device="cuda") for k, v in params.items()}
     ctx = _ctx()
@@ -226,9 +232,23 @@ def test_edge_cases(case):
     T, nc = ctx.pixel_state(H, W, "cuda")
     assert np.array_equal(nc.cpu().numpy()[ok], img["n_contrib"][ok])
     assert ctx.num_instances() == bins["I"]
-    dC = torch.full((H, W, 3), 1e-3, device="cuda")
-    gg, pose = ctx.backward(p, dC)
+    dC = np.random.default_rng(5).normal(0, 1e-3, (H, W, 3)).astype(np.float32)
+    gg, pose = ctx.backward(p, torch.from_numpy(dC).cuda())
     assert all(torch.isfinite(v).all() for v in gg.values()) and torch.isfinite(pose).all()
+    g = oracle.backward(params, cam, pre, bins, dC.astype(np.float64))
+    vis = pre["radius"] > 0
+    if case in ("empty", "all_behind"):
+        assert not vis.any()
+        assert all(float(v.abs().max()) == 0.0 for v in gg.values() if v.numel())
+        assert float(pose.abs().max()) == 0.0
+        return
+    assert vis.any()
+    for name in ("means", "log_scales", "quats", "logits", "sh"):
+        a = gg[name].cpu().numpy()
+        assert np.all(a[~vis] == 0), name
+        med, p99 = rel_stats(a[vis], g[name][vis])
+        assert med < 1e-3 and p99 < 1e-2, (case, name, med, p99)
+    assert_pose_matches(pose.cpu().numpy(), g["pose"])
 
 
 def test_invalid_arguments_are_rejected():
@@ -274,15 +294,74 @@ def test_window_step_parity():
     r = oracle.optimize_window(params, st, cams, targets, step=1, Ts=16)
     assert abs(loss - r["loss"]) <= 2e-5 * r["loss"]
     got = m.get_params()
-    vis = r["visible"]
-    lr = oracle.DEFAULT_LR
-    for name in ("means", "log_scales", "quats", "logits"):
-        d_gpu = got[name].astype(np.float64) - params[name]
-        d_or = st["p"][name] - params[name]
-        assert np.all(d_gpu[~vis] == 0), name
-        gref = r["grads"][name][vis]
-        clear = np.abs(gref) > 1e-3 * np.sqrt(np.mean(gref ** 2))
-        agree = np.abs(d_gpu[vis] - d_or[vis])[clear] <= 1e-3 * lr[name] + 1e-7
-        assert agree.mean() > 0.99, (name, agree.mean())
+    PT.assert_step_matches(got, params, st["p"], r["grads"], r["visible"], PT.learning_rates(oracle.DEFAULT_LR))
     for i in range(3):
         assert np.allclose(m.exposure(10 + i), st["p"]["E"][i], atol=1e-6)
+
+
+def _two_sided_scene():
+    """The 5k-Gaussian scene in front of camera A and its mirror image in
+    front of camera B, which looks the opposite way: every Gaussian is in
+    front of one camera and behind the other (culled at z <= 0.2)."""
+    sc = scenes.diff_check()
+    camA = sc["cam"]
+    p = sc["params"]
+    RA, tA = np.asarray(camA["R"], np.float64), np.asarray(camA["t"], np.float64)
+    flip = np.diag([-1.0, 1.0, -1.0])                 # half turn about the camera's y axis
+    RB, tB = flip @ RA, flip @ tA
+    # mirror of each mean: the point with the same coordinates in camera B as the original in A
+    xc = p["means"].astype(np.float64) @ RA.T + tA
+    mB = ((xc - tB) @ RB).astype(np.float32)
+    both = {k: np.concatenate([v, v]) for k, v in p.items()}
+    both["means"] = np.concatenate([p["means"], mB])
+    camB = dict(camA, R=RB, t=tB)
+    rng = np.random.default_rng(41)
+    H, W = camA["height"], camA["width"]
+    tgtA = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    tgtB = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    return both, camA, camB, tgtA, tgtB
+
+
+def test_dense_adam_steps_match_oracle():
+    """Dense Adam ("w/o acc", Sec. III-D 2): every Gaussian takes the Adam
+    step, visible or not.  Step 1 renders view A, step 2 view B, which sees
+    none of A's Gaussians.  After step 2 the Gaussians of A have moved again on
+    their moments alone, and both steps agree with the oracle's dense steps."""
+    from paper_2404_06926_gb300 import binding
+    params, camA, camB, tgtA, tgtB = _two_sided_scene()
+    n = len(params["logits"])
+    cfg = binding.default_config(n_sky=0, sh_degree=3, tile_size=16, capacity_hint=2 * n, sparse_adam=0,
+                                 lr_exposure=0.0)
+    m = binding.Map(cfg)
+    m.set_params(params)
+    lr = dict(oracle.DEFAULT_LR, exposure=0.0)
+    I34 = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
+    st = oracle.new_state(params, I34)
+    l1 = m.optimize_step([(1, camA, tgtA)], want_loss=True)
+    r1 = oracle.optimize_step(params, st, camA, tgtA, I34, step=1, Ts=16, lr=lr, sparse=False)
+    after1 = m.get_params()
+    p1 = {k: st["p"][k].astype(np.float32) for k in PT.GROUPS[:4] + ("sh",)}
+    p1_ref = {k: v.copy() for k, v in st["p"].items()}
+    l2 = m.optimize_step([(2, camB, tgtB)], want_loss=True)
+    r2 = oracle.optimize_step(p1, st, camB, tgtB, I34, step=2, Ts=16, lr=lr, sparse=False)
+    after2 = m.get_params()
+    visA = r1["pre"]["radius"] > 0
+    visB = r2["pre"]["radius"] > 0
+    assert visA.sum() > 1000 and visB.sum() > 1000 and not (visA & visB).any()
+    assert abs(l1 - r1["loss"]["loss"]) <= 2e-5 * r1["loss"]["loss"]
+    assert abs(l2 - r2["loss"]["loss"]) <= 2e-5 * r2["loss"]["loss"]
+    LR = PT.learning_rates(lr)
+    # step 1: A's Gaussians move, B's stay (zero gradient and zero moments)
+    PT.assert_step_matches(after1, params, p1_ref, r1["grads"], visA, LR)
+    # step 2, B's Gaussians: their first driven step
+    agree = PT.step_agreement(after2, after1, st["p"], r2["grads"], visB, LR)
+    assert min(agree.values()) > 0.99, agree
+    # step 2, A's Gaussians: out of view, moved on their moments (dense mode)
+    # by the same amount as the oracle's; compared over both steps from p0
+    for name in PT.GROUPS:
+        d_gpu = PT.group(after2, name)[visA].astype(np.float64) - PT.group(after1, name)[visA]
+        g1 = PT.group(r1["grads"], name)[visA]
+        clear = np.abs(g1) > 1e-3 * np.sqrt(np.mean(g1 ** 2))
+        assert (d_gpu[clear] != 0).mean() > 0.99, name
+    agree = PT.step_agreement(after2, params, st["p"], r1["grads"], visA, {k: 2 * v for k, v in LR.items()})
+    assert min(agree.values()) > 0.99, agree
