@@ -103,7 +103,8 @@ typedef struct {
 /* Gaussian parameters in caller memory, one array per attribute, row-major:
  * means n*3, log_scales n*3, quats n*4 (w,x,y,z), logits n (opacity =
  * sigmoid(logit)), sh n*K*3 with K = (sh_degree+1)^2, coefficient-major and
- * channel-minor (Sec. III-A: position, scale, rotation, opacity, SH). */
+ * channel-minor (Sec. III-A: position, scale, rotation, opacity, SH).  Each
+ * array starts on a 16-byte boundary (GL_ERR_INVALID otherwise). */
 typedef struct {
     int64_t n;
     int32_t sh_degree;
@@ -223,9 +224,18 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *                    Gaussians by separate warps; the transmittance is then
  *                    a product of per-segment products, equal to the
  *                    single running product up to float rounding.
+ *   per_gaussian     1: per-Gaussian backward (Sec. III-D 1): each lane
+ *                    of a warp owns Gaussians of the pixel block's list and
+ *                    sums their gradients in its registers while the
+ *                    pixels' transmittance and blended colour pass from
+ *                    lane to lane; 0: per-pixel backward (lanes own pixels,
+ *                    each Gaussian's sums folded across the warp).  The
+ *                    per-Gaussian backward works on 8 x 4 pixel blocks with
+ *                    32-record batches whatever pixels_per_lane and
+ *                    batch_depth say (those still drive the forward).
  * Apart from deterministic = 1, results differ between runs only by the
  * order of the backward's float atomics.
- * gl_map_create starts with {0, 0, 32, 1, 0, 0, 0, 1}.  Errors: GL_ERR_INVALID. */
+ * gl_map_create starts with {0, 0, 32, 1, 0, 0, 0, 1, 0}.  Errors: GL_ERR_INVALID. */
 typedef struct {
     int32_t use_graphs;
     int32_t persistent;
@@ -235,6 +245,7 @@ typedef struct {
     int32_t deterministic;
     int32_t segment;
     int32_t exact_cull;
+    int32_t per_gaussian;
 } gl_exec_config;
 
 GL_API gl_status gl_map_set_exec(gl_map* map, const gl_exec_config* exec);
@@ -243,9 +254,10 @@ GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
 /* Autotuner: `views` holds n_views / window windows of `window` views each
  * (as gl_optimize_step takes them; several windows make the timing
  * representative of steps over different views).  Coordinate descent from
- * {graphs, persistent, batch depth 32, 1 pixel per lane, segment 1024}: the
- * tile size (8/16/32), the segment length (0/256/512/1024), persistence,
- * the batch depth (32/64) and the pixels per lane (1/2/4) in turn take the
+ * {graphs, persistent, batch depth 32, 1 pixel per lane, segment 1024,
+ * per-pixel backward}: the tile size (8/16/32), the segment length
+ * (0/256/512/1024), persistence, the batch depth (32/64), the pixels per
+ * lane (1/2/4) and the backward (per pixel / per Gaussian) in turn take the
  * value whose `reps` rounds of one step per window are fastest (CUDA
  * events) with the other knobs fixed; deterministic and exact_cull stay as
  * set.  The Gaussians, their Adam moments, the views' exposures and the
@@ -462,8 +474,8 @@ GL_API gl_status gl_ctx_create(void* cuda_stream, gl_ctx** out);
 GL_API gl_status gl_ctx_destroy(gl_ctx* ctx);
 
 /* Raster execution of this context's calls: batch_depth, pixels_per_lane,
- * persistent, deterministic, segment and exact_cull as in gl_exec_config
- * (defaults 32, 1, 0, 0, 0, 1; use_graphs
+ * persistent, deterministic, segment, exact_cull and per_gaussian as in
+ * gl_exec_config (defaults 32, 1, 0, 0, 0, 1, 0; use_graphs
  * and tile_size are ignored: the tile size is each call's argument).  A
  * pixels_per_lane above tile_size / 4 is lowered to it.  Errors:
  * GL_ERR_INVALID. */

@@ -67,7 +67,7 @@ class Stats(C.Structure):
 class ExecConfig(C.Structure):
     _fields_ = [("use_graphs", C.c_int32), ("persistent", C.c_int32), ("batch_depth", C.c_int32),
                 ("pixels_per_lane", C.c_int32), ("tile_size", C.c_int32), ("deterministic", C.c_int32),
-                ("segment", C.c_int32), ("exact_cull", C.c_int32)]
+                ("segment", C.c_int32), ("exact_cull", C.c_int32), ("per_gaussian", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -266,10 +266,11 @@ class Ctx:
         return loss, dC, dE.view(3, 4)
 
     # introspection of the last forward
-    def set_exec(self, batch_depth=32, pixels_per_lane=1, persistent=0, deterministic=0, segment=0, exact_cull=1):
+    def set_exec(self, batch_depth=32, pixels_per_lane=1, persistent=0, deterministic=0, segment=0, exact_cull=1,
+                 per_gaussian=0):
         """Raster execution of this context's calls (see gl_ctx_set_exec)."""
         e = ExecConfig(0, int(persistent), int(batch_depth), int(pixels_per_lane), 0, int(deterministic),
-                       int(segment), int(exact_cull))
+                       int(segment), int(exact_cull), int(per_gaussian))
         check(lib().gl_ctx_set_exec(self._h, C.byref(e)))
 
     def preprocess(self, n: int, device):
@@ -429,13 +430,13 @@ class Map:
         check(lib().gl_map_set_timing(self._h, int(bool(on))))
 
     def set_exec(self, use_graphs=None, persistent=None, batch_depth=None, pixels_per_lane=None,
-                 tile_size=None, deterministic=None, segment=None, exact_cull=None):
+                 tile_size=None, deterministic=None, segment=None, exact_cull=None, per_gaussian=None):
         """Change how steps execute (fields left as None keep their value)."""
         e = ExecConfig()
         check(lib().gl_map_get_exec(self._h, C.byref(e)))
         for k, v in dict(use_graphs=use_graphs, persistent=persistent, batch_depth=batch_depth,
                          pixels_per_lane=pixels_per_lane, tile_size=tile_size, deterministic=deterministic,
-                         segment=segment, exact_cull=exact_cull).items():
+                         segment=segment, exact_cull=exact_cull, per_gaussian=per_gaussian).items():
             if v is not None:
                 setattr(e, k, int(v))
         check(lib().gl_map_set_exec(self._h, C.byref(e)))

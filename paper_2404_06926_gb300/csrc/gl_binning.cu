@@ -748,9 +748,10 @@ gl_status sort_wait_selftest(int32_t* expired)
 gl_status sort_wait_status(View& v, cudaStream_t s)
 {
     if (!v.h_count || v.h_count[8] == 0) return GL_OK;
-    v.h_count[8] = 0;
     GL_CUDA_TRY(cudaMemsetAsync(v.count.as<uint64_t>() + 8, 0, sizeof(uint64_t), s));
-    set_error("radix sort: a look-back wait gave up (result order invalid)");
+    set_error(v.h_count[8] & 2u ? "a bounded device wait gave up (parameter staging; the step's update is invalid)"
+                                : "radix sort: a look-back wait gave up (result order invalid)");
+    v.h_count[8] = 0;
     return GL_ERR_TIMEOUT;
 }
 

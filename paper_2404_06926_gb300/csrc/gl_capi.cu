@@ -404,10 +404,11 @@ gl_status check_gauss(const gl_gaussians* g, bool need_ptrs)
         set_error("null parameter array");
         return GL_ERR_INVALID;
     }
-    if (g->quats && (reinterpret_cast<uintptr_t>(g->quats) & 15u)) {
-        set_error("quats must be 16-byte aligned");
-        return GL_ERR_INVALID;
-    }
+    for (const float* a : {g->means, g->log_scales, g->quats, g->logits, g->sh})
+        if (a && (reinterpret_cast<uintptr_t>(a) & 15u)) {
+            set_error("parameter arrays must be 16-byte aligned");
+            return GL_ERR_INVALID;
+        }
     return GL_OK;
 }
 
@@ -485,7 +486,7 @@ extern "C" gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* e)
     if ((e->batch_depth != 32 && e->batch_depth != 64) || (e->deterministic != 0 && e->deterministic != 1) ||
         (e->pixels_per_lane != 1 && e->pixels_per_lane != 2 && e->pixels_per_lane != 4) ||
         (e->segment != 0 && (e->segment < 64 || e->segment > 65536 || (e->segment & (e->segment - 1)) != 0)) ||
-        (e->exact_cull != 0 && e->exact_cull != 1)) {
+        (e->exact_cull != 0 && e->exact_cull != 1) || (e->per_gaussian != 0 && e->per_gaussian != 1)) {
         set_error("invalid execution config");
         return GL_ERR_INVALID;
     }
@@ -540,6 +541,7 @@ extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, co
     c.view.persistent = c.exec.persistent != 0;
     c.view.seg = c.exec.segment;
     c.view.cull = c.exec.exact_cull != 0;
+    c.view.pg = c.exec.per_gaussian != 0;
     GL_TRY(bin_view(c.view, params_of(g), cam, tile_size, c.stream));
     GL_TRY(raster_forward(c.view, out_rgb, out_depth, out_opacity, c.stream));
     c.has_forward = 1;
@@ -663,7 +665,7 @@ struct gl_map {
     std::unordered_map<int64_t, std::unique_ptr<Keyframe>> kfs;
     Prof prof;
     // step execution and the captured step graph
-    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1};
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1, 0};
     cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
     struct StepGraph {
         std::vector<int64_t> key;        // the step shape it was captured for
@@ -850,7 +852,7 @@ extern "C" gl_status gl_map_destroy(gl_map* m)
     m->ctx.pose_part.release();
     m->ctx.loss_part.release();
     m->stage_img.release(); m->stage_pts.release(); m->dLdC.release(); m->loss_dev.release();
-    m->flags.release(); m->scan.release();
+    m->flags.release(); m->scan.release(); m->timed_counts.release();
     for (auto& kv : m->kfs) { kv.second->image.release(); kv.second->expo.release(); }
     if (m->h_loss) cudaFreeHost(m->h_loss);
     for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);
@@ -1053,6 +1055,7 @@ void apply_exec(gl_map* m)
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;
     v.cull = m->exec.exact_cull != 0;
+    v.pg = m->exec.per_gaussian != 0;
 }
 
 // Enqueue the whole step on `s`.  sync_free: the descriptors were uploaded by
@@ -1118,6 +1121,7 @@ std::vector<int64_t> graph_key(const gl_map* m, const StepPlan& sp)
 {
     std::vector<int64_t> k = {sp.V, step_tile(m), m->exec.batch_depth, m->exec.pixels_per_lane,
                               m->exec.persistent, m->exec.deterministic, m->exec.segment, m->exec.exact_cull,
+                              m->exec.per_gaussian,
                               m->n, m->deg,
                               m->cfg.sparse_adam};
     for (int i = 0; i < sp.V; i++) {
@@ -1239,8 +1243,7 @@ gl_status run_step(gl_map* m, StepPlan& sp, float* out_loss)
         m->graph_reruns++;
     }
     GL_TRY(enqueue_step(m, sp, m->stream, false));
-    if (m->prof.on) {
-        GL_TRY(m->timed_counts.reserve(4 * sizeof(uint64_t)));
+    if (m->prof.on && m->timed_counts.p) {
         GL_TRY(accumulate_view_counts(v, m->timed_counts.as<uint64_t>(), m->stream));
         m->timed_steps++;
         m->timed_views += sp.V;
@@ -1326,7 +1329,8 @@ extern "C" gl_status gl_map_set_timing(gl_map* m, int32_t enable)
     m->prof.on = enable != 0;
     if (m->prof.on) m->prof.prefill(8192);
     m->timed_steps = m->timed_views = 0;
-    if (m->timed_counts.p) GL_CUDA_TRY(cudaMemset(m->timed_counts.p, 0, 4 * sizeof(uint64_t)));
+    GL_TRY(m->timed_counts.reserve(4 * sizeof(uint64_t)));
+    GL_CUDA_TRY(cudaMemset(m->timed_counts.p, 0, 4 * sizeof(uint64_t)));
     return GL_OK;
 }
 
@@ -1397,6 +1401,7 @@ gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
     if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
     if (e.deterministic != 0 && e.deterministic != 1) { set_error("deterministic must be 0 or 1"); return GL_ERR_INVALID; }
     if (e.exact_cull != 0 && e.exact_cull != 1) { set_error("exact_cull must be 0 or 1"); return GL_ERR_INVALID; }
+    if (e.per_gaussian != 0 && e.per_gaussian != 1) { set_error("per_gaussian must be 0 or 1"); return GL_ERR_INVALID; }
     if (e.segment != 0 && (e.segment < 64 || e.segment > 65536 || (e.segment & (e.segment - 1)) != 0)) {
         set_error("segment must be 0 or a power of two in 64..65536");
         return GL_ERR_INVALID;
@@ -1531,16 +1536,17 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
     // value that is fastest with the others fixed
     float best_t = -1.0f;
     gl_exec_config best_e{1, 1, 32, 1, keep_tile_size ? 0 : m->cfg.tile_size, saved.deterministic, 1024,
-                          saved.exact_cull};
+                          saved.exact_cull, 0};
     if (st == GL_OK) st = trial(best_e, &best_t);
     const int tile_vals[3] = {8, 16, 32}, seg_vals[4] = {0, 256, 512, 1024}, pers_vals[2] = {0, 1},
-              bd_vals[2] = {32, 64}, ppl_vals[3] = {1, 2, 4};
+              bd_vals[2] = {32, 64}, ppl_vals[3] = {1, 2, 4}, pg_vals[2] = {0, 1};
     struct Dim { int32_t gl_exec_config::*field; const int* vals; int n; };
-    const Dim dims[5] = {{&gl_exec_config::tile_size, tile_vals, keep_tile_size ? 0 : 3},
+    const Dim dims[6] = {{&gl_exec_config::tile_size, tile_vals, keep_tile_size ? 0 : 3},
                          {&gl_exec_config::segment, seg_vals, 4},
                          {&gl_exec_config::persistent, pers_vals, 2},
                          {&gl_exec_config::batch_depth, bd_vals, saved.deterministic ? 1 : 2},
-                         {&gl_exec_config::pixels_per_lane, ppl_vals, 3}};
+                         {&gl_exec_config::pixels_per_lane, ppl_vals, 3},
+                         {&gl_exec_config::per_gaussian, pg_vals, 2}};
     for (const Dim& d : dims) {
         for (int i = 0; i < d.n && st == GL_OK; i++) {
             gl_exec_config cand = best_e;
@@ -1789,6 +1795,7 @@ void map_exec_knobs(const gl_map* m, View& v, int Ts)
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;
     v.cull = m->exec.exact_cull != 0;
+    v.pg = m->exec.per_gaussian != 0;
 }
 int map_sh_degree(const gl_map* m) { return m->deg; }
 int map_tile_size(const gl_map* m) { return m->cfg.tile_size; }

@@ -154,8 +154,10 @@ struct View {
     DevBuf bsum;              // u64 per scan block
     DevBuf count;             // u64[16]: I (0 after an overflow), overflow flag, N (depth
                               // sort), instances needed, view-count scratch [4..5],
-                              // work items [6], segment items [7], radix-sort wait
-                              // gave up [8] (sticky until sort_wait_status reads it)
+                              // work items [6], segment items [7], bounded device
+                              // waits that gave up [8] (bit 0: radix-sort look-back,
+                              // bit 1: parameter staging; sticky until
+                              // sort_wait_status reads it)
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
@@ -188,6 +190,8 @@ struct View {
     // exact tile culling: only tiles where the Gaussian can reach alpha >=
     // 1/255 at a pixel centre get an instance
     bool cull = true;
+    // per-Gaussian backward: lanes own Gaussians, pixel states travel the warp
+    bool pg = false;
     DevBuf items;             // uint2 per work item: (tile, segment), heaviest first
     DevBuf segstate;          // 8 floats per (segment item, pixel of its tile), see gl_raster.cu
     const ViewDesc* d_desc() const
@@ -206,7 +210,7 @@ struct View {
 struct gl_ctx_impl {
     cudaStream_t stream = nullptr;
     View view;
-    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1};
+    gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1, 0};
     DevBuf pose_part;   // per-block pose partials
     DevBuf loss_part;   // per-block loss partials
     float pose_jac[36] = {};   // J_l of the last forward's twist (row-major 6 x 6)

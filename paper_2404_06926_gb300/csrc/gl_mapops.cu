@@ -4,7 +4,13 @@
 // the world origin, drawn from a counter-based SplitMix64 stream (Steele, Lea
 // and Flood, 2014: output i = mix(seed + (i+1) * golden gamma), top 24 bits as
 // a uniform); each gets the distance to its nearest other sky point as its
-// isotropic scale (brute force, tiled through shared memory).
+// isotropic scale.  The nearest neighbour comes from a uniform grid: points
+// are sorted by a 30-bit cell key with the library's radix sort, and each
+// point searches shells of cells around its own (Chebyshev radius 1, 2, ...)
+// until the best distance found is below the searched radius -- every point
+// outside it is at least that far -- so the result is the exact minimum over
+// all other points, with the same float arithmetic per pair as a brute-force
+// scan.
 //
 // Expansion (Eq. 8): a point is kept if it lies in front of the camera and,
 // when masking, lands inside the image on a pixel whose rendered opacity is
@@ -14,6 +20,7 @@
 #include "gl_internal.h"
 
 #include <algorithm>
+#include <cmath>
 
 namespace gl {
 
@@ -48,37 +55,109 @@ __global__ void k_sky_points(float* __restrict__ means, int64_t n, double radius
     means[3 * i + 2] = (float)(radius * zc);
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_sky_init(const float* __restrict__ xyz, int64_t n, float* __restrict__ log_scales,
-           float* __restrict__ quats, float* __restrict__ logits, float* __restrict__ sh, int K,
-           float logit)
+// Grid of the sky's nearest-neighbour search: cubic cells of side c over
+// [-R, R] x [-R, R] x [0, R], at most 1024 per axis (10 bits each of a
+// 30-bit key, x fastest, so the cells of a row are consecutive keys).
+struct SkyGrid {
+    float R, c, inv_c;
+    int nx, nz;
+};
+
+__device__ __forceinline__ int sky_cell(float v, float lo, const SkyGrid& G, int n)
 {
-    __shared__ float3 tile[kThreads];
-    const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    float3 me = make_float3(0.f, 0.f, 0.f);
-    if (i < n) me = make_float3(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
-    float best = 3.0e38f;
-    for (int64_t base = 0; base < n; base += kThreads) {
-        const int64_t j = base + threadIdx.x;
-        __syncthreads();
-        if (j < n) tile[threadIdx.x] = make_float3(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]);
-        __syncthreads();
-        const int cnt = (int)min((int64_t)kThreads, n - base);
-        for (int k = 0; k < cnt; k++) {
-            if (base + k == i) continue;
-            const float dx = me.x - tile[k].x, dy = me.y - tile[k].y, dz = me.z - tile[k].z;
-            best = fminf(best, dx * dx + dy * dy + dz * dz);
-        }
+    const int i = (int)floorf(__fmul_rn(__fsub_rn(v, lo), G.inv_c));
+    return min(max(i, 0), n - 1);
+}
+
+__global__ void k_sky_cells(const float* __restrict__ xyz, int64_t n, SkyGrid G, uint32_t* __restrict__ key,
+                            uint32_t* __restrict__ idx, uint64_t* __restrict__ ctl)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) {
+        ctl[0] = (uint64_t)n;   // keys of the sort
+        ctl[8] = 0;             // its bounded-wait flag
     }
     if (i >= n) return;
+    const int ix = sky_cell(xyz[3 * i], -G.R, G, G.nx);
+    const int iy = sky_cell(xyz[3 * i + 1], -G.R, G, G.nx);
+    const int iz = sky_cell(xyz[3 * i + 2], 0.0f, G, G.nz);
+    key[i] = (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+    idx[i] = (uint32_t)i;
+}
+
+// First position in the sorted keys [0, n) whose key is >= k.
+__device__ __forceinline__ int64_t lower_key(const uint32_t* __restrict__ keys, int64_t n, uint32_t k)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Squared distance, explicitly rounded in a fixed order.
+__device__ __forceinline__ float sq_dist(float3 a, float3 b)
+{
+    const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Minimum over the points of cells x0..x1 of row (iy, iz).
+__device__ __forceinline__ void scan_row(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ idx,
+                                         const float* __restrict__ xyz, int64_t n, int64_t self, float3 me,
+                                         int x0, int x1, int iy, int iz, float& best)
+{
+    const uint32_t row = ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+    for (int64_t j = lower_key(keys, n, row | (uint32_t)x0); j < n && keys[j] <= (row | (uint32_t)x1); j++) {
+        const int64_t o = idx[j];
+        if (o == self) continue;
+        best = fminf(best, sq_dist(me, make_float3(xyz[3 * o], xyz[3 * o + 1], xyz[3 * o + 2])));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sky_nn(const float* __restrict__ xyz, int64_t n, SkyGrid G, const uint32_t* __restrict__ keys,
+         const uint32_t* __restrict__ idx, float* __restrict__ log_scales, float* __restrict__ quats,
+         float* __restrict__ logits, float* __restrict__ sh, int K, float logit)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 me = make_float3(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+    const int ix = sky_cell(me.x, -G.R, G, G.nx), iy = sky_cell(me.y, -G.R, G, G.nx);
+    const int iz = sky_cell(me.z, 0.0f, G, G.nz);
+    float best = 3.0e38f;
+    const int kmax = max(G.nx, G.nz);
+    for (int k = 1; k <= kmax; k++) {
+        // the shell at Chebyshev distance k around the point's cell (the
+        // whole 3 x 3 x 3 block for k = 1)
+        for (int dz = -k; dz <= k; dz++) {
+            const int z = iz + dz;
+            if (z < 0 || z >= G.nz) continue;
+            for (int dy = -k; dy <= k; dy++) {
+                const int y = iy + dy;
+                if (y < 0 || y >= G.nx) continue;
+                if (k == 1 || max(abs(dy), abs(dz)) == k) {
+                    scan_row(keys, idx, xyz, n, i, me, max(ix - k, 0), min(ix + k, G.nx - 1), y, z, best);
+                } else {
+                    if (ix - k >= 0) scan_row(keys, idx, xyz, n, i, me, ix - k, ix - k, y, z, best);
+                    if (ix + k < G.nx) scan_row(keys, idx, xyz, n, i, me, ix + k, ix + k, y, z, best);
+                }
+            }
+        }
+        // every point outside the searched block is at least k cell sides away
+        const float reach = (float)k * G.c * (1.0f - 1e-5f);
+        if (best <= reach * reach) break;
+    }
     const float ls = 0.5f * logf(best);
     log_scales[3 * i] = ls; log_scales[3 * i + 1] = ls; log_scales[3 * i + 2] = ls;
     reinterpret_cast<float4*>(quats)[i] = make_float4(1.f, 0.f, 0.f, 0.f);
     logits[i] = logit;
-    float* s = sh + (size_t)i * K * 3;
+    float* sp = sh + (size_t)i * K * 3;
     const float dc = (1.0f - 0.5f) / kSH0;   // white
-    s[0] = dc; s[1] = dc; s[2] = dc;
-    for (int k = 3; k < K * 3; k++) s[k] = 0.0f;
+    sp[0] = dc; sp[1] = dc; sp[2] = dc;
+    for (int k = 3; k < K * 3; k++) sp[k] = 0.0f;
 }
 
 // Keep flags of Eq. 8 with the same explicitly rounded projection as binning.
@@ -197,12 +276,49 @@ gl_status sky_create(float* means, float* log_scales, float* quats, float* logit
                      int64_t n, double radius, uint64_t seed, float opacity, cudaStream_t s)
 {
     if (n <= 0) return GL_OK;
+    if (n >= ((int64_t)1 << 30)) { set_error("too many sky points"); return GL_ERR_INVALID; }
     const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
     k_sky_points<<<grid, kThreads, 0, s>>>(means, n, radius, seed);
-    const float logit = logf(opacity / (1.0f - opacity));
-    k_sky_init<<<grid, kThreads, 0, s>>>(means, n, log_scales, quats, logits, sh, K, logit);
+    // cells about twice the mean spacing of n points on the hemisphere's
+    // 2 pi R^2, at most 1000 across
+    SkyGrid G;
+    G.R = (float)radius;
+    G.c = (float)std::max(radius * std::sqrt(2.0 * 3.14159265358979323846 / (double)n), 2.0 * radius / 1000.0);
+    G.inv_c = 1.0f / G.c;
+    G.nx = (int)std::min(1024.0, std::floor(2.0 * radius / (double)G.c) + 1.0);
+    G.nz = (int)std::min(1024.0, std::floor(radius / (double)G.c) + 1.0);
+    struct Tmp {
+        DevBuf keys, vals, keys2, vals2, scratch, ctl;
+        ~Tmp()
+        {
+            for (DevBuf* b : {&keys, &vals, &keys2, &vals2, &scratch, &ctl}) b->release();
+        }
+    } T;
+    const size_t nn = (size_t)n;
+    GL_TRY(T.keys.reserve(4 * nn));
+    GL_TRY(T.vals.reserve(4 * nn));
+    GL_TRY(T.keys2.reserve(4 * nn));
+    GL_TRY(T.vals2.reserve(4 * nn));
+    GL_TRY(T.ctl.reserve(16 * sizeof(uint64_t)));
+    uint64_t* ctl = T.ctl.as<uint64_t>();
+    k_sky_cells<<<grid, kThreads, 0, s>>>(means, n, G, T.keys.as<uint32_t>(), T.vals.as<uint32_t>(), ctl);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
+    uint32_t *sk, *sv;
+    GL_TRY(radix_sort_u32(T.keys.as<uint32_t>(), T.vals.as<uint32_t>(), T.keys2.as<uint32_t>(),
+                          T.vals2.as<uint32_t>(), ctl, n, n, 30, T.scratch, ctl, &sk, &sv, s));
+    const float logit = logf(opacity / (1.0f - opacity));
+    k_sky_nn<<<grid, kThreads, 0, s>>>(means, n, G, sk, sv, log_scales, quats, logits, sh, K, logit);
+    count_launches(1);
+    GL_CUDA_TRY(cudaGetLastError());
+    // the temporary buffers are released on return: wait for the kernels
+    uint64_t flag = 0;
+    GL_CUDA_TRY(cudaMemcpyAsync(&flag, ctl + 8, sizeof(flag), cudaMemcpyDeviceToHost, s));
+    GL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flag) {
+        set_error("sky creation: a radix-sort wait gave up");
+        return GL_ERR_TIMEOUT;
+    }
     return GL_OK;
 }
 

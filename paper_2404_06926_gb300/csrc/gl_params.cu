@@ -16,8 +16,7 @@ namespace gl {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kUnroll = 4;   // float4 loads per thread in flight in the Adam pass
+constexpr int kPG = 32;   // Gaussians per CTA: one warp, one Gaussian per lane
 constexpr int kNG = 10;
 
 struct Geo {
@@ -87,44 +86,6 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     G.dir[0] = d0 * idn; G.dir[1] = d1 * idn; G.dir[2] = d2 * idn;
 }
 
-// Hint the L2 to fetch [p, p + bytes) (the 16-byte aligned part of it) with
-// one bulk prefetch; nothing waits for it.
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
-{
-    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
-    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
-    if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
-}
-
-// Shared-memory row stride of an array of WIDTH floats per Gaussian: rows of
-// an even number of float4 get one float4 of padding, so that the float4
-// reads of a quarter warp (8 rows) fall in distinct banks.
-template <int WIDTH>
-constexpr int staged_stride() { return (WIDTH % 4 == 0 && (WIDTH / 4) % 2 == 0) ? WIDTH + 4 : WIDTH; }
-
-// Copy the block's rows [g0, g0 + cnt) of one parameter array into shared
-// memory at the staged stride; float4 loads where rows allow them.
-template <int WIDTH>
-__device__ __forceinline__ void stage_rows(const float* __restrict__ P, int64_t g0, int cnt, float* __restrict__ dst)
-{
-    constexpr int S = staged_stride<WIDTH>();
-    const float* src = P + (size_t)g0 * WIDTH;
-    const int ne = cnt * WIDTH;
-    if constexpr (WIDTH % 4 == 0) {
-        constexpr int R4 = WIDTH / 4;
-        const float4* s4 = reinterpret_cast<const float4*>(src);
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        for (int f = threadIdx.x; f < ne / 4; f += kThreads) d4[(f / R4) * (S / 4) + f % R4] = s4[f];
-    } else {
-        // S == WIDTH: the span is copied as is
-        const int nv = ne / 4;
-        const float4* s4 = reinterpret_cast<const float4*>(src);
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        for (int f = threadIdx.x; f < nv; f += kThreads) d4[f] = s4[f];
-        for (int e = 4 * nv + threadIdx.x; e < ne; e += kThreads) dst[e] = src[e];
-    }
-}
-
 // p -= lr (m / bc1) / (sqrt(v / bc2) + eps), with 1/bc1 and 1/sqrt(bc2)
 // precomputed for the step: the same update with one square root and one
 // fast division per element.
@@ -138,149 +99,211 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
     p -= __fdividef(lr * a.ibc1 * m, sv * a.isbc2 + a.eps);
 }
 
-// Block-cooperative pass over one parameter array of the block's Gaussians
-// (a contiguous span of cnt * WIDTH floats, 16-byte aligned because blocks
-// start at multiples of 128 Gaussians): MODE 0 writes the gradient rows
-// (sR, stride NR, this array's columns from off), MODE 1 applies Adam to the
-// parameters staged in shared memory (sP, rows at the staged stride) and
-// writes them back with the moments (the first three floats of a row take
-// lr0, the SH DC band; the rest lr).  Rows flagged off in upd are left
-// untouched (MODE 1).  Rows of a multiple of 4 floats go by float4, a row
-// quarter per thread; other widths element by element.  kUnroll accesses per
-// thread are in flight.
-template <int MODE, int WIDTH, int NR>
-__device__ __forceinline__ void coop(float* __restrict__ P, float* __restrict__ Mm, float* __restrict__ Vv,
-                                     int64_t g0, int cnt, const float* __restrict__ sR, int off,
-                                     const float* __restrict__ sP, const uint8_t* __restrict__ upd, float lr,
-                                     float lr0, const AdamArgs& ad)
+// ---------------------------------------------------------------------------
+// Bulk copies global -> shared memory (the copy engine behind TMA, untiled
+// form), completing on an mbarrier; each span starts and ends on 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
-    constexpr int S = staged_stride<WIDTH>();
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Polls of a staging barrier before the kernel gives up (each poll may
+// suspend the thread for a while): far beyond any real copy time.
+constexpr int kStageSpin = 1 << 22;
+
+// Hint the L2 to fetch [p, p + bytes) (its 16-byte aligned part) with one
+// bulk prefetch; nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
+{
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
+// Staged rows of a block of kPG Gaussians: each parameter array's span,
+// dense as in global memory, then the gradient rows at an odd stride
+// (against bank conflicts).  Offsets in floats; every span starts on 16
+// bytes.
+template <int DEG, int MODE>
+struct PStage {
+    static constexpr int KF = (DEG + 1) * (DEG + 1) * 3;
+    static constexpr int ROW = 11 + KF;                      // floats of one Gaussian's parameters
+    static constexpr int MU = 0, LS = 3 * kPG, Q = 6 * kPG, LG = 10 * kPG, SH = 11 * kPG;
+    static constexpr int SET = ROW * kPG;                    // the parameter rows
+    static constexpr int NSET = 1;
+    static constexpr int NR = ROW % 2 ? ROW : ROW + 1;
+    static constexpr int GR = NSET * SET;                    // gradient rows
+    static constexpr int FLOATS = GR + NR * kPG;
+    static_assert(SET % 4 == 0 && LG % 4 == 0 && SH % 4 == 0, "16-byte spans");
+};
+
+// Copy one array's span [g0, g0 + cnt) rows of WIDTH floats into shared
+// memory: a bulk copy for a whole block (cnt = kPG), lane-strided loads for
+// the last, partial one.
+template <int WIDTH>
+__device__ __forceinline__ void stage_span(const float* __restrict__ src, int64_t g0, int cnt, float* dst,
+                                           uint64_t* bar, int lane)
+{
+    const float* s0 = src + (size_t)g0 * WIDTH;
+    if (cnt == kPG) {
+        if (lane == 0) bulk_g2s(dst, s0, (uint32_t)(sizeof(float) * WIDTH * kPG), bar);
+    } else {
+        for (int e = lane; e < cnt * WIDTH; e += 32) dst[e] = s0[e];
+    }
+}
+
+// Adam (MODE 1) or the gradient write-out (MODE 0) over one array's span:
+// element e of the span is row e / WIDTH, column e % WIDTH; the parameter
+// comes from the staged rows, m and v from global memory (already asked of
+// the L2), the gradient from the row's gradient (columns from `off`).  Whole blocks go by float4 (a float4 may straddle
+// rows; the elements of rows left alone are written back unchanged), the
+// partial block element by element.  Rows whose bit in `upd` is clear are
+// left untouched.  The first three columns take lr0 (the SH DC band), the
+// rest lr.
+template <int MODE, int WIDTH, int NR>
+__device__ __forceinline__ void span_update(float* __restrict__ P, float* __restrict__ Mg, float* __restrict__ Vg,
+                                            int64_t g0, int cnt, const float* sP, const float* sR, int off,
+                                            uint32_t upd, float lr, float lr0, const AdamArgs& ad, int lane)
+{
     const size_t base = (size_t)g0 * WIDTH;
-    if constexpr (WIDTH % 4 == 0) {
-        constexpr int R4 = WIDTH / 4;
-        const int nv = cnt * R4;
-        float4* P4 = reinterpret_cast<float4*>(P + base);
-        float4* M4 = reinterpret_cast<float4*>(Mm + base);
-        float4* V4 = reinterpret_cast<float4*>(Vv + base);
-        const float4* S4 = reinterpret_cast<const float4*>(sP);
-        for (int f0 = threadIdx.x; f0 < nv; f0 += kUnroll * kThreads) {
-            float4 pp[kUnroll], mm[kUnroll], vv[kUnroll];
-            int row[kUnroll], c4[kUnroll];
-            bool ok[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const int f = f0 + u * kThreads;
-                row[u] = f / R4;
-                c4[u] = f - row[u] * R4;
-                ok[u] = f < nv && (MODE == 0 || upd[row[u]]);
-                if (ok[u] && MODE == 1) {
-                    mm[u] = M4[f];
-                    vv[u] = V4[f];
-                    pp[u] = S4[row[u] * (S / 4) + c4[u]];
-                }
+    if (cnt == kPG) {
+        constexpr int N4 = WIDTH * kPG / 4;
+#pragma unroll 4
+        for (int c = lane; c < N4; c += 32) {
+            const int e0 = 4 * c;
+            const int r0 = e0 / WIDTH, r3 = (e0 + 3) / WIDTH;
+            const uint32_t rows = (upd >> r0) & ((2u << (r3 - r0)) - 1u);
+            if (!rows) continue;
+            float pe[4], me[4], ve[4];
+            if (MODE == 1) {
+                const float4 pp = reinterpret_cast<const float4*>(sP)[c];
+                const float4 mm = reinterpret_cast<const float4*>(Mg + base)[c];
+                const float4 vv = reinterpret_cast<const float4*>(Vg + base)[c];
+                pe[0] = pp.x; pe[1] = pp.y; pe[2] = pp.z; pe[3] = pp.w;
+                me[0] = mm.x; me[1] = mm.y; me[2] = mm.z; me[3] = mm.w;
+                ve[0] = vv.x; ve[1] = vv.y; ve[2] = vv.z; ve[3] = vv.w;
             }
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                if (!ok[u]) continue;
-                const int f = f0 + u * kThreads;
-                const float* gr = sR + row[u] * NR + off + 4 * c4[u];
-                if (MODE == 0) {
-                    P4[f] = make_float4(gr[0], gr[1], gr[2], gr[3]);
-                } else {
-                    float* pa = &pp[u].x;
-                    float* ma = &mm[u].x;
-                    float* va = &vv[u].x;
-#pragma unroll
-                    for (int e = 0; e < 4; e++) adam1(pa[e], ma[e], va[e], gr[e], 4 * c4[u] + e < 3 ? lr0 : lr, ad);
-                    P4[f] = pp[u];
-                    M4[f] = mm[u];
-                    V4[f] = vv[u];
-                }
+            for (int k = 0; k < 4; k++) {
+                const int e = e0 + k, r = e / WIDTH, w = e - r * WIDTH;
+                const float g = sR[r * NR + off + w];
+                if (MODE == 0) pe[k] = (upd >> r) & 1u ? g : 0.0f;
+                else if ((upd >> r) & 1u) adam1(pe[k], me[k], ve[k], g, w < 3 ? lr0 : lr, ad);
+            }
+            reinterpret_cast<float4*>(P + base)[c] = make_float4(pe[0], pe[1], pe[2], pe[3]);
+            if (MODE == 1) {
+                reinterpret_cast<float4*>(Mg + base)[c] = make_float4(me[0], me[1], me[2], me[3]);
+                reinterpret_cast<float4*>(Vg + base)[c] = make_float4(ve[0], ve[1], ve[2], ve[3]);
             }
         }
     } else {
-        const int ne = cnt * WIDTH;
-        for (int e0 = threadIdx.x; e0 < ne; e0 += kUnroll * kThreads) {
-            float pv[kUnroll], mv[kUnroll], vv[kUnroll];
-            int row[kUnroll], w[kUnroll];
-            bool ok[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const int e = e0 + u * kThreads;
-                row[u] = e / WIDTH;
-                w[u] = e - row[u] * WIDTH;
-                ok[u] = e < ne && (MODE == 0 || upd[row[u]]);
-                if (ok[u] && MODE == 1) {
-                    mv[u] = Mm[base + e];
-                    vv[u] = Vv[base + e];
-                    pv[u] = sP[row[u] * S + w[u]];
-                }
+        for (int e = lane; e < cnt * WIDTH; e += 32) {
+            const int r = e / WIDTH, w = e - r * WIDTH;
+            if (!((upd >> r) & 1u)) {
+                if (MODE == 0) P[base + e] = 0.0f;
+                continue;
             }
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                if (!ok[u]) continue;
-                const int e = e0 + u * kThreads;
-                const float gr = sR[row[u] * NR + off + w[u]];
-                if (MODE == 0) {
-                    P[base + e] = gr;
-                } else {
-                    adam1(pv[u], mv[u], vv[u], gr, w[u] < 3 ? lr0 : lr, ad);
-                    P[base + e] = pv[u];
-                    Mm[base + e] = mv[u];
-                    Vv[base + e] = vv[u];
-                }
+            const float g = sR[r * NR + off + w];
+            if (MODE == 0) {
+                P[base + e] = g;
+            } else {
+                float pv = sP[e], mv = Mg[base + e], vv = Vg[base + e];
+                adam1(pv, mv, vv, g, w < 3 ? lr0 : lr, ad);
+                P[base + e] = pv;
+                Mg[base + e] = mv;
+                Vg[base + e] = vv;
             }
         }
     }
 }
 
-// Shared memory of k_params_bwd (floats): the gradient rows (odd stride NR),
-// then the block's staged parameter rows (means, log-scales, quaternions,
-// logits, SH at their staged strides), each part 16-byte aligned.
-template <int DEG>
-struct ParamsSmem {
-    static constexpr int KF = (DEG + 1) * (DEG + 1) * 3;   // SH floats per Gaussian
-    static constexpr int NR = 11 + KF + ((11 + KF) % 2 == 0 ? 1 : 0);
-    static constexpr int SHS = staged_stride<KF>();
-    static constexpr int R = (kThreads * NR + 3) / 4 * 4;
-    static constexpr int MU = R, LS = MU + kThreads * 3, Q = LS + kThreads * 3, LG = Q + kThreads * 4,
-                         SH = LG + kThreads, END = SH + kThreads * SHS;
-    static constexpr size_t bytes = sizeof(float) * (size_t)END;
-};
-
+// One warp per kPG consecutive Gaussians, 128 registers a thread, so that
+// 16 warps share an SM.  The block's visibility comes first (a block with
+// nothing visible is skipped by sparse Adam, or written as zero gradients);
+// then one lane starts bulk copies of the block's rows of every parameter
+// array into shared memory (7.5 KB in flight per block whatever the thread
+// count) and bulk L2 prefetches of its Adam moments; each lane chains its
+// Gaussian's screen-space gradients back to the parameters (and the pose),
+// and the warp applies Adam -- or writes the gradients -- array by array with
+// float4 accesses.  Parameters and moments are read once and written once,
+// and sparse Adam touches no moment of a block it skips.
 template <int DEG, int MODE>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(32, 16)
 k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __restrict__ radius,
-             const float* __restrict__ g2d, GMut out, AdamArgs ad, float* __restrict__ pose_part)
+             const float* __restrict__ g2d, GMut out, AdamArgs ad, float* __restrict__ pose_part,
+             unsigned long long* __restrict__ err)
 {
-    using SM = ParamsSmem<DEG>;
+    using ST = PStage<DEG, MODE>;
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int KF = SM::KF;
-    // one row of gradients per Gaussian of the block: means 3, log-scales 3,
-    // quaternion 4, logit 1, SH KF (odd stride against bank conflicts); the
-    // Adam update then streams every parameter array with coalesced accesses
-    constexpr int NR = SM::NR;
+    constexpr int KF = ST::KF;
+    constexpr int NR = ST::NR;
     if (MODE == 1) {
         // a step whose binning overflowed its buffers updates nothing (it is re-run)
         if (ad.abort && ad.abort[1]) return;
         if (ad.bc) { ad.ibc1 = ad.bc[0]; ad.isbc2 = ad.bc[1]; }
     }
-    extern __shared__ float4 smem4[];
-    float* smf = reinterpret_cast<float*>(smem4);
-    float* sR = smf;
-    float* sMu = smf + SM::MU;
-    float* sLs = smf + SM::LS;
-    float* sQ = smf + SM::Q;
-    float* sLg = smf + SM::LG;
-    float* sSH = smf + SM::SH;
-    __shared__ uint8_t sUpd[kThreads];
-    const int64_t g0 = blockIdx.x * (int64_t)kThreads;
-    const int64_t g = g0 + threadIdx.x;
-    const int cnt = (int)min((int64_t)kThreads, p.n - g0);
-    // the moments and screen-space gradients of the block head for the L2
-    // while its parameters are staged and its geometry is recomputed
-    if (threadIdx.x == 0) {
-        if (MODE == 1) {
+    __shared__ __align__(16) float smf[ST::FLOATS];
+    __shared__ uint64_t bar;
+    const int lane = threadIdx.x;
+    const int64_t g0 = blockIdx.x * (int64_t)kPG;
+    const int cnt = (int)min((int64_t)kPG, p.n - g0);
+    const int64_t g = g0 + lane;
+    const bool valid = lane < cnt;
+    bool vis = false;
+    for (int vw = 0; vw < V && valid; vw++) vis = vis || radius[(size_t)vw * p.n + g] > 0;
+    const uint32_t vmask = __ballot_sync(kFull, vis);
+    const uint32_t vrows = __ballot_sync(kFull, valid);
+    const uint32_t upd = MODE == 0 ? vrows : (ad.sparse ? vmask : vrows);
+    if (MODE == 1 && upd == 0) return;
+
+    float* sMu = smf + ST::MU;
+    float* sLs = smf + ST::LS;
+    float* sQ = smf + ST::Q;
+    float* sLg = smf + ST::LG;
+    float* sSH = smf + ST::SH;
+    float* sR = smf + ST::GR;
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    if (vmask) {
+        const bool bulk = cnt == kPG;
+        if (bulk && lane == 0) {
+            mbar_init(&bar, 1);
+            mbar_expect_tx(&bar, (uint32_t)(sizeof(float) * ST::SET * ST::NSET));
+        }
+        __syncwarp();
+        stage_span<3>(p.means, g0, cnt, sMu, &bar, lane);
+        stage_span<3>(p.log_scales, g0, cnt, sLs, &bar, lane);
+        stage_span<4>(p.quats, g0, cnt, sQ, &bar, lane);
+        stage_span<1>(p.logits, g0, cnt, sLg, &bar, lane);
+        stage_span<KF>(p.sh, g0, cnt, sSH, &bar, lane);
+        if (MODE == 1 && lane == 0) {
+            // the moments head for the L2 while the geometry is recomputed
             const size_t c4 = sizeof(float) * (size_t)cnt;
             prefetch_l2(ad.m.means + 3 * g0, 3 * c4);
             prefetch_l2(ad.v.means + 3 * g0, 3 * c4);
@@ -293,34 +316,34 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
             prefetch_l2(ad.m.sh + (size_t)KF * g0, KF * c4);
             prefetch_l2(ad.v.sh + (size_t)KF * g0, KF * c4);
         }
-        for (int vw = 0; vw < V; vw++) {
-            prefetch_l2(g2d + ((size_t)vw * p.n + g0) * kNG, sizeof(float) * kNG * (size_t)cnt);
-            prefetch_l2(radius + (size_t)vw * p.n + g0, sizeof(int) * (size_t)cnt);
+        if (bulk) {
+            // bounded wait; on giving up, raise the flag and wait once more
+            // (again bounded) for the copies still landing in this block's
+            // shared memory before leaving
+            int spins = 0;
+            bool ok = mbar_try_wait(&bar, 0);
+            while (!ok && ++spins < kStageSpin) ok = mbar_try_wait(&bar, 0);
+            if (!__all_sync(kFull, ok)) {
+                if (lane == 0) atomicOr(err, 2ull);
+                for (int k = 0; k < kStageSpin && !ok; k++) ok = mbar_try_wait(&bar, 0);
+                return;
+            }
         }
-    }
-    stage_rows<3>(p.means, g0, cnt, sMu);
-    stage_rows<3>(p.log_scales, g0, cnt, sLs);
-    stage_rows<4>(p.quats, g0, cnt, sQ);
-    stage_rows<1>(p.logits, g0, cnt, sLg);
-    stage_rows<KF>(p.sh, g0, cnt, sSH);
-    __syncthreads();
-    float pose[6] = {0, 0, 0, 0, 0, 0};
-    const bool valid = g < p.n;
-    bool vis = false, first = true;
+        __syncwarp();
 
-    float gm[3] = {0, 0, 0}, gl3[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glg = 0.0f;
-    float* dsh = sR + threadIdx.x * NR + 11;   // this Gaussian's SH gradient, summed over its views in place
+        bool first = true;
+        float gm[3] = {0, 0, 0}, gl3[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glg = 0.0f;
+        float* dsh = sR + lane * NR + 11;   // this Gaussian's SH gradient, summed over its views in place
 
     // every view the Gaussian is visible in contributes (window steps sum them)
     for (int vw = 0; vw < V && valid; vw++) {
     const int64_t tv = (int64_t)vw * p.n + g;
     if (radius[tv] <= 0) continue;
-    vis = true;
     const Cam cam = views[vw].cam;
     float grgb[3] = {0, 0, 0};
     {
         float Y[16];
-        const int r = threadIdx.x;
+        const int r = lane;
         float mu[3] = {sMu[3 * r], sMu[3 * r + 1], sMu[3 * r + 2]};
         float ls[3] = {sLs[3 * r], sLs[3 * r + 1], sLs[3 * r + 2]};
         const float4 q4 = reinterpret_cast<const float4*>(sQ)[r];
@@ -342,7 +365,7 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
 
         // colour -> SH and view direction (clamped channels pass no gradient)
         sh_eval<DEG>(G.dir[0], G.dir[1], G.dir[2], Y);
-        const float* sh = sSH + threadIdx.x * SM::SHS;
+        const float* sh = sSH + lane * KF;
         float raw[3] = {0.5f, 0.5f, 0.5f};
         for (int k = 0; k < K; k++)
             for (int c = 0; c < 3; c++) raw[c] += Y[k] * sh[3 * k + c];
@@ -447,42 +470,48 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         pose[5] += P[1] - P[3];
     }
     }
-    if (!vis)
-        for (int k = 0; k < KF; k++) dsh[k] = 0.0f;
 
-    const bool upd = valid && (MODE == 0 || !ad.sparse || vis);
-    sUpd[threadIdx.x] = upd ? 1 : 0;
-    {
-        float* row = sR + threadIdx.x * NR;
+        if (!vis)
+            for (int k = 0; k < KF; k++) dsh[k] = 0.0f;
+        float* row = sR + lane * NR;
         row[0] = gm[0]; row[1] = gm[1]; row[2] = gm[2];
         row[3] = gl3[0]; row[4] = gl3[1]; row[5] = gl3[2];
         row[6] = gq[0]; row[7] = gq[1]; row[8] = gq[2]; row[9] = gq[3];
         row[10] = glg;
+        __syncwarp();
+    } else {
+        // nothing visible: zero gradients (MODE 0, and dense Adam, which
+        // still moves every row on its moments; sparse Adam returned above)
+        for (int e = lane; e < kPG * NR; e += 32) sR[e] = 0.0f;
+        __syncwarp();
     }
-    __syncthreads();
-    if (cnt > 0) {
-        coop<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sR, 0, sMu, sUpd, ad.lr_pos, ad.lr_pos, ad);
-        coop<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sR, 3, sLs, sUpd, ad.lr_scale,
-                          ad.lr_scale, ad);
-        coop<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sR, 6, sQ, sUpd, ad.lr_rot, ad.lr_rot, ad);
-        coop<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sR, 10, sLg, sUpd, ad.lr_op, ad.lr_op,
-                          ad);
-        coop<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sR, 11, sSH, sUpd, ad.lr_rest, ad.lr_dc, ad);
+    if (MODE == 1 && !vmask) {
+        // dense Adam on a block nothing sees: its parameter rows, staged plainly
+        const float* srcs[5] = {p.means, p.log_scales, p.quats, p.logits, p.sh};
+        float* dsts[5] = {sMu, sLs, sQ, sLg, sSH};
+        const int widths[5] = {3, 3, 4, 1, KF};
+        for (int a = 0; a < 5; a++) {
+            const float* s0 = srcs[a] + (size_t)g0 * widths[a];
+            for (int e = lane; e < cnt * widths[a]; e += 32) dsts[a][e] = s0[e];
+        }
+        __syncwarp();
     }
+    span_update<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sMu, sR, 0, upd, ad.lr_pos, ad.lr_pos, ad,
+                             lane);
+    span_update<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sLs, sR, 3, upd,
+                             ad.lr_scale, ad.lr_scale, ad, lane);
+    span_update<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sQ, sR, 6, upd, ad.lr_rot, ad.lr_rot, ad,
+                             lane);
+    span_update<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sLg, sR, 10, upd, ad.lr_op, ad.lr_op,
+                             ad, lane);
+    span_update<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sSH, sR, 11, upd, ad.lr_rest, ad.lr_dc, ad, lane);
 
     if (MODE == 0 && pose_part) {
-        __shared__ float red[6][kThreads / 32];
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
         for (int k = 0; k < 6; k++) {
             float v = pose[k];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-            if (lane == 0) red[k][w] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            float v = 0.0f;
-            for (int ww = 0; ww < kThreads / 32; ww++) v += red[threadIdx.x][ww];
-            pose_part[blockIdx.x * 6 + threadIdx.x] = v;
+            if (lane == 0) pose_part[blockIdx.x * 6 + k] = v;
         }
     }
 }
@@ -514,16 +543,13 @@ template <int MODE>
 gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* pose_part, cudaStream_t s)
 {
     if (p.n == 0) return GL_OK;
-    const unsigned grid = (unsigned)((p.n + kThreads - 1) / kThreads);
+    const unsigned grid = (unsigned)((p.n + kPG - 1) / kPG);
     PhaseScope ps(v.prof, PH_PARAMS, s);
     count_launches(1);
-#define GL_PB(D_)                                                                                         \
-    {                                                                                                     \
-        GL_TRY(ensure_smem_limit(reinterpret_cast<const void*>(&k_params_bwd<D_, MODE>),                 \
-                                 (int)ParamsSmem<D_>::bytes));                                            \
-        k_params_bwd<D_, MODE><<<grid, kThreads, ParamsSmem<D_>::bytes, s>>>(                             \
-            p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), o, a, pose_part);                  \
-    }
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(v.count.as<uint64_t>() + 8);
+#define GL_PB(D_)                                                                                      \
+    k_params_bwd<D_, MODE><<<grid, kPG, 0, s>>>(p, v.d_desc(), v.V, v.radius.as<int>(), v.g2d.as<float>(), o, a, \
+                                                pose_part, err);
     switch (p.deg) {
         case 0: GL_PB(0); break;
         case 1: GL_PB(1); break;
@@ -538,7 +564,7 @@ gl_status launch(View& v, const GParams& p, GMut o, const AdamArgs& a, float* po
 
 }  // namespace
 
-int pose_partials_needed(int64_t n) { return (int)std::max<int64_t>(1, (n + kThreads - 1) / kThreads); }
+int pose_partials_needed(int64_t n) { return (int)std::max<int64_t>(1, (n + kPG - 1) / kPG); }
 
 gl_status params_backward(View& v, const GParams& p, GMut grad, float* pose_part, int npart, cudaStream_t s)
 {

@@ -739,6 +739,294 @@ k_raster_bwd(RasterArgs A, RasterGrad G)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-Gaussian backward (Sec. III-D 1: threads assigned to the Gaussians
+// rather than to the pixels).  A warp takes a (work item, 8x4 pixel block)
+// unit like the kernel above and walks, back to front, the Gaussians whose
+// alpha box touches the block (the hits); lane l owns hits l, l + 32, l + 64,
+// ... and sums each one's gradient over the block's 32 pixels in its own
+// registers.  The pixels' backward state -- the transmittance and the colour
+// (depth, opacity) blended behind -- travels round the warp: at step s, lane
+// l serves pixel p = (s - l) mod 32 for its hit s - p and then hands the
+// pixel's state to lane l + 1, which holds the next hit.  Every pixel thus
+// meets the hits in back-to-front order, one step apart, and H hits take
+// H + 31 steps.  At step s lane s mod 32 is done with hit s - 32: it leaves
+// its sums in a shared-memory slot and takes up hit s; every 32 steps the
+// warp adds the 32 finished hits to their Gaussians' accumulators (or, in
+// deterministic mode, stores them per instance and pixel block).  So a hit
+// costs no warp reduction, and a Gaussian's sums stay in one lane.
+// Hits are compacted from the sorted records in batches of 32, as above,
+// into a per-warp ring of kPgQ entries, at least 32 ahead of the steps.  A
+// list short enough to fit in the first fill (under 64 hits) is walked per
+// pixel instead: there the 31 steps of filling and draining the ring would
+// cost more than the per-hit reductions they save.
+// ---------------------------------------------------------------------------
+constexpr int kPgQ = 64;   // hit ring per warp: live hits are < 32 ahead + one batch of 32
+
+struct PgWarp {
+    float4 q0[kPgQ], q1[kPgQ], q2[kPgQ];   // hit records (sorted-order r0, r1, r2)
+    uint32_t qpos[kPgQ], qg[kPgQ];          // list position (relative to the tile) and owner
+    float4 pix[32];                         // per pixel: dL/dC and the last contributor (bits)
+    float2 pxy[32];                         // per pixel: tile-relative coordinates
+    float2 pde[32];                         // per pixel: dL/dD, dL/dO (EXTRA)
+    float4 st0[32], st1[32];                // finished hits' sums, one slot per lane:
+    float2 st2[32];                         //   0-3, 4-7, 8-9
+    uint32_t stg[32];                       // their owners (0xffffffff: empty)
+};
+static_assert(sizeof(PgWarp) * 8 <= 48 * 1024, "static shared memory of the per-Gaussian backward");
+
+template <bool EXTRA, bool DET>
+__device__ __forceinline__ void pg_flush(const RasterArgs& A, const RasterGrad& G, int wb, uint32_t g,
+                                         const float (&acc)[kNG])
+{
+    constexpr int NQ = EXTRA ? kNG : kNG - 1;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        if (DET) G.part[((size_t)g * A.nblk + wb) * kNG + q] = acc[q];
+        else atomicAdd(G.g2d + (size_t)g * kNG + q, acc[q]);
+    }
+}
+
+template <bool EXTRA, bool DET>
+__device__ __forceinline__ void bwd_item_pg(int u, const RasterArgs& A, const RasterGrad& G, PgWarp& W, int lane)
+{
+    Unit U;
+    unit_of<1>(u, A, U);
+    const unsigned lt = (1u << lane) - 1u;
+    // lane l starts with the state of pixel (32 - l) mod 32 of the block
+    const int p0 = (32 - lane) & 31;
+    const int lx = U.lx0 + (p0 & 7), ly = U.ly0 + (p0 >> 3);
+    const int x = U.x0 + (p0 & 7), y = U.y0 + (p0 >> 3);
+    float T = 1.0f, R0 = 0.0f, R1 = 0.0f, R2 = 0.0f, RD = 0.0f, RO = 0.0f;
+    uint32_t last = 0;
+    float4 pc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float2 pe = make_float2(0.0f, 0.0f);
+    if (x < U.W && y < U.H) {
+        const size_t p = (size_t)U.pix_base + (size_t)y * U.W + x;
+        last = G.ncon[p];
+        if (U.nseg == 1) {
+            T = G.Tfin[p];
+        } else {
+            const float* S = A.segstate;
+            const int q = ly * A.TS + lx;
+            T = S[seg_at(U.w, 0, q, A.TS)];
+            R0 = S[seg_at(U.w, 1, q, A.TS)];
+            R1 = S[seg_at(U.w, 2, q, A.TS)];
+            R2 = S[seg_at(U.w, 3, q, A.TS)];
+            RD = S[seg_at(U.w, 4, q, A.TS)];
+            RO = S[seg_at(U.w, 5, q, A.TS)];
+        }
+        pc = make_float4(G.dL_drgb[3 * p], G.dL_drgb[3 * p + 1], G.dL_drgb[3 * p + 2], __uint_as_float(last));
+        if (EXTRA) pe = make_float2(G.dL_ddepth ? G.dL_ddepth[p] : 0.0f, G.dL_dopac ? G.dL_dopac[p] : 0.0f);
+    }
+    W.pix[p0] = pc;
+    W.pxy[p0] = make_float2((float)lx, (float)ly);
+    if (EXTRA) W.pde[p0] = pe;
+    W.stg[lane] = 0xffffffffu;
+    uint32_t wmax = last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, off));
+    const uint32_t end = min(U.re, U.trs + wmax);
+    __syncwarp();
+    if (end <= U.rs) return;
+
+    // batches from the back: [bstart, bstart + 32) clipped at rs, next one prefetched
+    int64_t bstart = (int64_t)end - 32;
+    float4 n0, n1, n2, n3;
+    uint32_t ng = 0;
+    {
+        const int64_t i = bstart + lane;
+        if (i >= (int64_t)U.rs) {
+            n0 = A.s0[i]; n1 = A.s1[i]; n2 = A.s2[i]; n3 = A.s3[i];
+            ng = DET ? G.sinst[i] : A.sgid[i];
+        }
+    }
+    bool exhausted = false;
+    int qhead = 0;   // hits compacted so far (hit 0 is the deepest)
+
+    // the lane's current hit
+    bool cur = false;
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0, c2 = c0;
+    uint32_t cpos = 0, cg = 0;
+    float acc[kNG];
+#pragma unroll
+    for (int q = 0; q < kNG; q++) acc[q] = 0.0f;
+
+    for (int S = 0;; S += 32) {
+        if (S > 0) {
+            // the hits finished in the last 32 steps, one per lane
+            const uint32_t g = W.stg[lane];
+            if (g != 0xffffffffu) {
+                float a[kNG];
+                const float4 v0 = W.st0[lane], v1 = W.st1[lane];
+                const float2 v2 = W.st2[lane];
+                a[0] = v0.x; a[1] = v0.y; a[2] = v0.z; a[3] = v0.w;
+                a[4] = v1.x; a[5] = v1.y; a[6] = v1.z; a[7] = v1.w;
+                a[8] = v2.x; a[9] = v2.y;
+                pg_flush<EXTRA, DET>(A, G, U.wb, g, a);
+                W.stg[lane] = 0xffffffffu;
+            }
+        }
+        // refill: compacted hits must cover the steps S .. S + 31
+        while (!exhausted && qhead < S + 32) {
+            const float4 b0 = n0, b1 = n1, b2 = n2, b3 = n3;
+            const uint32_t bg = ng;
+            const int64_t i = bstart + lane;
+            const int64_t ni = i - 32;
+            if (ni >= (int64_t)U.rs) {
+                n0 = A.s0[ni]; n1 = A.s1[ni]; n2 = A.s2[ni]; n3 = A.s3[ni];
+                ng = DET ? G.sinst[ni] : A.sgid[ni];
+            }
+            const bool hit = i >= (int64_t)U.rs && box_hit(b3, (float)U.x0, (float)(U.x0 + 7), (float)U.y0,
+                                                            (float)(U.y0 + 3));
+            const unsigned mask = __ballot_sync(kFull, hit);
+            const int nh = __popc(mask);
+            if (hit) {
+                // deepest first: the batch's hits in reverse list order
+                const int k = (qhead + nh - 1 - __popc(mask & lt)) & (kPgQ - 1);
+                W.q0[k] = b0; W.q1[k] = b1; W.q2[k] = b2;
+                W.qpos[k] = (uint32_t)(i - U.trs);
+                W.qg[k] = bg;
+            }
+            qhead += nh;
+            bstart -= 32;
+            if (bstart + 32 <= (int64_t)U.rs) exhausted = true;
+        }
+        __syncwarp();
+        if (S == 0 && exhausted) {
+            // a short list (all of it fitted in the first fill): the ring
+            // would spend 31 steps filling and draining for fewer than 64
+            // hits, so walk it per pixel instead, each lane with the pixel
+            // it holds, and fold each hit's sums across the warp
+            const float px = (float)lx, py = (float)ly;
+            for (int k = 0; k < qhead; k++) {
+                const float4 a = W.q0[k], b = W.q1[k], c = W.q2[k];
+                const uint32_t pos = W.qpos[k];
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) v[q] = 0.0f;
+                float dx, dy, alpha;
+                bool capped;
+                const bool on = pos < last && pair_eval(a, b, px, py, dx, dy, alpha, capped);
+                if (on) {
+                    const float om = 1.0f - alpha;
+                    T = __fdividef(T, om);
+                    const float wgt = alpha * T;
+                    float ga = pc.x * (c.x - R0) + pc.y * (c.y - R1) + pc.z * (c.z - R2);
+                    if (EXTRA) ga += pe.x * (b.z - RD) + pe.y * (1.0f - RO);
+                    ga *= T;
+                    R0 = alpha * c.x + om * R0;
+                    R1 = alpha * c.y + om * R1;
+                    R2 = alpha * c.z + om * R2;
+                    if (EXTRA) {
+                        RD = alpha * b.z + om * RD;
+                        RO = alpha + om * RO;
+                    }
+                    const float gp = capped ? 0.0f : ga * alpha;
+                    v[0] = wgt * pc.x; v[1] = wgt * pc.y; v[2] = wgt * pc.z;
+                    v[3] = gp;
+                    v[4] = gp * dx; v[5] = gp * dy;
+                    v[6] = gp * dx * dx; v[7] = gp * dx * dy; v[8] = gp * dy * dy;
+                    if (EXTRA) v[9] = wgt * pe.x;
+                }
+                if (__any_sync(kFull, on)) {
+                    const float r = warp_transpose_reduce16(v);
+                    const int q = lane >> 1;
+                    if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1)) {
+                        const uint32_t g = W.qg[k];
+                        if (DET) G.part[((size_t)g * A.nblk + U.wb) * kNG + q] = r;
+                        else atomicAdd(G.g2d + (size_t)g * kNG + q, r);
+                    }
+                }
+            }
+            __syncwarp();
+            return;
+        }
+        if (exhausted && S > qhead + 30) break;
+        // 32 steps of the wavefront
+#pragma unroll 2
+        for (int j = 0; j < 32; j++) {
+            const int s = S + j;
+            if (lane == j) {
+                // done with hit s - 32: park its sums; take up hit s
+                if (cur) {
+                    W.st0[lane] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                    W.st1[lane] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                    W.st2[lane] = make_float2(acc[8], acc[9]);
+                    W.stg[lane] = cg;
+                }
+                cur = s < qhead;
+                if (cur) {
+                    const int k = s & (kPgQ - 1);
+                    c0 = W.q0[k]; c1 = W.q1[k]; c2 = W.q2[k];
+                    cpos = W.qpos[k];
+                    cg = W.qg[k];
+                }
+#pragma unroll
+                for (int q = 0; q < kNG; q++) acc[q] = 0.0f;
+            }
+            const int p = (s - lane) & 31;
+            const float4 c = W.pix[p];
+            const float2 xy = W.pxy[p];
+            float dx, dy, alpha;
+            bool capped;
+            if (cur && cpos < __float_as_uint(c.w) && pair_eval(c0, c1, xy.x, xy.y, dx, dy, alpha, capped)) {
+                const float om = 1.0f - alpha;
+                T = __fdividef(T, om);
+                const float wgt = alpha * T;
+                float ga = c.x * (c2.x - R0) + c.y * (c2.y - R1) + c.z * (c2.z - R2);
+                float2 e = make_float2(0.0f, 0.0f);
+                if (EXTRA) {
+                    e = W.pde[p];
+                    ga += e.x * (c1.z - RD) + e.y * (1.0f - RO);
+                }
+                ga *= T;
+                R0 = alpha * c2.x + om * R0;
+                R1 = alpha * c2.y + om * R1;
+                R2 = alpha * c2.z + om * R2;
+                if (EXTRA) {
+                    RD = alpha * c1.z + om * RD;
+                    RO = alpha + om * RO;
+                }
+                const float gp = capped ? 0.0f : ga * alpha;
+                acc[0] += wgt * c.x; acc[1] += wgt * c.y; acc[2] += wgt * c.z;
+                acc[3] += gp;
+                acc[4] += gp * dx; acc[5] += gp * dy;
+                acc[6] += gp * dx * dx; acc[7] += gp * dx * dy; acc[8] += gp * dy * dy;
+                if (EXTRA) acc[9] += wgt * e.x;
+            }
+            // the pixel's state moves on to the lane of the next hit
+            const int src = (lane + 31) & 31;
+            T = __shfl_sync(kFull, T, src);
+            R0 = __shfl_sync(kFull, R0, src);
+            R1 = __shfl_sync(kFull, R1, src);
+            R2 = __shfl_sync(kFull, R2, src);
+            if (EXTRA) {
+                RD = __shfl_sync(kFull, RD, src);
+                RO = __shfl_sync(kFull, RO, src);
+            }
+        }
+    }
+    // the hits still held by the lanes
+    if (cur) pg_flush<EXTRA, DET>(A, G, U.wb, cg, acc);
+    __syncwarp();
+}
+
+template <bool EXTRA, bool DET>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocksBwd)
+k_raster_bwd_pg(RasterArgs A, RasterGrad G)
+{
+    __shared__ PgWarp sw[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nunits = units_of(A, false);
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    while (u < nunits) {
+        bwd_item_pg<EXTRA, DET>(u, A, G, sw[w], lane);
+        if (!A.work) break;
+        u = next_unit(A.work, lane);
+    }
+}
+
 // Deterministic gradient sums: for each (view, Gaussian) pair, its instances
 // (emission indices dup_off .. dup_off + touched) and each instance's pixel
 // blocks in ascending order.
@@ -884,11 +1172,22 @@ void bwd_launch(const RasterArgs& A, const RasterGrad& G, int64_t units, bool pe
     k_raster_bwd<EXTRA, NB, D, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
 }
 
-template <bool EXTRA>
-void bwd_dispatch(int nb, int pd, bool det, const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent,
-                  cudaStream_t s)
+template <bool EXTRA, bool DET>
+void bwd_pg_launch(const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent, cudaStream_t s)
 {
-    if (det) {   // batch depth 32 only
+    const int variant = 64 + (DET ? 2 : 0) + (EXTRA ? 1 : 0);   // < 128
+    const int grid = grid_for(k_raster_bwd_pg<EXTRA, DET>, variant, units, persistent);
+    k_raster_bwd_pg<EXTRA, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
+}
+
+template <bool EXTRA>
+void bwd_dispatch(int nb, int pd, bool det, bool pg, const RasterArgs& A, const RasterGrad& G, int64_t units,
+                  bool persistent, cudaStream_t s)
+{
+    if (pg) {    // per-Gaussian: batch depth 32, one pixel per lane
+        if (det) bwd_pg_launch<EXTRA, true>(A, G, units, persistent, s);
+        else bwd_pg_launch<EXTRA, false>(A, G, units, persistent, s);
+    } else if (det) {   // batch depth 32 only
         if (pd == 1) bwd_launch<EXTRA, 1, 1, true>(A, G, units, persistent, s);
         else if (pd == 2) bwd_launch<EXTRA, 1, 2, true>(A, G, units, persistent, s);
         else bwd_launch<EXTRA, 1, 4, true>(A, G, units, persistent, s);
@@ -968,7 +1267,9 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
     GL_TRY(v.work.reserve(32));
     PhaseScope ps(v.prof, PH_RASTER_BWD, s);
     const bool det = v.det && v.ntiles > 0 && v.I != 0;
-    const int nblk = blocks_per_tile(v);
+    // the per-Gaussian backward works on 8x4 pixel blocks whatever the
+    // forward's pixels per lane
+    const int nblk = v.pg ? v.Ts * v.Ts / 32 : blocks_per_tile(v);
     if (!det) GL_CUDA_TRY(cudaMemsetAsync(v.g2d.p, 0, sizeof(float) * kNG * pairs, s));
     if (v.ntiles == 0 || v.I == 0) return GL_OK;
     int* work = nullptr;
@@ -976,7 +1277,8 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
         work = v.work.as<int>() + 1;
         GL_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int), s));
     }
-    const RasterArgs A = make_args(v, work);
+    RasterArgs A = make_args(v, work);
+    A.nblk = nblk;
     RasterGrad G{v.Tfin.as<float>(), v.ncon.as<uint32_t>(), dL_drgb, dL_ddepth, dL_dopac, v.g2d.as<float>(),
                  nullptr, v.sorted_inst};
     const size_t cap = v.itile.bytes / 4;
@@ -990,8 +1292,10 @@ gl_status raster_backward(View& v, const float* dL_drgb, const float* dL_ddepth,
         G.part = v.gpart.as<float>();
     }
     const int64_t units = work_items_bound(v) * nblk;
-    if (dL_ddepth != nullptr || dL_dopac != nullptr) bwd_dispatch<true>(v.nb, v.pd, det, A, G, units, v.persistent, s);
-    else bwd_dispatch<false>(v.nb, v.pd, det, A, G, units, v.persistent, s);
+    if (dL_ddepth != nullptr || dL_dopac != nullptr)
+        bwd_dispatch<true>(v.nb, v.pd, det, v.pg, A, G, units, v.persistent, s);
+    else
+        bwd_dispatch<false>(v.nb, v.pd, det, v.pg, A, G, units, v.persistent, s);
     count_launches(1);
     if (det) {
         const int blocks = (int)std::min<size_t>(8 * (size_t)sm_count(), (pairs + 255) / 256);

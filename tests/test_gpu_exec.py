@@ -80,7 +80,9 @@ def test_render_bit_identical_across_exec(ex):
                                      (16, dict(batch_depth=64, pixels_per_lane=4, persistent=1)),
                                      (16, dict(batch_depth=32, pixels_per_lane=1, persistent=0)),
                                      (32, dict(batch_depth=64, pixels_per_lane=2, persistent=0)),
-                                     (32, dict(batch_depth=32, pixels_per_lane=4, persistent=1))])
+                                     (32, dict(batch_depth=32, pixels_per_lane=4, persistent=1)),
+                                     (16, dict(batch_depth=32, pixels_per_lane=1, persistent=1, per_gaussian=1)),
+                                     (8, dict(batch_depth=64, pixels_per_lane=2, persistent=0, per_gaussian=1))])
 def test_window_step_parity_under_exec(tile, ex):
     """The mixed-resolution window step equals the oracle at the same tile
     size for every execution."""
@@ -98,14 +100,15 @@ def test_window_step_parity_under_exec(tile, ex):
         assert np.allclose(m.exposure(10 + i), st["p"]["E"][i], atol=1e-6)
 
 
-@pytest.mark.parametrize("tile,ppl,persistent", [(16, 1, 0), (16, 2, 1), (8, 1, 1)])
-def test_deterministic_steps_are_bit_identical(tile, ppl, persistent):
+@pytest.mark.parametrize("tile,ppl,persistent,pg", [(16, 1, 0, 0), (16, 2, 1, 0), (8, 1, 1, 0), (16, 1, 1, 1)])
+def test_deterministic_steps_are_bit_identical(tile, ppl, persistent, pg):
     """With the deterministic backward, eager and graph-replayed maps taking
     the same steps end bit-identical, and the first step equals the oracle."""
     params, cams, targets = _window_scene()
     maps = [_map(params), _map(params)]
     for m, graphs in zip(maps, (0, 1)):
-        m.set_exec(deterministic=1, use_graphs=graphs, tile_size=tile, pixels_per_lane=ppl, persistent=persistent)
+        m.set_exec(deterministic=1, use_graphs=graphs, tile_size=tile, pixels_per_lane=ppl, persistent=persistent,
+                   per_gaussian=pg)
     views = [(10 + i, cams[i], targets[i]) for i in range(3)]
     losses = [[m.optimize_step(views, want_loss=True) for _ in range(4)] for m in maps]
     assert losses[0] == losses[1]
@@ -117,7 +120,7 @@ def test_deterministic_steps_are_bit_identical(tile, ppl, persistent):
     assert maps[1].stats()["graph_replays"] == 3
     # one deterministic step against the oracle
     m = _map(params)
-    m.set_exec(deterministic=1, tile_size=tile, pixels_per_lane=ppl, persistent=persistent)
+    m.set_exec(deterministic=1, tile_size=tile, pixels_per_lane=ppl, persistent=persistent, per_gaussian=pg)
     m.optimize_step(views)
     st = oracle.new_window_state(params, 3)
     r = oracle.optimize_window(params, st, cams, targets, step=1, Ts=tile)

@@ -138,7 +138,8 @@ def test_loss_parity():
 
 @pytest.mark.parametrize("scene", SCENES)
 @pytest.mark.parametrize("extra", [False, True])
-def test_gradient_parity(scene, extra):
+@pytest.mark.parametrize("pg", [0, 1], ids=["per_pixel", "per_gaussian"])
+def test_gradient_parity(scene, extra, pg):
     sc = _scene(scene)
     cam = sc["cam"]
     pre, bins, img = oracle.forward(sc["params"], cam, 16)
@@ -152,6 +153,7 @@ def test_gradient_parity(scene, extra):
                         None if dO is None else dO.astype(np.float64))
     p = _dev(sc["params"])
     ctx = _ctx()
+    ctx.set_exec(per_gaussian=pg)
     ctx.forward(p, cam, 16)
     tt = lambda a: None if a is None else torch.from_numpy(a).cuda()
     gg, pose = ctx.backward(p, tt(dC), tt(dD), tt(dO))
@@ -213,7 +215,8 @@ def _edge_params(n, deg=0, seed=0):
 
 
 @pytest.mark.parametrize("case", ["empty", "one_pixel", "all_behind", "ragged", "single_big"])
-def test_edge_cases(case):
+@pytest.mark.parametrize("pg", [0, 1], ids=["per_pixel", "per_gaussian"])
+def test_edge_cases(case, pg):
     W, H = {"one_pixel": (1, 1), "ragged": (37, 23)}.get(case, (64, 48))
     cam = scenes.camera(W, H, 50.0)
     n = {"empty": 0, "single_big": 1}.get(case, 200)
@@ -226,6 +229,7 @@ def test_edge_cases(case):
     pre, bins, img = oracle.forward(params, cam, 16)
     p = _dev(params) if n else {k: torch.zeros((0,) + v.shape[1:], device="cuda") for k, v in params.items()}
     ctx = _ctx()
+    ctx.set_exec(per_gaussian=pg)
     rgb, dep, opa = ctx.forward(p, cam, 16)
     ok = img["ambiguous"] == 0
     assert np.abs(rgb.cpu().numpy() - img["color"])[ok].max() <= PIX_TOL
@@ -264,6 +268,11 @@ def test_invalid_arguments_are_rejected():
         ctx.forward(p, nanR, 16)
     with pytest.raises(binding.GLError, match="INVALID"):
         ctx.forward(p, cam, 12)
+    # every parameter array must start on 16 bytes (the kernels move rows in 16-byte pieces)
+    buf = torch.zeros(10 * 3 + 1, device="cuda")
+    shifted = dict(p, means=buf[1:].view(10, 3))
+    with pytest.raises(binding.GLError, match="INVALID"):
+        ctx.forward(shifted, cam, 16)
 
 
 def _window_scene():

@@ -62,7 +62,8 @@ def test_split_render_parity(scene, tile, ppl, seg, persistent):
 @pytest.mark.parametrize("scene", ["small_frustum", "diff_check"])
 @pytest.mark.parametrize("extra", [False, True])
 @pytest.mark.parametrize("det", [0, 1])
-def test_split_gradient_parity(scene, extra, det):
+@pytest.mark.parametrize("pg", [0, 1], ids=["per_pixel", "per_gaussian"])
+def test_split_gradient_parity(scene, extra, det, pg):
     from paper_2404_06926_gb300 import binding
     sc = getattr(scenes, scene)()
     cam = sc["cam"]
@@ -77,7 +78,7 @@ def test_split_gradient_parity(scene, extra, det):
                         None if dO is None else dO.astype(np.float64))
     p = _dev(sc["params"])
     ctx = binding.Ctx()
-    ctx.set_exec(segment=64, deterministic=det)
+    ctx.set_exec(segment=64, deterministic=det, per_gaussian=pg)
     ctx.forward(p, cam, 16)
     assert _split_tiles(ctx, cam, 16, 64) > 0
     tt = lambda a: None if a is None else torch.from_numpy(a).cuda()
@@ -88,8 +89,9 @@ def test_split_gradient_parity(scene, extra, det):
         assert np.all(a[~vis] == 0), name
         med, p99 = _rel(a[vis], g[name][vis])
         assert med < 1e-3 and p99 < 1e-2, (name, med, p99)
-    pose = pose.cpu().numpy()
-    assert np.linalg.norm(pose - g["pose"]) <= 1e-3 * np.linalg.norm(g["pose"])
+    pose = pose.cpu().numpy().astype(np.float64)
+    rel = np.abs(pose - g["pose"]) / np.maximum(np.abs(g["pose"]), 1e-4 * np.abs(g["pose"]).max())
+    assert np.median(rel) < 1e-3 and rel.max() < 1e-2, (pose, g["pose"], rel)
 
 
 def test_split_window_step_with_graphs_matches_oracle():
