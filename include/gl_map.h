@@ -201,7 +201,8 @@ GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t
  *                    end.  Ignored while timers are on.
  *   persistent       1: both raster kernels run one grid of resident warps
  *                    that take (tile, pixel block) units from a counter.
- *   batch_depth      records a warp stages per batch: 32 or 64.
+ *   batch_depth      records a warp stages per batch: 32, 64, 128 or 256
+ *                    (128 and 256 take one pixel per lane).
  *   pixels_per_lane  1, 2 or 4 pixels of a column per lane; 4 x this must
  *                    not exceed the tile size.
  *   tile_size        0: gl_config's; else 8, 16 or 32.
@@ -256,7 +257,7 @@ GL_API gl_status gl_map_get_exec(gl_map* map, gl_exec_config* exec);
  * representative of steps over different views).  Coordinate descent from
  * {graphs, persistent, batch depth 32, 1 pixel per lane, segment 1024,
  * per-pixel backward}: the tile size (8/16/32), the segment length
- * (0/256/512/1024), persistence, the batch depth (32/64), the pixels per
+ * (0/256/512/1024), persistence, the batch depth (32/64/128/256), the pixels per
  * lane (1/2/4) and the backward (per pixel / per Gaussian) in turn take the
  * value whose `reps` rounds of one step per window are fastest (CUDA
  * events) with the other knobs fixed; deterministic and exact_cull stay as

@@ -377,6 +377,14 @@ void se3_left_jacobian(const double xi[6], double Jl[36])
         }
 }
 
+// Records a raster warp stages per batch, in 32-record sub-batches.
+int batch_subs(int batch_depth, bool det)
+{
+    return det ? 1 : std::max(1, batch_depth / 32);
+}
+
+bool valid_batch_depth(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+
 bool is_device_ptr(const void* p)
 {
     if (!p) return false;
@@ -483,7 +491,8 @@ extern "C" gl_status gl_ctx_create(void* stream, gl_ctx** out)
 extern "C" gl_status gl_ctx_set_exec(gl_ctx* ctx, const gl_exec_config* e)
 {
     if (!ctx || !e) { set_error("null argument"); return GL_ERR_INVALID; }
-    if ((e->batch_depth != 32 && e->batch_depth != 64) || (e->deterministic != 0 && e->deterministic != 1) ||
+    if (!valid_batch_depth(e->batch_depth) || (e->batch_depth > 64 && e->pixels_per_lane != 1) ||
+        (e->deterministic != 0 && e->deterministic != 1) ||
         (e->pixels_per_lane != 1 && e->pixels_per_lane != 2 && e->pixels_per_lane != 4) ||
         (e->segment != 0 && (e->segment < 64 || e->segment > 65536 || (e->segment & (e->segment - 1)) != 0)) ||
         (e->exact_cull != 0 && e->exact_cull != 1) || (e->per_gaussian != 0 && e->per_gaussian != 1)) {
@@ -536,7 +545,7 @@ extern "C" gl_status gl_rasterize_forward(gl_ctx* ctx, const gl_gaussians* g, co
     if (!finite_all(cam.R, 9) || !finite_all(cam.t, 3)) { set_error("twisted pose is not finite"); return GL_ERR_INVALID; }
     for (int i = 0; i < 36; i++) c.pose_jac[i] = (float)Jl[i];
     c.view.det = c.exec.deterministic != 0;
-    c.view.nb = (c.exec.batch_depth == 64 && !c.view.det) ? 2 : 1;
+    c.view.nb = batch_subs(c.exec.batch_depth, c.view.det);
     c.view.pd = std::min(c.exec.pixels_per_lane, tile_size / 4);
     c.view.persistent = c.exec.persistent != 0;
     c.view.seg = c.exec.segment;
@@ -1050,7 +1059,7 @@ void apply_exec(gl_map* m)
 {
     View& v = m->ctx.view;
     v.det = m->exec.deterministic != 0;
-    v.nb = (m->exec.batch_depth == 64 && !v.det) ? 2 : 1;
+    v.nb = batch_subs(m->exec.batch_depth, v.det);
     v.pd = m->exec.pixels_per_lane;
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;
@@ -1398,7 +1407,11 @@ gl_status check_exec_config(const gl_map* m, const gl_exec_config& e)
         set_error("tile_size must be 0, 8, 16 or 32");
         return GL_ERR_INVALID;
     }
-    if (e.batch_depth != 32 && e.batch_depth != 64) { set_error("batch_depth must be 32 or 64"); return GL_ERR_INVALID; }
+    if (!valid_batch_depth(e.batch_depth)) { set_error("batch_depth must be 32, 64, 128 or 256"); return GL_ERR_INVALID; }
+    if (e.batch_depth > 64 && e.pixels_per_lane != 1) {
+        set_error("batch depths of 128 and 256 take one pixel per lane");
+        return GL_ERR_INVALID;
+    }
     if (e.deterministic != 0 && e.deterministic != 1) { set_error("deterministic must be 0 or 1"); return GL_ERR_INVALID; }
     if (e.exact_cull != 0 && e.exact_cull != 1) { set_error("exact_cull must be 0 or 1"); return GL_ERR_INVALID; }
     if (e.per_gaussian != 0 && e.per_gaussian != 1) { set_error("per_gaussian must be 0 or 1"); return GL_ERR_INVALID; }
@@ -1539,12 +1552,12 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
                           saved.exact_cull, 0};
     if (st == GL_OK) st = trial(best_e, &best_t);
     const int tile_vals[3] = {8, 16, 32}, seg_vals[4] = {0, 256, 512, 1024}, pers_vals[2] = {0, 1},
-              bd_vals[2] = {32, 64}, ppl_vals[3] = {1, 2, 4}, pg_vals[2] = {0, 1};
+              bd_vals[4] = {32, 64, 128, 256}, ppl_vals[3] = {1, 2, 4}, pg_vals[2] = {0, 1};
     struct Dim { int32_t gl_exec_config::*field; const int* vals; int n; };
     const Dim dims[6] = {{&gl_exec_config::tile_size, tile_vals, keep_tile_size ? 0 : 3},
                          {&gl_exec_config::segment, seg_vals, 4},
                          {&gl_exec_config::persistent, pers_vals, 2},
-                         {&gl_exec_config::batch_depth, bd_vals, saved.deterministic ? 1 : 2},
+                         {&gl_exec_config::batch_depth, bd_vals, saved.deterministic ? 1 : 4},
                          {&gl_exec_config::pixels_per_lane, ppl_vals, 3},
                          {&gl_exec_config::per_gaussian, pg_vals, 2}};
     for (const Dim& d : dims) {
@@ -1554,6 +1567,7 @@ extern "C" gl_status gl_map_autotune(gl_map* m, const gl_keyframe* views, int32_
             if (cand.*(d.field) == best_e.*(d.field)) continue;
             const int ts = cand.tile_size ? cand.tile_size : m->cfg.tile_size;
             if (4 * cand.pixels_per_lane > ts) continue;
+            if (cand.batch_depth > 64 && cand.pixels_per_lane != 1) continue;
             float ms = 0.0f;
             st = trial(cand, &ms);
             if (st == GL_OK && ms < best_t) {
@@ -1790,7 +1804,7 @@ cudaStream_t map_stream(const gl_map* m) { return m->stream; }
 
 void map_exec_knobs(const gl_map* m, View& v, int Ts)
 {
-    v.nb = (m->exec.batch_depth == 64 && !m->exec.deterministic) ? 2 : 1;
+    v.nb = batch_subs(m->exec.batch_depth, m->exec.deterministic != 0);
     v.pd = std::min(m->exec.pixels_per_lane, Ts / 4);
     v.persistent = m->exec.persistent != 0;
     v.seg = m->exec.segment;

@@ -53,11 +53,23 @@
 // the next unit from a counter; the number of units is read on the device.
 #include "gl_internal.h"
 
+#include <map>
+#include <mutex>
+
 namespace gl {
 
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+// Warps per CTA of the kernels that stage 32 NB records per warp: batches of
+// 128 and 256 records use 4 and 2 warps, so that every variant's staged hits
+// fit in 48 KB of shared memory with the same resident warps per SM.
+template <int NB>
+constexpr int wpb() { return NB <= 2 ? kWarpsPerBlock : 16 / NB; }
+// Prefetch slots (32 records each) of a batch of 32 NB records: the whole
+// next batch up to 64 records, one sub-batch ahead beyond.
+template <int NB>
+constexpr int pf_slots() { return NB <= 2 ? NB : 1; }
 // resident CTAs per SM the kernels are compiled for: the forward passes fit
 // 64 registers (4 CTAs); the backward is faster with 76 registers (3 CTAs)
 // than squeezed into 64
@@ -187,9 +199,10 @@ __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uin
                                             float4* sr2, uint32_t* spos, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
-    float4 n0[NB], n1[NB], n2[NB], n3[NB];
+    constexpr int PF = pf_slots<NB>();
+    float4 n0[PF], n1[PF], n2[PF], n3[PF];
 #pragma unroll
-    for (int q = 0; q < NB; q++) {
+    for (int q = 0; q < PF; q++) {
         const uint32_t i = a + q * 32 + lane;
         if (i < b) { n0[q] = A.s0[i]; n1[q] = A.s1[i]; n2[q] = A.s2[i]; n3[q] = A.s3[i]; }
     }
@@ -201,10 +214,11 @@ __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uin
         int nh = 0;
 #pragma unroll
         for (int q = 0; q < NB; q++) {
-            const float4 c0 = n0[q], c1 = n1[q], c2 = n2[q], c3 = n3[q];
+            const int sl = PF == NB ? q : 0;
+            const float4 c0 = n0[sl], c1 = n1[sl], c2 = n2[sl], c3 = n3[sl];
             const uint32_t i = base + q * 32 + lane;
-            const uint32_t ni = i + 32 * NB;
-            if (ni < b) { n0[q] = A.s0[ni]; n1[q] = A.s1[ni]; n2[q] = A.s2[ni]; n3[q] = A.s3[ni]; }
+            const uint32_t ni = i + 32 * PF;
+            if (ni < b) { n0[sl] = A.s0[ni]; n1[sl] = A.s1[ni]; n2[sl] = A.s2[ni]; n3[sl] = A.s3[ni]; }
             const bool hit = i < b && box_hit(c3, bx0, bx1, by0, by1);
             const unsigned mask = __ballot_sync(kFull, hit);
             if (hit) {
@@ -325,14 +339,15 @@ __device__ __forceinline__ void fwd_item(int u, const RasterArgs& A, const Raste
 }
 
 template <int NB, int D>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocks)
+__global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocks * kWarpsPerBlock / wpb<NB>())
 k_raster_fwd(RasterArgs A, RasterOut O)
 {
-    __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
-    __shared__ uint32_t spos[kWarpsPerBlock][32 * NB];
+    constexpr int WPB = wpb<NB>();
+    __shared__ float4 sr0[WPB][32 * NB], sr1[WPB][32 * NB], sr2[WPB][32 * NB];
+    __shared__ uint32_t spos[WPB][32 * NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nunits = units_of(A, false);
-    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * WPB + w;
     while (u < nunits) {
         fwd_item<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
         if (!A.work) break;
@@ -527,13 +542,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocks) k_seg_prefix(
 }
 
 template <int NB, int D>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocks) k_seg_replay(RasterArgs A)
+__global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocks * kWarpsPerBlock / wpb<NB>()) k_seg_replay(RasterArgs A)
 {
-    __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
-    __shared__ uint32_t spos[kWarpsPerBlock][32 * NB];
+    constexpr int WPB = wpb<NB>();
+    __shared__ float4 sr0[WPB][32 * NB], sr1[WPB][32 * NB], sr2[WPB][32 * NB];
+    __shared__ uint32_t spos[WPB][32 * NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nunits = units_of(A, true);
-    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * WPB + w;
     while (u < nunits) {
         replay_item<NB, D>(u, A, sr0[w], sr1[w], sr2[w], spos[w], lane);
         if (!A.work) break;
@@ -641,11 +657,12 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
     if (end <= U.rs) return;
     // batches from the back: [bstart, bstart + 32 NB) with bstart = end - 32 NB k, clipped at rs
     constexpr int BS = 32 * NB;
+    constexpr int PF = pf_slots<NB>();
     int64_t bstart = (int64_t)end - BS;
-    float4 n0[NB], n1[NB], n2[NB], n3[NB];
-    uint32_t ng[NB];
+    float4 n0[PF], n1[PF], n2[PF], n3[PF];
+    uint32_t ng[PF];
 #pragma unroll
-    for (int b = 0; b < NB; b++) {
+    for (int b = 0; b < PF; b++) {
         const int64_t i = bstart + b * 32 + lane;
         ng[b] = 0;
         if (i >= (int64_t)U.rs) {
@@ -657,13 +674,17 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
         int nh = 0;
 #pragma unroll
         for (int b = 0; b < NB; b++) {
-            const float4 c0 = n0[b], c1 = n1[b], c2 = n2[b], c3 = n3[b];
-            const uint32_t cg = ng[b];
+            const int sl = PF == NB ? b : 0;
+            const float4 c0 = n0[sl], c1 = n1[sl], c2 = n2[sl], c3 = n3[sl];
+            const uint32_t cg = ng[sl];
             const int64_t i = bstart + b * 32 + lane;
-            const int64_t ni = i - BS;
+            // next: the same sub-batch of the batch before (whole-batch
+            // prefetch), else the next sub-batch of this one, or the first
+            // of the batch before
+            const int64_t ni = PF == NB ? i - BS : (b < NB - 1 ? i + 32 : i + 32 - 2 * BS);
             if (ni >= (int64_t)U.rs) {
-                n0[b] = A.s0[ni]; n1[b] = A.s1[ni]; n2[b] = A.s2[ni]; n3[b] = A.s3[ni];
-                ng[b] = DET ? G.sinst[ni] : A.sgid[ni];
+                n0[sl] = A.s0[ni]; n1[sl] = A.s1[ni]; n2[sl] = A.s2[ni]; n3[sl] = A.s3[ni];
+                ng[sl] = DET ? G.sinst[ni] : A.sgid[ni];
             }
             const bool hit = i >= (int64_t)U.rs && box_hit(c3, L.bx0, L.bx1, L.by0, L.by1);
             const unsigned mask = __ballot_sync(kFull, hit);
@@ -724,14 +745,15 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
 }
 
 template <bool EXTRA, int NB, int D, bool DET>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocksBwd)
+__global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocksBwd * kWarpsPerBlock / wpb<NB>())
 k_raster_bwd(RasterArgs A, RasterGrad G)
 {
-    __shared__ float4 sr0[kWarpsPerBlock][32 * NB], sr1[kWarpsPerBlock][32 * NB], sr2[kWarpsPerBlock][32 * NB];
-    __shared__ uint32_t spos[kWarpsPerBlock][32 * NB], sg[kWarpsPerBlock][32 * NB];
+    constexpr int WPB = wpb<NB>();
+    __shared__ float4 sr0[WPB][32 * NB], sr1[WPB][32 * NB], sr2[WPB][32 * NB];
+    __shared__ uint32_t spos[WPB][32 * NB], sg[WPB][32 * NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nunits = units_of(A, false);
-    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * kWarpsPerBlock + w;
+    int u = A.work ? next_unit(A.work, lane) : blockIdx.x * WPB + w;
     while (u < nunits) {
         bwd_item<EXTRA, NB, D, DET>(u, A, G, sr0[w], sr1[w], sr2[w], spos[w], sg[w], lane);
         if (!A.work) break;
@@ -1080,21 +1102,34 @@ __global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __
     }
 }
 
-template <typename K>
-int grid_for(K kernel, int variant, int64_t units_bound, bool persistent)
+// Resident CTAs of a kernel on the current device (SMs x CTAs per SM),
+// looked up once per (kernel, device).
+int resident_ctas(const void* kernel, int threads)
 {
-    const int64_t need = std::max<int64_t>(1, (units_bound + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({kernel, dev});
+    if (it != cache.end()) return it->second;
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    const int r = std::max(1, sm_count() * std::max(1, per));
+    cache[{kernel, dev}] = r;
+    return r;
+}
+
+// Grid of `wpb`-warp CTAs for up to units_bound warp units: one unit per
+// warp, or (persistent) the resident CTAs, whose warps take units from a
+// counter.
+template <typename K>
+int grid_for(K kernel, int64_t units_bound, bool persistent, int wpb = kWarpsPerBlock)
+{
+    const int64_t need = std::max<int64_t>(1, (units_bound + wpb - 1) / wpb);
     if (!persistent) return (int)std::min<int64_t>(need, 0x7fffffff);
-    // resident CTAs of this variant, looked up once per process
-    static int cache[128] = {};
-    if (!cache[variant]) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32 * kWarpsPerBlock, 0);
-        cache[variant] = std::max(1, sms * std::max(1, per));
-    }
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, cache[variant]));
+    const int res = resident_ctas(reinterpret_cast<const void*>(kernel), 32 * wpb);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, res));
 }
 
 int blocks_per_tile(const View& v) { return v.Ts * v.Ts / (32 * v.pd); }
@@ -1130,7 +1165,14 @@ RasterArgs make_args(View& v, int* work)
 gl_status check_exec(const View& v)
 {
     if (v.Ts != 8 && v.Ts != 16 && v.Ts != 32) { set_error("tile_size must be 8, 16 or 32"); return GL_ERR_INVALID; }
-    if (v.nb != 1 && v.nb != 2) { set_error("batch depth must be 32 or 64"); return GL_ERR_INVALID; }
+    if (v.nb != 1 && v.nb != 2 && v.nb != 4 && v.nb != 8) {
+        set_error("batch depth must be 32, 64, 128 or 256");
+        return GL_ERR_INVALID;
+    }
+    if (v.nb > 2 && v.pd != 1) {
+        set_error("batch depths of 128 and 256 take one pixel per lane");
+        return GL_ERR_INVALID;
+    }
     if ((v.pd != 1 && v.pd != 2 && v.pd != 4) || 4 * v.pd > v.Ts) {
         set_error("pixels per lane must be 1, 2 or 4, with 4 x pixels per lane <= tile size");
         return GL_ERR_INVALID;
@@ -1148,35 +1190,32 @@ void fwd_launch(const RasterArgs& A, const RasterOut& O, int64_t units, int64_t 
 {
     RasterArgs a1 = A;
     a1.work = work;
-    k_raster_fwd<NB, D><<<grid_for(k_raster_fwd<NB, D>, (NB - 1) * 4 + D, units, persistent), 32 * kWarpsPerBlock,
-                          0, s>>>(a1, O);
+    k_raster_fwd<NB, D><<<grid_for(k_raster_fwd<NB, D>, units, persistent, wpb<NB>()), 32 * wpb<NB>(), 0, s>>>(a1,
+                                                                                                             O);
     if (split_units > 0) {
         // persistent grids take units from counters 2-4
         RasterArgs a2 = A, a3 = A, a4 = A;
         a2.work = work ? work + 2 : nullptr;
         a3.work = work ? work + 3 : nullptr;
         a4.work = work ? work + 4 : nullptr;
-        k_seg_prefix<D><<<grid_for(k_seg_prefix<D>, 80 + D, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a2);
-        k_seg_replay<NB, D><<<grid_for(k_seg_replay<NB, D>, 88 + (NB - 1) * 4 + D, split_units, persistent),
-                              32 * kWarpsPerBlock, 0, s>>>(a3);
-        k_seg_finish<D><<<grid_for(k_seg_finish<D>, 100 + D, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(
-            a4, O);
+        k_seg_prefix<D><<<grid_for(k_seg_prefix<D>, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a2);
+        k_seg_replay<NB, D><<<grid_for(k_seg_replay<NB, D>, split_units, persistent, wpb<NB>()), 32 * wpb<NB>(), 0,
+                              s>>>(a3);
+        k_seg_finish<D><<<grid_for(k_seg_finish<D>, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a4, O);
     }
 }
 
 template <bool EXTRA, int NB, int D, bool DET>
 void bwd_launch(const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent, cudaStream_t s)
 {
-    const int variant = 32 + (DET ? 16 : 0) + (EXTRA ? 8 : 0) + (NB - 1) * 4 + D;   // < 64
-    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D, DET>, variant, units, persistent);
-    k_raster_bwd<EXTRA, NB, D, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
+    const int grid = grid_for(k_raster_bwd<EXTRA, NB, D, DET>, units, persistent, wpb<NB>());
+    k_raster_bwd<EXTRA, NB, D, DET><<<grid, 32 * wpb<NB>(), 0, s>>>(A, G);
 }
 
 template <bool EXTRA, bool DET>
 void bwd_pg_launch(const RasterArgs& A, const RasterGrad& G, int64_t units, bool persistent, cudaStream_t s)
 {
-    const int variant = 64 + (DET ? 2 : 0) + (EXTRA ? 1 : 0);   // < 128
-    const int grid = grid_for(k_raster_bwd_pg<EXTRA, DET>, variant, units, persistent);
+    const int grid = grid_for(k_raster_bwd_pg<EXTRA, DET>, units, persistent);
     k_raster_bwd_pg<EXTRA, DET><<<grid, 32 * kWarpsPerBlock, 0, s>>>(A, G);
 }
 
@@ -1191,6 +1230,10 @@ void bwd_dispatch(int nb, int pd, bool det, bool pg, const RasterArgs& A, const 
         if (pd == 1) bwd_launch<EXTRA, 1, 1, true>(A, G, units, persistent, s);
         else if (pd == 2) bwd_launch<EXTRA, 1, 2, true>(A, G, units, persistent, s);
         else bwd_launch<EXTRA, 1, 4, true>(A, G, units, persistent, s);
+    } else if (nb == 4) {   // deeper batches: one pixel per lane
+        bwd_launch<EXTRA, 4, 1, false>(A, G, units, persistent, s);
+    } else if (nb == 8) {
+        bwd_launch<EXTRA, 8, 1, false>(A, G, units, persistent, s);
     } else if (nb == 1) {
         if (pd == 1) bwd_launch<EXTRA, 1, 1, false>(A, G, units, persistent, s);
         else if (pd == 2) bwd_launch<EXTRA, 1, 2, false>(A, G, units, persistent, s);
@@ -1244,7 +1287,11 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     RasterOut O{rgb, depth, opac, v.Tfin.as<float>(), v.ncon.as<uint32_t>()};
     const int nblk = blocks_per_tile(v);
     const int64_t units = work_items_bound(v) * nblk, split_units = split * nblk;
-    if (v.nb == 1) {
+    if (v.nb == 4) {
+        fwd_launch<4, 1>(A, O, units, split_units, v.persistent, work, s);
+    } else if (v.nb == 8) {
+        fwd_launch<8, 1>(A, O, units, split_units, v.persistent, work, s);
+    } else if (v.nb == 1) {
         if (v.pd == 1) fwd_launch<1, 1>(A, O, units, split_units, v.persistent, work, s);
         else if (v.pd == 2) fwd_launch<1, 2>(A, O, units, split_units, v.persistent, work, s);
         else fwd_launch<1, 4>(A, O, units, split_units, v.persistent, work, s);

@@ -23,7 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 EXECS = [dict(batch_depth=bd, pixels_per_lane=pp, persistent=pe)
-         for bd in (32, 64) for pp in (1, 2, 4) for pe in (0, 1)]
+         for bd in (32, 64) for pp in (1, 2, 4) for pe in (0, 1)] + \
+        [dict(batch_depth=bd, pixels_per_lane=1, persistent=pe) for bd in (128, 256) for pe in (0, 1)]
 
 
 def _map(params, tile=16):
@@ -82,7 +83,9 @@ def test_render_bit_identical_across_exec(ex):
                                      (32, dict(batch_depth=64, pixels_per_lane=2, persistent=0)),
                                      (32, dict(batch_depth=32, pixels_per_lane=4, persistent=1)),
                                      (16, dict(batch_depth=32, pixels_per_lane=1, persistent=1, per_gaussian=1)),
-                                     (8, dict(batch_depth=64, pixels_per_lane=2, persistent=0, per_gaussian=1))])
+                                     (8, dict(batch_depth=64, pixels_per_lane=2, persistent=0, per_gaussian=1)),
+                                     (16, dict(batch_depth=128, pixels_per_lane=1, persistent=1)),
+                                     (32, dict(batch_depth=256, pixels_per_lane=1, persistent=0))])
 def test_window_step_parity_under_exec(tile, ex):
     """The mixed-resolution window step equals the oracle at the same tile
     size for every execution."""
@@ -184,7 +187,8 @@ def test_autotune_picks_a_valid_config_and_restores_the_map():
     best, ms = m.autotune(views, reps=2)
     assert ms > 0
     assert best["use_graphs"] == 1 and best["tile_size"] in (8, 16, 32)
-    assert best["batch_depth"] in (32, 64) and best["pixels_per_lane"] in (1, 2, 4)
+    assert best["batch_depth"] in (32, 64, 128, 256) and best["pixels_per_lane"] in (1, 2, 4)
+    assert best["batch_depth"] <= 64 or best["pixels_per_lane"] == 1
     assert 4 * best["pixels_per_lane"] <= best["tile_size"]
     assert m.get_exec() == best
     after = m.get_params()

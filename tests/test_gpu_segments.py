@@ -134,3 +134,28 @@ def test_split_window_step_with_graphs_matches_oracle():
     pa, pb = a.get_params(), b.get_params()
     for k in pa:
         assert np.array_equal(pa[k], pb[k]), k
+
+
+@pytest.mark.parametrize("scene", ["small_frustum", "diff_check"])
+@pytest.mark.parametrize("bd", [128, 256])
+def test_deep_batches_render_and_gradients(scene, bd):
+    """Batches of 128 and 256 records per warp (segments of 64, so the split
+    tiles' replay pass runs them too): pixels and gradients equal the oracle."""
+    from paper_2404_06926_gb300 import binding
+    sc = getattr(scenes, scene)()
+    cam = sc["cam"]
+    pre, bins, img = oracle.forward(sc["params"], cam, 16)
+    H, W = cam["height"], cam["width"]
+    dC = (np.random.default_rng(22).normal(size=(H, W, 3)) * 1e-3).astype(np.float32)
+    g = oracle.backward(sc["params"], cam, pre, bins, dC.astype(np.float64))
+    p = _dev(sc["params"])
+    ctx = binding.Ctx()
+    ctx.set_exec(segment=64, batch_depth=bd, persistent=1)
+    rgb, _, _ = ctx.forward(p, cam, 16)
+    ok = img["ambiguous"] == 0
+    assert np.abs(rgb.cpu().numpy() - img["color"])[ok].max() <= PIX_TOL
+    gg, _ = ctx.backward(p, torch.from_numpy(dC).cuda())
+    vis = pre["radius"] > 0
+    for name in ("means", "log_scales", "quats", "logits", "sh"):
+        med, p99 = _rel(gg[name].cpu().numpy()[vis], g[name][vis])
+        assert med < 1e-3 and p99 < 1e-2, (name, med, p99)

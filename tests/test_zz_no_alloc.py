@@ -12,6 +12,7 @@ that an image beyond the array's limit is rejected.  Collected last on
 purpose.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -52,13 +53,23 @@ def test_noalloc_loss_matches_allocating_entry_point_and_oracle_twice():
     # warm-up: the first call on a device may load the library's device code
     assert _call(lib, *cases[0][1], cases[0][2], stream) == 0
     torch.cuda.synchronize()
-    used0 = torch.cuda.memory_allocated()
-    free0 = torch.cuda.mem_get_info()[0]
-    for host, dev, out in cases:      # two calls in a row, on different sizes
-        assert _call(lib, *dev, out, stream) == 0, lib.gl_last_error()
-    torch.cuda.synchronize()
-    assert torch.cuda.memory_allocated() == used0
-    assert torch.cuda.mem_get_info()[0] == free0
+    # objects left by earlier tests free device memory when collected: collect
+    # them now and keep the collector off while memory is measured
+    gc.collect()
+    gc.disable()
+    try:
+        torch.cuda.synchronize()
+        used0 = torch.cuda.memory_allocated()
+        free0 = torch.cuda.mem_get_info()[0]
+        for host, dev, out in cases:      # two calls in a row, on different sizes
+            assert _call(lib, *dev, out, stream) == 0, lib.gl_last_error()
+        torch.cuda.synchronize()
+        used1 = torch.cuda.memory_allocated()
+        free1 = torch.cuda.mem_get_info()[0]
+    finally:
+        gc.enable()
+    assert used1 == used0
+    assert free1 == free0, (free0, free1)
     for (C, T, E), dev, out in cases:
         l_na, dC_na, dE_na = (x.cpu().numpy().astype(np.float64) for x in out)
         l_ref, dC_ref, dE_ref = ctx.loss(*dev)
