@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kPreThreads)
 k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int Ts, bool cull,
              float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
              float4* __restrict__ rec3, int* __restrict__ radius, int4* __restrict__ rect,
-             uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey, uint32_t* __restrict__ gidx,
+             uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
              unsigned long long* __restrict__ kmask, uint64_t* __restrict__ ctl)
 {
     // t indexes (view, Gaussian) pairs: t = view * n + g
@@ -91,7 +91,6 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
     float ls[3] = {p.log_scales[3 * g], p.log_scales[3 * g + 1], p.log_scales[3 * g + 2]};
     const float4 q4 = reinterpret_cast<const float4*>(p.quats)[g];
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    gidx[t] = (uint32_t)t;
     Decision D;
     if (!decide(mu, ls, q, p.logits[g], cam, Ts, TX, TY, D)) {
         radius[t] = 0;
@@ -208,14 +207,23 @@ __device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v)
 // Digit counts of all passes (scratch counts and counters zeroed before) and
 // clearing of the look-back words of the tiles (tile_keys keys each) this
 // sort visits.  A thread loads kOsHistKeys keys before counting any of them.
+// With n_kept (zeroed before), keys 0xffffffff are left out of the counts and
+// the number of the other keys is added to *n_kept.  For 32-bit keys the top
+// digit takes few values (float keys of one range), so equal top digits of a
+// warp are counted with one shared atomic.
 constexpr int kOsHistKeys = 16;
 __global__ void __launch_bounds__(kOsThreads)
 k_os_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int passes, int tile_keys,
-          int64_t tiles_max, uint32_t* __restrict__ scratch)
+          int64_t tiles_max, uint32_t* __restrict__ scratch, unsigned long long* __restrict__ n_kept)
 {
     __shared__ uint32_t h[kOsMaxPasses * 256];
+    __shared__ unsigned long long s_kept;
     const uint64_t n = *n_dev;
+    const bool drop = n_kept != nullptr;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
     for (int i = threadIdx.x; i < kOsMaxPasses * 256; i += kOsThreads) h[i] = 0;
+    if (threadIdx.x == 0) s_kept = 0;
+    uint32_t kept = 0;
     const uint64_t nt = (n + tile_keys - 1) / tile_keys;
     const uint64_t gsz = (uint64_t)gridDim.x * kOsThreads;
     const uint64_t gid = (uint64_t)blockIdx.x * kOsThreads + threadIdx.x;
@@ -240,16 +248,31 @@ k_os_hist(const uint32_t* __restrict__ kin, const uint64_t* n_dev, int passes, i
 #pragma unroll
         for (int j = 0; j < kOsHistKeys; j++) {
             const bool ok = b + ((uint64_t)(j / 4) * kOsThreads + threadIdx.x) * 4 + (j % 4) < n;
-            if (ok)
+            const bool use = ok && !(drop && k[j] == 0xffffffffu);
+            kept += use;
+            if (passes == kOsMaxPasses) {   // uniform: every lane reaches the match
+                if (use)
+                    for (int p = 0; p < kOsMaxPasses - 1; p++) atomicAdd(&h[p * 256 + ((k[j] >> (8 * p)) & 255u)], 1u);
+                const int dt = use ? (int)(k[j] >> 24) : -1;
+                const unsigned peers = __match_any_sync(kFull, dt);
+                if (use && (peers & lt) == 0) atomicAdd(&h[3 * 256 + dt], (uint32_t)__popc(peers));
+            } else if (use) {
                 for (int p = 0; p < passes; p++) atomicAdd(&h[p * 256 + ((k[j] >> (8 * p)) & 255u)], 1u);
+            }
         }
+    }
+    if (drop) {
+        for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(kFull, kept, o);
+        if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&s_kept, (unsigned long long)kept);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += kOsThreads)
         if (h[i]) atomicAdd(&scratch[i], h[i]);
+    if (drop && threadIdx.x == 0 && s_kept) atomicAdd(n_kept, s_kept);
 }
 
-// One pass over tiles of NT x ITEMS keys; threads 0..255 own one digit each
+// One pass over tiles of NT x ITEMS keys (values 0, 1, 2, ... when vin is
+// null; keys 0xffffffff left out when `drop`); threads 0..255 own one digit each
 // in the per-digit phases (count, look-back, offsets).  Keys are ranked
 // within a warp item by item: the lanes holding digit d set their bits in a
 // shared mask word of d, read it back (the lanes below them with the same
@@ -259,7 +282,7 @@ template <int NT, int ITEMS, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
           uint32_t* __restrict__ vout, const uint64_t* n_dev, int pass, int64_t tiles_max,
-          uint32_t* __restrict__ scratch, unsigned long long* __restrict__ err)
+          uint32_t* __restrict__ scratch, unsigned long long* __restrict__ err, bool drop)
 {
     static_assert(NT >= 256 && NT % 32 == 0, "a thread per digit");
     constexpr int TILE = NT * ITEMS;
@@ -299,12 +322,12 @@ k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, ui
         const uint64_t idx = base + (uint64_t)w * (32 * ITEMS) + j * 32 + lane;
         const bool ok = idx < n;
         kk[j] = ok ? kin[idx] : 0u;
-        vv[j] = ok ? vin[idx] : 0u;
+        vv[j] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
         const uint64_t idx = base + (uint64_t)w * (32 * ITEMS) + j * 32 + lane;
-        const int d = idx < n ? (int)((kk[j] >> shift) & 255u) : 256;
+        const int d = (idx < n && !(drop && kk[j] == 0xffffffffu)) ? (int)((kk[j] >> shift) & 255u) : 256;
         if (d < 256) atomicOr(&wmask[w][d], 1u << lane);
         __syncwarp();
         const unsigned peers = d < 256 ? wmask[w][d] : 0u;
@@ -388,7 +411,7 @@ k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, ui
     }
     if (owner) gbase[tid] = gex + prefix - ex;   // output index = gbase[d] + position in the digit-sorted tile
     __syncthreads();
-    const int tn = (int)min((uint64_t)TILE, n - base);
+    const int tn = (int)tot;   // the tile's keys that were ranked
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
         const int i = tid + j * NT;
@@ -407,9 +430,10 @@ k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, ui
 // Scan of instance counts in depth order and duplication of the instances.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads)
-k_scan_count(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched, int64_t n,
+k_scan_count(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched, const uint64_t* n_dev,
              uint64_t* __restrict__ bsum)
 {
+    const int64_t n = (int64_t)*n_dev;
     __shared__ uint64_t sm[kPreThreads / 32 + 1];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
     uint64_t s = 0;
@@ -448,16 +472,48 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint6
     }
 }
 
+// Position of the n-th (0-based) set bit of m; m has more than n set bits.
+// Halving search: at width w, skip the low w bits when they hold n or fewer.
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        const int c = __popcll(m & ((1ull << w) - 1ull));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Emission of the instances.  The instances of consecutive Gaussians in
+// depth order are consecutive, so the kScanBlock Gaussians of a CTA own one
+// contiguous output run, which the CTA writes thread by thread (coalesced,
+// and balanced over the CTA however many tiles one Gaussian covers): output
+// e of the run belongs to the last Gaussian whose offset is <= e (binary
+// search over the CTA's offsets in shared memory) and is its (e - offset)-th
+// kept tile in row-major rectangle order.  A Gaussian's instances are
+// written only if all of them fit in `cap`.
+static_assert(kScanBlock == 1024, "the emission search takes 10 halvings");
+
 __global__ void __launch_bounds__(kPreThreads)
 k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched,
-            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int64_t n,
+            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, const uint64_t* n_dev,
             const ViewDesc* __restrict__ views, int64_t per_view, uint64_t cap,
             const unsigned long long* __restrict__ kmask,
-            uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile, uint32_t* __restrict__ ival,
-            uint32_t* __restrict__ iowner)
+            uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile, uint32_t* __restrict__ iowner)
 {
     __shared__ uint64_t sm[kPreThreads / 32 + 1];
+    __shared__ uint32_t s_off[kScanBlock + 1];   // run offsets; [kScanBlock] = run length
+    __shared__ uint32_t s_g[kScanBlock];
+    __shared__ uint32_t s_t0[kScanBlock];        // tile of the rectangle's first cell
+    __shared__ uint32_t s_wt[kScanBlock];        // rectangle width | tiles per row << 16
+    __shared__ unsigned long long s_km[kScanBlock];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    const int64_t n = (int64_t)*n_dev;
     uint32_t gg[kScanItems], cc[kScanItems];
     uint64_t s = 0;
 #pragma unroll
@@ -468,31 +524,43 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
         s += cc[k];
     }
     uint64_t tot;
-    uint64_t off = bsum[blockIdx.x] + block_exclusive_scan<uint64_t, kPreThreads>(s, sm, &tot);
+    const uint64_t bbase = bsum[blockIdx.x];
+    uint64_t o = block_exclusive_scan<uint64_t, kPreThreads>(s, sm, &tot);
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        if (base + k >= n) break;
+        const int li = threadIdx.x * kScanItems + k;
         const uint32_t g = gg[k];
-        dup_off[g] = (uint32_t)off;
-        if (cc[k] && off + cc[k] <= cap) {
+        s_off[li] = (uint32_t)o;
+        s_g[li] = g;
+        if (base + k < n) dup_off[g] = (uint32_t)(bbase + o);
+        if (cc[k]) {
             const int4 r = rect[g];
             const ViewDesc& vd = views[g / per_view];
-            const int TX = vd.TX, base = vd.tile_base;
-            // the exact culling's decisions, as the preprocess took them (its
-            // bit mask; all ones when the rectangle is not culled)
-            const unsigned long long km = kmask[g];
-            uint64_t d = off;
-            int i = 0;
-            for (int ty = r.y; ty < r.w; ty++)
-                for (int tx = r.x; tx < r.z; tx++, i++) {
-                    if (i < 64 && !((km >> i) & 1ull)) continue;
-                    itile[d] = (uint32_t)(base + ty * TX + tx);
-                    ival[d] = (uint32_t)d;
-                    iowner[d] = g;
-                    d++;
-                }
+            s_t0[li] = (uint32_t)(vd.tile_base + r.y * vd.TX + r.x);
+            s_wt[li] = (uint32_t)(r.z - r.x) | ((uint32_t)vd.TX << 16);
+            s_km[li] = kmask[g];
         }
-        off += cc[k];
+        o += cc[k];
+    }
+    if (threadIdx.x == 0) s_off[kScanBlock] = (uint32_t)tot;
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < (uint32_t)tot; e += kPreThreads) {
+        int lo = 0, hi = kScanBlock;   // s_off[lo] <= e < s_off[hi]
+#pragma unroll
+        for (int it = 0; it < 10; it++) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= e) lo = mid; else hi = mid;
+        }
+        const uint32_t first = s_off[lo], cnt = s_off[lo + 1] - first;
+        const uint64_t d = bbase + e;
+        if (bbase + first + cnt > cap) continue;
+        const uint32_t i = e - first;
+        const unsigned long long km = s_km[lo];
+        const int p = km == ~0ull ? (int)i : nth_set_bit(km, (int)i);
+        const uint32_t wt = s_wt[lo];
+        const uint32_t rw = wt & 0xffffu, TX = wt >> 16;
+        itile[d] = s_t0[lo] + (uint32_t)(p / rw) * TX + (uint32_t)(p % rw);
+        iowner[d] = s_g[lo];
     }
 }
 
@@ -500,58 +568,92 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
 // longest-processing-time first), so long tiles start early instead of
 // forming the tail.  Order within a bucket is arbitrary; tiles are
 // independent, so results do not depend on it.
-__device__ __forceinline__ void tile_order_block(const uint32_t* __restrict__ ranges, int ntiles,
-                                                 uint32_t* __restrict__ order)
-{
-    __shared__ uint32_t cnt[33], off[33];
-    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        const int b = 32 - __clz(len);   // 0 for empty, 1..32 otherwise
-        atomicAdd(&cnt[32 - b], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int b = 0; b < 33; b++) { off[b] = s; s += cnt[b]; }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        const int b = 32 - __clz(len);
-        order[atomicAdd(&off[32 - b], 1u)] = (uint32_t)t;
-    }
-}
-
+//
 // Work items of the raster kernels, in tile launch order: one per tile, or,
 // for a tile whose list holds at least 2 seg records, one per segment of
 // seg records (seg a power of two, so such tiles sit in the log2 buckets
 // ahead of all others and their items come first).  item = (tile,
 // segment); count[6] = items, count[7] = items of split tiles.  One CTA of
-// 1024 threads computes the tile launch order first, then the items.
+// 1024 threads computes the tile launch order first, then the items.  With
+// SMEM the list lengths and the order stay in shared memory (8 bytes per
+// tile), so that the ranges are read once and nothing is read back.
+constexpr int kOrderSmemTiles = 24576;   // 192 KB of shared memory
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_order_items(const uint32_t* __restrict__ ranges, int ntiles, int seg,
                                                       uint32_t* __restrict__ order, uint2* __restrict__ items,
                                                       uint64_t* __restrict__ count)
 {
-    tile_order_block(ranges, ntiles, order);
-    __syncthreads();   // the block's writes of order are visible to all its threads
+    extern __shared__ uint32_t dyn[];   // SMEM: list length [ntiles] | order [ntiles]
+    __shared__ uint32_t cnt[33], off[33];
     __shared__ uint32_t sm[1024 / 32 + 1];
     __shared__ uint32_t seg_end;
+    uint32_t* slen = dyn;
+    uint32_t* sord = dyn + ntiles;
+    const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) seg_end = 0;
+    __syncthreads();
+    // bucket b = clz(length): 0 for the longest lists, 32 for empty ones
+    constexpr int U = 4;   // lengths loaded before any is counted
+    for (int t0 = threadIdx.x; t0 < ntiles; t0 += 1024 * U) {
+        uint32_t L[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = t0 + u * 1024;
+            L[u] = 0;
+            if (t < ntiles) {
+                const uint2 r = r2[t];
+                L[u] = r.y - r.x;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = t0 + u * 1024;
+            if (t < ntiles) {
+                if (SMEM) slen[t] = L[u];
+                atomicAdd(&cnt[__clz(L[u])], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 0; b < 33; b++) { off[b] = acc; acc += cnt[b]; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += 1024) {
+        uint32_t L;
+        if (SMEM) {
+            L = slen[t];
+        } else {
+            const uint2 r = r2[t];
+            L = r.y - r.x;
+        }
+        const uint32_t pos = atomicAdd(&off[__clz(L)], 1u);
+        order[pos] = (uint32_t)t;
+        if (SMEM) sord[pos] = (uint32_t)t;
+    }
+    __syncthreads();   // the block's writes of order are visible to all its threads
     uint32_t carry = 0;
     for (int base = 0; base < ntiles; base += 1024) {
         const int k = base + threadIdx.x;
         uint32_t t = 0, nseg = 0;
         if (k < ntiles) {
-            t = order[k];
-            const uint32_t L = ranges[2 * t + 1] - ranges[2 * t];
+            uint32_t L;
+            if (SMEM) {
+                t = sord[k];
+                L = slen[t];
+            } else {
+                t = order[k];
+                const uint2 r = r2[t];
+                L = r.y - r.x;
+            }
             nseg = (seg > 0 && L >= 2u * (uint32_t)seg) ? (L + seg - 1) / seg : 1u;
         }
         uint32_t tot;
-        const uint32_t off = carry + block_exclusive_scan<uint32_t, 1024>(nseg, sm, &tot);
-        for (uint32_t j = 0; j < nseg; j++) items[off + j] = make_uint2(t, j);
-        if (nseg > 1) atomicMax(&seg_end, off + nseg);
+        const uint32_t off0 = carry + block_exclusive_scan<uint32_t, 1024>(nseg, sm, &tot);
+        for (uint32_t j = 0; j < nseg; j++) items[off0 + j] = make_uint2(t, j);
+        if (nseg > 1) atomicMax(&seg_end, off0 + nseg);
         carry += tot;
     }
     __syncthreads();
@@ -661,8 +763,17 @@ gl_status build_items(View& v, cudaStream_t s)
 {
     GL_TRY(v.items.reserve(sizeof(uint2) * (size_t)std::max<int64_t>(work_items_bound(v), 1)));
     GL_TRY(v.tile_order.reserve(4 * (size_t)std::max(v.ntiles, 1)));
-    k_order_items<<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.seg, v.tile_order.as<uint32_t>(),
-                                     v.items.as<uint2>(), v.count.as<uint64_t>());
+    if (v.ntiles <= kOrderSmemTiles) {
+        const int bytes = 8 * std::max(v.ntiles, 1);
+        GL_TRY(ensure_smem_limit(reinterpret_cast<const void*>(&k_order_items<true>), bytes));
+        k_order_items<true><<<1, 1024, bytes, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.seg,
+                                                   v.tile_order.as<uint32_t>(), v.items.as<uint2>(),
+                                                   v.count.as<uint64_t>());
+    } else {
+        k_order_items<false><<<1, 1024, 0, s>>>(v.ranges.as<uint32_t>(), v.ntiles, v.seg,
+                                                v.tile_order.as<uint32_t>(), v.items.as<uint2>(),
+                                                v.count.as<uint64_t>());
+    }
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;
@@ -670,7 +781,8 @@ gl_status build_items(View& v, cudaStream_t s)
 
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          const uint64_t* n_dev, int64_t n_max, int64_t n_reserve, int bits, DevBuf& scratch,
-                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s)
+                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s, bool index_values,
+                         uint64_t* n_kept)
 {
     const int passes = std::max(1, std::min(kOsMaxPasses, (bits + 7) / 8));
     // look-back words sized for the larger of this sort and its reserve, so
@@ -688,12 +800,18 @@ gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
     const int64_t tiles = std::max<int64_t>(1, (n_max + tile_keys - 1) / tile_keys);
     const int hblocks = (int)std::min<int64_t>(
         4 * (int64_t)sm_count(), std::max<int64_t>(1, (n_max + kOsThreads * kOsHistKeys - 1) / (kOsThreads * kOsHistKeys)));
-    k_os_hist<<<hblocks, kOsThreads, 0, s>>>(k0, n_dev, passes, tile_keys, tiles_max, sc);
+    unsigned long long* kept = reinterpret_cast<unsigned long long*>(n_kept);
+    if (kept) GL_CUDA_TRY(cudaMemsetAsync(kept, 0, sizeof(uint64_t), s));
+    k_os_hist<<<hblocks, kOsThreads, 0, s>>>(k0, n_dev, passes, tile_keys, tiles_max, sc, kept);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     unsigned long long* err = reinterpret_cast<unsigned long long*>(ctl + 8);
     for (int p = 0; p < passes; p++) {
-        k_os_pass<kOsThreads, kOsItems, 3><<<(unsigned)tiles, kOsThreads, 0, s>>>(ki, vi, ko, vo, n_dev, p, tiles_max,
-                                                                                  sc, err);
+        const uint32_t* vsrc = (p == 0 && index_values) ? nullptr : vi;
+        // the first pass drops the 0xffffffff keys; the later ones sort the rest
+        const uint64_t* np = (p > 0 && n_kept) ? n_kept : n_dev;
+        k_os_pass<kOsThreads, kOsItems, 3><<<(unsigned)tiles, kOsThreads, 0, s>>>(ki, vsrc, ko, vo, np, p,
+                                                                                  tiles_max, sc, err,
+                                                                                  p == 0 && n_kept);
         std::swap(ki, ko);
         std::swap(vi, vo);
     }
@@ -735,7 +853,7 @@ gl_status sort_wait_selftest(int32_t* expired)
     GL_CUDA_TRY(cudaMemcpy(scratch.as<uint32_t>() + kOsTicketOff, &one, sizeof(one), cudaMemcpyHostToDevice));
     k_os_pass<kOsThreads, kOsItems, 3><<<1, kOsThreads>>>(keys.as<uint32_t>(), vals.as<uint32_t>(), kout.as<uint32_t>(),
                                                          vout.as<uint32_t>(), c, 0, tiles_max, scratch.as<uint32_t>(),
-                                                         reinterpret_cast<unsigned long long*>(c + 8));
+                                                         reinterpret_cast<unsigned long long*>(c + 8), false);
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     GL_CUDA_TRY(cudaDeviceSynchronize());
@@ -896,21 +1014,23 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     PhaseScope ps(v.prof, PH_PREPROCESS, s);
     count_launches(1);
     switch (p.deg) {
-        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
-        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
-        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
-        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 0: k_preprocess<0><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 1: k_preprocess<1><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 2: k_preprocess<2><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
+        case 3: k_preprocess<3><<<grid, kPreThreads, 0, s>>>(p, dv, n, Ts, v.cull, v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(), v.rec3.as<float4>(), v.radius.as<int>(), v.rect.as<int4>(), v.touched.as<uint32_t>(), v.dkey.as<uint32_t>(), v.kmask.as<unsigned long long>(), count); break;
         default: set_error("sh_degree must be 0..3"); return GL_ERR_INVALID;
     }
     GL_CUDA_TRY(cudaGetLastError());
     }
 
-    // depth order of the Gaussians (culled ones carry key 0xffffffff and go last)
+    // depth order of the Gaussians; the culled ones (key 0xffffffff) are
+    // dropped, count[9] = the Gaussians left
     uint32_t *sk, *sv;
     {
         PhaseScope ps(v.prof, PH_DEPTH_SORT, s);
         GL_TRY(radix_sort_u32(v.dkey.as<uint32_t>(), v.gidx.as<uint32_t>(), v.dkey2.as<uint32_t>(),
-                              v.gidx2.as<uint32_t>(), count + 2, n, n, 32, v.hist, count, &sk, &sv, s));
+                              v.gidx2.as<uint32_t>(), count + 2, n, n, 32, v.hist, count, &sk, &sv, s,
+                              true, count + 9));
     }
     v.sorted_g = sv;
 
@@ -921,7 +1041,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         return GL_ERR_INVALID;
     }
     PhaseScope ps_scan(v.prof, PH_SCAN_DUP, s);
-    k_scan_count<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), n, v.bsum.as<uint64_t>());
+    k_scan_count<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), count + 9, v.bsum.as<uint64_t>());
     k_scan_top<<<1, 1024, 0, s>>>(v.bsum.as<uint64_t>(), nb, cap, count);
     count_launches(2);
     GL_CUDA_TRY(cudaGetLastError());
@@ -954,9 +1074,10 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     }
     const uint64_t cap2 = v.itile.bytes / 4;
     k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
-                                           v.bsum.as<uint64_t>(), n, dv, p.n, cap2, v.kmask.as<unsigned long long>(),
+                                           v.bsum.as<uint64_t>(), count + 9, dv, p.n, cap2,
+                                           v.kmask.as<unsigned long long>(),
                                            v.dup_off.as<uint32_t>(),
-                                           v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.iowner.as<uint32_t>());
+                                           v.itile.as<uint32_t>(), v.iowner.as<uint32_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     ps_scan.close();
@@ -972,7 +1093,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         PhaseScope ps(v.prof, PH_TILE_SORT, s);
         GL_TRY(radix_sort_u32(v.itile.as<uint32_t>(), v.ival.as<uint32_t>(), v.itile2.as<uint32_t>(),
                               v.ival2.as<uint32_t>(), count, nmax, (int64_t)cap2, tbits, v.hist, count, &sk, &sv,
-                              s));
+                              s, true));
     }
     v.sorted_tile = sk;
     v.sorted_inst = sv;

@@ -145,7 +145,7 @@ struct View {
     DevBuf radius;            // int
     DevBuf rect;              // int4 (x0,y0,x1,y1), tiles local to the view
     DevBuf touched;           // u32
-    DevBuf dkey, gidx;        // u32 depth key, u32 index (sort input)
+    DevBuf dkey, gidx;        // u32 depth key (sort input); u32 index (sort output buffer)
     DevBuf dkey2, gidx2;      // sort ping-pong
     DevBuf dup_off;           // u32 offset of the Gaussian's first instance
     DevBuf kmask;             // u64 kept-tile mask of the rectangle (all ones if it is not culled)
@@ -157,9 +157,10 @@ struct View {
                               // work items [6], segment items [7], bounded device
                               // waits that gave up [8] (bit 0: radix-sort look-back,
                               // bit 1: parameter staging; sticky until
-                              // sort_wait_status reads it)
+                              // sort_wait_status reads it), Gaussians left after
+                              // the depth sort drops the culled ones [9]
     // per instance
-    DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort)
+    DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort; input ids implied)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id
     DevBuf srec0, srec1, srec2, srec3;  // records in sorted-instance order
     DevBuf sgid;              // u32 owning (view, Gaussian) per sorted instance
@@ -296,10 +297,14 @@ gl_status apply_exposure(const float* src, float* dst, const float E[12], int64_
 // Stable radix sort of (u32 key, u32 value) pairs over bits [0, bits); n on
 // the device, at most n_max; scratch sized for max(n_max, n_reserve) keys;
 // ctl[8] is raised if a look-back wait gave up.  Returns in *out_k/*out_v the
-// buffers holding the result.
+// buffers holding the result.  index_values: the input values are 0..n-1 and
+// v0 is not read (it still serves as an output buffer).  n_kept (device, may
+// be null): keys 0xffffffff are dropped from the result, whose length is
+// written to *n_kept.
 gl_status radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                          const uint64_t* n_dev, int64_t n_max, int64_t n_reserve, int bits, DevBuf& scratch,
-                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s);
+                         uint64_t* ctl, uint32_t** out_k, uint32_t** out_v, cudaStream_t s,
+                         bool index_values = false, uint64_t* n_kept = nullptr);
 // Bytes of the counters copied to View::h_count (count[0..8]).
 constexpr size_t kCountCopy = 9 * sizeof(uint64_t);
 // GL_ERR_TIMEOUT (once) if a radix-sort pass gave up a look-back wait, as

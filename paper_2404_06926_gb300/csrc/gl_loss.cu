@@ -277,6 +277,7 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
 // null): block 0 over [0, nblk) -> loss_out, dE_out.  Views: block v over the
 // view's loss tiles -> loss_v[v] (unweighted) and, if the view has Em, one
 // Adam step of its exposure on the (already weighted) gradient.
+constexpr int kRedBatch = 8;
 __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, int H, float lambda,
                              float* __restrict__ loss_out, float* __restrict__ dE_out,
                              const ViewDesc* __restrict__ views, float* __restrict__ loss_v, float b1,
@@ -300,8 +301,20 @@ __global__ void k_loss_final(const float* __restrict__ part, int nblk, int W, in
     }
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < kNP) {
+        // lane sums of partials lane, lane + 32, ... in that order; kRedBatch
+        // loads in flight before they are added
         double acc = 0.0;
-        for (int i = lane; i < nblk; i += 32) acc += part[(size_t)(begin + i) * kNP + k];
+        for (int i0 = lane; i0 < nblk; i0 += 32 * kRedBatch) {
+            float x[kRedBatch];
+#pragma unroll
+            for (int b = 0; b < kRedBatch; b++) {
+                const int i = i0 + 32 * b;
+                x[b] = i < nblk ? part[(size_t)(begin + i) * kNP + k] : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < kRedBatch; b++)
+                if (i0 + 32 * b < nblk) acc += x[b];
+        }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
         if (lane == 0) tot[k] = acc;
     }

@@ -197,9 +197,19 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
         constexpr int N4 = WIDTH * kPG / 4;
 #pragma unroll 4
         for (int c = lane; c < N4; c += 32) {
+            // rows and columns of the four elements: one division, then the
+            // column steps by one and wraps into the next row
             const int e0 = 4 * c;
-            const int r0 = e0 / WIDTH, r3 = (e0 + 3) / WIDTH;
-            const uint32_t rows = (upd >> r0) & ((2u << (r3 - r0)) - 1u);
+            int rr[4], ww[4];
+            rr[0] = e0 / WIDTH;
+            ww[0] = e0 - rr[0] * WIDTH;
+#pragma unroll
+            for (int k = 1; k < 4; k++) {
+                const bool wrap = ww[k - 1] + 1 == WIDTH;
+                ww[k] = wrap ? 0 : ww[k - 1] + 1;
+                rr[k] = rr[k - 1] + (wrap ? 1 : 0);
+            }
+            const uint32_t rows = (upd >> rr[0]) & ((2u << (rr[3] - rr[0])) - 1u);
             if (!rows) continue;
             float pe[4], me[4], ve[4];
             if (MODE == 1) {
@@ -212,7 +222,7 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const int e = e0 + k, r = e / WIDTH, w = e - r * WIDTH;
+                const int r = rr[k], w = ww[k];
                 const float g = sR[r * NR + off + w];
                 if (MODE == 0) pe[k] = (upd >> r) & 1u ? g : 0.0f;
                 else if ((upd >> r) & 1u) adam1(pe[k], me[k], ve[k], g, w < 3 ? lr0 : lr, ad);
@@ -526,8 +536,16 @@ __global__ void k_pose_reduce(const float* __restrict__ part, int npart, Jac6 J,
     __shared__ double gsum[6];
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < 6) {
+        // partials lane, lane + 32, ... in that order, 8 loads in flight
         double acc = 0.0;
-        for (int i = lane; i < npart; i += 32) acc += part[i * 6 + k];
+        for (int i0 = lane; i0 < npart; i0 += 256) {
+            float x[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) x[b] = i0 + 32 * b < npart ? part[(size_t)(i0 + 32 * b) * 6 + k] : 0.0f;
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+                if (i0 + 32 * b < npart) acc += x[b];
+        }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
         if (lane == 0) gsum[k] = acc;
     }
