@@ -182,12 +182,13 @@ __device__ __forceinline__ void stage_span(const float* __restrict__ src, int64_
 // Adam (MODE 1) or the gradient write-out (MODE 0) over one array's span:
 // element e of the span is row e / WIDTH, column e % WIDTH; the parameter
 // comes from the staged rows, m and v from global memory (already asked of
-// the L2), the gradient from the row's gradient (columns from `off`).  Whole blocks go by float4 (a float4 may straddle
-// rows; the elements of rows left alone are written back unchanged), the
-// partial block element by element.  Rows whose bit in `upd` is clear are
-// left untouched.  The first three columns take lr0 (the SH DC band), the
-// rest lr.
-template <int MODE, int WIDTH, int NR>
+// the L2), the gradient from the row's gradient (columns from `off`).  Whole
+// blocks go by float4 (a float4 may straddle rows; the elements of rows left
+// alone are written back unchanged), the partial block element by element.
+// Rows whose bit in `upd` is clear are left untouched (FULL: every row of a
+// whole block is updated, and no row is tested).  On the SH span (WIDTH > 4)
+// the first three columns take lr0 (the DC band), the rest lr.
+template <int MODE, int WIDTH, int NR, bool FULL = false>
 __device__ __forceinline__ void span_update(float* __restrict__ P, float* __restrict__ Mg, float* __restrict__ Vg,
                                             int64_t g0, int cnt, const float* sP, const float* sR, int off,
                                             uint32_t upd, float lr, float lr0, const AdamArgs& ad, int lane)
@@ -209,7 +210,7 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
                 ww[k] = wrap ? 0 : ww[k - 1] + 1;
                 rr[k] = rr[k - 1] + (wrap ? 1 : 0);
             }
-            const uint32_t rows = (upd >> rr[0]) & ((2u << (rr[3] - rr[0])) - 1u);
+            const uint32_t rows = FULL ? 1u : (upd >> rr[0]) & ((2u << (rr[3] - rr[0])) - 1u);
             if (!rows) continue;
             float pe[4], me[4], ve[4];
             if (MODE == 1) {
@@ -224,8 +225,8 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
             for (int k = 0; k < 4; k++) {
                 const int r = rr[k], w = ww[k];
                 const float g = sR[r * NR + off + w];
-                if (MODE == 0) pe[k] = (upd >> r) & 1u ? g : 0.0f;
-                else if ((upd >> r) & 1u) adam1(pe[k], me[k], ve[k], g, w < 3 ? lr0 : lr, ad);
+                if (MODE == 0) pe[k] = (FULL || ((upd >> r) & 1u)) ? g : 0.0f;
+                else if (FULL || ((upd >> r) & 1u)) adam1(pe[k], me[k], ve[k], g, (WIDTH > 4 && w < 3) ? lr0 : lr, ad);
             }
             reinterpret_cast<float4*>(P + base)[c] = make_float4(pe[0], pe[1], pe[2], pe[3]);
             if (MODE == 1) {
@@ -506,15 +507,30 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         }
         __syncwarp();
     }
-    span_update<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sMu, sR, 0, upd, ad.lr_pos, ad.lr_pos, ad,
-                             lane);
-    span_update<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sLs, sR, 3, upd,
-                             ad.lr_scale, ad.lr_scale, ad, lane);
-    span_update<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sQ, sR, 6, upd, ad.lr_rot, ad.lr_rot, ad,
-                             lane);
-    span_update<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sLg, sR, 10, upd, ad.lr_op, ad.lr_op,
-                             ad, lane);
-    span_update<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sSH, sR, 11, upd, ad.lr_rest, ad.lr_dc, ad, lane);
+    // every row of a whole block updated: the spans skip the row tests
+    if (upd == kFull && cnt == kPG) {
+        span_update<MODE, 3, NR, true>(out.means, ad.m.means, ad.v.means, g0, cnt, sMu, sR, 0, upd, ad.lr_pos,
+                                       ad.lr_pos, ad, lane);
+        span_update<MODE, 3, NR, true>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sLs, sR, 3, upd,
+                                       ad.lr_scale, ad.lr_scale, ad, lane);
+        span_update<MODE, 4, NR, true>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sQ, sR, 6, upd, ad.lr_rot,
+                                       ad.lr_rot, ad, lane);
+        span_update<MODE, 1, NR, true>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sLg, sR, 10, upd, ad.lr_op,
+                                       ad.lr_op, ad, lane);
+        span_update<MODE, KF, NR, true>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sSH, sR, 11, upd, ad.lr_rest, ad.lr_dc,
+                                        ad, lane);
+    } else {
+        span_update<MODE, 3, NR>(out.means, ad.m.means, ad.v.means, g0, cnt, sMu, sR, 0, upd, ad.lr_pos, ad.lr_pos,
+                                 ad, lane);
+        span_update<MODE, 3, NR>(out.log_scales, ad.m.log_scales, ad.v.log_scales, g0, cnt, sLs, sR, 3, upd,
+                                 ad.lr_scale, ad.lr_scale, ad, lane);
+        span_update<MODE, 4, NR>(out.quats, ad.m.quats, ad.v.quats, g0, cnt, sQ, sR, 6, upd, ad.lr_rot, ad.lr_rot,
+                                 ad, lane);
+        span_update<MODE, 1, NR>(out.logits, ad.m.logits, ad.v.logits, g0, cnt, sLg, sR, 10, upd, ad.lr_op,
+                                 ad.lr_op, ad, lane);
+        span_update<MODE, KF, NR>(out.sh, ad.m.sh, ad.v.sh, g0, cnt, sSH, sR, 11, upd, ad.lr_rest, ad.lr_dc, ad,
+                                  lane);
+    }
 
     if (MODE == 0 && pose_part) {
 #pragma unroll

@@ -77,6 +77,7 @@ constexpr int kMinBlocks = 4;
 constexpr int kMinBlocksBwd = 3;
 constexpr int kNG = 10;   // screen-space gradient slots per Gaussian
 constexpr int kSegFields = 16;  // per (segment item, pixel): see below
+constexpr int kSegBatch = 4;    // segments whose state one load round trip brings (prefix, finish)
 
 // segstate fields of a segment item.  After the segment pass: 0 T_s, 1-3
 // colour, 4 depth, 5 opacity, 6 last position (as bits); 7 the incoming
@@ -374,30 +375,33 @@ __device__ __forceinline__ void prefix_item(int u, const RasterArgs& A, int lane
         float Tb = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, oo = 0.f;
         uint32_t last = 0;
         int stop = ns;
-        // segment s's seven fields are loaded during segment s - 1, so that
-        // the serial walk waits for memory once rather than once per segment
-        float f[7], nf[7];
+        // the seven fields of kSegBatch segments are loaded before any of
+        // them is used, so that the serial walk waits for memory once per
+        // kSegBatch segments
+        for (int s0 = 0; s0 < ns && stop == ns; s0 += kSegBatch) {
+            float f[kSegBatch][7];
 #pragma unroll
-        for (int k = 0; k < 7; k++) f[k] = S[seg_at(w0, k, q, TS)];
-        for (int s = 0; s < ns; s++) {
-            const int ws = w0 + s;
-            if (s + 1 < ns) {
+            for (int b = 0; b < kSegBatch; b++)
+                if (s0 + b < ns) {
 #pragma unroll
-                for (int k = 0; k < 7; k++) nf[k] = S[seg_at(ws + 1, k, q, TS)];
+                    for (int k = 0; k < 7; k++) f[b][k] = S[seg_at(w0 + s0 + b, k, q, TS)];
+                }
+#pragma unroll
+            for (int b = 0; b < kSegBatch; b++) {
+                const int s = s0 + b;
+                if (s >= ns || stop != ns) break;
+                const float Ts = f[b][0];
+                S[seg_at(w0 + s, 7, q, TS)] = Tb;
+                if (__fmul_rn(Tb, Ts) < kTransMin) { stop = s; break; }
+                c0 += Tb * f[b][1];
+                c1 += Tb * f[b][2];
+                c2 += Tb * f[b][3];
+                dd += Tb * f[b][4];
+                oo += Tb * f[b][5];
+                const uint32_t ls = __float_as_uint(f[b][6]);
+                if (ls) last = ls;
+                Tb = __fmul_rn(Tb, Ts);
             }
-            const float Ts = f[0];
-            S[seg_at(ws, 7, q, TS)] = Tb;
-            if (__fmul_rn(Tb, Ts) < kTransMin) { stop = s; break; }
-            c0 += Tb * f[1];
-            c1 += Tb * f[2];
-            c2 += Tb * f[3];
-            dd += Tb * f[4];
-            oo += Tb * f[5];
-            const uint32_t ls = __float_as_uint(f[6]);
-            if (ls) last = ls;
-            Tb = __fmul_rn(Tb, Ts);
-#pragma unroll
-            for (int k = 0; k < 7; k++) f[k] = nf[k];
         }
         S[seg_at(w0, 8, q, TS)] = __uint_as_float((uint32_t)stop);
         S[seg_at(w0, 9, q, TS)] = Tb;
@@ -499,31 +503,35 @@ __device__ __forceinline__ void finish_item(int u, const RasterArgs& A, const Ra
         const int jl = stop < ns ? stop : ns - 1;
         for (int s = ns - 1; s > jl; s--)
             for (int k = 0; k < 6; k++) S[seg_at(w0 + s, k, q, TS)] = 0.0f;
-        // back to front from the stop segment; segment s - 1's fields
-        // (0-5 and the incoming transmittance, 7) are loaded during segment s
+        // back to front from the stop segment; the fields (0-5 and the
+        // incoming transmittance, 7) of kSegBatch segments are loaded before
+        // any of them is used
         float R0 = 0.f, R1 = 0.f, R2 = 0.f, RD = 0.f, RO = 0.f;
-        float f[7], nf[7];
+        for (int s0 = jl; s0 >= 0; s0 -= kSegBatch) {
+            float f[kSegBatch][7];
 #pragma unroll
-        for (int k = 0; k < 6; k++) f[k] = S[seg_at(w0 + jl, k, q, TS)];
-        f[6] = S[seg_at(w0 + jl, 7, q, TS)];
-        for (int s = jl; s >= 0; s--) {
-            const int ws = w0 + s;
-            if (s > 0) {
+            for (int b = 0; b < kSegBatch; b++)
+                if (s0 - b >= 0) {
 #pragma unroll
-                for (int k = 0; k < 6; k++) nf[k] = S[seg_at(ws - 1, k, q, TS)];
-                nf[6] = S[seg_at(ws - 1, 7, q, TS)];
+                    for (int k = 0; k < 6; k++) f[b][k] = S[seg_at(w0 + s0 - b, k, q, TS)];
+                    f[b][6] = S[seg_at(w0 + s0 - b, 7, q, TS)];
+                }
+#pragma unroll
+            for (int b = 0; b < kSegBatch; b++) {
+                const int s = s0 - b;
+                if (s < 0) break;
+                const int ws = w0 + s;
+                const float Ts = f[b][0], cs0 = f[b][1], cs1 = f[b][2], cs2 = f[b][3], ds = f[b][4], os = f[b][5];
+                const float tin = f[b][6];
+                S[seg_at(ws, 0, q, TS)] = __fmul_rn(tin, Ts);
+                S[seg_at(ws, 1, q, TS)] = R0;
+                S[seg_at(ws, 2, q, TS)] = R1;
+                S[seg_at(ws, 3, q, TS)] = R2;
+                S[seg_at(ws, 4, q, TS)] = RD;
+                S[seg_at(ws, 5, q, TS)] = RO;
+                R0 = cs0 + Ts * R0; R1 = cs1 + Ts * R1; R2 = cs2 + Ts * R2;
+                RD = ds + Ts * RD; RO = os + Ts * RO;
             }
-            const float Ts = f[0], cs0 = f[1], cs1 = f[2], cs2 = f[3], ds = f[4], os = f[5], tin = f[6];
-            S[seg_at(ws, 0, q, TS)] = __fmul_rn(tin, Ts);
-            S[seg_at(ws, 1, q, TS)] = R0;
-            S[seg_at(ws, 2, q, TS)] = R1;
-            S[seg_at(ws, 3, q, TS)] = R2;
-            S[seg_at(ws, 4, q, TS)] = RD;
-            S[seg_at(ws, 5, q, TS)] = RO;
-            R0 = cs0 + Ts * R0; R1 = cs1 + Ts * R1; R2 = cs2 + Ts * R2;
-            RD = ds + Ts * RD; RO = os + Ts * RO;
-#pragma unroll
-            for (int k = 0; k < 7; k++) f[k] = nf[k];
         }
     }
 }
