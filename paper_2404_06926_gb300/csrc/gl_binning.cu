@@ -22,6 +22,7 @@ namespace {
 constexpr int kPreThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kPreThreads * kScanItems;   // 1024 Gaussians per scan block
+constexpr int kDupChunk = 4096;   // instances one duplication CTA writes at most
 
 // Block-wide exclusive scan (NT threads); returns the exclusive prefix and
 // writes the block total to *total.  `sm` needs NT/32 + 1 entries.
@@ -172,7 +173,9 @@ __global__ void k_set_u64(uint64_t* p, uint64_t v0, uint64_t v1)
 // and Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
 // 2016; the one-histogram-then-one-kernel-per-digit layout is the "Onesweep"
 // sort of Adinets and Merrill, 2022).  Keys then leave the tile in digit
-// order, so consecutive threads write consecutive addresses.
+// order, so consecutive threads write consecutive addresses.  A pass whose
+// digit is the same for every key (one non-empty histogram bin, seen on the
+// device) copies its tiles through instead.
 //
 // Scratch (u32 words): global digit counts [pass][256] | tile counters
 // [pass] | look-back words [pass][tiles][256], each (flag << 30 | count):
@@ -307,10 +310,25 @@ k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, ui
     }
     // global digit offsets (while the tile counter answers)
     uint32_t tot;
-    const uint32_t gex = block_exclusive_scan<uint32_t, NT>(owner ? scratch[pass * 256 + tid] : 0u, sm, &tot);
+    const uint32_t dcount = owner ? scratch[pass * 256 + tid] : 0u;
+    const uint32_t gex = block_exclusive_scan<uint32_t, NT>(dcount, sm, &tot);
+    // one digit holds every key: the stable pass keeps the order, so the
+    // tile is copied through (no ranking, no look-back)
+    const bool same = __syncthreads_or(n > 0 && (uint64_t)dcount == n);
     const uint32_t t = s_tile;
     if (t >= nt) return;
     const uint64_t base = (uint64_t)t * TILE;
+    if (same) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const uint64_t idx = base + (uint64_t)j * NT + tid;
+            if (idx < n) {
+                kout[idx] = kin[idx];
+                vout[idx] = vin ? vin[idx] : (uint32_t)idx;
+            }
+        }
+        return;
+    }
     const unsigned lt = (1u << lane) - 1u;
 
     // load (warp w holds the contiguous run [w * 32 * ITEMS, ...)) and rank
@@ -446,25 +464,42 @@ k_scan_count(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums.  count[3] = instances needed; if they
-// fit in `cap` (and in 32 bits) count[0] = that number and count[1] = 0,
-// else count[0] = 0 (nothing downstream runs) and count[1] = 1.
+// Duplication parts of a scan block with x instances: one per kDupChunk of
+// them, at least one.
+__device__ __forceinline__ uint64_t dup_parts(uint64_t x)
+{
+    return x > (uint64_t)kDupChunk ? (x + kDupChunk - 1) / kDupChunk : 1ull;
+}
+
+// Exclusive scan of the block sums (bsum[0, nb)) and of the blocks'
+// duplication parts (bsum[nb, 2 nb); count[10] = all parts).  count[3] =
+// instances needed; if they fit in `cap` (and in 32 bits) count[0] = that
+// number and count[1] = 0, else count[0] = 0 (nothing downstream runs) and
+// count[1] = 1.
 __global__ void __launch_bounds__(1024) k_scan_top(uint64_t* bsum, int nb, uint64_t cap,
                                                    uint64_t* count)
 {
     __shared__ uint64_t sm[33];
     const int per = (nb + 1023) / 1024;
     const int b = min(nb, (int)threadIdx.x * per), e = min(nb, b + per);
-    uint64_t s = 0;
-    for (int i = b; i < e; i++) s += bsum[i];
-    uint64_t tot;
+    uint64_t s = 0, su = 0;
+    for (int i = b; i < e; i++) {
+        s += bsum[i];
+        su += dup_parts(bsum[i]);
+    }
+    uint64_t tot, totu;
     uint64_t ex = block_exclusive_scan<uint64_t, 1024>(s, sm, &tot);
+    uint64_t exu = block_exclusive_scan<uint64_t, 1024>(su, sm, &totu);
+    uint64_t* uoff = bsum + nb;
     for (int i = b; i < e; i++) {
         uint64_t x = bsum[i];
         bsum[i] = ex;
+        uoff[i] = exu;
         ex += x;
+        exu += dup_parts(x);
     }
     if (threadIdx.x == 0) {
+        count[10] = totu;
         const bool ovf = tot > cap || tot > 0xffffffffull;
         count[0] = ovf ? 0ull : tot;
         count[1] = ovf ? 1ull : 0ull;
@@ -490,50 +525,84 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, int n)
 }
 
 // Emission of the instances.  The instances of consecutive Gaussians in
-// depth order are consecutive, so the kScanBlock Gaussians of a CTA own one
-// contiguous output run, which the CTA writes thread by thread (coalesced,
-// and balanced over the CTA however many tiles one Gaussian covers): output
-// e of the run belongs to the last Gaussian whose offset is <= e (binary
-// search over the CTA's offsets in shared memory) and is its (e - offset)-th
-// kept tile in row-major rectangle order.  A Gaussian's instances are
-// written only if all of them fit in `cap`.
+// depth order are consecutive, so a scan block's kScanBlock Gaussians own
+// one contiguous output run.  The nearest Gaussians -- the first in depth
+// order, the largest on screen -- cover the most tiles, so a run can be
+// tens of times the average: it is cut into parts of kDupChunk outputs, one
+// CTA each (the parts' offsets come from k_scan_top).  A CTA finds its
+// block (a 32-way search over the part offsets by warp 0, one load round
+// trip per level), reloads and scans the block's counts, and writes its
+// part thread by thread (coalesced): output e belongs to the last Gaussian
+// whose offset is <= e (binary search over the block's offsets in shared
+// memory) and is its (e - offset)-th kept tile in row-major rectangle
+// order.  A Gaussian's instances are written only if all of them fit in
+// `cap`; the CTA holding its first output writes its offset.
 static_assert(kScanBlock == 1024, "the emission search takes 10 halvings");
+
+// Largest b < nb with off[b] <= e (off non-decreasing, off[0] = 0 <= e), in
+// every lane of the calling warp.
+__device__ __forceinline__ int find_block(const uint64_t* __restrict__ off, int nb, uint64_t e, int lane)
+{
+    int lo = 0, hi = nb;   // off[lo] <= e; the answer is in [lo, hi)
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int idx = lo + lane * step;
+        const bool le = idx < hi && off[idx] <= e;
+        const unsigned m = __ballot_sync(kFull, le);
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
 
 __global__ void __launch_bounds__(kPreThreads)
 k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ touched,
-            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, const uint64_t* n_dev,
-            const ViewDesc* __restrict__ views, int64_t per_view, uint64_t cap,
+            const int4* __restrict__ rect, const uint64_t* __restrict__ bsum, int nb, const uint64_t* n_dev,
+            const uint64_t* __restrict__ count, const ViewDesc* __restrict__ views, int64_t per_view, uint64_t cap,
             const unsigned long long* __restrict__ kmask,
             uint32_t* __restrict__ dup_off, uint32_t* __restrict__ itile, uint32_t* __restrict__ iowner)
 {
     __shared__ uint64_t sm[kPreThreads / 32 + 1];
-    __shared__ uint32_t s_off[kScanBlock + 1];   // run offsets; [kScanBlock] = run length
+    __shared__ uint32_t s_off[kScanBlock + 1];   // run offsets in the scan block; [kScanBlock] = its total
     __shared__ uint32_t s_g[kScanBlock];
     __shared__ uint32_t s_t0[kScanBlock];        // tile of the rectangle's first cell
     __shared__ uint32_t s_wt[kScanBlock];        // rectangle width | tiles per row << 16
     __shared__ unsigned long long s_km[kScanBlock];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    __shared__ int s_b;
+    const uint64_t part = blockIdx.x;
+    if (part >= count[10]) return;
     const int64_t n = (int64_t)*n_dev;
+    const uint64_t* uoff = bsum + nb;
+    if (threadIdx.x < 32) {
+        const int b = find_block(uoff, nb, part, threadIdx.x);
+        if (threadIdx.x == 0) s_b = b;
+    }
+    __syncthreads();
+    const int b = s_b;
+    const uint64_t bbase = bsum[b];
+    const int64_t base = (int64_t)b * kScanBlock + threadIdx.x * kScanItems;
     uint32_t gg[kScanItems], cc[kScanItems];
     uint64_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        int64_t j = base + k;
+        const int64_t j = base + k;
         gg[k] = j < n ? sorted_g[j] : 0u;
         cc[k] = j < n ? touched[gg[k]] : 0u;
         s += cc[k];
     }
     uint64_t tot;
-    const uint64_t bbase = bsum[blockIdx.x];
     uint64_t o = block_exclusive_scan<uint64_t, kPreThreads>(s, sm, &tot);
+    // this CTA's part of the block's run
+    const uint64_t r0 = (part - uoff[b]) * (uint64_t)kDupChunk;
+    const uint64_t r1 = min(r0 + (uint64_t)kDupChunk, tot);
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
         const int li = threadIdx.x * kScanItems + k;
         const uint32_t g = gg[k];
         s_off[li] = (uint32_t)o;
         s_g[li] = g;
-        if (base + k < n) dup_off[g] = (uint32_t)(bbase + o);
-        if (cc[k]) {
+        if (cc[k] && o < r1 && o + cc[k] > r0) {
+            if (o >= r0) dup_off[g] = (uint32_t)(bbase + o);
             const int4 r = rect[g];
             const ViewDesc& vd = views[g / per_view];
             s_t0[li] = (uint32_t)(vd.tile_base + r.y * vd.TX + r.x);
@@ -544,7 +613,7 @@ k_duplicate(const uint32_t* __restrict__ sorted_g, const uint32_t* __restrict__ 
     }
     if (threadIdx.x == 0) s_off[kScanBlock] = (uint32_t)tot;
     __syncthreads();
-    for (uint32_t e = threadIdx.x; e < (uint32_t)tot; e += kPreThreads) {
+    for (uint32_t e = (uint32_t)r0 + threadIdx.x; e < (uint32_t)r1; e += kPreThreads) {
         int lo = 0, hi = kScanBlock;   // s_off[lo] <= e < s_off[hi]
 #pragma unroll
         for (int it = 0; it < 10; it++) {
@@ -660,18 +729,6 @@ __global__ void __launch_bounds__(1024) k_order_items(const uint32_t* __restrict
     if (threadIdx.x == 0) {
         count[6] = carry;
         count[7] = seg_end;
-    }
-}
-
-__global__ void k_ranges(const uint32_t* __restrict__ stile, const uint64_t* n_dev,
-                         uint32_t* __restrict__ ranges)
-{
-    const uint64_t I = *n_dev;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < I;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t t = stile[i];
-        if (i == 0 || stile[i - 1] != t) ranges[2 * t] = (uint32_t)i;
-        if (i == I - 1 || stile[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
     }
 }
 
@@ -997,7 +1054,7 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     GL_TRY(v.dup_off.reserve(4 * nn));
     GL_TRY(v.kmask.reserve(8 * nn));
     const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
-    GL_TRY(v.bsum.reserve(8 * (size_t)std::max(nb, 1)));
+    GL_TRY(v.bsum.reserve(16 * (size_t)std::max(nb, 1)));   // block offsets, then their duplication parts
     GL_TRY(v.ranges.reserve(8 * (size_t)v.ntiles));
     GL_CUDA_TRY(cudaMemsetAsync(v.ranges.p, 0, 8 * (size_t)v.ntiles, s));
 
@@ -1073,11 +1130,14 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
         nmax = (int64_t)I;
     }
     const uint64_t cap2 = v.itile.bytes / 4;
-    k_duplicate<<<nb, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
-                                           v.bsum.as<uint64_t>(), count + 9, dv, p.n, cap2,
-                                           v.kmask.as<unsigned long long>(),
-                                           v.dup_off.as<uint32_t>(),
-                                           v.itile.as<uint32_t>(), v.iowner.as<uint32_t>());
+    // one CTA per duplication part: at most one per scan block plus one per
+    // kDupChunk instances (their bound: the capacity for graph steps, else
+    // the count just read)
+    const int64_t nchunk = nb + (std::min<int64_t>(nmax, (int64_t)cap2) + kDupChunk - 1) / kDupChunk;
+    k_duplicate<<<(unsigned)nchunk, kPreThreads, 0, s>>>(v.sorted_g, v.touched.as<uint32_t>(), v.rect.as<int4>(),
+                                                         v.bsum.as<uint64_t>(), nb, count + 9, count, dv, p.n, cap2,
+                                                         v.kmask.as<unsigned long long>(), v.dup_off.as<uint32_t>(),
+                                                         v.itile.as<uint32_t>(), v.iowner.as<uint32_t>());
     count_launches(1);
     GL_CUDA_TRY(cudaGetLastError());
     ps_scan.close();
@@ -1099,14 +1159,11 @@ gl_status bin_views(View& v, const GParams& p, const Cam* cams, const ViewExtra*
     v.sorted_inst = sv;
     {
         PhaseScope ps(v.prof, PH_RANGES, s);
-        int rb = (int)std::min<int64_t>(4 * (int64_t)sm_count(), (nmax + 255) / 256);
-        k_ranges<<<rb, 256, 0, s>>>(v.sorted_tile, count, v.ranges.as<uint32_t>());
-        count_launches(1);
-        GL_CUDA_TRY(cudaGetLastError());
-        GL_TRY(build_items(v, s));
-        // the sorted records always get the full capacity, so that graph
-        // steps (which size nothing) find room for any count that fits
+        // the sorted records (and the tile ranges, found in the same pass)
+        // always get the full capacity, so that graph steps (which size
+        // nothing) find room for any count that fits
         GL_TRY(permute_records(v, (int64_t)(v.itile.bytes / 4), s));
+        GL_TRY(build_items(v, s));
     }
     // the counters reach the host at the caller's next synchronisation
     // (sort_wait_status); graph steps copy them at the end of the step

@@ -151,14 +151,15 @@ struct View {
     DevBuf kmask;             // u64 kept-tile mask of the rectangle (all ones if it is not culled)
     DevBuf g2d;               // float[10] screen-space gradient accumulators
     // scan
-    DevBuf bsum;              // u64 per scan block
+    DevBuf bsum;              // u64 per scan block: instance offset, then duplication-part offset
     DevBuf count;             // u64[16]: I (0 after an overflow), overflow flag, N (depth
                               // sort), instances needed, view-count scratch [4..5],
                               // work items [6], segment items [7], bounded device
                               // waits that gave up [8] (bit 0: radix-sort look-back,
                               // bit 1: parameter staging; sticky until
                               // sort_wait_status reads it), Gaussians left after
-                              // the depth sort drops the culled ones [9]
+                              // the depth sort drops the culled ones [9],
+                              // duplication parts [10]
     // per instance
     DevBuf itile, ival, itile2, ival2;  // u32 global tile id, u32 instance id (sort; input ids implied)
     DevBuf iowner;            // u32 owning (view, Gaussian) per instance id

@@ -1087,7 +1087,11 @@ __global__ void k_part_reduce(const float* __restrict__ part, const uint32_t* __
 // mean made relative to the origin of the instance's tile: (u_hi - x0) is
 // exact near the tile (Sterbenz), and adding u_lo leaves an offset accurate
 // to float precision of a number of pixels, not of the image coordinate.
-__global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __restrict__ sinst,
+// The same pass marks each tile's list [first, last + 1) in `ranges` where
+// the sorted tile id changes (tiles without instances keep the zeros the
+// caller wrote).
+__global__ void k_permute(const uint64_t* __restrict__ n_dev, uint32_t* __restrict__ ranges,
+                          const uint32_t* __restrict__ sinst,
                           const uint32_t* __restrict__ stile, const ViewDesc* __restrict__ views, int V, int TS,
                           const uint32_t* __restrict__ owner, const float4* __restrict__ r0,
                           const float4* __restrict__ r1, const float4* __restrict__ r2,
@@ -1098,6 +1102,8 @@ __global__ void k_permute(const uint64_t* __restrict__ n_dev, const uint32_t* __
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < I; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t g = owner[sinst[i]];
         const int tile = (int)stile[i];
+        if (i == 0 || stile[i - 1] != (uint32_t)tile) ranges[2 * tile] = (uint32_t)i;
+        if (i == I - 1 || stile[i + 1] != (uint32_t)tile) ranges[2 * tile + 1] = (uint32_t)(i + 1);
         const ViewDesc& d = views[view_of_tile(views, V, tile)];
         const int lt = tile - d.tile_base;
         const float x0 = (float)((lt % d.TX) * TS), y0 = (float)((lt / d.TX) * TS);
@@ -1265,7 +1271,7 @@ gl_status permute_records(View& v, int64_t nmax, cudaStream_t s)
     GL_TRY(v.srec3.reserve(16 * I));
     GL_TRY(v.sgid.reserve(4 * I));
     const int blocks = (int)std::min<size_t>(8 * (size_t)sm_count(), (I + 255) / 256);
-    k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.sorted_inst, v.sorted_tile, v.d_desc(), v.V, v.Ts,
+    k_permute<<<blocks, 256, 0, s>>>(v.count.as<uint64_t>(), v.ranges.as<uint32_t>(), v.sorted_inst, v.sorted_tile, v.d_desc(), v.V, v.Ts,
                                      v.iowner.as<uint32_t>(),
                                      v.rec0.as<float4>(), v.rec1.as<float4>(), v.rec2.as<float4>(),
                                      v.rec3.as<float4>(), v.srec0.as<float4>(), v.srec1.as<float4>(),

@@ -82,6 +82,42 @@ def test_preprocess_and_binning_bit_exact(scene, tile, cull):
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), bins["ranges"])
 
 
+def test_binning_with_single_digit_radix_passes():
+    """Depths in [2.2, 3.8] share the top byte of their float bits, and every
+    instance lies in tiles 0..239 (the top three rows of 80 x 64 tiles of 8
+    px), so the depth sort's last pass and the tile sort's second pass see
+    the same digit in every key and copy their tiles through.  Binning stays
+    bit-exact against the oracle."""
+    rng = np.random.default_rng(11)
+    W, H, n, f, tile = 640, 512, 3000, 500.0, 8
+    cam = scenes.camera(W, H, f, f, W / 2, H / 2)
+    u = rng.uniform(16, W - 16, n)
+    v = rng.uniform(4, 8, n)
+    z = rng.uniform(2.2, 3.8, n)
+    q = rng.normal(0, 1, (n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    f32 = np.float32
+    params = dict(means=np.stack([(u - W / 2) * z / f, (v - H / 2) * z / f, z], 1).astype(f32),
+                  log_scales=rng.normal(-5.0, 0.15, (n, 3)).astype(f32), quats=q.astype(f32),
+                  logits=rng.normal(1.0, 0.5, n).astype(f32), sh=rng.normal(0, 0.5, (n, 1, 3)).astype(f32))
+    pre = oracle.preprocess(params, cam, tile, cull=True)
+    bins = oracle.bin_instances(pre, cam)
+    # the preconditions of the single-digit passes, on the oracle's side
+    assert bins["I"] > 1000
+    assert np.all((bins["keys"] >> np.uint64(32)) < 256)
+    vis = pre["radius"] > 0
+    assert np.all((pre["depth_bits"][vis] >> np.uint32(24)) == 0x40)
+    ctx = _ctx()
+    ctx.forward(_dev(params), cam, tile)
+    pp = ctx.preprocess(n, "cuda")
+    assert np.array_equal(pp["radius"].cpu().numpy(), pre["radius"])
+    keys, vals, ranges = ctx.instances(bins["TX"] * bins["TY"], "cuda")
+    assert ctx.num_instances() == bins["I"]
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), bins["keys"])
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), bins["vals"])
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), bins["ranges"])
+
+
 @pytest.mark.parametrize("scene", SCENES)
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_render_parity(scene, tile):
