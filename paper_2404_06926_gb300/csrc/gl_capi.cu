@@ -676,6 +676,11 @@ struct gl_map {
     // step execution and the captured step graph
     gl_exec_config exec{0, 0, 32, 1, 0, 0, 0, 1, 0};
     cudaStream_t gstream = nullptr;      // capture stream (the map's may be the legacy one)
+    // caller host images of a step are copied on cstream while the step's
+    // first kernels run; the loss waits for stage_ev (ready_ev: the map's
+    // stream has finished with the staging buffer)
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t stage_ev = nullptr, ready_ev = nullptr;
     struct StepGraph {
         std::vector<int64_t> key;        // the step shape it was captured for
         cudaGraphExec_t exec = nullptr;
@@ -866,6 +871,12 @@ extern "C" gl_status gl_map_destroy(gl_map* m)
     if (m->h_loss) cudaFreeHost(m->h_loss);
     for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);
     if (m->gstream) cudaStreamDestroy(m->gstream);
+    if (m->cstream) {
+        cudaStreamSynchronize(m->cstream);
+        cudaStreamDestroy(m->cstream);
+    }
+    if (m->stage_ev) cudaEventDestroy(m->stage_ev);
+    if (m->ready_ev) cudaEventDestroy(m->ready_ev);
     m->prof.release();
     delete m;
     return GL_OK;
@@ -983,6 +994,16 @@ struct StepPlan {
     Keyframe* kfs[kMaxViews];
 };
 
+// The copy stream and its events (created once per map, before the first
+// staging or capture, so that every captured step holds the loss's wait).
+gl_status ensure_stage(gl_map* m)
+{
+    if (!m->cstream) GL_CUDA_TRY(cudaStreamCreateWithFlags(&m->cstream, cudaStreamNonBlocking));
+    if (!m->stage_ev) GL_CUDA_TRY(cudaEventCreateWithFlags(&m->stage_ev, cudaEventDisableTiming));
+    if (!m->ready_ev) GL_CUDA_TRY(cudaEventCreateWithFlags(&m->ready_ev, cudaEventDisableTiming));
+    return GL_OK;
+}
+
 gl_status plan_step(gl_map* m, const gl_keyframe* views, int V, StepPlan& sp)
 {
     if (!m || !views || V < 1) { set_error("need at least one view"); return GL_ERR_INVALID; }
@@ -1008,7 +1029,12 @@ gl_status plan_step(gl_map* m, const gl_keyframe* views, int V, StepPlan& sp)
     bool need_stage = false;
     for (int i = 0; i < V; i++)
         if (views[i].image && !is_device_ptr(views[i].image)) need_stage = true;
-    if (need_stage) GL_TRY(m->stage_img.reserve(12 * (size_t)sp.P));
+    if (need_stage) {
+        GL_TRY(m->stage_img.reserve(12 * (size_t)sp.P));
+        GL_TRY(ensure_stage(m));
+        GL_CUDA_TRY(cudaEventRecord(m->ready_ev, m->stream));
+        GL_CUDA_TRY(cudaStreamWaitEvent(m->cstream, m->ready_ev, 0));
+    }
     int64_t off = 0;
     for (int i = 0; i < V; i++) {
         const size_t Pi = (size_t)sp.cams[i].W * sp.cams[i].H;
@@ -1017,7 +1043,7 @@ gl_status plan_step(gl_map* m, const gl_keyframe* views, int V, StepPlan& sp)
         else if (is_device_ptr(views[i].image)) tgt = views[i].image;
         else {
             float* dst = m->stage_img.as<float>() + 3 * off;
-            GL_CUDA_TRY(cudaMemcpyAsync(dst, views[i].image, 12 * Pi, cudaMemcpyHostToDevice, m->stream));
+            GL_CUDA_TRY(cudaMemcpyAsync(dst, views[i].image, 12 * Pi, cudaMemcpyHostToDevice, m->cstream));
             tgt = dst;
         }
         off += (int64_t)Pi;
@@ -1027,6 +1053,7 @@ gl_status plan_step(gl_map* m, const gl_keyframe* views, int V, StepPlan& sp)
         sp.extra[i].Em = e + 12;
         sp.extra[i].weight = 1.0f / (float)V;
     }
+    if (need_stage) GL_CUDA_TRY(cudaEventRecord(m->stage_ev, m->cstream));
     return GL_OK;
 }
 
@@ -1081,6 +1108,10 @@ gl_status enqueue_step(gl_map* m, const StepPlan& sp, cudaStream_t s, bool sync_
     GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * 14 * (size_t)v.nltiles));
     GL_TRY(m->loss_dev.reserve(sizeof(float) * kMaxViews));
     const uint64_t* ctl = v.count.as<uint64_t>();
+    // the targets copied from host memory (if any) have landed; captured
+    // steps hold this wait as an external event node, so a replay waits for
+    // the copy of its own step
+    if (m->stage_ev) GL_CUDA_TRY(cudaStreamWaitEvent(s, m->stage_ev, sync_free ? cudaEventWaitExternal : 0));
     {
         PhaseScope ps(&m->prof, PH_LOSS, s);
         GL_TRY(photometric_loss_views(v, v.rgb.as<float>(), c.lambda_dssim, m->dLdC.as<float>(),
@@ -1179,6 +1210,7 @@ gl_map::StepGraph* find_graph(gl_map* m, const std::vector<int64_t>& key)
 // failure leaves no graph and is not an error: steps stay eager.
 void capture_step(gl_map* m, const StepPlan& sp)
 {
+    if (ensure_stage(m) != GL_OK) return;
     if (!m->gstream && cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking) != cudaSuccess) {
         m->gstream = nullptr;
         return;

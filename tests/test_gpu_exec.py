@@ -131,6 +131,34 @@ def test_deterministic_steps_are_bit_identical(tile, ppl, persistent, pg):
     PT.assert_step_matches(got, params, st["p"], r["grads"], r["visible"], PT.learning_rates(oracle.DEFAULT_LR))
 
 
+def test_host_and_device_targets_give_identical_steps():
+    """Targets in host memory (pageable or pinned) are copied on a side
+    stream while the step's first kernels run, and the loss waits for that
+    copy (in captured steps through an external event node): with the
+    deterministic backward, steps with host targets are bit-identical to
+    steps with the same targets in device memory, eager and replayed."""
+    params, cams, targets = _window_scene()
+    dev = [torch.from_numpy(t).cuda() for t in targets]
+    pinned = [torch.from_numpy(t).pin_memory() for t in targets]
+    maps = [_map(params) for _ in range(3)]
+    for m in maps:
+        m.set_exec(deterministic=1, use_graphs=1)
+    losses = [[], [], []]
+    for _ in range(5):
+        for j, imgs in enumerate((dev, targets, pinned)):
+            views = [(10 + i, cams[i], imgs[i]) for i in range(3)]
+            losses[j].append(maps[j].optimize_step(views, want_loss=True))
+    assert losses[0] == losses[1] == losses[2]
+    ref = maps[0].get_params()
+    for m in maps[1:]:
+        got = m.get_params()
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+        for i in range(3):
+            assert np.array_equal(maps[0].exposure(10 + i), m.exposure(10 + i))
+        assert m.stats()["graph_replays"] == 4
+
+
 def test_graph_replay_equals_eager_over_steps():
     """With atomic gradient accumulation (the default) the order of the
     float additions depends on the warps' timing, so after several Adam steps
