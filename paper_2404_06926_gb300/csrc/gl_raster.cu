@@ -619,6 +619,46 @@ __device__ __forceinline__ float warp_transpose_reduce16(float (&v)[16])
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
+// Sum 9 per-lane values over the warp: values 0..7 by a transposed butterfly
+// (on return lane l holds the total of value l >> 2), value 8 by a plain one
+// (*t8 in every lane) -- 14 shuffles where the 16-slot fold takes 16.
+__device__ __forceinline__ float warp_transpose_reduce8(const float (&v)[16], float* t8)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    float w[4];
+    {
+        const bool up = lane & 16u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float send = up ? v[k] : v[k + 4];
+            const float keep = up ? v[k + 4] : v[k];
+            w[k] = keep + __shfl_xor_sync(kFull, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8u;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float send = up ? w[k] : w[k + 2];
+            const float keep = up ? w[k + 2] : w[k];
+            w[k] = keep + __shfl_xor_sync(kFull, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4u;
+        const float send = up ? w[0] : w[1];
+        const float keep = up ? w[1] : w[0];
+        w[0] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    w[0] += __shfl_xor_sync(kFull, w[0], 2);
+    w[0] += __shfl_xor_sync(kFull, w[0], 1);
+    float x = v[8];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+    *t8 = x;
+    return w[0];
+}
+
 template <bool EXTRA, int NB, int D, bool DET>
 __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const RasterGrad& G, float4* sr0,
                                          float4* sr1, float4* sr2, uint32_t* spos, uint32_t* sg, int lane)
@@ -740,11 +780,23 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
                 }
             }
             if (__any_sync(kFull, any)) {
-                const float r = warp_transpose_reduce16(v);
-                const int q = lane >> 1;
-                if ((lane & 1) == 0 && q < (EXTRA ? kNG : kNG - 1)) {
-                    if (DET) G.part[((size_t)sg[k] * A.nblk + U.wb) * kNG + q] = r;
-                    else atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, r);
+                if (EXTRA) {
+                    const float r = warp_transpose_reduce16(v);
+                    const int q = lane >> 1;
+                    if ((lane & 1) == 0 && q < kNG) {
+                        if (DET) G.part[((size_t)sg[k] * A.nblk + U.wb) * kNG + q] = r;
+                        else atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, r);
+                    }
+                } else {
+                    // nine live slots (no depth or opacity gradient)
+                    float r8;
+                    const float r = warp_transpose_reduce8(v, &r8);
+                    const int q = (lane & 3) == 0 ? (int)(lane >> 2) : (lane == 1 ? 8 : -1);
+                    if (q >= 0) {
+                        const float val = q == 8 ? r8 : r;
+                        if (DET) G.part[((size_t)sg[k] * A.nblk + U.wb) * kNG + q] = val;
+                        else atomicAdd(G.g2d + (size_t)sg[k] * kNG + q, val);
+                    }
                 }
             }
         }
