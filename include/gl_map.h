@@ -182,8 +182,12 @@ GL_API gl_status gl_render(gl_map* map, const gl_pose* pose, const gl_intrinsics
  * on the Gaussians (sparse or dense per the config) and on the view's
  * exposure.  n_views > 1 renders and back-propagates all views as one
  * window and takes one Adam step on the mean of their losses.  out_loss
- * (host, nullable) receives the mean loss.  Errors: GL_ERR_INVALID,
- * GL_ERR_NOT_FOUND (image NULL and id not registered), GL_ERR_CAPACITY. */
+ * (host, nullable) receives the mean loss.  Images in host memory (pinned
+ * or pageable) are copied to the device on a stream of the map's own while
+ * the step's binning and forward run, and only the loss waits for them;
+ * the call returns when the step is done, so the caller may reuse them
+ * then.  Errors: GL_ERR_INVALID, GL_ERR_NOT_FOUND (image NULL and id not
+ * registered), GL_ERR_CAPACITY. */
 GL_API gl_status gl_optimize_step(gl_map* map, const gl_keyframe* views, int32_t n_views,
                            float* out_loss);
 
