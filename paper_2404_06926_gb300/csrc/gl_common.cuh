@@ -500,6 +500,21 @@ __device__ __forceinline__ bool pair_eval(const float4 r0, const float4 r1, floa
     return true;
 }
 
+// pair_eval without the early exit: alpha and capped are computed whatever
+// the outcome (meaningful only when it returns true).
+__device__ __forceinline__ bool pair_eval_nb(const float4 r0, const float4 r1, float px, float py, float& dx,
+                                             float& dy, float& alpha, bool& capped)
+{
+    dx = __fsub_rn(r0.x, px);
+    dy = __fsub_rn(r0.y, py);
+    const float e = __fmaf_rn(__fmul_rn(r0.z, dx), dx,
+                              __fmaf_rn(__fmul_rn(r0.w, dy), dy, __fmaf_rn(__fmul_rn(r1.x, dx), dy, r1.y)));
+    const float araw = ex2_approx(e);
+    capped = araw >= kAlphaMax;
+    alpha = fminf(kAlphaMax, araw);
+    return e >= kLog2AlphaMin && !(e > r1.y);
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 }  // namespace gl

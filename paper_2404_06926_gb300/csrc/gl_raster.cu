@@ -748,37 +748,41 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
         for (int k = nh - 1; k >= 0; k--) {
             const float4 a = sr0[k], b = sr1[k], c = sr2[k];
             const uint32_t pos = spos[k];
+            // Branch-free: a pixel the hit does not reach takes alpha = 0,
+            // which leaves its R exactly unchanged (0 c + 1 R) and zeroes its
+            // sums; only T needs a select.  No per-hit zeroing of the sums and
+            // no divergent branch around the update.
             float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; q++) v[q] = 0.0f;
             bool any = false;
 #pragma unroll
             for (int j = 0; j < D; j++) {
                 float dx, dy, alpha;
                 bool capped;
-                if (pos < last[j] && pair_eval(a, b, L.px, L.py[j], dx, dy, alpha, capped)) {
-                    const float om = 1.0f - alpha;
-                    T[j] = __fdividef(T[j], om);
-                    const float wgt = alpha * T[j];
-                    float ga = g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]);
-                    if (EXTRA) ga += gD[j] * (b.z - RD[j]) + gO[j] * (1.0f - RO[j]);
-                    ga *= T[j];
-                    R0[j] = alpha * c.x + om * R0[j];
-                    R1[j] = alpha * c.y + om * R1[j];
-                    R2[j] = alpha * c.z + om * R2[j];
-                    if (EXTRA) {
-                        RD[j] = alpha * b.z + om * RD[j];
-                        RO[j] = alpha + om * RO[j];
-                    }
-                    const float gp = capped ? 0.0f : ga * alpha;
-                    v[0] += wgt * g0[j]; v[1] += wgt * g1[j]; v[2] += wgt * g2[j];
-                    v[3] += gp;
-                    v[4] += gp * dx; v[5] += gp * dy;
-                    v[6] += gp * dx * dx; v[7] += gp * dx * dy; v[8] += gp * dy * dy;
-                    if (EXTRA) v[9] += wgt * gD[j];
-                    any = true;
+                const bool live = pair_eval_nb(a, b, L.px, L.py[j], dx, dy, alpha, capped) && pos < last[j];
+                const float al = live ? alpha : 0.0f;
+                const float om = 1.0f - al;
+                T[j] = live ? __fdividef(T[j], om) : T[j];
+                const float wgt = al * T[j];
+                float ga = g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]);
+                if (EXTRA) ga += gD[j] * (b.z - RD[j]) + gO[j] * (1.0f - RO[j]);
+                ga *= T[j];
+                R0[j] = al * c.x + om * R0[j];
+                R1[j] = al * c.y + om * R1[j];
+                R2[j] = al * c.z + om * R2[j];
+                if (EXTRA) {
+                    RD[j] = al * b.z + om * RD[j];
+                    RO[j] = al + om * RO[j];
                 }
+                const float gp = capped ? 0.0f : ga * al;
+                const float gx = gp * dx, gy = gp * dy;
+                const float t[10] = {wgt * g0[j], wgt * g1[j], wgt * g2[j], gp, gx, gy, gx * dx, gx * dy, gy * dy,
+                                     EXTRA ? wgt * gD[j] : 0.0f};
+#pragma unroll
+                for (int q = 0; q < 10; q++) v[q] = j == 0 ? t[q] : v[q] + t[q];
+                any = any || live;
             }
+#pragma unroll
+            for (int q = 10; q < 16; q++) v[q] = 0.0f;
             if (__any_sync(kFull, any)) {
                 if (EXTRA) {
                     const float r = warp_transpose_reduce16(v);
