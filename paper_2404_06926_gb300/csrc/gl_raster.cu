@@ -231,31 +231,25 @@ __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uin
         }
         __syncwarp();
         for (int k = 0; k < nh && !lane_done; k++) {
-            const float4 g0 = sr0[k], g1 = sr1[k];
-            bool used = false;
-            float wgt[D];
+            // Branch-free: a pixel that is done, or that the hit misses or
+            // stops at, blends with weight 0 (its sums exactly unchanged);
+            // T and the last position move by selects.
+            const float4 g0 = sr0[k], g1 = sr1[k], c = sr2[k];
+            const uint32_t pos1 = spos[k] + 1;
 #pragma unroll
             for (int j = 0; j < D; j++) {
-                wgt[j] = 0.0f;
-                if (done[j]) continue;
                 float dx, dy, alpha;
                 bool capped;
-                if (!pair_eval(g0, g1, px, py[j], dx, dy, alpha, capped)) continue;
+                const bool live = pair_eval_nb(g0, g1, px, py[j], dx, dy, alpha, capped) && !done[j];
                 const float tT = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
-                if (stop && __fmul_rn(Tin[j], tT) < kTransMin) { done[j] = true; continue; }
-                wgt[j] = alpha * T[j];
-                T[j] = tT;
-                last[j] = spos[k] + 1;
-                used = true;
-                if (!stop && tT == 0.0f) done[j] = true;
-            }
-            if (used) {
-                const float4 c = sr2[k];
-#pragma unroll
-                for (int j = 0; j < D; j++) {
-                    C0[j] += c.x * wgt[j]; C1[j] += c.y * wgt[j]; C2[j] += c.z * wgt[j];
-                    Dd[j] += g1.z * wgt[j]; Oo[j] += wgt[j];
-                }
+                const bool halt = stop && live && __fmul_rn(Tin[j], tT) < kTransMin;
+                const bool blend = live && !halt;
+                const float wgt = blend ? alpha * T[j] : 0.0f;
+                T[j] = blend ? tT : T[j];
+                last[j] = blend ? pos1 : last[j];
+                done[j] = done[j] || halt || (!stop && blend && tT == 0.0f);
+                C0[j] += c.x * wgt; C1[j] += c.y * wgt; C2[j] += c.z * wgt;
+                Dd[j] += g1.z * wgt; Oo[j] += wgt;
             }
             lane_done = true;
 #pragma unroll
