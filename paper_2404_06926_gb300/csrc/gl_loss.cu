@@ -10,8 +10,9 @@
 // five moment maps separably over a 5-pixel halo, forms the SSIM map and its
 // partials w.r.t. (mu_x, E[x^2], E[xy]), blurs those back (the adjoint of a
 // zero-padded symmetric correlation is the same correlation) and adds the
-// channel's part of dL/dC = A^T dL/dE[C] (the thread owning a pixel is the
-// same in every channel).  In every pass a thread slides the 11 taps along a
+// channel's part of dL/dC = A^T dL/dE[C] in registers (the thread owning a
+// pixel is the same in every channel, so dL/dC is written once, after the
+// third channel, and never read back).  In every pass a thread slides the 11 taps along a
 // run of 3-8 outputs held in registers, so each shared-memory value is read
 // once per run rather than once per tap and output; the run lengths (and the
 // split of the horizontal adjoint by map) are chosen so that each pass gives
@@ -107,6 +108,12 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
     float l1acc = 0.0f, sacc = 0.0f;
     const int lane = tid & 31, wid = tid >> 5;
 
+    // the adjoint pass gives every thread one run of AVR rows of one column,
+    // the same in every channel: its pixels' dL/dC stays in registers
+    static_assert(LT * (LT / AVR) == kThreads, "one adjoint run per thread");
+    float dC[AVR][3];
+#pragma unroll
+    for (int o = 0; o < AVR; o++) dC[o][0] = dC[o][1] = dC[o][2] = 0.0f;
     for (int ch = 0; ch < 3; ch++) {
         // exposure gradient partials of this channel: sum g C_j (j < 3), sum g
         float pe[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -235,15 +242,9 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
                     const float g = acc[0][o] + 2.f * x * acc[1][o] + y * acc[2][o] +
                                     gL1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f));
                     pe[0] += g * c0; pe[1] += g * c1; pe[2] += g * c2; pe[3] += g;
-                    if (ch == 0) {
-                        dL_drgb[3 * p] = e0 * g;
-                        dL_drgb[3 * p + 1] = e1 * g;
-                        dL_drgb[3 * p + 2] = e2 * g;
-                    } else {
-                        dL_drgb[3 * p] += e0 * g;
-                        dL_drgb[3 * p + 1] += e1 * g;
-                        dL_drgb[3 * p + 2] += e2 * g;
-                    }
+                    dC[o][0] = ch == 0 ? e0 * g : dC[o][0] + e0 * g;
+                    dC[o][1] = ch == 0 ? e1 * g : dC[o][1] + e1 * g;
+                    dC[o][2] = ch == 0 ? e2 * g : dC[o][2] + e2 * g;
                 }
             }
         }
@@ -256,6 +257,19 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
         __syncthreads();
     }
 
+    {
+        const int c = tid % LT, r0 = (tid / LT) * AVR;
+#pragma unroll
+        for (int o = 0; o < AVR; o++) {
+            const int gx = ox + c, gy = oy + r0 + o;
+            if (gx < W && gy < H) {
+                const size_t p = (size_t)gy * W + gx;
+                dL_drgb[3 * p] = dC[o][0];
+                dL_drgb[3 * p + 1] = dC[o][1];
+                dL_drgb[3 * p + 2] = dC[o][2];
+            }
+        }
+    }
     {
         const float vals[2] = {l1acc, sacc};
 #pragma unroll
