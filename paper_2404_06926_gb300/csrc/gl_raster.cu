@@ -754,20 +754,27 @@ __device__ __forceinline__ void bwd_item(int u, const RasterArgs& A, const Raste
                 bool capped;
                 const bool live = pair_eval_nb(a, b, L.px, L.py[j], dx, dy, alpha, capped) && pos < last[j];
                 const float al = live ? alpha : 0.0f;
-                const float om = 1.0f - al;
-                T[j] = live ? __fdividef(T[j], om) : T[j];
+                T[j] = live ? __fdividef(T[j], 1.0f - al) : T[j];
                 const float wgt = al * T[j];
-                float ga = g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]);
-                if (EXTRA) ga += gD[j] * (b.z - RD[j]) + gO[j] * (1.0f - RO[j]);
-                ga *= T[j];
-                R0[j] = al * c.x + om * R0[j];
-                R1[j] = al * c.y + om * R1[j];
-                R2[j] = al * c.z + om * R2[j];
+                const float d0 = c.x - R0[j], d1 = c.y - R1[j], d2 = c.z - R2[j];
+                float dot = g0[j] * d0 + g1[j] * d1 + g2[j] * d2;
+                float dD = 0.0f, dO = 0.0f;
                 if (EXTRA) {
-                    RD[j] = al * b.z + om * RD[j];
-                    RO[j] = al + om * RO[j];
+                    dD = b.z - RD[j];
+                    dO = 1.0f - RO[j];
+                    dot += gD[j] * dD + gO[j] * dO;
                 }
-                const float gp = capped ? 0.0f : ga * al;
+                // what is blended behind moves toward this Gaussian by alpha:
+                // R + alpha (c - R) = alpha c + (1 - alpha) R
+                R0[j] = fmaf(al, d0, R0[j]);
+                R1[j] = fmaf(al, d1, R1[j]);
+                R2[j] = fmaf(al, d2, R2[j]);
+                if (EXTRA) {
+                    RD[j] = fmaf(al, dD, RD[j]);
+                    RO[j] = fmaf(al, dO, RO[j]);
+                }
+                // dL/d(exponent) = alpha dL/dalpha = alpha T g . (c - R)
+                const float gp = capped ? 0.0f : wgt * dot;
                 const float gx = gp * dx, gy = gp * dy;
                 const float t[10] = {wgt * g0[j], wgt * g1[j], wgt * g2[j], gp, gx, gy, gx * dx, gx * dy, gy * dy,
                                      EXTRA ? wgt * gD[j] : 0.0f};
