@@ -1103,7 +1103,7 @@ gl_status enqueue_step(gl_map* m, const StepPlan& sp, cudaStream_t s, bool sync_
     const int V = sp.V;
     GL_TRY(v.rgb.reserve(12 * (size_t)sp.P));
     GL_TRY(bin_views(v, m->params(), sp.cams, sp.extra, V, step_tile(m), s, sync_free));
-    GL_TRY(raster_forward(v, v.rgb.as<float>(), nullptr, nullptr, s));
+    GL_TRY(raster_forward(v, v.rgb.as<float>(), nullptr, nullptr, s, false));
     GL_TRY(m->dLdC.reserve(12 * (size_t)sp.P));
     GL_TRY(m->ctx.loss_part.reserve(sizeof(float) * 14 * (size_t)v.nltiles));
     GL_TRY(m->loss_dev.reserve(sizeof(float) * kMaxViews));

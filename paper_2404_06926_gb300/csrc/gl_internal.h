@@ -240,7 +240,9 @@ gl_status bin_view(View& v, const GParams& p, const Cam& cam, int Ts, cudaStream
 
 // Forward raster of a binned view into (rgb, depth, opacity) device images
 // (depth/opacity may be null) plus T_final / n_contrib in `v`.
-gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s);
+// extras: also blend depth and opacity (needed for those outputs and for a
+// later backward with depth or opacity gradients on split tiles).
+gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s, bool extras = true);
 
 // Upper bound of the work items of a binned step (every tile once, plus one
 // per seg records of the instance capacity).

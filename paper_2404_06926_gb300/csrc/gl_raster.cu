@@ -186,12 +186,12 @@ __device__ __forceinline__ int units_of(const RasterArgs& A, bool split_only)
 
 // Front-to-back blend of the records [a, b) of a tile list for the warp's
 // pixel block.  Per pixel: T (running transmittance), colour, depth and
-// opacity sums and the last blended position (relative to trs).  With
-// `stop`, a pixel stops (without blending) at the first record whose
-// T * (1 - alpha), scaled by its Tin, falls below 1e-4; without it every
-// accepted record is blended and a pixel stops only when T reaches 0.
-// Pixels with done set take no part.
-template <int NB, int D>
+// opacity sums (XD; without it they stay 0) and the last blended position
+// (relative to trs).  With `stop`, a pixel stops (without blending) at the
+// first record whose T * (1 - alpha), scaled by its Tin, falls below 1e-4;
+// without it every accepted record is blended and a pixel stops only when T
+// reaches 0.  Pixels with done set take no part.
+template <int NB, int D, bool XD>
 __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uint32_t b, uint32_t trs, float px,
                                             const float (&py)[D], float bx0, float bx1, float by0, float by1,
                                             bool stop, const float (&Tin)[D], bool (&done)[D], float (&T)[D],
@@ -249,7 +249,10 @@ __device__ __forceinline__ void blend_range(const RasterArgs& A, uint32_t a, uin
                 last[j] = blend ? pos1 : last[j];
                 done[j] = done[j] || halt || (!stop && blend && tT == 0.0f);
                 C0[j] += c.x * wgt; C1[j] += c.y * wgt; C2[j] += c.z * wgt;
-                Dd[j] += g1.z * wgt; Oo[j] += wgt;
+                if (XD) {
+                    Dd[j] += g1.z * wgt;
+                    Oo[j] += wgt;
+                }
             }
             lane_done = true;
 #pragma unroll
@@ -289,7 +292,7 @@ struct LanePix {
     }
 };
 
-template <int NB, int D>
+template <int NB, int D, bool XD>
 __device__ __forceinline__ void fwd_item(int u, const RasterArgs& A, const RasterOut& O, float4* sr0, float4* sr1,
                                          float4* sr2, uint32_t* spos, int lane)
 {
@@ -307,8 +310,8 @@ __device__ __forceinline__ void fwd_item(int u, const RasterArgs& A, const Raste
         done[j] = !L.inside[j];
     }
     const bool whole = U.nseg == 1;
-    blend_range<NB, D>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, whole, one, done, T, C0, C1,
-                       C2, Dd, Oo, last, sr0, sr1, sr2, spos, lane);
+    blend_range<NB, D, XD>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, whole, one, done, T, C0, C1,
+                           C2, Dd, Oo, last, sr0, sr1, sr2, spos, lane);
 #pragma unroll
     for (int j = 0; j < D; j++) {
         if (!L.inside[j]) continue;
@@ -333,7 +336,7 @@ __device__ __forceinline__ void fwd_item(int u, const RasterArgs& A, const Raste
     }
 }
 
-template <int NB, int D>
+template <int NB, int D, bool XD>
 __global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocks * kWarpsPerBlock / wpb<NB>())
 k_raster_fwd(RasterArgs A, RasterOut O)
 {
@@ -344,7 +347,7 @@ k_raster_fwd(RasterArgs A, RasterOut O)
     const int nunits = units_of(A, false);
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * WPB + w;
     while (u < nunits) {
-        fwd_item<NB, D>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
+        fwd_item<NB, D, XD>(u, A, O, sr0[w], sr1[w], sr2[w], spos[w], lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
     }
@@ -411,7 +414,7 @@ __device__ __forceinline__ void prefix_item(int u, const RasterArgs& A, int lane
 // Split tiles, pass 3 of 4: each segment item replays its records from the
 // incoming transmittance for the pixels whose stop segment it is, and stores
 // their truncated sums in place of the segment pass's.
-template <int NB, int D>
+template <int NB, int D, bool XD>
 __device__ __forceinline__ void replay_item(int u, const RasterArgs& A, float4* sr0, float4* sr1, float4* sr2,
                                             uint32_t* spos, int lane)
 {
@@ -439,8 +442,8 @@ __device__ __forceinline__ void replay_item(int u, const RasterArgs& A, float4* 
         any = true;
     }
     if (!__any_sync(kFull, any)) return;
-    blend_range<NB, D>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, true, Tin, dn, T, c0, c1, c2,
-                       dd, oo, last, sr0, sr1, sr2, spos, lane);
+    blend_range<NB, D, XD>(A, U.rs, U.re, U.trs, L.px, L.py, L.bx0, L.bx1, L.by0, L.by1, true, Tin, dn, T, c0, c1,
+                           c2, dd, oo, last, sr0, sr1, sr2, spos, lane);
 #pragma unroll
     for (int j = 0; j < D; j++) {
         if (!L.inside[j]) continue;
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kMinBlocks) k_seg_prefix(
     }
 }
 
-template <int NB, int D>
+template <int NB, int D, bool XD>
 __global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocks * kWarpsPerBlock / wpb<NB>()) k_seg_replay(RasterArgs A)
 {
     constexpr int WPB = wpb<NB>();
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(32 * wpb<NB>(), kMinBlocks * kWarpsPerBlock / 
     const int nunits = units_of(A, true);
     int u = A.work ? next_unit(A.work, lane) : blockIdx.x * WPB + w;
     while (u < nunits) {
-        replay_item<NB, D>(u, A, sr0[w], sr1[w], sr2[w], spos[w], lane);
+        replay_item<NB, D, XD>(u, A, sr0[w], sr1[w], sr2[w], spos[w], lane);
         if (!A.work) break;
         u = next_unit(A.work, lane);
     }
@@ -1255,14 +1258,14 @@ gl_status check_exec(const View& v)
     return GL_OK;
 }
 
-template <int NB, int D>
+template <int NB, int D, bool XD>
 void fwd_launch(const RasterArgs& A, const RasterOut& O, int64_t units, int64_t split_units, bool persistent,
                 int* work, cudaStream_t s)
 {
     RasterArgs a1 = A;
     a1.work = work;
-    k_raster_fwd<NB, D><<<grid_for(k_raster_fwd<NB, D>, units, persistent, wpb<NB>()), 32 * wpb<NB>(), 0, s>>>(a1,
-                                                                                                             O);
+    k_raster_fwd<NB, D, XD><<<grid_for(k_raster_fwd<NB, D, XD>, units, persistent, wpb<NB>()), 32 * wpb<NB>(), 0,
+                              s>>>(a1, O);
     if (split_units > 0) {
         // persistent grids take units from counters 2-4
         RasterArgs a2 = A, a3 = A, a4 = A;
@@ -1270,8 +1273,8 @@ void fwd_launch(const RasterArgs& A, const RasterOut& O, int64_t units, int64_t 
         a3.work = work ? work + 3 : nullptr;
         a4.work = work ? work + 4 : nullptr;
         k_seg_prefix<D><<<grid_for(k_seg_prefix<D>, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a2);
-        k_seg_replay<NB, D><<<grid_for(k_seg_replay<NB, D>, split_units, persistent, wpb<NB>()), 32 * wpb<NB>(), 0,
-                              s>>>(a3);
+        k_seg_replay<NB, D, XD><<<grid_for(k_seg_replay<NB, D, XD>, split_units, persistent, wpb<NB>()),
+                                  32 * wpb<NB>(), 0, s>>>(a3);
         k_seg_finish<D><<<grid_for(k_seg_finish<D>, split_units, persistent), 32 * kWarpsPerBlock, 0, s>>>(a4, O);
     }
 }
@@ -1338,8 +1341,31 @@ gl_status permute_records(View& v, int64_t nmax, cudaStream_t s)
     return GL_OK;
 }
 
-gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s)
+template <bool XD>
+void fwd_dispatch(const View& v, const RasterArgs& A, const RasterOut& O, int64_t units, int64_t split_units,
+                  int* work, cudaStream_t s)
 {
+    if (v.nb == 4) {
+        fwd_launch<4, 1, XD>(A, O, units, split_units, v.persistent, work, s);
+    } else if (v.nb == 8) {
+        fwd_launch<8, 1, XD>(A, O, units, split_units, v.persistent, work, s);
+    } else if (v.nb == 1) {
+        if (v.pd == 1) fwd_launch<1, 1, XD>(A, O, units, split_units, v.persistent, work, s);
+        else if (v.pd == 2) fwd_launch<1, 2, XD>(A, O, units, split_units, v.persistent, work, s);
+        else fwd_launch<1, 4, XD>(A, O, units, split_units, v.persistent, work, s);
+    } else {
+        if (v.pd == 1) fwd_launch<2, 1, XD>(A, O, units, split_units, v.persistent, work, s);
+        else if (v.pd == 2) fwd_launch<2, 2, XD>(A, O, units, split_units, v.persistent, work, s);
+        else fwd_launch<2, 4, XD>(A, O, units, split_units, v.persistent, work, s);
+    }
+}
+
+gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStream_t s, bool extras)
+{
+    if (!extras && (depth || opac)) {
+        set_error("raster_forward: depth and opacity outputs need the extra sums");
+        return GL_ERR_INVALID;
+    }
     const size_t P = (size_t)v.P;
     GL_TRY(v.Tfin.reserve(4 * P));
     GL_TRY(v.ncon.reserve(4 * P));
@@ -1358,19 +1384,8 @@ gl_status raster_forward(View& v, float* rgb, float* depth, float* opac, cudaStr
     RasterOut O{rgb, depth, opac, v.Tfin.as<float>(), v.ncon.as<uint32_t>()};
     const int nblk = blocks_per_tile(v);
     const int64_t units = work_items_bound(v) * nblk, split_units = split * nblk;
-    if (v.nb == 4) {
-        fwd_launch<4, 1>(A, O, units, split_units, v.persistent, work, s);
-    } else if (v.nb == 8) {
-        fwd_launch<8, 1>(A, O, units, split_units, v.persistent, work, s);
-    } else if (v.nb == 1) {
-        if (v.pd == 1) fwd_launch<1, 1>(A, O, units, split_units, v.persistent, work, s);
-        else if (v.pd == 2) fwd_launch<1, 2>(A, O, units, split_units, v.persistent, work, s);
-        else fwd_launch<1, 4>(A, O, units, split_units, v.persistent, work, s);
-    } else {
-        if (v.pd == 1) fwd_launch<2, 1>(A, O, units, split_units, v.persistent, work, s);
-        else if (v.pd == 2) fwd_launch<2, 2>(A, O, units, split_units, v.persistent, work, s);
-        else fwd_launch<2, 4>(A, O, units, split_units, v.persistent, work, s);
-    }
+    if (extras) fwd_dispatch<true>(v, A, O, units, split_units, work, s);
+    else fwd_dispatch<false>(v, A, O, units, split_units, work, s);
     count_launches(split_units > 0 ? 4 : 1);
     GL_CUDA_TRY(cudaGetLastError());
     return GL_OK;

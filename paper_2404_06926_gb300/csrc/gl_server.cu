@@ -380,7 +380,7 @@ void render_worker(gl_server* s)
             if (st == GL_OK) st = s->rgb.reserve(12 * (size_t)P);
             map_exec_knobs(s->map, s->rview, Ts);
             if (st == GL_OK) st = bin_views(s->rview, p, cams.data(), nullptr, V, Ts, s->rstream);
-            if (st == GL_OK) st = raster_forward(s->rview, s->rgb.as<float>(), nullptr, nullptr, s->rstream);
+            if (st == GL_OK) st = raster_forward(s->rview, s->rgb.as<float>(), nullptr, nullptr, s->rstream, false);
             size_t off = 0;
             for (int i = 0; i < V && st == GL_OK; i++) {
                 const size_t b = 12 * (size_t)cams[i].W * cams[i].H;
