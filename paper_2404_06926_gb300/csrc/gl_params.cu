@@ -215,8 +215,11 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
             float pe[4], me[4], ve[4];
             if (MODE == 1) {
                 const float4 pp = reinterpret_cast<const float4*>(sP)[c];
-                const float4 mm = reinterpret_cast<const float4*>(Mg + base)[c];
-                const float4 vv = reinterpret_cast<const float4*>(Vg + base)[c];
+                // moments and parameters are touched once per step: streaming
+                // loads and stores leave the L2 to the moments prefetched for
+                // the blocks still to come
+                const float4 mm = __ldcs(reinterpret_cast<const float4*>(Mg + base) + c);
+                const float4 vv = __ldcs(reinterpret_cast<const float4*>(Vg + base) + c);
                 pe[0] = pp.x; pe[1] = pp.y; pe[2] = pp.z; pe[3] = pp.w;
                 me[0] = mm.x; me[1] = mm.y; me[2] = mm.z; me[3] = mm.w;
                 ve[0] = vv.x; ve[1] = vv.y; ve[2] = vv.z; ve[3] = vv.w;
@@ -228,10 +231,10 @@ __device__ __forceinline__ void span_update(float* __restrict__ P, float* __rest
                 if (MODE == 0) pe[k] = (FULL || ((upd >> r) & 1u)) ? g : 0.0f;
                 else if (FULL || ((upd >> r) & 1u)) adam1(pe[k], me[k], ve[k], g, (WIDTH > 4 && w < 3) ? lr0 : lr, ad);
             }
-            reinterpret_cast<float4*>(P + base)[c] = make_float4(pe[0], pe[1], pe[2], pe[3]);
+            __stcs(reinterpret_cast<float4*>(P + base) + c, make_float4(pe[0], pe[1], pe[2], pe[3]));
             if (MODE == 1) {
-                reinterpret_cast<float4*>(Mg + base)[c] = make_float4(me[0], me[1], me[2], me[3]);
-                reinterpret_cast<float4*>(Vg + base)[c] = make_float4(ve[0], ve[1], ve[2], ve[3]);
+                __stcs(reinterpret_cast<float4*>(Mg + base) + c, make_float4(me[0], me[1], me[2], me[3]));
+                __stcs(reinterpret_cast<float4*>(Vg + base) + c, make_float4(ve[0], ve[1], ve[2], ve[3]));
             }
         }
     } else {
