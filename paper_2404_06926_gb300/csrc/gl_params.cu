@@ -36,11 +36,14 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     G.x = R[0] * mu[0] + R[1] * mu[1] + R[2] * mu[2] + cam.t[0];
     G.y = R[3] * mu[0] + R[4] * mu[1] + R[5] * mu[2] + cam.t[1];
     G.z = R[6] * mu[0] + R[7] * mu[1] + R[8] * mu[2] + cam.t[2];
-    G.iz = 1.0f / G.z;
-    for (int i = 0; i < 3; i++) G.s[i] = expf(ls[i]);
+    // the backward's geometry divides by the hardware's approximate
+    // reciprocal and exponentiates by its approximate exponential (a few ulp;
+    // the gradients' tolerance is 1e-3): no divide sequences on the chain
+    G.iz = __fdividef(1.0f, G.z);
+    for (int i = 0; i < 3; i++) G.s[i] = __expf(ls[i]);
     float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     G.qnorm = sqrtf(qq);
-    float inv = 1.0f / G.qnorm;
+    const float inv = __fdividef(1.0f, G.qnorm);
     for (int i = 0; i < 4; i++) G.qn[i] = q[i] * inv;
     const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
     G.Rq[0] = 1.f - 2.f * (y * y + z * z); G.Rq[1] = 2.f * (x * y - w * z); G.Rq[2] = 2.f * (x * z + w * y);
@@ -51,8 +54,8 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++)
             G.Sig[i * 3 + j] = G.M[i * 3] * G.M[j * 3] + G.M[i * 3 + 1] * G.M[j * 3 + 1] + G.M[i * 3 + 2] * G.M[j * 3 + 2];
-    const float limx = kJacClamp * (0.5f * (float)cam.W / cam.fx);
-    const float limy = kJacClamp * (0.5f * (float)cam.H / cam.fy);
+    const float limx = kJacClamp * __fdividef(0.5f * (float)cam.W, cam.fx);
+    const float limy = kJacClamp * __fdividef(0.5f * (float)cam.H, cam.fy);
     const float xz = G.x * G.iz, yz = G.y * G.iz;
     G.clx = xz < -limx || xz > limx;
     G.cly = yz < -limy || yz > limy;
@@ -72,17 +75,18 @@ __device__ __forceinline__ void geometry(const float mu[3], const float ls[3], c
     G.a = U[0] * G.T[0] + U[1] * G.T[1] + U[2] * G.T[2] + kDilation;
     G.b = U[0] * G.T[3] + U[1] * G.T[4] + U[2] * G.T[5];
     G.c = U[3] * G.T[3] + U[4] * G.T[4] + U[5] * G.T[5] + kDilation;
-    const float idet = 1.0f / (G.a * G.c - G.b * G.b);
+    const float idet = __fdividef(1.0f, G.a * G.c - G.b * G.b);
     G.A = G.c * idet;
     G.B = -G.b * idet;
     G.C = G.a * idet;
-    G.o = 1.0f / (1.0f + expf(-logit));
+    G.o = __fdividef(1.0f, 1.0f + __expf(-logit));
     const float cw0 = -(R[0] * cam.t[0] + R[3] * cam.t[1] + R[6] * cam.t[2]);
     const float cw1 = -(R[1] * cam.t[0] + R[4] * cam.t[1] + R[7] * cam.t[2]);
     const float cw2 = -(R[2] * cam.t[0] + R[5] * cam.t[1] + R[8] * cam.t[2]);
     const float d0 = mu[0] - cw0, d1 = mu[1] - cw1, d2 = mu[2] - cw2;
-    G.dnorm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    const float idn = 1.0f / G.dnorm;
+    const float dd2 = d0 * d0 + d1 * d1 + d2 * d2;
+    G.dnorm = sqrtf(dd2);
+    const float idn = __fdividef(1.0f, G.dnorm);
     G.dir[0] = d0 * idn; G.dir[1] = d1 * idn; G.dir[2] = d2 * idn;
 }
 
@@ -371,7 +375,7 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         const float du = -G.A * s[4] - G.B * s[5];
         const float dv = -G.C * s[5] - G.B * s[4];
         const float dA = -0.5f * s[6], dB = -s[7], dC = -0.5f * s[8];
-        const float dop = s[3] / G.o;
+        const float dop = __fdividef(s[3], G.o);
         const float dz = s[9];
 
         // opacity
@@ -394,7 +398,7 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         if (DEG > 0) sh_grad_acc<DEG>(G.dir[0], G.dir[1], G.dir[2], sh, grgb, gdir);
         const float dd = G.dir[0] * gdir[0] + G.dir[1] * gdir[1] + G.dir[2] * gdir[2];
         float gdu[3];
-        for (int j = 0; j < 3; j++) gdu[j] = (gdir[j] - G.dir[j] * dd) / G.dnorm;
+        for (int j = 0; j < 3; j++) gdu[j] = __fdividef(gdir[j] - G.dir[j] * dd, G.dnorm);
         for (int j = 0; j < 3; j++) gm[j] += gdu[j];
         const float* R = cam.R;
         for (int i = 0; i < 3; i++) pose[i] += R[i * 3] * gdu[0] + R[i * 3 + 1] * gdu[1] + R[i * 3 + 2] * gdu[2];
@@ -442,7 +446,7 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
             gn[3] = 2.f * (-2.f * z * gRq[0] - w * gRq[1] + x * gRq[2] + w * gRq[3] - 2.f * z * gRq[4]
                            + y * gRq[5] + x * gRq[6] + y * gRq[7]);
             const float qd = w * gn[0] + x * gn[1] + y * gn[2] + z * gn[3];
-            for (int i = 0; i < 4; i++) gq[i] += (gn[i] - G.qn[i] * qd) / G.qnorm;
+            for (int i = 0; i < 4; i++) gq[i] += __fdividef(gn[i] - G.qn[i] * qd, G.qnorm);
         }
         // T = J W
         float gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
