@@ -100,8 +100,10 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
         rect[t] = make_int4(0, 0, 0, 0);
         return;
     }
-    const float o = 1.0f / (1.0f + __expf(-p.logits[g]));
-    const float id = 1.0f / D.det;
+    // raster records (not decisions): approximate reciprocal and logarithms,
+    // a few ulp, far inside the pixels' tolerance and the alpha box's margin
+    const float o = __fdividef(1.0f, 1.0f + __expf(-p.logits[g]));
+    const float id = __fdividef(1.0f, D.det);
     // view direction from the camera centre c_w = -R^T t to the mean
     const float* R = cam.R;
     float cw0 = -(R[0] * cam.t[0] + R[3] * cam.t[1] + R[6] * cam.t[2]);
@@ -138,10 +140,10 @@ k_preprocess(GParams p, const ViewDesc* __restrict__ views, int64_t total, int T
     float uh, ul, vh, vl;
     mean2d_df(mu, cam, uh, ul, vh, vl);
     rec0[t] = make_float4(uh, vh, -0.5f * kLog2e * A, -0.5f * kLog2e * C);
-    rec1[t] = make_float4(-kLog2e * B, log2f(o), D.z, vl);
+    rec1[t] = make_float4(-kLog2e * B, __log2f(o), D.z, vl);
     rec2[t] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), ul);
     // conservative box of {alpha >= 1/255}: the ellipse d^T Sigma'^-1 d <= 2 ln(255 o)
-    const float kappa = 2.0f * logf(255.0f * o);
+    const float kappa = 2.0f * __logf(255.0f * o);
     if (kappa > 0.0f) {
         const float hx = sqrtf(kappa * D.a) * 1.001f + 0.01f, hy = sqrtf(kappa * D.c) * 1.001f + 0.01f;
         rec3[t] = make_float4(D.u - hx, D.u + hx, D.v - hy, D.v + hy);

@@ -179,10 +179,12 @@ k_loss(LossOne one, const ViewDesc* __restrict__ views, int V, const float* __re
                     const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
                     const float N1 = 2.f * mx * my + kC1, N2 = 2.f * sxy + kC2;
                     const float D1 = mx * mx + my * my + kC1, D2 = sxx + syy + kC2;
-                    const float iD = 1.0f / (D1 * D2);
+                    // one approximate reciprocal (a few ulp) serves S and both
+                    // partials: 1/D1 = D2 iD, 1/D2 = D1 iD
+                    const float iD = __fdividef(1.0f, D1 * D2);
                     const float S = N1 * N2 * iD;
                     if (r >= HW && r < HW + LT && c >= HW && c < HW + LT) sacc += S;
-                    const float dN1 = N2 * iD, dN2 = N1 * iD, dD1 = -S / D1, dD2 = -S / D2;
+                    const float dN1 = N2 * iD, dN2 = N1 * iD, dD1 = -S * (D2 * iD), dD2 = -S * (D1 * iD);
                     const float dmx = dN1 * 2.f * my - dN2 * 2.f * my + dD1 * 2.f * mx - dD2 * 2.f * mx;
                     ga = gS * dmx;
                     gb = gS * dD2;
