@@ -136,17 +136,19 @@ struct Unit {
 template <int D>
 __device__ __forceinline__ void unit_of(int u, const RasterArgs& A, Unit& U)
 {
-    const int TS = A.TS, bpr = TS / 8;
-    U.w = u / A.nblk;
-    U.wb = u % A.nblk;
+    // pixel blocks per tile, blocks per tile row and the segment length are
+    // powers of two: shifts and masks instead of integer divisions
+    const int TS = A.TS, bsh = __ffs(TS >> 3) - 1, nsh = __ffs(A.nblk) - 1;
+    U.w = u >> nsh;
+    U.wb = u & (A.nblk - 1);
     const uint2 it = A.items[U.w];
     const int tile = (int)it.x;
     U.j = (int)it.y;
     const int v = view_of_tile(A.views, A.V, tile);
     const ViewDesc& d = A.views[v];
     const int lt = tile - d.tile_base;
-    U.lx0 = (U.wb % bpr) * 8;
-    U.ly0 = (U.wb / bpr) * 4 * D;
+    U.lx0 = (U.wb & ((1 << bsh) - 1)) * 8;
+    U.ly0 = (U.wb >> bsh) * 4 * D;
     U.x0 = (lt % d.TX) * TS + U.lx0;
     U.y0 = (lt / d.TX) * TS + U.ly0;
     U.W = d.cam.W;
@@ -155,7 +157,7 @@ __device__ __forceinline__ void unit_of(int u, const RasterArgs& A, Unit& U)
     U.trs = A.ranges[2 * tile];
     U.tre = A.ranges[2 * tile + 1];
     const uint32_t L = U.tre - U.trs;
-    U.nseg = (A.seg > 0 && L >= 2u * (uint32_t)A.seg) ? (int)((L + A.seg - 1) / A.seg) : 1;
+    U.nseg = (A.seg > 0 && L >= 2u * (uint32_t)A.seg) ? (int)((L + A.seg - 1) >> (__ffs(A.seg) - 1)) : 1;
     if (U.nseg > 1) {
         U.rs = U.trs + (uint32_t)U.j * (uint32_t)A.seg;
         U.re = min(U.tre, U.rs + (uint32_t)A.seg);
