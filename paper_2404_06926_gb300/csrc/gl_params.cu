@@ -375,11 +375,11 @@ k_params_bwd(GParams p, const ViewDesc* __restrict__ views, int V, const int* __
         const float du = -G.A * s[4] - G.B * s[5];
         const float dv = -G.C * s[5] - G.B * s[4];
         const float dA = -0.5f * s[6], dB = -s[7], dC = -0.5f * s[8];
-        const float dop = __fdividef(s[3], G.o);
         const float dz = s[9];
 
-        // opacity
-        glg += dop * G.o * (1.0f - G.o);
+        // opacity: alpha = o exp(power), so dL/do = s[3] / o and
+        // dL/dlogit = dL/do o (1 - o) = s[3] (1 - o), with no division
+        glg += s[3] * (1.0f - G.o);
 
         // colour -> SH and view direction (clamped channels pass no gradient)
         sh_eval<DEG>(G.dir[0], G.dir[1], G.dir[2], Y);
