@@ -261,6 +261,38 @@ def test_loss_identity_and_constant_images():
     assert np.allclose(interior, (2 * p * qq + C1) / (p * p + qq * qq + C1), atol=1e-12)
 
 
+def test_loss_matches_separable_library_filtering():
+    """On random images the oracle's Eq. 9 equals the same statistics taken with
+    scipy's separable correlation (zero padding, the 11-tap Gaussian window of
+    sigma 1.5): a wrong window, padding, axis or SSIM term would differ."""
+    from scipy.ndimage import correlate1d
+    rng = np.random.default_rng(13)
+    H, W = 37, 29
+    C = rng.uniform(0, 1, (H, W, 3))
+    T = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    E = np.hstack([np.eye(3), np.zeros((3, 1))])
+    w = np.exp(-((np.arange(11) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    w /= w.sum()
+
+    def blur(a):
+        return correlate1d(correlate1d(a, w, axis=0, mode="constant"), w, axis=1, mode="constant")
+
+    x, y = C, T.astype(np.float64)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ssim = []
+    for c in range(3):
+        xc, yc = x[..., c], y[..., c]
+        mx, my = blur(xc), blur(yc)
+        sxx, syy, sxy = blur(xc * xc) - mx * mx, blur(yc * yc) - my * my, blur(xc * yc) - mx * my
+        ssim.append(((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2)))
+    S = float(np.mean(ssim))
+    l1 = float(np.mean(np.abs(x - y)))
+    L = oracle.loss(C, T, E)
+    assert abs(L["ssim"] - S) < 1e-12
+    assert abs(L["l1"] - l1) < 1e-12
+    assert abs(L["loss"] - (0.8 * l1 + 0.2 * (1 - S))) < 1e-12
+
+
 def test_loss_exposure_reduces_to_affine():
     """E = [aI | b 1] on C equals the plain loss of a C + b."""
     rng = np.random.default_rng(3)
