@@ -454,6 +454,45 @@ def test_adam_first_step_closed_form_and_mask():
     assert np.all(m[mask == 0] == 0) and np.all(v[mask == 0] == 0)
 
 
+def test_first_step_moves_each_group_by_its_learning_rate():
+    """Sec. III-C 3 / IV-A: one step from zero moments is Adam's first step on
+    the step's gradient, so every parameter the view sees moves by its group's
+    rate against the sign of its gradient (3DGS's rates, not decayed: means
+    1.6e-4, SH DC 2.5e-3 and higher bands 1/20 of it, opacity 0.05, scale 5e-3,
+    rotation 1e-3; exposure 1e-3), and a Gaussian the view does not see stays
+    put (sparse Adam, Sec. III-D 2).  A swapped rate between groups, or between
+    the SH DC and higher bands, fails here."""
+    sc = scenes.diff_check(n=600, width=96, height=72, f=80.0)
+    params, cam, target, E = sc["params"], sc["cam"], sc["target"], sc["E"]
+    params = {k: np.array(v) for k, v in params.items()}
+    params["means"][:60] = -params["means"][:60]   # behind the camera: culled
+    st = oracle.new_state(params, E)
+    r = oracle.optimize_step(params, st, cam, target, E, step=1)
+    g = r["grads"]
+    vis = r["pre"]["radius"] > 0
+    assert 0 < vis.sum() < len(vis)
+    rates = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "logits": 0.05}
+    for name, lr in rates.items():
+        d = st["p"][name] - np.asarray(params[name], np.float64)
+        gg = np.asarray(g[name], np.float64)
+        on = vis.reshape((-1,) + (1,) * (gg.ndim - 1)) & (np.abs(gg) > 1e-8)
+        on = np.broadcast_to(on, gg.shape)
+        assert on.sum() > 0, name
+        assert np.allclose(d[on], -lr * np.sign(gg[on]), rtol=1e-6, atol=0), name
+        assert np.all(d[~vis] == 0), name
+    d = st["p"]["sh"] - np.asarray(params["sh"], np.float64)
+    gs = np.asarray(g["sh"], np.float64)
+    for sl, lr in ((slice(0, 1), 2.5e-3), (slice(1, None), 2.5e-3 / 20)):
+        dd, gg = d[:, sl], gs[:, sl]
+        on = vis[:, None, None] & (np.abs(gg) > 1e-8)
+        assert on.sum() > 0
+        assert np.allclose(dd[on], -lr * np.sign(gg[on]), rtol=1e-6, atol=0)
+        assert np.all(dd[~vis] == 0)
+    dE = st["p"]["E"] - np.asarray(E, np.float64).reshape(3, 4)
+    gE = r["loss"]["dL_dE"]
+    assert np.allclose(dE, -1e-3 * np.sign(gE), rtol=1e-6, atol=0)
+
+
 def test_adam_matches_torch_optim():
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(8)
