@@ -900,9 +900,11 @@ def run_ours(args):
         ach = per_pair * kp / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": ncu_traffic(dom, byts[dom]), "kernel": dom,
-                "flops": ("executed FP32 flops per pair from ncu instruction counters (%s), x pairs walked"
-                          % ex["source"]) if ex else "nominal %g flop per pair walked (no counters of this source)"
-                          % nominal[dom],
+                "flops": ("executed FP32 flops per pair from ncu instruction counters (%s), x pairs walked; "
+                          "the per-hit update runs on every lane of the warp, so lanes whose pixel the hit "
+                          "misses count too (an upper bound on the useful flops; issue.frac is the bound the "
+                          "kernel sits on)" % ex["source"]) if ex else
+                         "nominal %g flop per pair walked (no counters of this source)" % nominal[dom],
                 "flops_per_pair": per_pair, "pairs_per_launch": kp,
                 "nominal_frac": nominal[dom] * kp / t_launch / 1e12 / peak,
                 "issue": ({"achieved_ginst_s": ex["warp_inst_per_pair"] * kp / t_launch / 1e9,
